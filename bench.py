@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark: Gauss-Newton linear solves per second on one GB300.
+
+One step = one full GN linear solve of (alpha (K + M) + J^T J) x = b on the
+128^3 cell-centred FV grid with m = 496 measurements (32 line electrodes,
+pole-dipole pairs, analytic half-space sensitivities, alpha = 1e-3, FP64):
+lines H, C and chol of the Laplace-Woodbury algorithm (h1w_capacitance)
+followed by PCG from x0 = 0 to ||r||_2 <= 1e-8 ||b||_2 with the FP64 true
+residual check (h1w_pcg). This matches the paper's t_norm, which includes
+lines H, C and chol.
+
+Prints one JSON line (rank 0). With torchrun (N > 1) every rank solves its
+own independent GN step (replicas; no collective on the data path) and the
+value is the whole-job rate.
+
+--impl reference times the FP64 CPU oracle (the same method written plainly
+with scipy/numpy) on the host cores, on bounded samples extrapolated to one
+solve with the oracle's own iteration count.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 128
+N_E = 32
+ALPHA = 1e-3
+RTOL = 1e-8
+MAXIT = 1000
+METRIC = "GN linear solves/s at rel-res 1e-8"
+WORKLOAD = "3D ERT GN step, 128^3 cell-centred FV, m=496 pole-dipole, alpha=1e-3, FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_SIDE)
+    ap.add_argument("--ne", type=int, default=N_E)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-s", type=float, default=20.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ----------------------------------------------------------------------------
+
+def dist_init(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing on bounded samples (cpu_baseline and --impl reference)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(J_host, logsigma, m_ref, d, n, budget_s: float) -> dict:
+    """Times the oracle's phases on bounded samples and extrapolates to one solve:
+    t = m * t_vcycle + t_gemm(m x N x m) + iters * t_iteration. The iteration count
+    comes from the oracle's own full solve of this workload (oracle/reference_run.json)."""
+    import numpy as np
+    from oracle import ccg
+    from oracle import discretization as disc
+    from oracle import multigrid as mg
+    from oracle import woodbury as wb
+
+    h = (1.0 / n,) * 3
+    m = J_host.shape[0]
+    A = disc.regularization_operator("fv", (n, n, n), h)
+    H = mg.build_hierarchy("fv", (n, n, n), h)
+    op = ccg.CsrOperator(A, ALPHA, J_host)
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal(A.shape[0])
+    t0 = time.perf_counter()
+    nv = 0
+    while nv < 2 or (time.perf_counter() - t0 < 0.25 * budget_s and nv < 8):
+        mg.vcycle(H, v)
+        nv += 1
+    t_v = (time.perf_counter() - t0) / nv
+    t0 = time.perf_counter()
+    na = 0
+    while na < 1 or (time.perf_counter() - t0 < 0.25 * budget_s and na < 4):
+        op.apply(v)
+        na += 1
+    t_apply = (time.perf_counter() - t0) / na          # J p, J^T w and the stencil
+    t0 = time.perf_counter()
+    s = J_host @ v
+    t_jpass = time.perf_counter() - t0                 # one pass over an m x N matrix
+    k = min(m, 64)
+    t0 = time.perf_counter()
+    _ = J_host[:k] @ J_host[:k].T                       # GEMM sample: k x N x k
+    t_g = time.perf_counter() - t0
+    t_gemm = t_g * (m / k) ** 2
+    path = os.path.join(ROOT, "oracle", "reference_run.json")
+    iters = None
+    if os.path.exists(path) and n == N_SIDE:
+        with open(path) as f:
+            iters = json.load(f).get("iterations")
+    # one PCG iteration: operator apply + V-cycle + H^T r + H v (two more m x N passes)
+    t_it = t_apply + t_v + 2 * t_jpass
+    t_solve = m * t_v + t_gemm + (iters or 0) * t_it
+    return {"t_vcycle_s": t_v, "t_apply_s": t_apply, "t_jpass_s": t_jpass, "t_gemm_s": t_gemm,
+            "t_iteration_s": t_it, "iterations": iters, "t_solve_s": t_solve,
+            "threads": ccg.threads(), "vcycles_timed": nv, "applies_timed": na}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2209_02815_gb300 import h1w, inputs
+
+    world, rank, local = dist_init(args)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    n = args.n
+    with torch.cuda.stream(stream):
+        pr = inputs.ert_problem(n, n_e_line=args.ne, alpha=ALPHA, device=dev)
+        J = pr.J
+        m, N = J.shape
+        S = h1w.Solver(h1w.H1W_FV_CELL, (n, n, n), (1.0 / n,) * 3, ALPHA, m, device=dev, stream=stream)
+        dm = torch.as_tensor(pr.logsigma - pr.m_ref, device=dev)
+        d = torch.as_tensor(pr.d, device=dev)
+        S.capacitance(J)
+        b = S.gn_rhs(dm, d)
+        x = torch.empty_like(b)
+        for _ in range(args.warmup):
+            S.capacitance(J)
+            _, info = S.pcg(b, RTOL, MAXIT, x=x)
+        stream.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        phase = {"t_H_ms": [], "t_C_ms": [], "t_chol_ms": [], "t_pcg_ms": []}
+        launches = 0
+        iters = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            S.capacitance(J)
+            _, info = S.pcg(b, RTOL, MAXIT, x=x)
+            t = S.timings()
+            for k_ in phase:
+                phase[k_].append(getattr(t, k_))
+            launches += t.launches_capacitance + t.launches_pcg
+            iters.append(info.iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        barrier(world)
+        ms = e0.elapsed_time(e1)
+        ms_max = allmax(world, ms)
+        rel_true = info.rel_res_true
+
+        # end to end: host buffers in, host result out, through the public API
+        e2e = None
+        if args.e2e_steps > 0:
+            J_host = torch.empty(J.shape, dtype=torch.float64, pin_memory=True)
+            J_host.copy_(J)
+            b_host = torch.empty(b.shape, dtype=torch.float64, pin_memory=True)
+            b_host.copy_(b)
+            x_host = torch.empty_like(b_host).pin_memory()
+            J_dev = torch.empty_like(J)
+            b_dev = torch.empty_like(b)
+            torch.cuda.synchronize()
+            barrier(world)
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(args.e2e_steps):
+                J_dev.copy_(J_host, non_blocking=True)
+                b_dev.copy_(b_host, non_blocking=True)
+                S.capacitance(J_dev)
+                S.pcg(b_dev, RTOL, MAXIT, x=x)
+                x_host.copy_(x, non_blocking=True)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            ems = allmax(world, f0.elapsed_time(f1))
+            e2e = {"value": world * args.e2e_steps / (ems / 1e3), "unit": "solves/s",
+                   "h2d_bytes_per_step": int(J.numel() * 8 + b.numel() * 8),
+                   "d2h_bytes_per_step": int(x.numel() * 8), "steps": args.e2e_steps}
+            del J_host, J_dev
+
+    value = world * args.steps / (ms_max / 1e3)
+    mean = {k_: float(np.mean(v_)) for k_, v_ in phase.items()}
+    # dominant kernel: the capacitance GEMM (line C), FP64 on the CUDA cores
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    gemm_flops = float(m) * (m + 1) * N          # symmetric C: m(m+1)/2 entries x 2N flops
+    fp64_peak = 152 * 4 * 2.07e9 / 1e12          # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+    achieved = gemm_flops / (mean["t_C_ms"] / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_cap_gemm (line C, FP64 CUDA cores)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz",
+                "share_of_step": mean["t_C_ms"] / (ms_max / args.steps)}
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": [n, n, n], "N": N, "m": m, "alpha": ALPHA, "rtol": RTOL,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (J is %.1f GB)" % (J.numel() * 8 / 1e9)},
+        "phases_ms": mean, "pcg_iters": iters, "rel_res_true": rel_true,
+        "mg_dof_per_s": float(m) * N / (mean["t_H_ms"] / 1e3),
+        "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
+        "impl": "ours",
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        J_host = J.cpu().numpy()
+        s = oracle_sample(J_host, pr.logsigma, pr.m_ref, pr.d, n, args.cpu_sample_s)
+        out["cpu_baseline"] = {"value": (1.0 / s["t_solve_s"]) if s["iterations"] else None,
+                               "unit": "solves/s", "cores": s["threads"], "kind": "oracle",
+                               "sample": ("oracle phases timed on bounded samples and extrapolated: "
+                                          f"{s['vcycles_timed']} scipy V-cycles (x m), "
+                                          f"{s['applies_timed']} operator applies, one 64-row GEMM "
+                                          "(scaled by (m/64)^2), iterations from the oracle's full "
+                                          "solve of this workload"), "detail": s}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    import numpy as np
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2209_02815_gb300 import inputs
+    n = args.n
+    pr = inputs.ert_problem(n, n_e_line=args.ne, alpha=ALPHA, device="cpu")
+    J = np.ascontiguousarray(pr.J)
+    vals = []
+    last = None
+    budget = max(5.0, min(args.cpu_sample_s, 120.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        s = oracle_sample(J, pr.logsigma, pr.m_ref, pr.d, n, budget)
+        if i >= args.warmup:
+            vals.append(s["t_solve_s"])
+        last = s
+    t = statistics.median(vals)
+    value = 1.0 / t if last["iterations"] else None
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": [n, n, n], "m": int(J.shape[0]), "alpha": ALPHA, "rtol": RTOL},
+           "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": "solves/s", "kind": "oracle", "cores": last["threads"],
+                            "sample": "per step: oracle phases timed on bounded samples, extrapolated "
+                                      "to one solve with the oracle's own iteration count",
+                            "detail": last},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,168 @@
+/*
+ * h1w: GB300 (sm_103a) solver for the Gauss-Newton linear system of
+ * H1-regularized parameter identification,
+ *
+ *     (alpha (K + M) + J^T J) x = b,
+ *
+ * preconditioned through the Sherman-Morrison-Woodbury formula around a fast
+ * Laplace solver (Blechta & Ernst, arXiv 2209.02815). Notation: alpha is the
+ * paper's regularization weight beta; K is the Neumann stiffness operator of
+ * the term int |grad m|^2 (operator L of Eq. 2.8); M is a mass operator that
+ * makes K + M definite; J (m x N) is the measurement Jacobian of Eq. 2.15.
+ *
+ * Discretizations: H1W_Q1_VERTEX (2D bilinear elements on an nx x ny vertex
+ * grid, row-sum lumped mass) and H1W_FV_CELL (3D cell-centred finite volumes
+ * on an nx x ny x nz cell grid: the lowest-order Raviart-Thomas Schur
+ * complement with diagonal Q that the paper uses as its Laplace
+ * approximation S-hat in Sec. 3.2). Vectors are indexed x fastest:
+ * p = (k * ny + j) * nx + i.
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers (FP64 unless stated) on the GPU the
+ *    context was created on, read and written in stream order on the context's
+ *    stream. The caller owns them. J is row-major [m][N] (one row per
+ *    measurement, the rows of Eq. 2.15).
+ *  - Device memory: the library allocates none. The caller passes one
+ *    workspace of at least h1w_workspace_size() bytes (256-byte aligned) to
+ *    h1w_setup; the context keeps pointers into it until h1w_destroy.
+ *  - Errors are returned as h1w_status codes; no exceptions cross this
+ *    boundary, and no device trap or assert is used. h1w_last_error() gives
+ *    a text description. Kernels report failures (a non-positive Cholesky
+ *    pivot) through a device status word that the host reads back.
+ *  - Calls that return solver results (h1w_capacitance, h1w_pcg) synchronize
+ *    the stream before returning; the others are asynchronous.
+ *  - A context is not thread safe; distinct contexts are independent.
+ */
+#ifndef H1W_H
+#define H1W_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  H1W_OK = 0,
+  H1W_EINVAL = 1,        /* invalid argument (null pointer, bad size, bad grid) */
+  H1W_ENOMEM = 2,        /* workspace smaller than h1w_workspace_size() */
+  H1W_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  H1W_ENOTCONV = 4,      /* PCG did not reach rtol within maxit (x holds the last iterate) */
+  H1W_ENOTSPD = 5,       /* Cholesky met a non-positive pivot (capacitance or coarse matrix) */
+  H1W_ETIMEOUT = 6,      /* reserved: a bounded device wait ran out */
+  H1W_EUNSUPPORTED = 7,  /* grid that the multigrid hierarchy cannot coarsen to <= 1024 unknowns */
+  H1W_ESTATE = 8         /* call out of order (e.g. h1w_pcg before h1w_capacitance) */
+} h1w_status;
+
+enum { H1W_Q1_VERTEX = 1, H1W_FV_CELL = 2 };
+
+typedef struct {
+  int32_t dim;     /* 2 (with H1W_Q1_VERTEX) or 3 (with H1W_FV_CELL) */
+  int32_t disc;    /* H1W_Q1_VERTEX or H1W_FV_CELL */
+  int32_t n[3];    /* vertices (Q1) or cells (FV) per axis, x first; n[2] = 1 in 2D */
+  double h[3];     /* mesh spacing per axis (> 0) */
+  double alpha;    /* regularization weight (> 0), the paper's beta */
+} h1w_grid;
+
+typedef struct {
+  int32_t cheb_degree;   /* Chebyshev smoother degree per half-cycle (1..7, default 2) */
+  int32_t rhs_block;     /* right-hand sides per batched V-cycle while building H (1..64, default 32) */
+  int32_t max_restarts;  /* true-residual restarts allowed in h1w_pcg (default 3) */
+  int32_t reserved;      /* must be 0 */
+} h1w_options;
+
+typedef struct {
+  int32_t iters;         /* PCG iterations performed */
+  int32_t restarts;      /* restarts from the true residual */
+  double rel_res_true;   /* ||b - A x||_2 / ||b||_2, recomputed in FP64 at exit */
+  double rel_res_rec;    /* last recursively updated ||r||_2 / ||b||_2 */
+} h1w_info;
+
+/* Device-side phase times of the last calls on a context, taken with CUDA
+ * events on the context's stream (the paper reports the same breakdown as
+ * t_H, t_C, t_chol and the solver time, Table 4.1), and the number of kernels
+ * the library launched in them. */
+typedef struct {
+  float t_H_ms;                 /* line H: batched V-cycles of the last h1w_capacitance */
+  float t_C_ms;                 /* line C: the capacitance GEMM kernel */
+  float t_chol_ms;              /* forming C from the GEMM partials and its Cholesky factor */
+  float t_pcg_ms;               /* the last h1w_pcg, launch to convergence */
+  int64_t launches_capacitance; /* kernels launched by the last h1w_capacitance */
+  int64_t launches_pcg;         /* kernels launched by the last h1w_pcg */
+} h1w_timings;
+
+typedef struct h1w_ctx h1w_ctx;
+
+/* Fills *opt with the defaults listed in h1w_options. */
+void h1w_default_options(h1w_options* opt);
+
+/* Bytes of device workspace needed for this grid and at most m_max
+ * measurements (opt may be NULL for defaults). Returns 0 for invalid input. */
+size_t h1w_workspace_size(const h1w_grid* grid, int32_t m_max, const h1w_options* opt);
+
+/* Builds the multigrid hierarchy for L-hat^-1 (one symmetric V-cycle on K + M;
+ * the paper's AMG line of Algorithm "Gauss-Newton with iterative solver",
+ * here a matrix-free geometric cycle) inside `workspace` and returns a
+ * context bound to `stream` (a cudaStream_t; NULL = legacy default stream).
+ * The coarsest-level Cholesky factor is computed on the GPU. */
+h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt, void* workspace,
+                     size_t ws_bytes, void* stream, h1w_ctx** out);
+
+/* Lines H, C and chol of Algorithm "MINRES with the Laplace-Woodbury
+ * preconditioner": H = L-hat^-1 J^T (m batched V-cycles), C = I + alpha^-1 J H
+ * (formed from its upper triangle and mirrored), C = L L^T. J (m x N,
+ * row-major, device) is borrowed: it must stay valid and unchanged until the
+ * next h1w_capacitance or h1w_destroy. 0 <= m <= m_max; m = 0 gives the
+ * Laplace-only preconditioner. Synchronizes; H1W_ENOTSPD if C is not
+ * numerically positive definite. */
+h1w_status h1w_capacitance(h1w_ctx* ctx, int32_t m, const double* J);
+
+/* z = P^-1 r with P = alpha L-hat + J^T J, evaluated by the Woodbury formula
+ * of Sec. 3.2: z = alpha^-1 [ L-hat^-1 r - alpha^-1 H C^-1 H^T r ].
+ * r and z have N entries and must not overlap. */
+h1w_status h1w_apply_prec(h1w_ctx* ctx, const double* r, double* z);
+
+/* q = alpha (K + M) p + J^T (J p) (the matrix-free system operator; J^T J is
+ * never formed). p and q have N entries and must not overlap. */
+h1w_status h1w_apply_op(h1w_ctx* ctx, const double* p, double* q);
+
+/* x = L-hat^-1 b for nrhs right-hand sides stored contiguously (b[r * N + p]);
+ * one V-cycle each, batched. b and x must not overlap. */
+h1w_status h1w_vcycle(h1w_ctx* ctx, int32_t nrhs, const double* b, double* x);
+
+/* Gauss-Newton right-hand side of Eq. 2.9 scaled by beta, with the mass term:
+ * b = -alpha (K + M) dm - J^T d, where dm = m - m_ref (N entries) and
+ * d = g_m - g_obs (m entries, DEVICE). Uses the J of the last h1w_capacitance. */
+h1w_status h1w_gn_rhs(h1w_ctx* ctx, const double* dm, const double* d, double* b);
+
+/* Preconditioned conjugate gradients for the system above from x0 = 0,
+ * stopping when ||r_k||_2 <= rtol ||b||_2 (the Euclidean criterion of Sec. 4)
+ * on the recursively updated residual; the true residual b - A x is then
+ * recomputed in FP64 and, if it fails the test, the iteration restarts from
+ * it (at most max_restarts times). info may be NULL. Synchronizes. Returns
+ * H1W_ENOTCONV when maxit is reached first (x holds the last iterate). */
+h1w_status h1w_pcg(h1w_ctx* ctx, const double* b, double* x, double rtol, int32_t maxit,
+                   h1w_info* info);
+
+/* Copies the capacitance matrix C and its lower Cholesky factor L (m x m,
+ * row-major, DEVICE) into caller buffers (either may be NULL). */
+h1w_status h1w_capacitance_factors(h1w_ctx* ctx, double* C, double* L);
+
+/* Phase times and launch counts of the last h1w_capacitance / h1w_pcg. */
+h1w_status h1w_get_timings(const h1w_ctx* ctx, h1w_timings* out);
+
+/* Number of multigrid levels and the grid size of level `level` (n[3]). */
+h1w_status h1w_level_info(const h1w_ctx* ctx, int32_t level, int32_t* nlevels, int32_t* n);
+
+/* Text of the last error on this context (ctx = NULL: the last error of
+ * h1w_setup on this thread). Never NULL. */
+const char* h1w_last_error(const h1w_ctx* ctx);
+
+/* Releases the host-side context. The workspace stays owned by the caller. */
+void h1w_destroy(h1w_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* H1W_H */

@@ -1,0 +1,700 @@
+// Host runtime and C ABI of h1w: workspace planning, multigrid hierarchy
+// construction, the batched V-cycle driver, the capacitance setup (lines H,
+// C, chol of Algorithm "MINRES with the Laplace-Woodbury preconditioner"),
+// the Woodbury preconditioner apply (Sec. 3.2) and the PCG driver with the
+// Euclidean stopping rule of Sec. 4. All device memory comes from the
+// caller's workspace; nothing here allocates device memory.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "h1w_internal.cuh"
+
+using namespace h1w;
+
+std::atomic<long long> h1w::g_kernel_launches{0};
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+struct Bump {
+  char* base;   // nullptr while sizing
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += sizeof(T) * (count ? count : 1);
+    return p;
+  }
+};
+
+struct LevelBufs {
+  double *x, *b, *r, *da, *db;
+};
+
+}  // namespace
+
+struct h1w_ctx {
+  h1w_grid grid;
+  h1w_options opt;
+  int disc;
+  int m_max;
+  cudaStream_t stream;
+  int nlev;
+  Level lev[kMaxLevels];
+  ChebCoef cheb[kMaxLevels];
+  LevelBufs buf[kMaxLevels];
+  std::vector<double> qhost[kMaxLevels][2];  // Q1 1D coefficients (host copy)
+  double* qdev;          // Q1 coefficients, all levels
+  double* coarse_X;      // dense inverse of the coarsest operator
+  double* coarse_L;      // scratch for its factorization
+  int* dstatus;          // device status word
+  unsigned long long* dbits;
+  // capacitance state
+  int m;                 // current number of measurements (-1: none yet)
+  const double* J;       // borrowed
+  double* H;             // m_max x N
+  double* C;             // m_max x m_max
+  double* Lc;            // m_max x m_max
+  double* gemm_partial;
+  int64_t gemm_partial_len;
+  // Krylov vectors
+  double *r, *z, *z0, *p, *q;
+  double *svec, *jz, *w, *wtmp;
+  double* partial;       // reductions over N (per-block)
+  int64_t partial_len;
+  double* scal;          // scalar slots
+  // phase timing: 0 H start, 1 H end / C start, 2 C end, 3 chol end, 4 pcg start, 5 pcg end
+  cudaEvent_t ev[6];
+  bool have_ev;
+  long long launches_cap, launches_pcg;
+  std::string err;
+};
+
+namespace {
+
+h1w_status fail(h1w_ctx* c, h1w_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_setup_error = msg;
+  return st;
+}
+
+h1w_status cuda_check(h1w_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(c, H1W_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return H1W_OK;
+}
+
+void q1_fine_1d(int n, double h, std::vector<double>& q) {
+  // [Kd, Ko, Md, Mo, Dd, Do] for linear elements with natural boundary conditions
+  q.assign(6 * (size_t)n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const bool end = (i == 0 || i == n - 1);
+    q[0 * n + i] = (end ? 1.0 : 2.0) / h;
+    q[2 * n + i] = (end ? 1.0 : 2.0) * h / 3.0;
+    q[4 * n + i] = (end ? 0.5 : 1.0) * h;
+    if (i < n - 1) {
+      q[1 * n + i] = -1.0 / h;
+      q[3 * n + i] = h / 6.0;
+      q[5 * n + i] = 0.0;
+    }
+  }
+}
+
+// 1D Q1 prolongation entries of fine vertex f: (coarse index, weight)
+int q1_p_entries(int f, int nf, int nc, int* I, double* w) {
+  if ((f & 1) == 0) { I[0] = f >> 1; w[0] = 1.0; return 1; }
+  if (f == nf - 1) { I[0] = nc - 1; w[0] = 1.0; return 1; }
+  I[0] = (f - 1) >> 1; w[0] = 0.5;
+  I[1] = (f + 1) >> 1; w[1] = 0.5;
+  return 2;
+}
+
+// Galerkin product P^T T P of the three tridiagonal pairs in q (size nf -> nc)
+void q1_coarse_1d(const std::vector<double>& q, int nf, int nc, std::vector<double>& out) {
+  out.assign(6 * (size_t)nc, 0.0);
+  for (int t = 0; t < 3; ++t) {
+    const double* d = q.data() + (2 * t) * nf;
+    const double* o = q.data() + (2 * t + 1) * nf;
+    double* cd = out.data() + (2 * t) * nc;
+    double* co = out.data() + (2 * t + 1) * nc;
+    for (int f = 0; f < nf; ++f) {
+      int If[2]; double wf[2];
+      const int nfe = q1_p_entries(f, nf, nc, If, wf);
+      for (int g = std::max(0, f - 1); g <= std::min(nf - 1, f + 1); ++g) {
+        const double tfg = (g == f) ? d[f] : (g > f ? o[f] : o[g]);
+        if (tfg == 0.0) continue;
+        int Ig[2]; double wg[2];
+        const int nge = q1_p_entries(g, nf, nc, Ig, wg);
+        for (int a = 0; a < nfe; ++a)
+          for (int b = 0; b < nge; ++b) {
+            const int I = If[a], Jc = Ig[b];
+            const double v = wf[a] * tfg * wg[b];
+            if (I == Jc) cd[I] += v;
+            else if (Jc == I + 1) co[I] += 0.5 * v;   // (I, I+1) and (I+1, I) both land here
+            else if (I == Jc + 1) co[Jc] += 0.5 * v;
+          }
+      }
+    }
+  }
+}
+
+struct Plan {
+  int nlev = 0;
+  int n[kMaxLevels][3];
+  double h[kMaxLevels][3];
+  int c[kMaxLevels][3];
+  bool ok = false;
+  std::string why;
+};
+
+Plan plan_levels(const h1w_grid& g) {
+  Plan P;
+  int n[3] = {g.n[0], g.n[1], g.dim == 3 ? g.n[2] : 1};
+  double h[3] = {g.h[0], g.h[1], g.dim == 3 ? g.h[2] : 1.0};
+  for (int l = 0; l < kMaxLevels; ++l) {
+    for (int a = 0; a < 3; ++a) { P.n[l][a] = n[a]; P.h[l][a] = h[a]; P.c[l][a] = 0; }
+    P.nlev = l + 1;
+    const int64_t N = (int64_t)n[0] * n[1] * n[2];
+    if (N <= kCoarseTarget) break;
+    bool any = false;
+    int nn[3] = {n[0], n[1], n[2]};
+    for (int a = 0; a < g.dim; ++a) {
+      bool co;
+      if (g.disc == H1W_Q1_VERTEX) co = n[a] >= 3;
+      else co = (n[a] % 2 == 0) && n[a] >= 4;
+      if (co) {
+        P.c[l][a] = 1;
+        any = true;
+        nn[a] = (g.disc == H1W_Q1_VERTEX) ? ((n[a] - 1) / 2 + 1 + ((n[a] - 1) % 2)) : n[a] / 2;
+        h[a] *= 2.0;
+      }
+    }
+    if (!any) break;
+    if (l == kMaxLevels - 1) { P.why = "too many multigrid levels"; return P; }
+    for (int a = 0; a < 3; ++a) n[a] = nn[a];
+  }
+  const int l = P.nlev - 1;
+  const int64_t Nc = (int64_t)P.n[l][0] * P.n[l][1] * P.n[l][2];
+  if (Nc > kCoarseLimit) {
+    P.why = "grid cannot be coarsened to <= 1024 unknowns (coarsest has " + std::to_string(Nc) + ")";
+    return P;
+  }
+  P.ok = true;
+  return P;
+}
+
+h1w_status validate(const h1w_grid* g, int32_t m_max, const h1w_options* o, std::string& why) {
+  if (!g) { why = "grid is NULL"; return H1W_EINVAL; }
+  if (!((g->dim == 2 && g->disc == H1W_Q1_VERTEX) || (g->dim == 3 && g->disc == H1W_FV_CELL))) {
+    why = "supported: dim 2 with H1W_Q1_VERTEX, dim 3 with H1W_FV_CELL";
+    return H1W_EUNSUPPORTED;
+  }
+  for (int a = 0; a < g->dim; ++a) {
+    if (g->n[a] < 2 || g->n[a] > (1 << 20)) { why = "n out of range"; return H1W_EINVAL; }
+    if (!(g->h[a] > 0.0) || !std::isfinite(g->h[a])) { why = "h must be positive"; return H1W_EINVAL; }
+  }
+  if (g->dim == 2 && g->n[2] != 1) { why = "n[2] must be 1 in 2D"; return H1W_EINVAL; }
+  if (!(g->alpha > 0.0) || !std::isfinite(g->alpha)) { why = "alpha must be positive"; return H1W_EINVAL; }
+  if (m_max < 0 || m_max > kMaxM) { why = "m_max out of range [0, 4096]"; return H1W_EINVAL; }
+  if (o) {
+    if (o->cheb_degree < 1 || o->cheb_degree > 7) { why = "cheb_degree out of range [1, 7]"; return H1W_EINVAL; }
+    if (o->rhs_block < 1 || o->rhs_block > 64) { why = "rhs_block out of range [1, 64]"; return H1W_EINVAL; }
+    if (o->max_restarts < 0 || o->max_restarts > 100) { why = "max_restarts out of range"; return H1W_EINVAL; }
+    if (o->reserved != 0) { why = "reserved must be 0"; return H1W_EINVAL; }
+  }
+  return H1W_OK;
+}
+
+int64_t gemm_partial_len(int m_max, int64_t N) {
+  int64_t best = 1;
+  for (int m = 1; m <= m_max; ++m) best = std::max(best, (int64_t)cap_gemm_splits(m, N) * m * m);
+  return best;
+}
+
+// Lays out every buffer; with ctx->... pointers filled when base != nullptr.
+size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w_options& o,
+              char* base) {
+  Bump B{base};
+  const int nb = o.rhs_block;
+  const int64_t N0 = (int64_t)P.n[0][0] * P.n[0][1] * P.n[0][2];
+  int64_t qlen = 0;
+  for (int l = 0; l < P.nlev; ++l) qlen += 6 * (int64_t)(P.n[l][0] + P.n[l][1]);
+  double* qdev = B.take<double>(g.disc == H1W_Q1_VERTEX ? qlen : 1);
+  LevelBufs bufs[kMaxLevels];
+  for (int l = 0; l < P.nlev; ++l) {
+    const int64_t Nl = (int64_t)P.n[l][0] * P.n[l][1] * P.n[l][2];
+    bufs[l].x = l ? B.take<double>(nb * Nl) : nullptr;
+    bufs[l].b = l ? B.take<double>(nb * Nl) : nullptr;
+    bufs[l].r = B.take<double>(nb * Nl);
+    bufs[l].da = B.take<double>(nb * Nl);
+    bufs[l].db = B.take<double>(nb * Nl);
+  }
+  const int l = P.nlev - 1;
+  const int64_t Nc = (int64_t)P.n[l][0] * P.n[l][1] * P.n[l][2];
+  double* cX = B.take<double>(Nc * Nc);
+  double* cL = B.take<double>(Nc * Nc);
+  int* dstatus = B.take<int>(4);
+  unsigned long long* dbits = B.take<unsigned long long>(4);
+  double* H = B.take<double>((int64_t)m_max * N0);
+  double* C = B.take<double>((int64_t)m_max * m_max);
+  double* Lc = B.take<double>((int64_t)m_max * m_max);
+  const int64_t gpl = gemm_partial_len(m_max, N0);
+  double* gp = B.take<double>(gpl);
+  double* r = B.take<double>(N0);
+  double* z = B.take<double>(N0);
+  double* z0 = B.take<double>(N0);
+  double* p = B.take<double>(N0);
+  double* q = B.take<double>(N0);
+  double* svec = B.take<double>(m_max);
+  double* jz = B.take<double>(m_max);
+  double* w = B.take<double>(m_max);
+  double* wtmp = B.take<double>(m_max);
+  const int64_t plen = std::max<int64_t>({(int64_t)rows_dot_chunks(N0) * std::max(m_max, 1),
+                                          (int64_t)colsum_blocks(N0), (int64_t)dot_blocks(N0)});
+  double* partial = B.take<double>(plen);
+  double* scal = B.take<double>(16);
+  if (c) {
+    c->qdev = qdev;
+    for (int k = 0; k < P.nlev; ++k) c->buf[k] = bufs[k];
+    c->coarse_X = cX; c->coarse_L = cL; c->dstatus = dstatus; c->dbits = dbits;
+    c->H = H; c->C = C; c->Lc = Lc; c->gemm_partial = gp; c->gemm_partial_len = gpl;
+    c->r = r; c->z = z; c->z0 = z0; c->p = p; c->q = q;
+    c->svec = svec; c->jz = jz; c->w = w; c->wtmp = wtmp;
+    c->partial = partial; c->partial_len = plen; c->scal = scal;
+  }
+  return B.off + 256;
+}
+
+// ---- multigrid driver -------------------------------------------------------------
+
+void smooth(h1w_ctx* c, int l, int nrhs, const double* b, double* x, bool zero_x) {
+  const Level& L = c->lev[l];
+  const ChebCoef& K = c->cheb[l];
+  double* da = c->buf[l].da;
+  double* db = c->buf[l].db;
+  launch_cheb_first(c->disc, L, nrhs, b, x, c->buf[l].r, da, zero_x, K.inv_theta, c->stream);
+  // with a nonzero start the first correction d_0 is added by the next step
+  bool pending = !zero_x;
+  for (int j = 1; j < c->opt.cheb_degree; ++j) {
+    launch_cheb_step(c->disc, L, nrhs, c->buf[l].r, da, db, x, K.c1[j], K.c2[j], pending, c->stream);
+    pending = false;
+    std::swap(da, db);
+  }
+  if (pending) launch_add((int64_t)nrhs * L.N, da, x, c->stream);
+}
+
+// x = L-hat^-1 b for nrhs <= rhs_block vectors (b, x: level-0 sized, contiguous)
+void vcycle_block(h1w_ctx* c, int nrhs, const double* b0, double* x0) {
+  const int nl = c->nlev;
+  if (nl == 1) {
+    launch_coarse_apply(c->coarse_X, (int)c->lev[0].N, nrhs, b0, x0, c->stream);
+    return;
+  }
+  const double* bp[kMaxLevels];
+  double* xp[kMaxLevels];
+  bp[0] = b0; xp[0] = x0;
+  for (int l = 1; l < nl; ++l) { bp[l] = c->buf[l].b; xp[l] = c->buf[l].x; }
+  for (int l = 0; l < nl - 1; ++l) {
+    smooth(c, l, nrhs, bp[l], xp[l], true);
+    launch_residual(c->disc, c->lev[l], nrhs, bp[l], xp[l], c->buf[l].r, c->stream);
+    launch_restrict(c->disc, c->lev[l], c->lev[l + 1], nrhs, c->buf[l].r, c->buf[l + 1].b, c->stream);
+  }
+  launch_coarse_apply(c->coarse_X, (int)c->lev[nl - 1].N, nrhs, bp[nl - 1], xp[nl - 1], c->stream);
+  for (int l = nl - 2; l >= 0; --l) {
+    launch_prolong_add(c->disc, c->lev[l], c->lev[l + 1], nrhs, xp[l + 1], xp[l], c->stream);
+    smooth(c, l, nrhs, bp[l], xp[l], false);
+  }
+}
+
+void vcycle_many(h1w_ctx* c, int nrhs, const double* b, double* x) {
+  const int64_t N = c->lev[0].N;
+  for (int r0 = 0; r0 < nrhs; r0 += c->opt.rhs_block) {
+    const int nr = std::min(c->opt.rhs_block, nrhs - r0);
+    vcycle_block(c, nr, b + (int64_t)r0 * N, x + (int64_t)r0 * N);
+  }
+}
+
+// w = J v (m-vector), through per-chunk partials
+void j_times(h1w_ctx* c, const double* A, const double* v, double* out, double scale = 1.0) {
+  const int64_t N = c->lev[0].N;
+  if (c->m <= 0) return;
+  launch_rows_dot(A, c->m, N, v, c->partial, c->stream);
+  launch_reduce_partials(c->partial, rows_dot_chunks(N), c->m, scale, out, c->stream);
+}
+
+// z = P^-1 r; when rz_slot >= 0 also scal[rz_slot] = r . z
+void apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
+  const int64_t N = c->lev[0].N;
+  vcycle_many(c, 1, r, c->z0);
+  const int m = c->m;
+  if (m > 0) {
+    j_times(c, c->H, r, c->svec);                   // s = H^T r
+    launch_trsv_lower(c->Lc, m, c->svec, 1, c->stream);
+    launch_trsv_upper_t(c->Lc, m, c->svec, 1, c->stream);  // v = C^-1 s
+  }
+  launch_woodbury_update(c->H, m, N, c->svec, c->z0, c->grid.alpha, z, rz_slot >= 0 ? r : nullptr,
+                         rz_slot >= 0 ? c->partial : nullptr, c->stream);
+  if (rz_slot >= 0) launch_sum_to_scalar(c->partial, colsum_blocks(N), c->scal + rz_slot, c->stream);
+}
+
+// q = alpha (K+M) p + J^T w with w = J p given; scal[pq_slot] = p . q when pq_slot >= 0
+void apply_op_w(h1w_ctx* c, const double* p, const double* w, double* q, int pq_slot) {
+  int nb = 0;
+  launch_apply_op(c->disc, c->lev[0], c->grid.alpha, p, 1.0, c->J, w, c->m > 0 ? c->m : 0, q,
+                  pq_slot >= 0 ? c->partial : nullptr, &nb, c->stream);
+  if (pq_slot >= 0) launch_sum_to_scalar(c->partial, nb, c->scal + pq_slot, c->stream);
+}
+
+double read_scalar(h1w_ctx* c, int slot) {
+  double v = 0.0;
+  cudaMemcpyAsync(&v, c->scal + slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+void h1w_default_options(h1w_options* opt) {
+  if (!opt) return;
+  opt->cheb_degree = 2;
+  opt->rhs_block = 32;
+  opt->max_restarts = 3;
+  opt->reserved = 0;
+}
+
+size_t h1w_workspace_size(const h1w_grid* grid, int32_t m_max, const h1w_options* opt) {
+  h1w_options o;
+  h1w_default_options(&o);
+  if (opt) o = *opt;
+  std::string why;
+  if (validate(grid, m_max, &o, why) != H1W_OK) return 0;
+  Plan P = plan_levels(*grid);
+  if (!P.ok) return 0;
+  return layout(nullptr, P, *grid, m_max, o, nullptr);
+}
+
+h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt, void* workspace,
+                     size_t ws_bytes, void* stream, h1w_ctx** out) {
+  if (!out) return fail(nullptr, H1W_EINVAL, "out is NULL");
+  *out = nullptr;
+  h1w_options o;
+  h1w_default_options(&o);
+  if (opt) o = *opt;
+  std::string why;
+  h1w_status st = validate(grid, m_max, &o, why);
+  if (st != H1W_OK) return fail(nullptr, st, why);
+  Plan P = plan_levels(*grid);
+  if (!P.ok) return fail(nullptr, H1W_EUNSUPPORTED, P.why);
+  const size_t need = layout(nullptr, P, *grid, m_max, o, nullptr);
+  if (!workspace) return fail(nullptr, H1W_EINVAL, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(nullptr, H1W_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < need)
+    return fail(nullptr, H1W_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
+  h1w_ctx* c = new (std::nothrow) h1w_ctx();
+  if (!c) return fail(nullptr, H1W_ENOMEM, "host allocation of the context failed");
+  c->grid = *grid;
+  c->opt = o;
+  c->disc = grid->disc;
+  c->m_max = m_max;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  c->nlev = P.nlev;
+  c->m = -1;
+  c->J = nullptr;
+  layout(c, P, *grid, m_max, o, static_cast<char*>(workspace));
+  c->have_ev = true;
+  for (int e = 0; e < 6; ++e)
+    if (cudaEventCreate(&c->ev[e]) != cudaSuccess) c->have_ev = false;
+  c->launches_cap = c->launches_pcg = 0;
+
+  // level descriptors
+  int64_t qoff = 0;
+  for (int l = 0; l < P.nlev; ++l) {
+    Level& L = c->lev[l];
+    L = Level{};
+    L.nx = P.n[l][0]; L.ny = P.n[l][1]; L.nz = P.n[l][2];
+    L.N = (int64_t)L.nx * L.ny * L.nz;
+    L.cx = P.c[l][0]; L.cy = P.c[l][1]; L.cz = P.c[l][2];
+    if (c->disc == H1W_FV_CELL) {
+      const double hx = P.h[l][0], hy = P.h[l][1], hz = P.h[l][2];
+      L.Tx = hy * hz / hx; L.Ty = hx * hz / hy; L.Tz = hx * hy / hz; L.V = hx * hy * hz;
+    } else {
+      for (int a = 0; a < 2; ++a) {
+        if (l == 0) q1_fine_1d(P.n[0][a], grid->h[a], c->qhost[0][a]);
+        else if (P.c[l - 1][a]) q1_coarse_1d(c->qhost[l - 1][a], P.n[l - 1][a], P.n[l][a], c->qhost[l][a]);
+        else c->qhost[l][a] = c->qhost[l - 1][a];
+      }
+      double* qx = c->qdev + qoff;
+      qoff += 6 * (int64_t)L.nx;
+      double* qy = c->qdev + qoff;
+      qoff += 6 * (int64_t)L.ny;
+      cudaMemcpyAsync(qx, c->qhost[l][0].data(), sizeof(double) * 6 * L.nx, cudaMemcpyHostToDevice, c->stream);
+      cudaMemcpyAsync(qy, c->qhost[l][1].data(), sizeof(double) * 6 * L.ny, cudaMemcpyHostToDevice, c->stream);
+      L.qx = qx; L.qy = qy;
+    }
+  }
+  // Gershgorin bounds and Chebyshev coefficients
+  for (int l = 0; l < P.nlev; ++l) {
+    cudaMemsetAsync(c->dbits, 0, sizeof(unsigned long long), c->stream);
+    launch_gershgorin(c->disc, c->lev[l], c->dbits, c->stream);
+    unsigned long long bits = 0;
+    cudaMemcpyAsync(&bits, c->dbits, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      st = cuda_check(c, "setup");
+      g_setup_error = c->err;
+      delete c;
+      return st == H1W_OK ? H1W_ECUDA : st;
+    }
+    double lam;
+    std::memcpy(&lam, &bits, sizeof(lam));
+    c->lev[l].lam = lam;
+    const double lo = lam / 30.0, hi = lam;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+    ChebCoef& K = c->cheb[l];
+    K.inv_theta = 1.0 / theta;
+    double rho_prev = 1.0 / sigma;
+    for (int j = 1; j < o.cheb_degree; ++j) {
+      const double rho = 1.0 / (2.0 * sigma - rho_prev);
+      K.c1[j] = rho * rho_prev;
+      K.c2[j] = 2.0 * rho / delta;
+      rho_prev = rho;
+    }
+  }
+  // coarsest level: dense matrix, Cholesky, explicit symmetric inverse
+  {
+    const Level& L = c->lev[P.nlev - 1];
+    const int n = (int)L.N;
+    cudaMemsetAsync(c->coarse_L, 0, sizeof(double) * n * n, c->stream);
+    launch_assemble_dense(c->disc, L, c->coarse_L, c->stream);
+    cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
+    launch_chol(c->coarse_L, n, c->dstatus, c->stream);
+    launch_set_identity(c->coarse_X, n, c->stream);
+    launch_trsv_lower(c->coarse_L, n, c->coarse_X, n, c->stream);
+    launch_trsv_upper_t(c->coarse_L, n, c->coarse_X, n, c->stream);
+    launch_symmetrize_identity_solve(c->coarse_X, n, c->stream);
+    int status = 0;
+    cudaMemcpyAsync(&status, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      g_setup_error = std::string("setup: ") + cudaGetErrorString(e);
+      delete c;
+      return H1W_ECUDA;
+    }
+    if (status & kStatusNotSpd) {
+      g_setup_error = "coarsest-level matrix is not positive definite";
+      delete c;
+      return H1W_ENOTSPD;
+    }
+  }
+  *out = c;
+  return H1W_OK;
+}
+
+h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
+  if (!c) return H1W_EINVAL;
+  if (m < 0 || m > c->m_max) return fail(c, H1W_EINVAL, "m out of range [0, m_max]");
+  if (m > 0 && !J) return fail(c, H1W_EINVAL, "J is NULL");
+  const int64_t N = c->lev[0].N;
+  c->m = m;
+  c->J = J;
+  const long long l0 = g_kernel_launches.load();
+  if (m == 0) { c->launches_cap = 0; return H1W_OK; }
+  if (c->have_ev) cudaEventRecord(c->ev[0], c->stream);
+  vcycle_many(c, m, J, c->H);                                       // line H
+  if (c->have_ev) cudaEventRecord(c->ev[1], c->stream);
+  const int splits = cap_gemm_splits(m, N);
+  launch_cap_gemm(J, c->H, m, N, c->gemm_partial, splits, c->stream);  // line C
+  if (c->have_ev) cudaEventRecord(c->ev[2], c->stream);
+  launch_cap_finalize(c->gemm_partial, splits, m, c->grid.alpha, c->C, c->stream);
+  cudaMemcpyAsync(c->Lc, c->C, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
+  launch_chol(c->Lc, m, c->dstatus, c->stream);                    // line chol
+  if (c->have_ev) cudaEventRecord(c->ev[3], c->stream);
+  c->launches_cap = g_kernel_launches.load() - l0;
+  int status = 0;
+  cudaMemcpyAsync(&status, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, H1W_ECUDA, std::string("capacitance: ") + cudaGetErrorString(e));
+  h1w_status st = cuda_check(c, "capacitance");
+  if (st != H1W_OK) return st;
+  if (status & kStatusNotSpd) {
+    c->m = -1;
+    return fail(c, H1W_ENOTSPD, "capacitance matrix is not numerically positive definite");
+  }
+  return H1W_OK;
+}
+
+h1w_status h1w_apply_prec(h1w_ctx* c, const double* r, double* z) {
+  if (!c) return H1W_EINVAL;
+  if (!r || !z || r == z) return fail(c, H1W_EINVAL, "r and z must be distinct non-NULL pointers");
+  if (c->m < 0) return fail(c, H1W_ESTATE, "call h1w_capacitance first");
+  apply_prec_impl(c, r, z, -1);
+  return cuda_check(c, "apply_prec");
+}
+
+h1w_status h1w_apply_op(h1w_ctx* c, const double* p, double* q) {
+  if (!c) return H1W_EINVAL;
+  if (!p || !q || p == q) return fail(c, H1W_EINVAL, "p and q must be distinct non-NULL pointers");
+  if (c->m < 0) return fail(c, H1W_ESTATE, "call h1w_capacitance first");
+  j_times(c, c->J, p, c->wtmp);
+  apply_op_w(c, p, c->wtmp, q, -1);
+  return cuda_check(c, "apply_op");
+}
+
+h1w_status h1w_vcycle(h1w_ctx* c, int32_t nrhs, const double* b, double* x) {
+  if (!c) return H1W_EINVAL;
+  if (nrhs < 0 || (nrhs > 0 && (!b || !x))) return fail(c, H1W_EINVAL, "bad vcycle arguments");
+  if (nrhs == 0) return H1W_OK;
+  vcycle_many(c, nrhs, b, x);
+  return cuda_check(c, "vcycle");
+}
+
+h1w_status h1w_gn_rhs(h1w_ctx* c, const double* dm, const double* d, double* b) {
+  if (!c) return H1W_EINVAL;
+  if (!dm || !b || dm == b) return fail(c, H1W_EINVAL, "dm and b must be distinct non-NULL pointers");
+  if (c->m < 0) return fail(c, H1W_ESTATE, "call h1w_capacitance first");
+  if (c->m > 0 && !d) return fail(c, H1W_EINVAL, "d is NULL");
+  launch_apply_op(c->disc, c->lev[0], -c->grid.alpha, dm, -1.0, c->J, d, c->m, b, nullptr, nullptr,
+                  c->stream);
+  return cuda_check(c, "gn_rhs");
+}
+
+h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t maxit,
+                   h1w_info* info) {
+  if (!c) return H1W_EINVAL;
+  if (!b || !x || b == x) return fail(c, H1W_EINVAL, "b and x must be distinct non-NULL pointers");
+  if (!(rtol > 0.0) || maxit < 0) return fail(c, H1W_EINVAL, "rtol must be > 0 and maxit >= 0");
+  if (c->m < 0) return fail(c, H1W_ESTATE, "call h1w_capacitance first");
+  const int64_t N = c->lev[0].N;
+  const int m = c->m;
+  cudaStream_t s = c->stream;
+  enum { RZ = 0, PQ = 1, A = 2, RZN = 3, BETA = 4, RR = 5, BB = 6 };
+  const long long l0 = g_kernel_launches.load();
+  if (c->have_ev) cudaEventRecord(c->ev[4], s);
+  launch_dot_partial(b, b, N, c->partial, s);
+  launch_sum_to_scalar(c->partial, dot_blocks(N), c->scal + BB, s);
+  const double bnorm = std::sqrt(read_scalar(c, BB));
+  cudaMemsetAsync(x, 0, sizeof(double) * N, s);
+  h1w_info inf{0, 0, 0.0, 0.0};
+  if (bnorm == 0.0) {
+    if (info) *info = inf;
+    if (c->have_ev) cudaEventRecord(c->ev[5], s);
+    cudaStreamSynchronize(s);
+    c->launches_pcg = g_kernel_launches.load() - l0;
+    return cuda_check(c, "pcg");
+  }
+  cudaMemcpyAsync(c->r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  double rr = bnorm * bnorm;
+  const double tol = rtol * bnorm;
+  int it = 0;
+  double rel_true = 1.0;
+  for (int restart = 0; restart <= c->opt.max_restarts; ++restart) {
+    apply_prec_impl(c, c->r, c->z, RZ);
+    j_times(c, c->J, c->z, c->jz);
+    launch_p_update(c->p, c->z, c->w, c->jz, c->scal, N, m > 0 ? m : 0, true, s);
+    while (it < maxit && std::sqrt(rr) > tol) {
+      apply_op_w(c, c->p, c->w, c->q, PQ);
+      launch_pcg_alpha(c->scal, s);
+      launch_xr_update(x, c->r, c->p, c->q, c->scal, N, c->partial, s);
+      launch_sum_to_scalar(c->partial, colsum_blocks(N), c->scal + RR, s);
+      rr = read_scalar(c, RR);
+      ++it;
+      if (!std::isfinite(rr)) break;
+      if (std::sqrt(rr) <= tol) break;
+      apply_prec_impl(c, c->r, c->z, RZN);
+      j_times(c, c->J, c->z, c->jz);
+      launch_pcg_beta(c->scal, s);
+      launch_p_update(c->p, c->z, c->w, c->jz, c->scal, N, m > 0 ? m : 0, false, s);
+    }
+    // true residual r = b - A x
+    j_times(c, c->J, x, c->wtmp);
+    apply_op_w(c, x, c->wtmp, c->q, -1);
+    cudaMemcpyAsync(c->r, c->q, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+    launch_axpby(c->r, 1.0, b, -1.0, N, s);
+    launch_dot_partial(c->r, c->r, N, c->partial, s);
+    launch_sum_to_scalar(c->partial, dot_blocks(N), c->scal + RR, s);
+    const double rr_rec = rr;
+    rr = read_scalar(c, RR);
+    rel_true = std::sqrt(rr) / bnorm;
+    inf.rel_res_rec = std::sqrt(rr_rec) / bnorm;
+    if (rel_true <= rtol || it >= maxit || !std::isfinite(rel_true)) break;
+    ++inf.restarts;
+  }
+  inf.iters = it;
+  inf.rel_res_true = rel_true;
+  if (info) *info = inf;
+  if (c->have_ev) {
+    cudaEventRecord(c->ev[5], s);
+    cudaEventSynchronize(c->ev[5]);
+  }
+  c->launches_pcg = g_kernel_launches.load() - l0;
+  h1w_status st = cuda_check(c, "pcg");
+  if (st != H1W_OK) return st;
+  if (!(rel_true <= rtol)) return fail(c, H1W_ENOTCONV, "PCG did not reach rtol within maxit");
+  return H1W_OK;
+}
+
+h1w_status h1w_capacitance_factors(h1w_ctx* c, double* C, double* L) {
+  if (!c) return H1W_EINVAL;
+  if (c->m < 0) return fail(c, H1W_ESTATE, "call h1w_capacitance first");
+  const size_t bytes = sizeof(double) * c->m * c->m;
+  if (C && bytes) cudaMemcpyAsync(C, c->C, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (L && bytes) cudaMemcpyAsync(L, c->Lc, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  return cuda_check(c, "capacitance_factors");
+}
+
+h1w_status h1w_get_timings(const h1w_ctx* c, h1w_timings* out) {
+  if (!c || !out) return H1W_EINVAL;
+  h1w_timings t{};
+  if (c->have_ev) {
+    auto el = [&](int a, int b) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) != cudaSuccess) ms = 0.f;
+      return ms;
+    };
+    if (c->m > 0) {
+      t.t_H_ms = el(0, 1);
+      t.t_C_ms = el(1, 2);
+      t.t_chol_ms = el(2, 3);
+    }
+    t.t_pcg_ms = el(4, 5);
+  }
+  cudaGetLastError();  // elapsed-time queries on unrecorded events are not errors here
+  t.launches_capacitance = c->launches_cap;
+  t.launches_pcg = c->launches_pcg;
+  *out = t;
+  return H1W_OK;
+}
+
+h1w_status h1w_level_info(const h1w_ctx* c, int32_t level, int32_t* nlevels, int32_t* n) {
+  if (!c) return H1W_EINVAL;
+  if (nlevels) *nlevels = c->nlev;
+  if (n) {
+    if (level < 0 || level >= c->nlev) return H1W_EINVAL;
+    n[0] = c->lev[level].nx; n[1] = c->lev[level].ny; n[2] = c->lev[level].nz;
+  }
+  return H1W_OK;
+}
+
+const char* h1w_last_error(const h1w_ctx* c) {
+  if (!c) return g_setup_error.c_str();
+  return c->err.c_str();
+}
+
+void h1w_destroy(h1w_ctx* c) {
+  if (!c) return;
+  if (c->have_ev)
+    for (int e = 0; e < 6; ++e) cudaEventDestroy(c->ev[e]);
+  delete c;
+}
+
+}  // extern "C"

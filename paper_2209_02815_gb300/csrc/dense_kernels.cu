@@ -1,0 +1,584 @@
+// Dense and Krylov kernels: the skinny passes over J and H (m x N row-major),
+// the capacitance GEMM C = I + alpha^-1 J H^T (line C of Algorithm "MINRES
+// with the Laplace-Woodbury preconditioner"), the FP64 Cholesky factorization
+// (line chol) and triangular solves, the dense coarsest-level solve and the
+// PCG vector/scalar updates. Every reduction is deterministic: per-block
+// partial sums followed by a fixed-order second stage.
+#include <cmath>
+
+#include "h1w_internal.cuh"
+
+namespace h1w {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum for blockDim.x == kThreads; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[kThreads / 32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    t = (lane < kThreads / 32) ? sh[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// ---- skinny passes ------------------------------------------------------------
+
+constexpr int kRowsChunk = 4096;            // elements of N per block
+constexpr int kRowsPerBlock = 8;            // rows of A per block
+constexpr int kPerThread = kRowsChunk / kThreads;
+
+// partial[c * m + i] = sum_{k in chunk c} A[i * N + k] * v[k]
+__global__ void __launch_bounds__(kThreads) k_rows_dot(const double* __restrict__ A, int m,
+                                                       int64_t N, const double* __restrict__ v,
+                                                       double* __restrict__ partial) {
+  const int64_t k0 = (int64_t)blockIdx.x * kRowsChunk;
+  const int r0 = blockIdx.y * kRowsPerBlock;
+  double vv[kPerThread];
+#pragma unroll
+  for (int e = 0; e < kPerThread; ++e) {
+    const int64_t k = k0 + threadIdx.x + (int64_t)e * kThreads;
+    vv[e] = (k < N) ? v[k] : 0.0;
+  }
+  __shared__ double sh[kRowsPerBlock][kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int rr = 0; rr < kRowsPerBlock; ++rr) {
+    const int row = r0 + rr;
+    double acc = 0.0;
+    if (row < m) {
+      const double* a = A + (int64_t)row * N;
+#pragma unroll
+      for (int e = 0; e < kPerThread; ++e) {
+        const int64_t k = k0 + threadIdx.x + (int64_t)e * kThreads;
+        if (k < N) acc += a[k] * vv[e];
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) sh[rr][wid] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < kRowsPerBlock) {
+    const int row = r0 + threadIdx.x;
+    if (row < m) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) t += sh[threadIdx.x][w];
+      partial[(int64_t)blockIdx.x * m + row] = t;
+    }
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nchunks, int m,
+                                  double scale, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double t = 0.0;
+  for (int c = 0; c < nchunks; ++c) t += partial[(int64_t)c * m + i];
+  out[i] = scale * t;
+}
+
+// z_k = (z0_k - (1/alpha) sum_i H[i][k] v_i) / alpha ; partial[block] = sum_k r_k z_k
+__global__ void __launch_bounds__(kThreads) k_woodbury_update(
+    const double* __restrict__ H, int m, int64_t N, const double* __restrict__ v,
+    const double* __restrict__ z0, double alpha, double* __restrict__ z,
+    const double* __restrict__ r, double* __restrict__ partial) {
+  extern __shared__ double sv[];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = v[i];
+  __syncthreads();
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double prod = 0.0;
+  if (k < N) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    const double* col = H + k;
+    int i = 0;
+    for (; i + 4 <= m; i += 4) {
+      a0 += col[(int64_t)(i + 0) * N] * sv[i + 0];
+      a1 += col[(int64_t)(i + 1) * N] * sv[i + 1];
+      a2 += col[(int64_t)(i + 2) * N] * sv[i + 2];
+      a3 += col[(int64_t)(i + 3) * N] * sv[i + 3];
+    }
+    for (; i < m; ++i) a0 += col[(int64_t)i * N] * sv[i];
+    const double hv = (a0 + a1) + (a2 + a3);
+    const double zk = (z0[k] - hv / alpha) / alpha;
+    z[k] = zk;
+    if (r) prod = r[k] * zk;
+  }
+  if (partial) {
+    const double s = block_sum(prod);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  }
+}
+
+// ---- Cholesky (lower, in place, row-major n x n), 32-wide panels --------------
+
+constexpr int kNB = 32;
+
+__device__ void factor_diag_block(double (*Ld)[kNB + 1], int nb, int* status) {
+  const int tid = threadIdx.x;
+  const int r = tid / kNB, c2 = tid % kNB;
+  for (int c = 0; c < nb; ++c) {
+    if (tid == 0) {
+      double piv = Ld[c][c];
+      if (!(piv > 0.0)) {
+        if (status) atomicOr(status, kStatusNotSpd);
+        piv = 1.0;
+      }
+      Ld[c][c] = sqrt(piv);
+    }
+    __syncthreads();
+    if (tid > c && tid < nb) Ld[tid][c] /= Ld[c][c];
+    __syncthreads();
+    if (r > c && r < nb && c2 > c && c2 <= r) Ld[r][c2] -= Ld[r][c] * Ld[c2][c];
+    __syncthreads();
+  }
+}
+
+// grid.x = 1 + number of 32-row blocks below the panel; blockDim = 1024
+__global__ void __launch_bounds__(1024) k_chol_panel(double* A, int n, int kb, int* status) {
+  __shared__ double Ld[kNB][kNB + 1];
+  const int nb = min(kNB, n - kb);
+  const int tid = threadIdx.x;
+  {
+    const int r = tid / kNB, c = tid % kNB;
+    if (r < nb && c <= r) Ld[r][c] = A[(int64_t)(kb + r) * n + kb + c];
+  }
+  __syncthreads();
+  factor_diag_block(Ld, nb, blockIdx.x == 0 ? status : nullptr);
+  if (blockIdx.x == 0) {
+    const int r = tid / kNB, c = tid % kNB;
+    if (r < nb && c <= r) A[(int64_t)(kb + r) * n + kb + c] = Ld[r][c];
+    return;
+  }
+  // rows of this block: solve x L11^T = a for each row (warp w -> row w)
+  const int row = kb + kNB * blockIdx.x + (tid >> 5);
+  const int lane = tid & 31;
+  if (row >= n) return;
+  double a = (lane < nb) ? A[(int64_t)row * n + kb + lane] : 0.0;
+  for (int c = 0; c < nb; ++c) {
+    double xc = 0.0;
+    if (lane == c) xc = a / Ld[c][c];
+    xc = __shfl_sync(0xffffffffu, xc, c);
+    if (lane == c) a = xc;
+    else if (lane > c && lane < nb) a -= xc * Ld[lane][c];
+  }
+  if (lane < nb) A[(int64_t)row * n + kb + lane] = a;
+}
+
+// trailing update A22 -= L21 L21^T over lower tiles (ti >= tj) of 32 x 32
+__global__ void __launch_bounds__(256) k_chol_update(double* A, int n, int kb) {
+  __shared__ double Li[kNB][kNB + 1];
+  __shared__ double Lj[kNB][kNB + 1];
+  const int t = blockIdx.x;
+  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  while (ti * (ti + 1) / 2 > t) --ti;
+  const int tj = t - ti * (ti + 1) / 2;
+  const int base = kb + kNB;
+  const int ri = base + ti * kNB, rj = base + tj * kNB;
+  const int nbk = min(kNB, n - kb);
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+    const int r = e / kNB, c = e % kNB;
+    Li[r][c] = (ri + r < n && c < nbk) ? A[(int64_t)(ri + r) * n + kb + c] : 0.0;
+    Lj[r][c] = (rj + r < n && c < nbk) ? A[(int64_t)(rj + r) * n + kb + c] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+    const int r = e / kNB, c = e % kNB;
+    if (ri + r >= n || rj + c >= n) continue;
+    double s = 0.0;
+#pragma unroll 8
+    for (int l = 0; l < kNB; ++l) s += Li[r][l] * Lj[c][l];
+    A[(int64_t)(ri + r) * n + rj + c] -= s;
+  }
+}
+
+__global__ void k_zero_upper(double* A, int n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int r = (int)(e / n), c = (int)(e % n);
+  if (c > r) A[e] = 0.0;
+}
+
+// ---- triangular solves, one block per right-hand side --------------------------
+
+// x <- L^-1 x (forward substitution), 32-wide blocks; x in shared memory.
+__global__ void __launch_bounds__(512) k_trsv_lower(const double* __restrict__ L, int n,
+                                                    double* __restrict__ xg) {
+  extern __shared__ double x[];
+  double* xr = xg + (int64_t)blockIdx.x * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = xr[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int kb = 0; kb < n; kb += kNB) {
+    const int nb = min(kNB, n - kb);
+    if (wid == 0) {
+      double a = (lane < nb) ? x[kb + lane] : 0.0;
+      for (int c = 0; c < nb; ++c) {
+        double yc = 0.0;
+        if (lane == c) yc = a / L[(int64_t)(kb + c) * n + kb + c];
+        yc = __shfl_sync(0xffffffffu, yc, c);
+        if (lane == c) a = yc;
+        else if (lane > c && lane < nb) a -= yc * L[(int64_t)(kb + lane) * n + kb + c];
+      }
+      if (lane < nb) x[kb + lane] = a;
+    }
+    __syncthreads();
+    for (int i = kb + nb + threadIdx.x; i < n; i += blockDim.x) {
+      const double* li = L + (int64_t)i * n + kb;
+      double s = 0.0;
+      for (int c = 0; c < nb; ++c) s += li[c] * x[kb + c];
+      x[i] -= s;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xr[i] = x[i];
+}
+
+// x <- L^-T x (backward substitution with the transpose of the lower factor)
+__global__ void __launch_bounds__(512) k_trsv_upper_t(const double* __restrict__ L, int n,
+                                                      double* __restrict__ xg) {
+  extern __shared__ double x[];
+  double* xr = xg + (int64_t)blockIdx.x * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = xr[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nblk = (n + kNB - 1) / kNB;
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int kb = bi * kNB;
+    const int nb = min(kNB, n - kb);
+    if (wid == 0) {
+      double a = (lane < nb) ? x[kb + lane] : 0.0;
+      for (int c = nb - 1; c >= 0; --c) {
+        double vc = 0.0;
+        if (lane == c) vc = a / L[(int64_t)(kb + c) * n + kb + c];
+        vc = __shfl_sync(0xffffffffu, vc, c);
+        if (lane == c) a = vc;
+        else if (lane < c) a -= vc * L[(int64_t)(kb + c) * n + kb + lane];
+      }
+      if (lane < nb) x[kb + lane] = a;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kb; i += blockDim.x) {
+      double s = 0.0;
+      for (int c = 0; c < nb; ++c) s += L[(int64_t)(kb + c) * n + i] * x[kb + c];
+      x[i] -= s;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xr[i] = x[i];
+}
+
+// x[r] = X b[r]: one warp per (row, rhs)
+__global__ void k_coarse_apply(const double* __restrict__ X, int n, const double* __restrict__ b,
+                               double* __restrict__ x) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* br = b + (int64_t)blockIdx.y * n;
+  const double* xr = X + (int64_t)row * n;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s += xr[j] * br[j];
+  s = warp_sum(s);
+  if (lane == 0) x[(int64_t)blockIdx.y * n + row] = s;
+}
+
+__global__ void k_set_identity(double* X, int n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  X[e] = ((e / n) == (e % n)) ? 1.0 : 0.0;
+}
+
+// X holds the columns of the inverse as rows (row r = A^-1 e_r); make it exactly symmetric.
+__global__ void k_symmetrize(double* X, int n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int r = (int)(e / n), c = (int)(e % n);
+  if (c <= r) return;
+  const double v = 0.5 * (X[(int64_t)r * n + c] + X[(int64_t)c * n + r]);
+  X[(int64_t)r * n + c] = v;
+  X[(int64_t)c * n + r] = v;
+}
+
+// ---- capacitance GEMM: partial[s][i][j] = sum_{k in split s} J[i][k] H[j][k], upper tiles --
+
+constexpr int kTM = 64, kTK = 16;
+
+__global__ void __launch_bounds__(256) k_cap_gemm(const double* __restrict__ J,
+                                                  const double* __restrict__ H, int m, int64_t N,
+                                                  int64_t kchunk, double* __restrict__ partial) {
+  __shared__ double As[kTK][kTM + 1];
+  __shared__ double Bs[kTK][kTM + 1];
+  const int t = blockIdx.x;
+  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  while (ti * (ti + 1) / 2 > t) --ti;
+  const int tj0 = t - ti * (ti + 1) / 2;  // tj0 <= ti: tile (row tj0, col ti) is upper
+  const int i0 = tj0 * kTM, j0 = ti * kTM;
+  const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
+  const int64_t kend = min(N, kbeg + kchunk);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int64_t k = kbeg; k < kend; k += kTK) {
+    for (int e = threadIdx.x; e < kTM * kTK; e += blockDim.x) {
+      const int r = e / kTK, c = e % kTK;
+      const int64_t kk = k + c;
+      As[c][r] = (i0 + r < m && kk < kend) ? J[(int64_t)(i0 + r) * N + kk] : 0.0;
+      Bs[c][r] = (j0 + r < m && kk < kend) ? H[(int64_t)(j0 + r) * N + kk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kTK; ++c) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { a[u] = As[c][ty * 4 + u]; b[u] = Bs[c][tx * 4 + u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+    }
+    __syncthreads();
+  }
+  double* P = partial + (int64_t)blockIdx.y * m * m;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+      if (i < m && j < m) P[(int64_t)i * m + j] = acc[u][v];
+    }
+}
+
+// C[i][j] = delta_ij + (1/alpha) sum_s partial[s][min(i,j)][max(i,j)]
+__global__ void k_cap_finalize(const double* __restrict__ partial, int splits, int m, double alpha,
+                               double* __restrict__ C) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)m * m) return;
+  const int i = (int)(e / m), j = (int)(e % m);
+  const int a = min(i, j), b = max(i, j);
+  double s = 0.0;
+  for (int q = 0; q < splits; ++q) s += partial[(int64_t)q * m * m + (int64_t)a * m + b];
+  C[e] = (i == j ? 1.0 : 0.0) + s / alpha;
+}
+
+// ---- PCG vectors and scalars -----------------------------------------------------
+// scalar slots: 0 rz, 1 pq, 2 a, 3 rz_new, 4 beta, 5 rr, 6 bb
+
+__global__ void k_sum_to_scalar(const double* __restrict__ partial, int n, double* dst) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t += partial[i];
+  t = block_sum(t);
+  if (threadIdx.x == 0) *dst = t;
+}
+
+__global__ void k_pcg_alpha(double* scal) { scal[2] = scal[0] / scal[1]; }
+
+__global__ void k_pcg_beta(double* scal) {
+  scal[4] = scal[3] / scal[0];
+  scal[0] = scal[3];
+}
+
+__global__ void __launch_bounds__(kThreads) k_xr_update(double* __restrict__ x, double* __restrict__ r,
+                                                        const double* __restrict__ p,
+                                                        const double* __restrict__ q,
+                                                        const double* __restrict__ scal, int64_t N,
+                                                        double* __restrict__ partial) {
+  const double a = scal[2];
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double rr = 0.0;
+  if (k < N) {
+    x[k] += a * p[k];
+    const double rv = r[k] - a * q[k];
+    r[k] = rv;
+    rr = rv * rv;
+  }
+  const double s = block_sum(rr);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_p_update(double* __restrict__ p, const double* __restrict__ z,
+                           double* __restrict__ w, const double* __restrict__ jz,
+                           const double* __restrict__ scal, int64_t N, int m, int first) {
+  const double beta = first ? 0.0 : scal[4];
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) p[k] = first ? z[k] : z[k] + beta * p[k];
+  if (k < m) w[k] = first ? jz[k] : jz[k] + beta * w[k];
+}
+
+__global__ void k_axpby(double* __restrict__ y, double a, const double* __restrict__ x, double b,
+                        int64_t N) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) y[k] = a * x[k] + b * y[k];
+}
+
+__global__ void __launch_bounds__(kThreads) k_dot_partial(const double* __restrict__ a,
+                                                          const double* __restrict__ b, int64_t N,
+                                                          double* __restrict__ partial) {
+  double s = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x)
+    s += a[k] * b[k];
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_fill(double* y, double v, int64_t N) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) y[k] = v;
+}
+
+inline unsigned nblk(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+int rows_dot_chunks(int64_t N) { return (int)((N + kRowsChunk - 1) / kRowsChunk); }
+
+void launch_rows_dot(const double* A, int m, int64_t N, const double* v, double* partial,
+                     cudaStream_t s) {
+  if (m <= 0) return;
+  dim3 g(rows_dot_chunks(N), (m + kRowsPerBlock - 1) / kRowsPerBlock);
+  k_rows_dot<<<g, kThreads, 0, s>>>(A, m, N, v, partial);
+  note_launches(1);
+}
+
+void launch_reduce_partials(const double* partial, int nchunks, int m, double scale, double* out,
+                            cudaStream_t s) {
+  if (m <= 0) return;
+  k_reduce_partials<<<nblk(m, 128), 128, 0, s>>>(partial, nchunks, m, scale, out);
+  note_launches(1);
+}
+
+int colsum_blocks(int64_t N) { return (int)nblk(N); }
+
+void launch_woodbury_update(const double* H, int m, int64_t N, const double* v, const double* z0,
+                            double alpha, double* z, const double* r, double* partial,
+                            cudaStream_t s) {
+  const size_t smem = sizeof(double) * (size_t)(m > 0 ? m : 1);
+  k_woodbury_update<<<nblk(N), kThreads, smem, s>>>(H, m, N, v, z0, alpha, z, r, partial);
+  note_launches(1);
+}
+
+void launch_chol(double* A, int n, int* status, cudaStream_t s) {
+  for (int kb = 0; kb < n; kb += kNB) {
+    const int below = (n - kb - 1) / kNB;  // 32-row blocks after the diagonal block
+    k_chol_panel<<<1 + below, 1024, 0, s>>>(A, n, kb, status);
+    note_launches(1);
+    if (below > 0) {
+      const int tiles = below * (below + 1) / 2;
+      k_chol_update<<<tiles, 256, 0, s>>>(A, n, kb);
+      note_launches(1);
+    }
+  }
+  k_zero_upper<<<nblk((int64_t)n * n), kThreads, 0, s>>>(A, n);
+  note_launches(1);
+}
+
+void launch_trsv_lower(const double* L, int n, double* x, int nrhs, cudaStream_t s) {
+  k_trsv_lower<<<nrhs, 512, sizeof(double) * n, s>>>(L, n, x);
+  note_launches(1);
+}
+
+void launch_trsv_upper_t(const double* L, int n, double* x, int nrhs, cudaStream_t s) {
+  k_trsv_upper_t<<<nrhs, 512, sizeof(double) * n, s>>>(L, n, x);
+  note_launches(1);
+}
+
+void launch_coarse_apply(const double* X, int n, int nrhs, const double* b, double* x,
+                         cudaStream_t s) {
+  dim3 g(nblk(n, 8), nrhs);
+  k_coarse_apply<<<g, 256, 0, s>>>(X, n, b, x);
+  note_launches(1);
+}
+
+void launch_set_identity(double* X, int n, cudaStream_t s) {
+  k_set_identity<<<nblk((int64_t)n * n), kThreads, 0, s>>>(X, n);
+  note_launches(1);
+}
+
+void launch_symmetrize_identity_solve(double* X, int n, cudaStream_t s) {
+  k_symmetrize<<<nblk((int64_t)n * n), kThreads, 0, s>>>(X, n);
+  note_launches(1);
+}
+
+int cap_gemm_splits(int m, int64_t N) {
+  const int tiles = (m + kTM - 1) / kTM;
+  const int utiles = tiles * (tiles + 1) / 2;
+  int splits = (4 * 152 + utiles - 1) / utiles;
+  const int64_t max_splits = (N + 255) / 256;  // at least 256 columns per split
+  if (splits > max_splits) splits = (int)max_splits;
+  return splits < 1 ? 1 : splits;
+}
+
+void launch_cap_gemm(const double* J, const double* H, int m, int64_t N, double* partial,
+                     int splits, cudaStream_t s) {
+  const int tiles = (m + kTM - 1) / kTM;
+  const int utiles = tiles * (tiles + 1) / 2;
+  int64_t kchunk = (N + splits - 1) / splits;
+  kchunk = (kchunk + kTK - 1) / kTK * kTK;
+  dim3 g(utiles, splits);
+  k_cap_gemm<<<g, 256, 0, s>>>(J, H, m, N, kchunk, partial);
+  note_launches(1);
+}
+
+void launch_cap_finalize(const double* partial, int splits, int m, double alpha, double* C,
+                         cudaStream_t s) {
+  k_cap_finalize<<<nblk((int64_t)m * m), kThreads, 0, s>>>(partial, splits, m, alpha, C);
+  note_launches(1);
+}
+
+void launch_sum_to_scalar(const double* partial, int n, double* dst, cudaStream_t s) {
+  k_sum_to_scalar<<<1, kThreads, 0, s>>>(partial, n, dst);
+  note_launches(1);
+}
+
+void launch_pcg_alpha(double* scal, cudaStream_t s) { k_pcg_alpha<<<1, 1, 0, s>>>(scal); }
+void launch_pcg_beta(double* scal, cudaStream_t s) { k_pcg_beta<<<1, 1, 0, s>>>(scal); }
+
+void launch_xr_update(double* x, double* r, const double* p, const double* q, const double* scal,
+                      int64_t N, double* partial, cudaStream_t s) {
+  k_xr_update<<<nblk(N), kThreads, 0, s>>>(x, r, p, q, scal, N, partial);
+  note_launches(1);
+}
+
+void launch_p_update(double* p, const double* z, double* w, const double* jz, const double* scal,
+                     int64_t N, int m, bool first, cudaStream_t s) {
+  const int64_t n = N > m ? N : m;
+  k_p_update<<<nblk(n), kThreads, 0, s>>>(p, z, w, jz, scal, N, m, first ? 1 : 0);
+  note_launches(1);
+}
+
+void launch_axpby(double* y, double a, const double* x, double b, int64_t N, cudaStream_t s) {
+  k_axpby<<<nblk(N), kThreads, 0, s>>>(y, a, x, b, N);
+  note_launches(1);
+}
+
+int dot_blocks(int64_t N) {
+  const int64_t b = nblk(N);
+  return (int)(b < 1024 ? b : 1024);
+}
+
+void launch_dot_partial(const double* a, const double* b, int64_t N, double* partial,
+                        cudaStream_t s) {
+  k_dot_partial<<<dot_blocks(N), kThreads, 0, s>>>(a, b, N, partial);
+  note_launches(1);
+}
+
+void launch_fill(double* y, double v, int64_t N, cudaStream_t s) {
+  k_fill<<<nblk(N), kThreads, 0, s>>>(y, v, N);
+  note_launches(1);
+}
+
+}  // namespace h1w

@@ -1,0 +1,109 @@
+// Internal declarations shared by the h1w CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+
+#include "h1w.h"
+
+namespace h1w {
+
+constexpr int kMaxLevels = 16;
+constexpr int kCoarseTarget = 512;   // stop coarsening once a level has <= this many unknowns
+constexpr int kCoarseLimit = 1024;   // largest coarsest level accepted for the dense solve
+constexpr int kMaxM = 4096;          // largest number of measurements accepted
+
+// One multigrid level. Plain data, passed to kernels by value.
+//  FV (3D cell-centred): (A u)_c = V u_c + sum_d T_d sum_{nb c' along d} (u_c - u_c').
+//  Q1 (2D vertex): A = Kx (x) My + Mx (x) Ky + Dx (x) Dy with symmetric
+//  tridiagonal 1D factors stored as six arrays of length n per axis:
+//  [Kd, Ko, Md, Mo, Dd, Do] (diagonal, and coupling (i, i+1) at index i).
+struct Level {
+  int nx, ny, nz;
+  int64_t N;
+  double Tx, Ty, Tz, V;         // FV coefficients
+  const double* qx;              // Q1 x-axis coefficients [6][nx] (device)
+  const double* qy;              // Q1 y-axis coefficients [6][ny] (device)
+  double lam;                    // upper bound of spec(D^-1 A) (Gershgorin)
+  int cx, cy, cz;                // axis coarsened towards the next level
+};
+
+struct ChebCoef {
+  double inv_theta;   // 1 / theta
+  double c1[8];       // rho_j rho_{j-1} for step j (1-based; index 0 unused)
+  double c2[8];       // 2 rho_j / delta
+};
+
+// Kernels launched by this library in this process (every launcher adds its count).
+extern std::atomic<long long> g_kernel_launches;
+inline void note_launches(int k) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Device status word bits (written by kernels, read back by the host).
+enum : int { kStatusNotSpd = 1 };
+
+// ---- kernel launchers (mg_kernels.cu) --------------------------------------
+// r = b - A x (r = b when zero_x); d = D^-1 r / theta; x = d only when zero_x
+void launch_cheb_first(int disc, const Level& L, int nrhs, const double* b, double* x, double* r,
+                       double* d, bool zero_x, double inv_theta, cudaStream_t s);
+// r -= A d_old; d_new = c1 d_old + c2 D^-1 r; x += d_new (+ d_old when add_old)
+void launch_cheb_step(int disc, const Level& L, int nrhs, double* r, const double* d_old,
+                      double* d_new, double* x, double c1, double c2, bool add_old, cudaStream_t s);
+void launch_add(int64_t n, const double* d, double* x, cudaStream_t s);
+void launch_residual(int disc, const Level& L, int nrhs, const double* b, const double* x,
+                     double* r, cudaStream_t s);
+void launch_restrict(int disc, const Level& Lf, const Level& Lc, int nrhs, const double* rf,
+                     double* bc, cudaStream_t s);
+void launch_prolong_add(int disc, const Level& Lf, const Level& Lc, int nrhs, const double* xc,
+                        double* xf, cudaStream_t s);
+void launch_gershgorin(int disc, const Level& L, unsigned long long* out_bits, cudaStream_t s);
+void launch_assemble_dense(int disc, const Level& L, double* A, cudaStream_t s);
+// out = ca * (A p) + cj * sum_i J[i][k] w[i]; partial[block] = sum_k p_k out_k when partial != null.
+void launch_apply_op(int disc, const Level& L, double ca, const double* p, double cj,
+                     const double* J, const double* w, int m, double* out, double* partial,
+                     int* nblocks_out, cudaStream_t s);
+int apply_op_blocks(const Level& L);
+
+// ---- dense / Krylov kernels (dense_kernels.cu) ------------------------------
+// partial[c * m + i] = sum_{k in chunk c} A[i * lda + k] v[k]
+int rows_dot_chunks(int64_t N);
+void launch_rows_dot(const double* A, int m, int64_t N, const double* v, double* partial,
+                     cudaStream_t s);
+// out[i] = scale * sum_c partial[c * m + i]
+void launch_reduce_partials(const double* partial, int nchunks, int m, double scale, double* out,
+                            cudaStream_t s);
+// z_k = (z0_k - (1/alpha) sum_i H[i][k] v_i) / alpha; partial[block] = sum r_k z_k
+int colsum_blocks(int64_t N);
+void launch_woodbury_update(const double* H, int m, int64_t N, const double* v, const double* z0,
+                            double alpha, double* z, const double* r, double* partial,
+                            cudaStream_t s);
+void launch_chol(double* A, int n, int* status, cudaStream_t s);
+// in-place triangular solves with the lower factor L (n x n): x <- L^-1 x, x <- L^-T x
+void launch_trsv_lower(const double* L, int n, double* x, int nrhs, cudaStream_t s);
+void launch_trsv_upper_t(const double* L, int n, double* x, int nrhs, cudaStream_t s);
+void launch_coarse_apply(const double* X, int n, int nrhs, const double* b, double* x,
+                         cudaStream_t s);
+void launch_symmetrize_identity_solve(double* X, int n, cudaStream_t s);
+void launch_set_identity(double* X, int n, cudaStream_t s);
+int cap_gemm_splits(int m, int64_t N);
+void launch_cap_gemm(const double* J, const double* H, int m, int64_t N, double* partial,
+                     int splits, cudaStream_t s);
+void launch_cap_finalize(const double* partial, int splits, int m, double alpha, double* C,
+                         cudaStream_t s);
+// Krylov scalar kernels: scal is a small device array (see ScalarSlot in capi.cu)
+void launch_sum_to_scalar(const double* partial, int n, double* dst, cudaStream_t s);
+void launch_pcg_alpha(double* scal, cudaStream_t s);
+void launch_pcg_beta(double* scal, cudaStream_t s);
+void launch_xr_update(double* x, double* r, const double* p, const double* q, const double* scal,
+                      int64_t N, double* partial, cudaStream_t s);
+void launch_p_update(double* p, const double* z, double* w, const double* jz, const double* scal,
+                     int64_t N, int m, bool first, cudaStream_t s);
+void launch_axpby(double* y, double a, const double* x, double b, int64_t N, cudaStream_t s);
+void launch_dot_partial(const double* a, const double* b, int64_t N, double* partial,
+                        cudaStream_t s);
+int dot_blocks(int64_t N);
+void launch_fill(double* y, double v, int64_t N, cudaStream_t s);
+
+}  // namespace h1w

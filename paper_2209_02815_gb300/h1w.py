@@ -1,0 +1,282 @@
+"""Python binding of the h1w C ABI (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: tensors are checked for device, dtype, contiguity and
+size, and their data pointers are passed through ctypes. PyTorch supplies
+device memory (the workspace and the vectors) and the CUDA stream.
+
+The shared library is built in-tree by ``paper_2209_02815_gb300.build``. If it
+is missing or cannot be loaded, ``load()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+H1W_OK, H1W_EINVAL, H1W_ENOMEM, H1W_ECUDA, H1W_ENOTCONV = 0, 1, 2, 3, 4
+H1W_ENOTSPD, H1W_ETIMEOUT, H1W_EUNSUPPORTED, H1W_ESTATE = 5, 6, 7, 8
+H1W_Q1_VERTEX, H1W_FV_CELL = 1, 2
+
+_STATUS_NAMES = {0: "H1W_OK", 1: "H1W_EINVAL", 2: "H1W_ENOMEM", 3: "H1W_ECUDA", 4: "H1W_ENOTCONV",
+                 5: "H1W_ENOTSPD", 6: "H1W_ETIMEOUT", 7: "H1W_EUNSUPPORTED", 8: "H1W_ESTATE"}
+
+
+class H1wError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("disc", ctypes.c_int32), ("n", ctypes.c_int32 * 3),
+                ("h", ctypes.c_double * 3), ("alpha", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("cheb_degree", ctypes.c_int32), ("rhs_block", ctypes.c_int32),
+                ("max_restarts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Timings(ctypes.Structure):
+    _fields_ = [("t_H_ms", ctypes.c_float), ("t_C_ms", ctypes.c_float), ("t_chol_ms", ctypes.c_float),
+                ("t_pcg_ms", ctypes.c_float), ("launches_capacitance", ctypes.c_int64),
+                ("launches_pcg", ctypes.c_int64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("rel_res_true", ctypes.c_double), ("rel_res_rec", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libh1w.so (building it first when asked). Raises when unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and (not os.path.exists(path) or _build._stale([])):
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"h1w CUDA library not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, D, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
+    G, O, IN = ctypes.POINTER(Grid), ctypes.POINTER(Options), ctypes.POINTER(Info)
+    sig = {
+        "h1w_default_options": (None, [O]),
+        "h1w_workspace_size": (SZ, [G, I32, O]),
+        "h1w_setup": (I32, [G, I32, O, P, SZ, P, ctypes.POINTER(P)]),
+        "h1w_capacitance": (I32, [P, I32, P]),
+        "h1w_apply_prec": (I32, [P, P, P]),
+        "h1w_apply_op": (I32, [P, P, P]),
+        "h1w_vcycle": (I32, [P, I32, P, P]),
+        "h1w_gn_rhs": (I32, [P, P, P, P]),
+        "h1w_pcg": (I32, [P, P, P, D, I32, IN]),
+        "h1w_capacitance_factors": (I32, [P, P, P]),
+        "h1w_level_info": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "h1w_get_timings": (I32, [P, ctypes.POINTER(Timings)]),
+        "h1w_last_error": (ctypes.c_char_p, [P]),
+        "h1w_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t: torch.Tensor | None, n: int | None = None, name: str = "tensor") -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} entries, needs {n}")
+    return t.data_ptr()
+
+
+def make_grid(disc: int, n, h, alpha: float) -> Grid:
+    g = Grid()
+    g.dim = 2 if disc == H1W_Q1_VERTEX else 3
+    g.disc = disc
+    nn = list(n) + [1] * (3 - len(n))
+    hh = list(h) + [1.0] * (3 - len(h))
+    for a in range(3):
+        g.n[a] = int(nn[a])
+        g.h[a] = float(hh[a])
+    g.alpha = float(alpha)
+    return g
+
+
+def h1w_default_options() -> Options:
+    o = Options()
+    load().h1w_default_options(ctypes.byref(o))
+    return o
+
+
+def h1w_workspace_size(grid: Grid, m_max: int, opt: Options | None = None) -> int:
+    return int(load().h1w_workspace_size(ctypes.byref(grid), int(m_max),
+                                         ctypes.byref(opt) if opt is not None else None))
+
+
+def h1w_last_error(ctx) -> str:
+    s = load().h1w_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def _check(st: int, ctx) -> None:
+    if st != H1W_OK:
+        raise H1wError(st, h1w_last_error(ctx))
+
+
+def h1w_setup(grid: Grid, m_max: int, opt: Options | None, workspace: torch.Tensor,
+              stream: torch.cuda.Stream | None = None):
+    """Returns an opaque context handle (int)."""
+    if not workspace.is_cuda or workspace.dtype != torch.uint8:
+        raise ValueError("workspace must be a CUDA uint8 tensor")
+    out = ctypes.c_void_p()
+    s = (stream or torch.cuda.current_stream(workspace.device)).cuda_stream
+    st = load().h1w_setup(ctypes.byref(grid), int(m_max), ctypes.byref(opt) if opt is not None else None,
+                          workspace.data_ptr(), workspace.numel(), s, ctypes.byref(out))
+    _check(st, None)
+    return out.value
+
+
+def h1w_capacitance(ctx, m: int, J: torch.Tensor | None, N: int) -> None:
+    _check(load().h1w_capacitance(ctx, int(m), _ptr(J, m * N, "J") if m > 0 else None), ctx)
+
+
+def h1w_apply_prec(ctx, r: torch.Tensor, z: torch.Tensor, N: int) -> None:
+    _check(load().h1w_apply_prec(ctx, _ptr(r, N, "r"), _ptr(z, N, "z")), ctx)
+
+
+def h1w_apply_op(ctx, p: torch.Tensor, q: torch.Tensor, N: int) -> None:
+    _check(load().h1w_apply_op(ctx, _ptr(p, N, "p"), _ptr(q, N, "q")), ctx)
+
+
+def h1w_vcycle(ctx, nrhs: int, b: torch.Tensor, x: torch.Tensor, N: int) -> None:
+    _check(load().h1w_vcycle(ctx, int(nrhs), _ptr(b, nrhs * N, "b"), _ptr(x, nrhs * N, "x")), ctx)
+
+
+def h1w_gn_rhs(ctx, dm: torch.Tensor, d: torch.Tensor | None, b: torch.Tensor, N: int, m: int) -> None:
+    _check(load().h1w_gn_rhs(ctx, _ptr(dm, N, "dm"), _ptr(d, m, "d") if m > 0 else None,
+                             _ptr(b, N, "b")), ctx)
+
+
+def h1w_pcg(ctx, b: torch.Tensor, x: torch.Tensor, rtol: float, maxit: int, N: int,
+            raise_on_notconv: bool = True) -> Info:
+    info = Info()
+    st = load().h1w_pcg(ctx, _ptr(b, N, "b"), _ptr(x, N, "x"), float(rtol), int(maxit), ctypes.byref(info))
+    if st == H1W_ENOTCONV and not raise_on_notconv:
+        return info
+    _check(st, ctx)
+    return info
+
+
+def h1w_capacitance_factors(ctx, C: torch.Tensor | None, L: torch.Tensor | None, m: int) -> None:
+    _check(load().h1w_capacitance_factors(ctx, _ptr(C, m * m, "C"), _ptr(L, m * m, "L")), ctx)
+
+
+def h1w_level_info(ctx, level: int = 0):
+    nl = ctypes.c_int32()
+    n = (ctypes.c_int32 * 3)()
+    _check(load().h1w_level_info(ctx, int(level), ctypes.byref(nl), n), ctx)
+    return nl.value, tuple(n)
+
+
+def h1w_get_timings(ctx) -> Timings:
+    t = Timings()
+    _check(load().h1w_get_timings(ctx, ctypes.byref(t)), ctx)
+    return t
+
+
+def h1w_destroy(ctx) -> None:
+    if ctx:
+        load().h1w_destroy(ctx)
+
+
+class Solver:
+    """Owns a workspace tensor and a context for one grid (convenience wrapper)."""
+
+    def __init__(self, disc: int, n, h, alpha: float, m_max: int, device="cuda",
+                 opt: Options | None = None, stream: torch.cuda.Stream | None = None):
+        self.grid = make_grid(disc, n, h, alpha)
+        self.N = 1
+        for v in list(n):
+            self.N *= int(v)
+        self.m_max = int(m_max)
+        size = h1w_workspace_size(self.grid, self.m_max, opt)
+        if size == 0:
+            raise H1wError(H1W_EINVAL, "invalid grid/options for h1w_workspace_size")
+        self.workspace = torch.empty(size, dtype=torch.uint8, device=device)
+        self.ctx = h1w_setup(self.grid, self.m_max, opt, self.workspace, stream)
+        self.m = None
+        self.J = None
+
+    def capacitance(self, J: torch.Tensor | None) -> None:
+        m = 0 if J is None else int(J.shape[0])
+        self.J = J  # keep the borrowed matrix alive
+        h1w_capacitance(self.ctx, m, J, self.N)
+        self.m = m
+
+    def apply_prec(self, r, z=None):
+        z = torch.empty_like(r) if z is None else z
+        h1w_apply_prec(self.ctx, r, z, self.N)
+        return z
+
+    def apply_op(self, p, q=None):
+        q = torch.empty_like(p) if q is None else q
+        h1w_apply_op(self.ctx, p, q, self.N)
+        return q
+
+    def vcycle(self, b, x=None):
+        nrhs = b.numel() // self.N
+        x = torch.empty_like(b) if x is None else x
+        h1w_vcycle(self.ctx, nrhs, b, x, self.N)
+        return x
+
+    def gn_rhs(self, dm, d):
+        b = torch.empty_like(dm)
+        h1w_gn_rhs(self.ctx, dm, d, b, self.N, self.m or 0)
+        return b
+
+    def pcg(self, b, rtol: float, maxit: int = 500, x=None, raise_on_notconv=True):
+        x = torch.empty_like(b) if x is None else x
+        info = h1w_pcg(self.ctx, b, x, rtol, maxit, self.N, raise_on_notconv)
+        return x, info
+
+    def factors(self):
+        m = self.m or 0
+        C = torch.empty((m, m), dtype=torch.float64, device=self.workspace.device)
+        L = torch.empty_like(C)
+        h1w_capacitance_factors(self.ctx, C, L, m)
+        return C, L
+
+    def timings(self) -> Timings:
+        return h1w_get_timings(self.ctx)
+
+    def levels(self):
+        nl, _ = h1w_level_info(self.ctx, 0)
+        return [h1w_level_info(self.ctx, l)[1] for l in range(nl)]
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            h1w_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

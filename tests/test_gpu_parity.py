@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Sizes span several 256-thread blocks and multigrid levels with ragged tails
+(grid sides that are not multiples of the tile or of powers of two), plus the
+degenerate cases m = 0 and m = 1.
+
+Tolerances (FP64 throughout). Both sides evaluate the same formulas in FP64
+but with different summation orders, so each elementary result differs by a
+few units of roundoff, amplified by the conditioning of the step:
+* V-cycle, operator apply, right-hand side: 1e-12 relative (norm-wise), the
+  operators have O(1)-conditioned rounding (tens of flops per entry).
+* capacitance C: 1e-11 relative, a sum of N products (error ~ sqrt(N) eps).
+* Cholesky factor and preconditioner apply: 1e-9 relative, the error of C is
+  amplified by at most cond(C) (<= 1e3 for the cases here).
+* solution of the system: 1e-9 relative to the dense direct solve, the
+  bound stated for FP64 paths; PCG is run to rtol 1e-12 (C1) so that
+  cond(A) * rtol stays below it.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ccg
+from oracle import discretization as disc
+from oracle import multigrid as mg
+from oracle import woodbury as wb
+from paper_2209_02815_gb300 import h1w, inputs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+Q1_CASES = [(29, 23), (64, 64), (37, 41), (130, 67)]
+FV_CASES = [(16, 8, 12), (24, 24, 24), (20, 12, 28)]
+
+
+def _q1(n):
+    return "q1", tuple(n), tuple(1.0 / (v - 1) for v in n)
+
+
+def _fv(n):
+    return "fv", tuple(n), tuple(1.0 / v for v in n)
+
+
+def _gpu(d, n, h, alpha, m_max, **opt):
+    o = None
+    if opt:
+        o = h1w.h1w_default_options()
+        for k, v in opt.items():
+            setattr(o, k, v)
+    code = h1w.H1W_Q1_VERTEX if d == "q1" else h1w.H1W_FV_CELL
+    return h1w.Solver(code, n, h, alpha, m_max, device=DEV, opt=o)
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+ALL = [_q1(n) for n in Q1_CASES] + [_fv(n) for n in FV_CASES]
+
+
+@pytest.mark.parametrize("case", ALL, ids=lambda c: f"{c[0]}{'x'.join(map(str, c[1]))}")
+def test_hierarchy_matches_oracle(case):
+    d, n, h = case
+    H = mg.build_hierarchy(d, n, h)
+    S = _gpu(d, n, h, 1e-2, 4)
+    lv = S.levels()
+    want = [tuple(list(l.n) + [1] * (3 - len(l.n))) for l in H.levels]
+    assert lv == want
+
+
+@pytest.mark.parametrize("case", ALL, ids=lambda c: f"{c[0]}{'x'.join(map(str, c[1]))}")
+def test_vcycle_parity(case):
+    d, n, h = case
+    H = mg.build_hierarchy(d, n, h)
+    N = H.N
+    rng = np.random.default_rng(21)
+    B = rng.standard_normal((3, N))
+    S = _gpu(d, n, h, 1e-2, 4, rhs_block=2)  # 3 right-hand sides: blocks of 2 and 1
+    X = S.vcycle(_t(B)).cpu().numpy()
+    for r in range(3):
+        ref = mg.vcycle(H, B[r])
+        assert _rel(X[r], ref) <= 1e-12
+
+
+@pytest.mark.parametrize("case", ALL, ids=lambda c: f"{c[0]}{'x'.join(map(str, c[1]))}")
+def test_apply_op_and_rhs_parity(case):
+    d, n, h = case
+    A = disc.regularization_operator(d, n, h)
+    N = A.shape[0]
+    rng = np.random.default_rng(22)
+    m, alpha = 7, 3e-3
+    J = rng.standard_normal((m, N)) / np.sqrt(N)
+    p = rng.standard_normal(N)
+    S = _gpu(d, n, h, alpha, m)
+    Jt = _t(J)
+    S.capacitance(Jt)
+    q = S.apply_op(_t(p)).cpu().numpy()
+    assert _rel(q, wb.apply_operator(A, alpha, J, p)) <= 1e-12
+    dm = rng.standard_normal(N)
+    dd = rng.standard_normal(m)
+    b = S.gn_rhs(_t(dm), _t(dd)).cpu().numpy()
+    assert _rel(b, wb.gn_rhs(A, alpha, dm, J, dd)) <= 1e-12
+
+
+@pytest.mark.parametrize("case", ALL, ids=lambda c: f"{c[0]}{'x'.join(map(str, c[1]))}")
+@pytest.mark.parametrize("m", [1, 13, 70])
+def test_capacitance_and_prec_parity(case, m):
+    d, n, h = case
+    H = mg.build_hierarchy(d, n, h)
+    N = H.N
+    rng = np.random.default_rng(23 + m)
+    alpha = 1e-2
+    J = rng.standard_normal((m, N)) / np.sqrt(N)
+    P = wb.WoodburyPreconditioner(lambda v: mg.vcycle(H, v), J, alpha)
+    S = _gpu(d, n, h, alpha, m, rhs_block=16)
+    S.capacitance(_t(J))
+    C, L = (t.cpu().numpy() for t in S.factors())
+    assert np.array_equal(C, C.T)
+    assert _rel(C, P.C) <= 1e-11
+    assert _rel(L, np.linalg.cholesky(P.C)) <= 1e-9
+    r = rng.standard_normal(N)
+    z = S.apply_prec(_t(r)).cpu().numpy()
+    assert _rel(z, P(r)) <= 1e-9
+
+
+def test_m0_prec_is_scaled_vcycle():
+    d, n, h = _fv((16, 8, 12))
+    H = mg.build_hierarchy(d, n, h)
+    S = _gpu(d, n, h, 0.25, 4)
+    S.capacitance(None)
+    r = np.random.default_rng(5).standard_normal(H.N)
+    z = S.apply_prec(_t(r)).cpu().numpy()
+    assert _rel(z, mg.vcycle(H, r) / 0.25) <= 1e-12
+
+
+def test_pcg_small_2d_matches_dense_solve():
+    """The 64 x 64 Q1 problem: J ~ N(0,1)/64 (16 rows), alpha = 1e-2, rtol 1e-12."""
+    pr = inputs.small_c1_problem()
+    A = disc.regularization_operator("q1", (pr.nx, pr.ny), pr.h)
+    x_ref = np.linalg.solve(pr.alpha * A.toarray() + pr.J.T @ pr.J, pr.b)
+    H = mg.build_hierarchy("q1", (pr.nx, pr.ny), pr.h)
+    P = wb.WoodburyPreconditioner(lambda v: mg.vcycle(H, v), pr.J, pr.alpha)
+    _, it_ref, _ = wb.pcg(lambda v: wb.apply_operator(A, pr.alpha, pr.J, v), P, pr.b, 1e-12, 200)
+    S = _gpu("q1", (pr.nx, pr.ny), pr.h, pr.alpha, pr.J.shape[0])
+    S.capacitance(_t(pr.J))
+    x, info = S.pcg(_t(pr.b), 1e-12, 200)
+    x = x.cpu().numpy()
+    assert info.rel_res_true <= 1e-12
+    assert _rel(x, x_ref) <= 1e-9
+    assert abs(info.iters - it_ref) <= 1
+
+
+@pytest.mark.parametrize("case", [_fv((24, 24, 24)), _q1((130, 67)), _fv((20, 12, 28))],
+                         ids=["fv24", "q1_130x67", "fv20x12x28"])
+@pytest.mark.parametrize("alpha,rtol,xtol", [(1e-1, 1e-11, 1e-9), (1e-2, 1e-11, 1e-9), (1e-4, 1e-8, None)])
+def test_pcg_matches_oracle_pcg(case, alpha, rtol, xtol):
+    """rtol is chosen above the attainable accuracy eps * cond(A) of each case
+    (alpha = 1e-4 on the FV grids has cond(A) ~ 1e8); where cond(A) * rtol
+    exceeds 1e-9 only the residual and the iteration count are compared."""
+    d, n, h = case
+    A = disc.regularization_operator(d, n, h)
+    N = A.shape[0]
+    rng = np.random.default_rng(31)
+    m = 40
+    J = rng.standard_normal((m, N)) / np.sqrt(N)
+    b = rng.standard_normal(N)
+    H = mg.build_hierarchy(d, n, h)
+    P = wb.WoodburyPreconditioner(lambda v: mg.vcycle(H, v), J, alpha)
+    x_ref, it_ref, rel_ref = wb.pcg(lambda v: wb.apply_operator(A, alpha, J, v), P, b, rtol, 300)
+    assert rel_ref <= rtol
+    S = _gpu(d, n, h, alpha, m)
+    S.capacitance(_t(J))
+    x, info = S.pcg(_t(b), rtol, 300)
+    assert info.rel_res_true <= rtol
+    if xtol is not None:
+        assert _rel(x.cpu().numpy(), x_ref) <= xtol
+    assert abs(info.iters - it_ref) <= 1
+    # the true residual agrees with the C oracle's operator
+    op = ccg.CsrOperator(A, alpha, J)
+    rt = b - op.apply(x.cpu().numpy())
+    assert np.linalg.norm(rt) <= 1.5 * rtol * np.linalg.norm(b)
+
+
+def test_ert_small_gn_step():
+    """A 32^3 ERT step (analytic half-space sensitivities, 8 line electrodes):
+    b from Eq. 2.9, solution vs the oracle's PCG."""
+    pr = inputs.ert_problem(32, n_e_line=8, alpha=1e-3)
+    n = (32, 32, 32)
+    h = (pr.h,) * 3
+    A = disc.regularization_operator("fv", n, h)
+    dm = pr.logsigma - pr.m_ref
+    b_ref = wb.gn_rhs(A, pr.alpha, dm, pr.J, pr.d)
+    H = mg.build_hierarchy("fv", n, h)
+    P = wb.WoodburyPreconditioner(lambda v: mg.vcycle(H, v), pr.J, pr.alpha)
+    x_ref, it_ref, _ = wb.pcg(lambda v: wb.apply_operator(A, pr.alpha, pr.J, v), P, b_ref, 1e-10, 300)
+    S = _gpu("fv", n, h, pr.alpha, pr.J.shape[0])
+    S.capacitance(_t(pr.J))
+    b = S.gn_rhs(_t(dm), _t(pr.d))
+    assert _rel(b.cpu().numpy(), b_ref) <= 1e-12
+    x, info = S.pcg(b, 1e-10, 300)
+    assert info.rel_res_true <= 1e-10
+    xg = x.cpu().numpy()
+    op = ccg.CsrOperator(A, pr.alpha, pr.J)
+    assert np.linalg.norm(b_ref - op.apply(xg)) <= 1.5e-10 * np.linalg.norm(b_ref)
+    # both iterates satisfy the same residual bound; their difference is at
+    # most cond(A) * rtol and is printed for the record
+    print("ert32: iters gpu/oracle", info.iters, it_ref, "rel diff", _rel(xg, x_ref))
+    assert abs(info.iters - it_ref) <= 2
+
+
+def test_status_codes():
+    d, n, h = _fv((16, 8, 12))
+    S = _gpu(d, n, h, 1e-2, 4)
+    b = torch.randn(S.N, dtype=torch.float64, device=DEV)
+    with pytest.raises(h1w.H1wError) as e:
+        S.pcg(b, 1e-8)
+    assert e.value.status == h1w.H1W_ESTATE
+    J = torch.randn(4, S.N, dtype=torch.float64, device=DEV) / S.N ** 0.5
+    S.capacitance(J)
+    x, info = S.pcg(b, 1e-14, maxit=1, raise_on_notconv=False)
+    assert info.iters == 1 and info.rel_res_true > 1e-14
+    with pytest.raises(h1w.H1wError) as e:
+        S.pcg(b, 1e-14, maxit=1)
+    assert e.value.status == h1w.H1W_ENOTCONV
+    with pytest.raises(h1w.H1wError) as e:
+        h1w.h1w_capacitance(S.ctx, 5, torch.zeros(5 * S.N, dtype=torch.float64, device=DEV), S.N)
+    assert e.value.status == h1w.H1W_EINVAL
+    g = h1w.make_grid(h1w.H1W_FV_CELL, n, h, 1e-2)
+    small = torch.empty(1024, dtype=torch.uint8, device=DEV)
+    with pytest.raises(h1w.H1wError) as e:
+        h1w.h1w_setup(g, 4, None, small)
+    assert e.value.status == h1w.H1W_ENOMEM
+    bad = h1w.make_grid(h1w.H1W_FV_CELL, (33, 33, 33), (1 / 33,) * 3, 1e-2)
+    with pytest.raises(h1w.H1wError) as e:
+        h1w.h1w_setup(bad, 4, None, torch.empty(1 << 20, dtype=torch.uint8, device=DEV))
+    assert e.value.status == h1w.H1W_EUNSUPPORTED
+    # zero right-hand side: x = 0, no iterations
+    x, info = S.pcg(torch.zeros_like(b), 1e-8)
+    assert info.iters == 0 and float(x.abs().max()) == 0.0
