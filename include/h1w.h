@@ -155,6 +155,32 @@ h1w_status h1w_get_timings(const h1w_ctx* ctx, h1w_timings* out);
 /* Number of multigrid levels and the grid size of level `level` (n[3]). */
 h1w_status h1w_level_info(const h1w_ctx* ctx, int32_t level, int32_t* nlevels, int32_t* n);
 
+/* q = alpha (K + M) p + J^T (J p), like h1w_apply_op, for callers that cannot
+ * allocate device memory: code whose memory belongs to another allocator (a
+ * framework's caching pool or a fixed arena) and that must not call
+ * cudaMalloc itself, since cudaMalloc synchronizes the device and takes
+ * memory outside that budget. The paper has no counterpart; it is a service
+ * of this library. No context and no workspace: the grid (fine level only)
+ * is passed directly, and the scratch (partial sums of J p, J p itself and
+ * the Q1 element coefficients) lives in one file-scope __device__ array of
+ * 2^20 doubles (8 MiB) that every GPU loading this library holds until the
+ * process exits. Calls needing more scratch than that, i.e.
+ *   32*ceil(ceil(N/4096)*m/32) + 32*ceil(max(m,1)/32) + [Q1] 6*(nx+ny)
+ * doubles, return H1W_EINVAL; use h1w_setup with a workspace for those.
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine). The first call on each device, with that device current, looks
+ * up the array's device address once; make that first call before any
+ * stream capture. All calls on a device share the one array, and it keeps
+ * the last call's contents (every value is written before it is read, so
+ * nothing needs clearing): calls that overlap on the GPU, e.g. on two
+ * streams, race and must be serialized by the caller. Arguments: grid as in
+ * h1w_setup; J (m x N row-major), p, q (N entries) are DEVICE pointers of
+ * the current device, p and q distinct; stream is a cudaStream_t (NULL =
+ * legacy default stream). Asynchronous; errors of the launch are returned,
+ * with text in h1w_last_error(NULL). */
+h1w_status h1w_apply_op_static(const h1w_grid* grid, int32_t m, const double* J, const double* p,
+                               double* q, void* stream);
+
 /* Text of the last error on this context (ctx = NULL: the last error of
  * h1w_setup on this thread). Never NULL. */
 const char* h1w_last_error(const h1w_ctx* ctx);

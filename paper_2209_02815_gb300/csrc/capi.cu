@@ -79,6 +79,15 @@ struct h1w_ctx {
 
 namespace {
 
+}  // namespace
+
+h1w_status h1w::set_global_error(h1w_status st, const std::string& msg) {
+  g_setup_error = msg;
+  return st;
+}
+
+namespace {
+
 h1w_status fail(h1w_ctx* c, h1w_status st, const std::string& msg) {
   if (c) c->err = msg;
   else g_setup_error = msg;

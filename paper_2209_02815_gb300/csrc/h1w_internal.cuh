@@ -41,6 +41,9 @@ struct ChebCoef {
 extern std::atomic<long long> g_kernel_launches;
 inline void note_launches(int k) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
 
+// Records msg as the thread's last error (h1w_last_error(NULL)) and returns st.
+h1w_status set_global_error(h1w_status st, const std::string& msg);
+
 // Device status word bits (written by kernels, read back by the host).
 enum : int { kStatusNotSpd = 1 };
 

@@ -81,6 +81,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "h1w_capacitance_factors": (I32, [P, P, P]),
         "h1w_level_info": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "h1w_get_timings": (I32, [P, ctypes.POINTER(Timings)]),
+        "h1w_apply_op_static": (I32, [G, I32, P, P, P, P]),
         "h1w_last_error": (ctypes.c_char_p, [P]),
         "h1w_destroy": (None, [P]),
     }
@@ -199,6 +200,14 @@ def h1w_get_timings(ctx) -> Timings:
     t = Timings()
     _check(load().h1w_get_timings(ctx, ctypes.byref(t)), ctx)
     return t
+
+
+def h1w_apply_op_static(grid: Grid, m: int, J: torch.Tensor | None, p: torch.Tensor, q: torch.Tensor,
+                        N: int, stream: torch.cuda.Stream | None = None) -> None:
+    """Workspace-free operator apply (scratch in a fixed device array)."""
+    s = (stream or torch.cuda.current_stream(p.device)).cuda_stream
+    _check(load().h1w_apply_op_static(ctypes.byref(grid), int(m), _ptr(J, m * N, "J") if m > 0 else None,
+                                      _ptr(p, N, "p"), _ptr(q, N, "q"), s), None)
 
 
 def h1w_destroy(ctx) -> None:
