@@ -50,7 +50,7 @@ typedef enum {
   H1W_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
   H1W_ENOTCONV = 4,      /* PCG did not reach rtol within maxit (x holds the last iterate) */
   H1W_ENOTSPD = 5,       /* Cholesky met a non-positive pivot (capacitance or coarse matrix) */
-  H1W_ETIMEOUT = 6,      /* reserved: a bounded device wait ran out */
+  H1W_ETIMEOUT = 6,      /* a bounded device-side wait ran out (the kernel returned early) */
   H1W_EUNSUPPORTED = 7,  /* grid that the multigrid hierarchy cannot coarsen to <= 1024 unknowns */
   H1W_ESTATE = 8         /* call out of order (e.g. h1w_pcg before h1w_capacitance) */
 } h1w_status;
@@ -69,6 +69,10 @@ typedef struct {
   int32_t cheb_degree;   /* Chebyshev smoother degree per half-cycle (1..7, default 2) */
   int32_t rhs_block;     /* right-hand sides per batched V-cycle while building H (1..64, default 32) */
   int32_t max_restarts;  /* true-residual restarts allowed in h1w_pcg (default 3) */
+  int32_t cap_gemm;      /* line C: 0 = tensor cores on an exact BF16 digit split of the FP64
+                            operands (48-bit, default), 1 = FP64 CUDA cores */
+  int32_t mg_arith;      /* V-cycle arithmetic on FV grids: 0 = double-float (FP32 pairs, about
+                            48 bits, default), 1 = FP64. Q1 grids always use FP64. */
   int32_t reserved;      /* must be 0 */
 } h1w_options;
 
@@ -111,7 +115,11 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
 
 /* Lines H, C and chol of Algorithm "MINRES with the Laplace-Woodbury
  * preconditioner": H = L-hat^-1 J^T (m batched V-cycles), C = I + alpha^-1 J H
- * (formed from its upper triangle and mirrored), C = L L^T. J (m x N,
+ * (formed from its upper triangle and mirrored), C = L L^T. With
+ * cap_gemm = 0 the product J H^T runs on the tensor cores: each row of J
+ * and H is scaled by a power of two, rounded to 42 bits and written exactly
+ * as seven BF16 digits; digit products are accumulated exactly in FP32
+ * chunks and combined in FP64 (error below 2^-42 of the row maxima). J (m x N,
  * row-major, device) is borrowed: it must stay valid and unchanged until the
  * next h1w_capacitance or h1w_destroy. 0 <= m <= m_max; m = 0 gives the
  * Laplace-only preconditioner. Synchronizes; H1W_ENOTSPD if C is not

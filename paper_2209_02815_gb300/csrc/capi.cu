@@ -64,6 +64,8 @@ struct h1w_ctx {
   double* Lc;            // m_max x m_max
   double* gemm_partial;
   int64_t gemm_partial_len;
+  OzakiWork oz;                  // tensor-core capacitance buffers (cap_gemm = 0)
+  std::vector<int> oz_tiles_host;
   // Krylov vectors
   double *r, *z, *z0, *p, *q;
   double *svec, *jz, *w, *wtmp;
@@ -217,14 +219,20 @@ h1w_status validate(const h1w_grid* g, int32_t m_max, const h1w_options* o, std:
     if (o->cheb_degree < 1 || o->cheb_degree > 7) { why = "cheb_degree out of range [1, 7]"; return H1W_EINVAL; }
     if (o->rhs_block < 1 || o->rhs_block > 64) { why = "rhs_block out of range [1, 64]"; return H1W_EINVAL; }
     if (o->max_restarts < 0 || o->max_restarts > 100) { why = "max_restarts out of range"; return H1W_EINVAL; }
+    if (o->cap_gemm != 0 && o->cap_gemm != 1) { why = "cap_gemm must be 0 or 1"; return H1W_EINVAL; }
+    if (o->mg_arith != 0 && o->mg_arith != 1) { why = "mg_arith must be 0 or 1"; return H1W_EINVAL; }
     if (o->reserved != 0) { why = "reserved must be 0"; return H1W_EINVAL; }
   }
   return H1W_OK;
 }
 
-int64_t gemm_partial_len(int m_max, int64_t N) {
+int64_t gemm_partial_len(int m_max, int64_t N, bool ozaki) {
   int64_t best = 1;
-  for (int m = 1; m <= m_max; ++m) best = std::max(best, (int64_t)cap_gemm_splits(m, N) * m * m);
+  const long long kp = ozaki_panel_width(N);
+  for (int m = 1; m <= m_max; ++m) {
+    best = std::max(best, (int64_t)cap_gemm_splits(m, N) * m * m);
+    if (ozaki) best = std::max(best, (int64_t)ozaki_splits(m, kp) * m * m);
+  }
   return best;
 }
 
@@ -240,8 +248,8 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   LevelBufs bufs[kMaxLevels];
   for (int l = 0; l < P.nlev; ++l) {
     const int64_t Nl = (int64_t)P.n[l][0] * P.n[l][1] * P.n[l][2];
-    bufs[l].x = l ? B.take<double>(nb * Nl) : nullptr;
-    bufs[l].b = l ? B.take<double>(nb * Nl) : nullptr;
+    bufs[l].x = B.take<double>(nb * Nl);  // level 0: used by the double-float cycle
+    bufs[l].b = B.take<double>(nb * Nl);
     bufs[l].r = B.take<double>(nb * Nl);
     bufs[l].da = B.take<double>(nb * Nl);
     bufs[l].db = B.take<double>(nb * Nl);
@@ -255,8 +263,19 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   double* H = B.take<double>((int64_t)m_max * N0);
   double* C = B.take<double>((int64_t)m_max * m_max);
   double* Lc = B.take<double>((int64_t)m_max * m_max);
-  const int64_t gpl = gemm_partial_len(m_max, N0);
+  const bool oz = (o.cap_gemm == 0) && m_max > 0;
+  const int64_t gpl = gemm_partial_len(m_max, N0, oz);
   double* gp = B.take<double>(gpl);
+  const long long kp = ozaki_panel_width(N0);
+  OzakiWork ow{};
+  if (oz) {
+    ow.digitsA = B.take<uint16_t>((size_t)8 * ((m_max + 127) / 128 * 128) * kp);
+    ow.digitsB = B.take<uint16_t>((size_t)8 * ((m_max + 63) / 64 * 64) * kp);
+    ow.colexp = B.take<short>((size_t)N0);
+    ow.expo = B.take<int>(2 * (size_t)m_max);
+    ow.tiles = B.take<int>(2 * (size_t)ozaki_num_tiles(m_max));
+    ow.klen = kp;
+  }
   double* r = B.take<double>(N0);
   double* z = B.take<double>(N0);
   double* z0 = B.take<double>(N0);
@@ -275,6 +294,9 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
     for (int k = 0; k < P.nlev; ++k) c->buf[k] = bufs[k];
     c->coarse_X = cX; c->coarse_L = cL; c->dstatus = dstatus; c->dbits = dbits;
     c->H = H; c->C = C; c->Lc = Lc; c->gemm_partial = gp; c->gemm_partial_len = gpl;
+    c->oz = ow;
+    c->oz.partial = gp;
+    c->oz.status = dstatus;
     c->r = r; c->z = z; c->z0 = z0; c->p = p; c->q = q;
     c->svec = svec; c->jz = jz; c->w = w; c->wtmp = wtmp;
     c->partial = partial; c->partial_len = plen; c->scal = scal;
@@ -323,11 +345,52 @@ void vcycle_block(h1w_ctx* c, int nrhs, const double* b0, double* x0) {
   }
 }
 
+// ---- the same cycle in double-float arithmetic (FV grids) -------------------------
+
+inline df* dfp(double* p) { return reinterpret_cast<df*>(p); }
+
+void smooth_df(h1w_ctx* c, int l, int nrhs, bool zero_x) {
+  const Level& L = c->lev[l];
+  const ChebCoef& K = c->cheb[l];
+  df* x = dfp(c->buf[l].x);
+  df* r = dfp(c->buf[l].r);
+  df* da = dfp(c->buf[l].da);
+  df* db = dfp(c->buf[l].db);
+  launch_cheb_first_df(L, nrhs, dfp(c->buf[l].b), x, r, da, zero_x, K.inv_theta_df, c->stream);
+  bool pending = !zero_x;
+  for (int j = 1; j < c->opt.cheb_degree; ++j) {
+    launch_cheb_step_df(L, nrhs, r, da, db, x, K.c1_df[j], K.c2_df[j], pending, c->stream);
+    pending = false;
+    std::swap(da, db);
+  }
+  if (pending) launch_add_df((int64_t)nrhs * L.N, da, x, c->stream);
+}
+
+void vcycle_block_df(h1w_ctx* c, int nrhs, const double* b0, double* x0) {
+  const int nl = c->nlev;
+  const int64_t n0 = (int64_t)nrhs * c->lev[0].N;
+  launch_d2df(n0, b0, dfp(c->buf[0].b), c->stream);
+  for (int l = 0; l < nl - 1; ++l) {
+    smooth_df(c, l, nrhs, true);
+    launch_residual_df(c->lev[l], nrhs, dfp(c->buf[l].b), dfp(c->buf[l].x), dfp(c->buf[l].r), c->stream);
+    launch_restrict_df(c->lev[l], c->lev[l + 1], nrhs, dfp(c->buf[l].r), dfp(c->buf[l + 1].b), c->stream);
+  }
+  launch_coarse_apply_df(c->coarse_X, (int)c->lev[nl - 1].N, nrhs, dfp(c->buf[nl - 1].b), dfp(c->buf[nl - 1].x),
+                         c->stream);
+  for (int l = nl - 2; l >= 0; --l) {
+    launch_prolong_add_df(c->lev[l], c->lev[l + 1], nrhs, dfp(c->buf[l + 1].x), dfp(c->buf[l].x), c->stream);
+    smooth_df(c, l, nrhs, false);
+  }
+  launch_df2d(n0, dfp(c->buf[0].x), x0, c->stream);
+}
+
 void vcycle_many(h1w_ctx* c, int nrhs, const double* b, double* x) {
   const int64_t N = c->lev[0].N;
+  const bool use_df = (c->disc == H1W_FV_CELL) && (c->opt.mg_arith == 0);
   for (int r0 = 0; r0 < nrhs; r0 += c->opt.rhs_block) {
     const int nr = std::min(c->opt.rhs_block, nrhs - r0);
-    vcycle_block(c, nr, b + (int64_t)r0 * N, x + (int64_t)r0 * N);
+    if (use_df) vcycle_block_df(c, nr, b + (int64_t)r0 * N, x + (int64_t)r0 * N);
+    else vcycle_block(c, nr, b + (int64_t)r0 * N, x + (int64_t)r0 * N);
   }
 }
 
@@ -378,6 +441,8 @@ void h1w_default_options(h1w_options* opt) {
   opt->cheb_degree = 2;
   opt->rhs_block = 32;
   opt->max_restarts = 3;
+  opt->cap_gemm = 0;
+  opt->mg_arith = 0;
   opt->reserved = 0;
 }
 
@@ -436,6 +501,19 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
     if (c->disc == H1W_FV_CELL) {
       const double hx = P.h[l][0], hy = P.h[l][1], hz = P.h[l][2];
       L.Tx = hy * hz / hx; L.Ty = hx * hz / hy; L.Tz = hx * hy / hz; L.V = hx * hy * hz;
+      L.iso = (L.Tx == L.Ty && L.Ty == L.Tz) ? 1 : 0;
+      for (int cz = 0; cz < 3; ++cz)
+        for (int cy = 0; cy < 3; ++cy)
+          for (int cx = 0; cx < 3; ++cx) {
+            const double dg = L.V + L.Tx * cx + L.Ty * cy + L.Tz * cz;
+            L.fv_diag[cx + 3 * cy + 9 * cz] = dg;
+            L.fv_dinv[cx + 3 * cy + 9 * cz] = 1.0 / dg;
+            L.fvd_diag[cx + 3 * cy + 9 * cz] = df_host(dg);
+            L.fvd_dinv[cx + 3 * cy + 9 * cz] = df_host(1.0 / dg);
+          }
+      L.fvd_T[0] = df_host(L.Tx);
+      L.fvd_T[1] = df_host(L.Ty);
+      L.fvd_T[2] = df_host(L.Tz);
     } else {
       for (int a = 0; a < 2; ++a) {
         if (l == 0) q1_fine_1d(P.n[0][a], grid->h[a], c->qhost[0][a]);
@@ -470,11 +548,14 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
     ChebCoef& K = c->cheb[l];
     K.inv_theta = 1.0 / theta;
+    K.inv_theta_df = df_host(K.inv_theta);
     double rho_prev = 1.0 / sigma;
     for (int j = 1; j < o.cheb_degree; ++j) {
       const double rho = 1.0 / (2.0 * sigma - rho_prev);
       K.c1[j] = rho * rho_prev;
       K.c2[j] = 2.0 * rho / delta;
+      K.c1_df[j] = df_host(K.c1[j]);
+      K.c2_df[j] = df_host(K.c2[j]);
       rho_prev = rho;
     }
   }
@@ -520,12 +601,23 @@ h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
   if (c->have_ev) cudaEventRecord(c->ev[0], c->stream);
   vcycle_many(c, m, J, c->H);                                       // line H
   if (c->have_ev) cudaEventRecord(c->ev[1], c->stream);
-  const int splits = cap_gemm_splits(m, N);
-  launch_cap_gemm(J, c->H, m, N, c->gemm_partial, splits, c->stream);  // line C
+  cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
+  int splits = 0;
+  if (c->opt.cap_gemm == 0) {                                       // line C, tensor cores
+    if (!ozaki_supported()) return fail(c, H1W_EUNSUPPORTED, "tensor-core capacitance GEMM needs sm_100-class GPU");
+    ozaki_tiles(m, c->oz_tiles_host);
+    cudaMemcpyAsync(c->oz.tiles, c->oz_tiles_host.data(), sizeof(int) * c->oz_tiles_host.size(),
+                    cudaMemcpyHostToDevice, c->stream);
+    splits = ozaki_splits(m, c->oz.klen);
+    if (!launch_ozaki_capacitance(J, c->H, m, N, c->oz, splits, c->stream))
+      return fail(c, H1W_ECUDA, "capacitance: tensor map encoding or kernel attribute failed");
+  } else {                                                          // line C, FP64 CUDA cores
+    splits = cap_gemm_splits(m, N);
+    launch_cap_gemm(J, c->H, m, N, c->gemm_partial, splits, c->stream);
+  }
   if (c->have_ev) cudaEventRecord(c->ev[2], c->stream);
   launch_cap_finalize(c->gemm_partial, splits, m, c->grid.alpha, c->C, c->stream);
   cudaMemcpyAsync(c->Lc, c->C, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, c->stream);
-  cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
   launch_chol(c->Lc, m, c->dstatus, c->stream);                    // line chol
   if (c->have_ev) cudaEventRecord(c->ev[3], c->stream);
   c->launches_cap = g_kernel_launches.load() - l0;
@@ -535,6 +627,10 @@ h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
   if (e != cudaSuccess) return fail(c, H1W_ECUDA, std::string("capacitance: ") + cudaGetErrorString(e));
   h1w_status st = cuda_check(c, "capacitance");
   if (st != H1W_OK) return st;
+  if (status & kStatusTimeout) {
+    c->m = -1;
+    return fail(c, H1W_ETIMEOUT, "capacitance GEMM: a bounded device wait ran out");
+  }
   if (status & kStatusNotSpd) {
     c->m = -1;
     return fail(c, H1W_ENOTSPD, "capacitance matrix is not numerically positive definite");

@@ -6,7 +6,9 @@
 #include <atomic>
 #include <cstdint>
 #include <string>
+#include <vector>
 
+#include "df64.cuh"
 #include "h1w.h"
 
 namespace h1w {
@@ -29,12 +31,21 @@ struct Level {
   const double* qy;              // Q1 y-axis coefficients [6][ny] (device)
   double lam;                    // upper bound of spec(D^-1 A) (Gershgorin)
   int cx, cy, cz;                // axis coarsened towards the next level
+  int iso;                       // FV with Tx == Ty == Tz
+  // FV diagonal and its inverse by neighbour counts (cx + 3 cy + 9 cz, each 0..2)
+  double fv_diag[27];
+  double fv_dinv[27];
+  // the same FV coefficients as double-floats (double-float V-cycle)
+  df fvd_diag[27];
+  df fvd_dinv[27];
+  df fvd_T[3];
 };
 
 struct ChebCoef {
   double inv_theta;   // 1 / theta
   double c1[8];       // rho_j rho_{j-1} for step j (1-based; index 0 unused)
   double c2[8];       // 2 rho_j / delta
+  df inv_theta_df, c1_df[8], c2_df[8];  // the same as double-floats
 };
 
 // Kernels launched by this library in this process (every launcher adds its count).
@@ -45,7 +56,26 @@ inline void note_launches(int k) { g_kernel_launches.fetch_add(k, std::memory_or
 h1w_status set_global_error(h1w_status st, const std::string& msg);
 
 // Device status word bits (written by kernels, read back by the host).
-enum : int { kStatusNotSpd = 1 };
+enum : int { kStatusNotSpd = 1, kStatusTimeout = 2 };
+
+// Device buffers of the tensor-core capacitance GEMM (ozaki_gemm.cu).
+struct OzakiWork {
+  void* digitsA;                 // BF16 digits of a K panel of J, stage-tiled (128-row blocks)
+  void* digitsB;                 // BF16 digits of the same panel of H, stage-tiled (64-row blocks)
+  short* colexp;                 // [N] column balance exponents s_k
+  int* expo;                     // [2m] row exponents of the balanced J, then H
+  int* tiles;                    // [2 * tiles] (row block, column block)
+  double* partial;               // [splits][m][m]
+  int* status;                   // device status word
+  long long klen;                // K panel width (multiple of 2048)
+};
+long long ozaki_panel_width(long long N);
+int ozaki_num_tiles(int m);
+int ozaki_splits(int m, long long kp);
+bool ozaki_supported();
+bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long N, const OzakiWork& w,
+                              int splits, cudaStream_t s);
+void ozaki_tiles(int m, std::vector<int>& out);
 
 // ---- kernel launchers (mg_kernels.cu) --------------------------------------
 // r = b - A x (r = b when zero_x); d = D^-1 r / theta; x = d only when zero_x
@@ -68,6 +98,19 @@ void launch_apply_op(int disc, const Level& L, double ca, const double* p, doubl
                      const double* J, const double* w, int m, double* out, double* partial,
                      int* nblocks_out, cudaStream_t s);
 int apply_op_blocks(const Level& L);
+
+// ---- double-float V-cycle on FV grids (mg_df64.cu) ----------------------------
+void launch_cheb_first_df(const Level& L, int nrhs, const df* b, df* x, df* r, df* d, bool zero_x, df inv_theta,
+                          cudaStream_t s);
+void launch_cheb_step_df(const Level& L, int nrhs, df* r, const df* d_old, df* d_new, df* x, df c1, df c2,
+                         bool add_old, cudaStream_t s);
+void launch_add_df(int64_t n, const df* d, df* x, cudaStream_t s);
+void launch_residual_df(const Level& L, int nrhs, const df* b, const df* x, df* r, cudaStream_t s);
+void launch_restrict_df(const Level& Lf, const Level& Lc, int nrhs, const df* rf, df* bc, cudaStream_t s);
+void launch_prolong_add_df(const Level& Lf, const Level& Lc, int nrhs, const df* xc, df* xf, cudaStream_t s);
+void launch_coarse_apply_df(const double* X, int n, int nrhs, const df* b, df* x, cudaStream_t s);
+void launch_d2df(int64_t n, const double* src, df* dst, cudaStream_t s);
+void launch_df2d(int64_t n, const df* src, double* dst, cudaStream_t s);
 
 // ---- dense / Krylov kernels (dense_kernels.cu) ------------------------------
 // partial[c * m + i] = sum_{k in chunk c} A[i * lda + k] v[k]

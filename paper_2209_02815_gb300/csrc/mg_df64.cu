@@ -1,0 +1,260 @@
+// The V-cycle on FV grids in double-float arithmetic (FP32 pairs, ~48 bits).
+//
+// The V-cycle is a preconditioner: it must be a fixed, symmetric-to-rounding
+// operator that builds H = L-hat^-1 J^T and is applied again inside PCG, but
+// it need not be FP64. On GB300 the FP64 version is bound by the FP64 pipe
+// (1/64 of the FP32 rate). Here every level vector is stored as a
+// double-float (8 bytes, like FP64) and every operation runs on the FP32
+// pipes with error-free transformations (df64.cuh), so the kernels become
+// bound by memory traffic instead. The operator is the same one the FP64
+// kernels (mg_kernels.cu) and the oracle apply: 7-point FV operator, degree-k
+// Chebyshev-Jacobi smoothing, cell-centred trilinear transfer with R = P^T,
+// dense coarsest solve (kept in FP64).
+#include "df64.cuh"
+#include "h1w_internal.cuh"
+
+namespace h1w {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int fv_cls(const Level& L, int i, int j, int k) {
+  return ((i > 0) + (i < L.nx - 1)) + 3 * ((j > 0) + (j < L.ny - 1)) + 9 * ((k > 0) + (k < L.nz - 1));
+}
+
+__device__ __forceinline__ void decompose(const Level& L, int64_t p, int& i, int& j, int& k) {
+  i = (int)(p % L.nx);
+  const int64_t t = p / L.nx;
+  j = (int)(t % L.ny);
+  k = (int)(t / L.ny);
+}
+
+__device__ __forceinline__ df dzero() { return df_make(0.f, 0.f); }
+
+// (A u)_p for the FV operator, class c = fv_cls(i, j, k)
+__device__ __forceinline__ df fv_apply_df(const Level& L, const df* __restrict__ u, int i, int j, int k,
+                                          int64_t p, int c) {
+  const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny;
+  if (L.iso) {
+    df s = dzero();
+    if (i > 0) s = df_add(s, u[p - 1]);
+    if (i < L.nx - 1) s = df_add(s, u[p + 1]);
+    if (j > 0) s = df_add(s, u[p - sy]);
+    if (j < L.ny - 1) s = df_add(s, u[p + sy]);
+    if (k > 0) s = df_add(s, u[p - sz]);
+    if (k < L.nz - 1) s = df_add(s, u[p + sz]);
+    return df_sub(df_mul(L.fvd_diag[c], u[p]), df_mul(L.fvd_T[0], s));
+  }
+  df sx = dzero(), syy = dzero(), szz = dzero();
+  if (i > 0) sx = df_add(sx, u[p - 1]);
+  if (i < L.nx - 1) sx = df_add(sx, u[p + 1]);
+  if (j > 0) syy = df_add(syy, u[p - sy]);
+  if (j < L.ny - 1) syy = df_add(syy, u[p + sy]);
+  if (k > 0) szz = df_add(szz, u[p - sz]);
+  if (k < L.nz - 1) szz = df_add(szz, u[p + sz]);
+  df a = df_mul(L.fvd_diag[c], u[p]);
+  a = df_sub(a, df_mul(L.fvd_T[0], sx));
+  a = df_sub(a, df_mul(L.fvd_T[1], syy));
+  return df_sub(a, df_mul(L.fvd_T[2], szz));
+}
+
+__global__ void k_cheb_first_df(Level L, const df* __restrict__ b, df* __restrict__ x, df* __restrict__ r,
+                                df* __restrict__ d, int zero_x, df inv_theta) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  const int64_t off = (int64_t)blockIdx.y * L.N;
+  int i, j, k;
+  decompose(L, p, i, j, k);
+  const int c = fv_cls(L, i, j, k);
+  df rv = b[off + p];
+  if (!zero_x) rv = df_sub(rv, fv_apply_df(L, x + off, i, j, k, p, c));
+  const df dv = df_mul(df_mul(rv, L.fvd_dinv[c]), inv_theta);
+  r[off + p] = rv;
+  d[off + p] = dv;
+  if (zero_x) x[off + p] = dv;  // otherwise x is read by neighbours; the next step adds d
+}
+
+__global__ void k_cheb_step_df(Level L, df* __restrict__ r, const df* __restrict__ d_old, df* __restrict__ d_new,
+                               df* __restrict__ x, df c1, df c2, int add_old) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  const int64_t off = (int64_t)blockIdx.y * L.N;
+  int i, j, k;
+  decompose(L, p, i, j, k);
+  const int c = fv_cls(L, i, j, k);
+  const df dold = d_old[off + p];
+  const df rv = df_sub(r[off + p], fv_apply_df(L, d_old + off, i, j, k, p, c));
+  const df dv = df_add(df_mul(c1, dold), df_mul(c2, df_mul(rv, L.fvd_dinv[c])));
+  r[off + p] = rv;
+  d_new[off + p] = dv;
+  x[off + p] = df_add(x[off + p], add_old ? df_add(dold, dv) : dv);
+}
+
+__global__ void k_add_df(int64_t n, const df* __restrict__ d, df* __restrict__ x) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) x[p] = df_add(x[p], d[p]);
+}
+
+__global__ void k_residual_df(Level L, const df* __restrict__ b, const df* __restrict__ x, df* __restrict__ r) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  const int64_t off = (int64_t)blockIdx.y * L.N;
+  int i, j, k;
+  decompose(L, p, i, j, k);
+  r[off + p] = df_sub(b[off + p], fv_apply_df(L, x + off, i, j, k, p, fv_cls(L, i, j, k)));
+}
+
+// FV 1D transfer weights (rows of P^T and of P), as in mg_kernels.cu
+__device__ __forceinline__ int fv_restrict_1d(int I, int nc, int coarsened, int* f, float* w) {
+  if (!coarsened) { f[0] = I; w[0] = 1.f; return 1; }
+  int c = 0;
+  if (I >= 1) { f[c] = 2 * I - 1; w[c++] = 0.25f; }
+  f[c] = 2 * I;     w[c++] = (I >= 1) ? 0.75f : 1.f;
+  f[c] = 2 * I + 1; w[c++] = (I + 1 < nc) ? 0.75f : 1.f;
+  if (I + 1 < nc) { f[c] = 2 * I + 2; w[c++] = 0.25f; }
+  return c;
+}
+
+__device__ __forceinline__ int fv_prolong_1d(int i, int nc, int coarsened, int* f, float* w) {
+  if (!coarsened) { f[0] = i; w[0] = 1.f; return 1; }
+  const int I = i >> 1;
+  const int J = (i & 1) ? I + 1 : I - 1;
+  if (J >= 0 && J < nc) { f[0] = I; w[0] = 0.75f; f[1] = J; w[1] = 0.25f; return 2; }
+  f[0] = I; w[0] = 1.f;
+  return 1;
+}
+
+__global__ void k_restrict_df(Level Lf, Level Lc, const df* __restrict__ rf, df* __restrict__ bc) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Lc.N) return;
+  const df* r = rf + (int64_t)blockIdx.y * Lf.N;
+  int I, J, K;
+  decompose(Lc, p, I, J, K);
+  int fx[4], fy[4], fz[4];
+  float wx[4], wy[4], wz[4];
+  const int nx_ = fv_restrict_1d(I, Lc.nx, Lf.cx, fx, wx);
+  const int ny_ = fv_restrict_1d(J, Lc.ny, Lf.cy, fy, wy);
+  const int nz_ = fv_restrict_1d(K, Lc.nz, Lf.cz, fz, wz);
+  df acc = dzero();
+  for (int c = 0; c < nz_; ++c) {
+    df sz = dzero();
+    for (int b = 0; b < ny_; ++b) {
+      const df* row = r + ((int64_t)fz[c] * Lf.ny + fy[b]) * Lf.nx;
+      df sx = dzero();
+      for (int a = 0; a < nx_; ++a) sx = df_add(sx, df_mul_f(row[fx[a]], wx[a]));
+      sz = df_add(sz, df_mul_f(sx, wy[b]));
+    }
+    acc = df_add(acc, df_mul_f(sz, wz[c]));
+  }
+  bc[(int64_t)blockIdx.y * Lc.N + p] = acc;
+}
+
+__global__ void k_prolong_add_df(Level Lf, Level Lc, const df* __restrict__ xc, df* __restrict__ xf) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Lf.N) return;
+  const df* c = xc + (int64_t)blockIdx.y * Lc.N;
+  int i, j, k;
+  decompose(Lf, p, i, j, k);
+  int fx[2], fy[2], fz[2];
+  float wx[2], wy[2], wz[2];
+  const int nx_ = fv_prolong_1d(i, Lc.nx, Lf.cx, fx, wx);
+  const int ny_ = fv_prolong_1d(j, Lc.ny, Lf.cy, fy, wy);
+  const int nz_ = fv_prolong_1d(k, Lc.nz, Lf.cz, fz, wz);
+  df acc = dzero();
+  for (int cc = 0; cc < nz_; ++cc) {
+    df sz = dzero();
+    for (int b = 0; b < ny_; ++b) {
+      const df* row = c + ((int64_t)fz[cc] * Lc.ny + fy[b]) * Lc.nx;
+      df sx = dzero();
+      for (int a = 0; a < nx_; ++a) sx = df_add(sx, df_mul_f(row[fx[a]], wx[a]));
+      sz = df_add(sz, df_mul_f(sx, wy[b]));
+    }
+    acc = df_add(acc, df_mul_f(sz, wz[cc]));
+  }
+  const int64_t q = (int64_t)blockIdx.y * Lf.N + p;
+  xf[q] = df_add(xf[q], acc);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// x[r] = X b[r] with the FP64 dense inverse of the coarsest operator; one warp per (row, rhs)
+__global__ void k_coarse_apply_df(const double* __restrict__ X, int n, const df* __restrict__ b,
+                                  df* __restrict__ x) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const df* br = b + (int64_t)blockIdx.y * n;
+  const double* xr = X + (int64_t)row * n;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s += xr[j] * df_to_double(br[j]);
+  s = warp_sum(s);
+  if (lane == 0) x[(int64_t)blockIdx.y * n + row] = df_from_double(s);
+}
+
+__global__ void k_d2df(int64_t n, const double* __restrict__ src, df* __restrict__ dst) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) dst[p] = df_from_double(src[p]);
+}
+
+__global__ void k_df2d(int64_t n, const df* __restrict__ src, double* __restrict__ dst) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) dst[p] = df_to_double(src[p]);
+}
+
+inline dim3 grid_for(int64_t N, int nrhs) { return dim3((unsigned)((N + kThreads - 1) / kThreads), (unsigned)nrhs); }
+inline unsigned nblk(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+void launch_cheb_first_df(const Level& L, int nrhs, const df* b, df* x, df* r, df* d, bool zero_x, df inv_theta,
+                          cudaStream_t s) {
+  k_cheb_first_df<<<grid_for(L.N, nrhs), kThreads, 0, s>>>(L, b, x, r, d, zero_x ? 1 : 0, inv_theta);
+  note_launches(1);
+}
+
+void launch_cheb_step_df(const Level& L, int nrhs, df* r, const df* d_old, df* d_new, df* x, df c1, df c2,
+                         bool add_old, cudaStream_t s) {
+  k_cheb_step_df<<<grid_for(L.N, nrhs), kThreads, 0, s>>>(L, r, d_old, d_new, x, c1, c2, add_old ? 1 : 0);
+  note_launches(1);
+}
+
+void launch_add_df(int64_t n, const df* d, df* x, cudaStream_t s) {
+  k_add_df<<<nblk(n), kThreads, 0, s>>>(n, d, x);
+  note_launches(1);
+}
+
+void launch_residual_df(const Level& L, int nrhs, const df* b, const df* x, df* r, cudaStream_t s) {
+  k_residual_df<<<grid_for(L.N, nrhs), kThreads, 0, s>>>(L, b, x, r);
+  note_launches(1);
+}
+
+void launch_restrict_df(const Level& Lf, const Level& Lc, int nrhs, const df* rf, df* bc, cudaStream_t s) {
+  k_restrict_df<<<grid_for(Lc.N, nrhs), kThreads, 0, s>>>(Lf, Lc, rf, bc);
+  note_launches(1);
+}
+
+void launch_prolong_add_df(const Level& Lf, const Level& Lc, int nrhs, const df* xc, df* xf, cudaStream_t s) {
+  k_prolong_add_df<<<grid_for(Lf.N, nrhs), kThreads, 0, s>>>(Lf, Lc, xc, xf);
+  note_launches(1);
+}
+
+void launch_coarse_apply_df(const double* X, int n, int nrhs, const df* b, df* x, cudaStream_t s) {
+  k_coarse_apply_df<<<dim3((unsigned)((n + 7) / 8), nrhs), 256, 0, s>>>(X, n, b, x);
+  note_launches(1);
+}
+
+void launch_d2df(int64_t n, const double* src, df* dst, cudaStream_t s) {
+  k_d2df<<<nblk(n), kThreads, 0, s>>>(n, src, dst);
+  note_launches(1);
+}
+
+void launch_df2d(int64_t n, const df* src, double* dst, cudaStream_t s) {
+  k_df2d<<<nblk(n), kThreads, 0, s>>>(n, src, dst);
+  note_launches(1);
+}
+
+}  // namespace h1w

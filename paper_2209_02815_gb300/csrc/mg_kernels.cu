@@ -30,16 +30,28 @@ __device__ __forceinline__ double tri(const double* q, int n, int t, int i, int 
 
 struct FV {
   static constexpr int kDisc = H1W_FV_CELL;
-  __device__ static double diag(const Level& L, int i, int j, int k) {
-    const int cx = (i > 0) + (i < L.nx - 1);
-    const int cy = (j > 0) + (j < L.ny - 1);
-    const int cz = (k > 0) + (k < L.nz - 1);
-    return L.V + L.Tx * cx + L.Ty * cy + L.Tz * cz;
+  __device__ static int cls(const Level& L, int i, int j, int k) {
+    return ((i > 0) + (i < L.nx - 1)) + 3 * ((j > 0) + (j < L.ny - 1)) + 9 * ((k > 0) + (k < L.nz - 1));
   }
-  // returns (A u)_p and the diagonal A_pp
+  __device__ static double diag(const Level& L, int i, int j, int k) { return L.fv_diag[cls(L, i, j, k)]; }
+  __device__ static double dinv(const Level& L, int i, int j, int k) { return L.fv_dinv[cls(L, i, j, k)]; }
+  // returns (A u)_p; dg and di receive the diagonal A_pp and its inverse
   __device__ static double apply(const Level& L, const double* u, int i, int j, int k, int64_t p,
-                                 double& dg) {
+                                 double& dg, double& di) {
     const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny;
+    const int c = cls(L, i, j, k);
+    dg = L.fv_diag[c];
+    di = L.fv_dinv[c];
+    if (L.iso) {
+      double s = 0.0;
+      if (i > 0) s += u[p - 1];
+      if (i < L.nx - 1) s += u[p + 1];
+      if (j > 0) s += u[p - sy];
+      if (j < L.ny - 1) s += u[p + sy];
+      if (k > 0) s += u[p - sz];
+      if (k < L.nz - 1) s += u[p + sz];
+      return dg * u[p] - L.Tx * s;
+    }
     double sx_ = 0.0, sy_ = 0.0, sz_ = 0.0;
     if (i > 0) sx_ += u[p - 1];
     if (i < L.nx - 1) sx_ += u[p + 1];
@@ -47,8 +59,12 @@ struct FV {
     if (j < L.ny - 1) sy_ += u[p + sy];
     if (k > 0) sz_ += u[p - sz];
     if (k < L.nz - 1) sz_ += u[p + sz];
-    dg = diag(L, i, j, k);
     return dg * u[p] - L.Tx * sx_ - L.Ty * sy_ - L.Tz * sz_;
+  }
+  __device__ static double apply(const Level& L, const double* u, int i, int j, int k, int64_t p,
+                                 double& dg) {
+    double di;
+    return apply(L, u, i, j, k, p, dg, di);
   }
   __device__ static double gersh(const Level& L, int i, int j, int k) {
     const double d = diag(L, i, j, k);
@@ -62,6 +78,13 @@ struct Q1 {
     return tri(L.qx, L.nx, 0, i, 0) * tri(L.qy, L.ny, 1, j, 0) +
            tri(L.qx, L.nx, 1, i, 0) * tri(L.qy, L.ny, 0, j, 0) +
            tri(L.qx, L.nx, 2, i, 0) * tri(L.qy, L.ny, 2, j, 0);
+  }
+  __device__ static double dinv(const Level& L, int i, int j, int k) { return 1.0 / diag(L, i, j, k); }
+  __device__ static double apply(const Level& L, const double* u, int i, int j, int k, int64_t p,
+                                 double& dg, double& di) {
+    const double a = apply(L, u, i, j, k, p, dg);
+    di = 1.0 / dg;
+    return a;
   }
   __device__ static double apply(const Level& L, const double* u, int i, int j, int, int64_t p,
                                  double& dg) {
@@ -118,15 +141,15 @@ __global__ void k_cheb_first(Level L, const double* __restrict__ b, double* __re
   const int64_t off = (int64_t)blockIdx.y * L.N;
   int i, j, k;
   decompose(L, p, i, j, k);
-  double dg, rv;
+  double dg, di, rv;
   if (zero_x) {
-    dg = D::diag(L, i, j, k);
+    di = D::dinv(L, i, j, k);
     rv = b[off + p];
   } else {
-    const double ax = D::apply(L, x + off, i, j, k, p, dg);
+    const double ax = D::apply(L, x + off, i, j, k, p, dg, di);
     rv = b[off + p] - ax;
   }
-  const double dv = rv / dg * inv_theta;
+  const double dv = rv * di * inv_theta;
   r[off + p] = rv;
   d[off + p] = dv;
   // x is read through the stencil by neighbouring threads, so it is only
@@ -144,10 +167,10 @@ __global__ void k_cheb_step(Level L, double* __restrict__ r, const double* __res
   const int64_t off = (int64_t)blockIdx.y * L.N;
   int i, j, k;
   decompose(L, p, i, j, k);
-  double dg;
-  const double ad = D::apply(L, d_old + off, i, j, k, p, dg);
+  double dg, di;
+  const double ad = D::apply(L, d_old + off, i, j, k, p, dg, di);
   const double rv = r[off + p] - ad;
-  const double dv = c1 * d_old[off + p] + c2 * rv / dg;
+  const double dv = c1 * d_old[off + p] + c2 * (rv * di);
   r[off + p] = rv;
   d_new[off + p] = dv;
   x[off + p] += add_old ? d_old[off + p] + dv : dv;

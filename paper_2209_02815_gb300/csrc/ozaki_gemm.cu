@@ -1,0 +1,511 @@
+// Capacitance GEMM C = I + alpha^-1 J H^T (line C of Algorithm "MINRES with
+// the Laplace-Woodbury preconditioner") on the tcgen05 tensor cores with an
+// error-free split of the FP64 operands.
+//
+// GB300 runs FP64 at 1/64 of the FP32 rate, so the FP64 GEMM is slow, and C
+// needs more than single precision: its eigenvalues reach ~1e9, and an
+// absolute error of order one in C makes the Woodbury preconditioner
+// indefinite (errors of 1e-2 already cost PCG iterations on the ERT
+// workloads). The operands are therefore written exactly as sums of BF16
+// "digits" and multiplied digit by digit on the tensor cores, with every
+// FP32 accumulation kept exact:
+//
+//  * Column balancing: column k of J is scaled by 2^s_k and column k of H by
+//    2^-s_k (exact; J H^T is unchanged), s_k = floor((b_k - a_k) / 2) from
+//    the binary exponents a_k, b_k of the column maxima, so that peaked
+//    sensitivity columns do not dominate their rows.
+//  * Row scaling: row i of the balanced J (or H) has an exponent e_i with
+//    max_k |x_ik| < 2^e_i. Each entry becomes the integer
+//    Y = round(x 2^(47 - e_i)), |Y| <= 2^47, written in balanced base 64 as
+//    eight digits Y = sum_p d_p 64^(7-p), d_p in [-32, 32]; each digit is
+//    exact in BF16. The rounding error is at most 2^-48 of the row maximum.
+//  * Digit products d_p d'_q (|.| <= 2^10) of the same level l = p + q are
+//    summed into one FP32 TMEM accumulator (64 columns per level); pairs with
+//    p + q > 7 (weight below 2^-48) are dropped, leaving 36 pairs in 8 levels,
+//    issued as 12 MMAs per 16-wide K step (digit p of J against a stack of
+//    consecutive digits of H lands on consecutive levels). Over a chunk of
+//    1024 K entries a level sum is an integer below 8 * 1024 * 2^10 = 2^23,
+//    so the FP32 accumulation is exact.
+//  * After every chunk the epilogue warps read the 8 level sums from TMEM,
+//    combine them exactly in 64-bit integers as T_hi = sum_{l<4} S_l 64^(3-l)
+//    and T_lo = sum_{l>=4} S_l 64^(7-l), and add 2^24 T_hi + T_lo to FP64
+//    accumulators. The tile result is
+//    sum_k x_ik y_jk ~= 2^(e_i + f_j - 52) * sum_chunks (2^24 T_hi + T_lo).
+//
+// Kernel layout: one CTA per (128 x 64 output tile, K range); warp 0 moves
+// all eight digit slices of both operands per 32-wide K stage with two bulk
+// copies (the digits are stored pre-swizzled in the stage's shared-memory
+// image; 64-byte swizzle, double buffered), warp 1 owns TMEM (512 columns = 8
+// levels x 64) and issues tcgen05.mma, warps 2..9 drain TMEM. Every
+// mbarrier wait is bounded (about one second); on expiry the CTA records
+// status bit kStatusTimeout, drains what it started and returns.
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "h1w_internal.cuh"
+
+namespace h1w {
+namespace {
+
+constexpr int kSlices = 8;
+constexpr int kLevels = 8;                 // p + q in 0..7
+constexpr int kTileM = 128;                // rows of J per tile (TMEM lanes)
+constexpr int kTileN = 64;                 // rows of H per tile (columns per level)
+constexpr int kKt = 32;                    // K per stage: 64-byte rows
+constexpr int kChunkK = 1024;              // K per exact accumulation chunk
+constexpr int kItersPerChunk = kChunkK / kKt;
+constexpr int kABytes = kSlices * kTileM * kKt * 2;   // 65536
+constexpr int kBBytes = kSlices * kTileN * kKt * 2;   // 32768
+constexpr int kStageBytes = kABytes + kBBytes;        // 98304
+constexpr int kStages = 2;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 128;
+constexpr int kGemmThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // one second per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the abort flag is set or about a second passes.
+__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(a, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (uint32_t n = 1;; ++n) {
+    if (mbar_try(a, parity)) return true;
+    if ((n & 255) == 0) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > kWaitNs) return false;
+    }
+  }
+}
+// 1D bulk copy global -> shared, completion counted on an mbarrier (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand with 64-byte swizzle: 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr & 0x3FFFF) >> 4) | (1ull << 16) | (static_cast<uint64_t>(512 >> 4) << 32) |
+         (1ull << 46) | (4ull << 61);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+struct OzakiArgs {
+  const uint16_t* dA;   // digits of J, stage-tiled (see k_split_digits)
+  const uint16_t* dB;   // digits of H, stage-tiled
+  const int* eA;        // row exponents of J
+  const int* eB;        // row exponents of H
+  const int2* tiles;    // (128-row block of J, 64-row block of H)
+  double* partial;      // [gridDim.y][m][m]
+  int* status;
+  int m;
+  int accumulate;       // add into partial instead of storing
+  long long kcta;       // K entries per CTA (multiple of kChunkK)
+  long long klen;       // K extent of the digit tensors (multiple of kChunkK)
+};
+
+__global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  // bars: 0,1 stage full; 2,3 stage empty; 4 tmem full; 5 tmem empty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* issued = reinterpret_cast<int*>(tmem_slot + 2);     // stage loads issued
+  int* committed = reinterpret_cast<int*>(tmem_slot + 3);  // chunks committed to tmem_full
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int2 tile = g.tiles[blockIdx.x];
+  const int row0 = tile.x * kTileM, col0 = tile.y * kTileN;
+  const long long kbeg = static_cast<long long>(blockIdx.y) * g.kcta;
+  long long kend = kbeg + g.kcta;
+  if (kend > g.klen) kend = g.klen;
+  const int nchunks = kend > kbeg ? static_cast<int>((kend - kbeg) / kChunkK) : 0;
+  const int iters = nchunks * kItersPerChunk;
+
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 4; ++b) mbar_init(smem_u32(&bars[b]), 1);
+    mbar_init(smem_u32(&bars[4]), 1);
+    mbar_init(smem_u32(&bars[5]), kEpiWarps);
+    *abort_flag = 0;
+    *issued = 0;
+    *committed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int it = 0; it < iters; ++it) {
+        const int s = it & 1;
+        const uint32_t ph = (it >> 1) & 1;
+        if (!mbar_wait(smem_u32(&bars[2 + s]), ph ^ 1, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t full = smem_u32(&bars[s]);
+        mbar_expect_tx(full, kStageBytes);
+        const long long kb = (kbeg + static_cast<long long>(it) * kKt) / kKt;  // K block in the panel
+        const long long nkb = g.klen / kKt;
+        const uint32_t dst = smem_u32(smem + s * kStageBytes);
+        bulk_load(dst, g.dA + (static_cast<long long>(tile.x) * nkb + kb) * (kABytes / 2), kABytes, full);
+        bulk_load(dst + kABytes, g.dB + (static_cast<long long>(tile.y) * nkb + kb) * (kBBytes / 2), kBBytes, full);
+        *issued = it + 1;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // BF16 x BF16 -> FP32, both K-major, M = 128, N = 64 nq. The B slices of a
+      // stage are consecutive 64-row blocks, so digit p of J against the
+      // stacked digits q0 .. q0 + nq - 1 of H is one MMA whose accumulator
+      // columns (p + q0) 64 .. (p + q0 + nq) 64 are exactly the levels p + q.
+      uint32_t idesc[5];
+#pragma unroll
+      for (int nq = 1; nq <= 4; ++nq)
+        idesc[nq] = (1u << 4) | (1u << 7) | (1u << 10) | (((nq * kTileN) >> 3) << 17) | ((kTileM >> 4) << 24);
+      // (p, q0, nq) covering every pair p + q <= 7 once, N <= 256 per MMA
+      constexpr int kMmas = 12;
+      constexpr int kP[kMmas] = {0, 0, 1, 1, 2, 2, 3, 3, 4, 5, 6, 7};
+      constexpr int kQ0[kMmas] = {0, 4, 0, 4, 0, 4, 0, 4, 0, 0, 0, 0};
+      constexpr int kNq[kMmas] = {4, 4, 4, 3, 4, 2, 4, 1, 4, 3, 2, 1};
+      int it = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        if (!mbar_wait(smem_u32(&bars[5]), (c & 1) ^ 1, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        for (int j = 0; j < kItersPerChunk; ++j, ++it) {
+          const int s = it & 1;
+          const uint32_t ph = (it >> 1) & 1;
+          if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem + s * kStageBytes);
+          const uint64_t adesc0 = desc_sw64(a0);
+          const uint64_t bdesc0 = desc_sw64(a0 + kABytes);
+#pragma unroll
+          for (int ks = 0; ks < kKt / 16; ++ks) {
+#pragma unroll
+            for (int u = 0; u < kMmas; ++u) {
+              // descriptor start addresses are in 16-byte units
+              const uint64_t ad = adesc0 + static_cast<uint64_t>((kP[u] * kTileM * kKt * 2 + ks * 32) >> 4);
+              const uint64_t bd = bdesc0 + static_cast<uint64_t>((kQ0[u] * kTileN * kKt * 2 + ks * 32) >> 4);
+              // the first MMA of a chunk (p = 0, both halves) overwrites all 512 columns
+              const uint32_t acc = (j == 0 && ks == 0 && kP[u] == 0) ? 0u : 1u;
+              mma_bf16(tmem + static_cast<uint32_t>((kP[u] + kQ0[u]) * kTileN), ad, bd, idesc[kNq[u]], acc);
+            }
+          }
+          mma_commit(smem_u32(&bars[2 + s]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bars[4]));
+        *committed = c + 1;
+      }
+      if (!ok) *abort_flag = 1;
+    }
+  } else {
+    // epilogue: warps 2..9; lane quadrant = warp % 4, column half = (warp - 2) / 4
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    double acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+    for (int c = 0; c < nchunks; ++c) {
+      // lane 0 waits; the warp follows its verdict so that the .sync.aligned
+      // TMEM loads below stay warp-uniform
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(smem_u32(&bars[4]), c & 1, abort_flag) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) { if (lane == 0) *abort_flag = 1; break; }
+      __syncwarp();
+      tc_fence_after();
+#pragma unroll 1
+      for (int grp = 0; grp < 2; ++grp) {
+        // levels 4 grp .. 4 grp + 3 combined exactly: |T| < 2^23 * 64^3 * 1.02 < 2^42
+        long long T[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) T[j] = 0;
+#pragma unroll 1
+        for (int lev = 4 * grp; lev < 4 * grp + 4; ++lev) {
+          uint32_t v[32];
+          tmem_ld32(tmem + (static_cast<uint32_t>(32 * quad) << 16) + lev * kTileN + half * 32, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) T[j] = T[j] * 64 + static_cast<long long>(__float2int_rn(__uint_as_float(v[j])));
+        }
+        const double w = grp == 0 ? 16777216.0 : 1.0;  // 64^4 for the upper group
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = fma(static_cast<double>(T[j]), w, acc[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars[5]));
+    }
+    const int row = row0 + 32 * quad + lane;
+    if (!*abort_flag && row < g.m) {
+      double* dst = g.partial + static_cast<long long>(blockIdx.y) * g.m * g.m + static_cast<long long>(row) * g.m;
+      const int er = g.eA[row];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = col0 + half * 32 + j;
+        if (col < g.m) {
+          const double v = ldexp(acc[j], er + g.eB[col] - 52);
+          dst[col] = g.accumulate ? dst[col] + v : v;
+        }
+      }
+    }
+  }
+
+  // teardown: on a timeout wait (bounded) for copies and MMAs still in flight
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    atomicOr(g.status, kStatusTimeout);
+    const int n = *issued;
+    for (int it = (n > 2 ? n - 2 : 0); it < n; ++it) {
+      const uint64_t t0 = gtimer();
+      while (!mbar_try(smem_u32(&bars[it & 1]), (it >> 1) & 1) && gtimer() - t0 < kWaitNs) {
+      }
+    }
+    const int cc = *committed;
+    if (cc > 0) {
+      const uint64_t t0 = gtimer();
+      while (!mbar_try(smem_u32(&bars[4]), (cc - 1) & 1) && gtimer() - t0 < kWaitNs) {
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// ---- operand split ---------------------------------------------------------------
+
+__device__ __forceinline__ int exp_field(double x) {
+  return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7FF);
+}
+
+// Column balance exponents: s_k = floor((b_k - a_k) / 2) with a_k, b_k the
+// exponent fields of max_i |J_ik| and max_i |H_ik| (0 when a column is zero).
+__global__ void k_col_balance(const double* __restrict__ Jm, const double* __restrict__ Hm, int m, long long N,
+                              short* __restrict__ sk) {
+  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  int a = 0, b = 0;
+  for (int i = 0; i < m; ++i) {
+    const int ea = exp_field(Jm[i * N + k]);
+    const int eb = exp_field(Hm[i * N + k]);
+    a = ea > a ? ea : a;
+    b = eb > b ? eb : b;
+  }
+  sk[k] = (a == 0 || b == 0) ? 0 : static_cast<short>((b - a) >> 1);
+}
+
+// Row exponents of the balanced matrix X 2^(sign * s_k): e[i] with max_k |x_ik 2^(sign s_k)| < 2^e[i].
+__global__ void k_row_exp_balanced(const double* __restrict__ X, int m, long long N, const short* __restrict__ sk,
+                                   int sign, int* __restrict__ emax) {
+  const int row = blockIdx.y;
+  int best = -100000;
+  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < N;
+       k += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int ex = exp_field(X[row * N + k]);
+    if (ex != 0) {  // zeros (and subnormals) do not raise the row maximum
+      const int e = ex - 1022 + sign * sk[k];  // |x| 2^(sign s_k) < 2^e
+      best = e > best ? e : best;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const int t = __shfl_down_sync(0xffffffffu, best, o);
+    best = t > best ? t : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(emax + row, best);
+}
+
+// Digits of X[i][k0 + k] 2^(sign s_k) for k < kw (zeros for kw <= k < klen and
+// for padded rows m <= i < rows_pad), written in the exact shared-memory image
+// of a pipeline stage so that one bulk copy moves a stage:
+//   [row block of R rows][K block of 32][slice p][row r][32 BF16, 64-byte swizzle]
+// where the 16-byte chunk c of row r sits at chunk c ^ ((r >> 1) & 3) (the
+// 64-byte swizzle of the K-major UMMA operand layout, 512-byte atoms).
+__global__ void k_split_digits(const double* __restrict__ X, int m, long long N, long long k0, long long kw,
+                               long long klen, int R, const int* __restrict__ e, const short* __restrict__ sk,
+                               int sign, uint16_t* __restrict__ S) {
+  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int row = blockIdx.y;
+  if (k >= klen) return;
+  long long Y = 0;
+  if (k < kw && row < m) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(X[row * N + k0 + k]));
+    const int ex = static_cast<int>((b >> 52) & 0x7FF);
+    const long long M = static_cast<long long>((b & 0xFFFFFFFFFFFFFull) | (ex ? (1ull << 52) : 0ull));
+    // |x| 2^(sign s) = M 2^(ex_eff - 1075 + sign s); Y = round(that * 2^(47 - e))
+    const int sh = 1028 + e[row] - (ex ? ex : 1) - sign * sk[k0 + k];
+    if (M != 0 && sh >= 1 && sh <= 54) Y = (M + (1ll << (sh - 1))) >> sh;
+    if (b >> 63) Y = -Y;
+  }
+  int d[kSlices];
+#pragma unroll
+  for (int p = kSlices - 1; p >= 1; --p) {
+    const long long r = ((Y + 32) & 63) - 32;
+    d[p] = static_cast<int>(r);
+    Y = (Y - r) >> 6;
+  }
+  d[0] = static_cast<int>(Y);
+  const int rb = row / R, ri = row % R;
+  const long long kb = k / kKt;
+  const int kin = static_cast<int>(k % kKt);
+  const int elem = (((kin >> 3) ^ ((ri >> 1) & 3)) << 3) | (kin & 7);
+  const long long nkb = klen / kKt;
+  uint16_t* base = S + ((static_cast<long long>(rb) * nkb + kb) * kSlices) * (R * kKt) + ri * kKt + elem;
+#pragma unroll
+  for (int p = 0; p < kSlices; ++p)
+    base[static_cast<long long>(p) * R * kKt] = __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d[p])));
+}
+
+__global__ void k_fill_int(int* p, int n, int v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+}  // namespace
+
+long long ozaki_panel_width(long long N) {
+  long long kp = (N + kChunkK - 1) / kChunkK * kChunkK;
+  const long long cap = 262144;
+  return kp < cap ? kp : cap;
+}
+
+int ozaki_num_tiles(int m) {
+  const int rb = (m + kTileM - 1) / kTileM, cb = (m + kTileN - 1) / kTileN;
+  int t = 0;
+  for (int I = 0; I < rb; ++I)
+    for (int J = 2 * I; J < cb; ++J) ++t;
+  return t;
+}
+
+void ozaki_tiles(int m, std::vector<int>& out) {
+  const int rb = (m + kTileM - 1) / kTileM, cb = (m + kTileN - 1) / kTileN;
+  out.clear();
+  for (int I = 0; I < rb; ++I)
+    for (int J = 2 * I; J < cb; ++J) {
+      out.push_back(I);
+      out.push_back(J);
+    }
+}
+
+int ozaki_splits(int m, long long kp) {
+  const int tiles = ozaki_num_tiles(m);
+  int s = (152 + tiles - 1) / tiles;
+  const long long maxs = kp / kChunkK;
+  if (s > maxs) s = static_cast<int>(maxs);
+  return s < 1 ? 1 : s;
+}
+
+bool ozaki_supported() {
+  int dev = 0, major = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  return major == 10;
+}
+
+// C partials (FP64, [splits][m][m], upper tiles) of J H^T via the digit split.
+// Returns false when a tensor map cannot be encoded.
+bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long N, const OzakiWork& w, int splits,
+                              cudaStream_t s) {
+  const long long kp = w.klen;
+  k_col_balance<<<static_cast<unsigned>((N + 255) / 256), 256, 0, s>>>(J, H, m, N, w.colexp);
+  {
+    k_fill_int<<<(2 * m + 127) / 128, 128, 0, s>>>(w.expo, 2 * m, -100000);
+    dim3 g(64, m);
+    k_row_exp_balanced<<<g, 256, 0, s>>>(J, m, N, w.colexp, +1, w.expo);
+    k_row_exp_balanced<<<g, 256, 0, s>>>(H, m, N, w.colexp, -1, w.expo + m);
+    note_launches(4);
+  }
+  if (cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
+    return false;
+  const int tiles = ozaki_num_tiles(m);
+  long long kcta = (kp + splits - 1) / splits;
+  kcta = (kcta + kChunkK - 1) / kChunkK * kChunkK;
+  int panel = 0;
+  for (long long k0 = 0; k0 < N; k0 += kp, ++panel) {
+    const long long kw = (N - k0) < kp ? (N - k0) : kp;
+    const int rowsA = (m + kTileM - 1) / kTileM * kTileM, rowsB = (m + kTileN - 1) / kTileN * kTileN;
+    k_split_digits<<<dim3(static_cast<unsigned>((kp + 255) / 256), rowsA), 256, 0, s>>>(
+        J, m, N, k0, kw, kp, kTileM, w.expo, w.colexp, +1, static_cast<uint16_t*>(w.digitsA));
+    k_split_digits<<<dim3(static_cast<unsigned>((kp + 255) / 256), rowsB), 256, 0, s>>>(
+        H, m, N, k0, kw, kp, kTileN, w.expo + m, w.colexp, -1, static_cast<uint16_t*>(w.digitsB));
+    OzakiArgs a;
+    a.dA = static_cast<const uint16_t*>(w.digitsA);
+    a.dB = static_cast<const uint16_t*>(w.digitsB);
+    a.eA = w.expo;
+    a.eB = w.expo + m;
+    a.tiles = reinterpret_cast<const int2*>(w.tiles);
+    a.partial = w.partial;
+    a.status = w.status;
+    a.m = m;
+    a.accumulate = panel > 0 ? 1 : 0;
+    a.kcta = kcta;
+    a.klen = kp;
+    k_ozaki_gemm<<<dim3(tiles, splits), kGemmThreads, kSmemBytes, s>>>(a);
+    note_launches(3);
+  }
+  return true;
+}
+
+}  // namespace h1w

@@ -107,6 +107,11 @@ extern "C" h1w_status h1w_apply_op_static(const h1w_grid* g, int32_t m, const do
   if (g->disc == H1W_FV_CELL) {
     const double hx = g->h[0], hy = g->h[1], hz = g->h[2];
     L.Tx = hy * hz / hx; L.Ty = hx * hz / hy; L.Tz = hx * hy / hz; L.V = hx * hy * hz;
+    L.iso = (L.Tx == L.Ty && L.Ty == L.Tz) ? 1 : 0;
+    for (int cz = 0; cz < 3; ++cz)
+      for (int cy = 0; cy < 3; ++cy)
+        for (int cx = 0; cx < 3; ++cx)
+          L.fv_diag[cx + 3 * cy + 9 * cz] = L.V + L.Tx * cx + L.Ty * cy + L.Tz * cz;
   } else {
     double* qx = base + off_q;
     double* qy = qx + 6 * (int64_t)L.nx;

@@ -72,14 +72,22 @@ def test_hierarchy_matches_oracle(case):
     assert lv == want
 
 
-@pytest.mark.parametrize("case", ALL, ids=lambda c: f"{c[0]}{'x'.join(map(str, c[1]))}")
-def test_vcycle_parity(case):
+VC_CASES = [(c, a) for c in ALL for a in ((0, 1) if c[0] == "fv" else (1,))]
+
+
+@pytest.mark.parametrize("case,mg_arith", VC_CASES,
+                         ids=lambda v: f"{v[0]}{'x'.join(map(str, v[1]))}" if isinstance(v, tuple)
+                         else ("df64" if v == 0 else "fp64"))
+def test_vcycle_parity(case, mg_arith):
+    """FP64 cycle (Q1, FV) and double-float cycle (FV, FP32 pairs of about 48
+    bits: errors of a few 1e-15 per operation, ~1e-13 over a cycle) against
+    the oracle's V-cycle, relative error 1e-12."""
     d, n, h = case
     H = mg.build_hierarchy(d, n, h)
     N = H.N
     rng = np.random.default_rng(21)
     B = rng.standard_normal((3, N))
-    S = _gpu(d, n, h, 1e-2, 4, rhs_block=2)  # 3 right-hand sides: blocks of 2 and 1
+    S = _gpu(d, n, h, 1e-2, 4, rhs_block=2, mg_arith=mg_arith)  # 3 right-hand sides: blocks of 2 and 1
     X = S.vcycle(_t(B)).cpu().numpy()
     for r in range(3):
         ref = mg.vcycle(H, B[r])
@@ -108,7 +116,11 @@ def test_apply_op_and_rhs_parity(case):
 
 @pytest.mark.parametrize("case", ALL, ids=lambda c: f"{c[0]}{'x'.join(map(str, c[1]))}")
 @pytest.mark.parametrize("m", [1, 13, 70])
-def test_capacitance_and_prec_parity(case, m):
+@pytest.mark.parametrize("cap_gemm", [0, 1], ids=["tensor", "fp64"])
+def test_capacitance_and_prec_parity(case, m, cap_gemm):
+    """C, its Cholesky factor and the preconditioner, with line C on the tensor
+    cores (42-bit digit split: error below 2^-42 of the row maxima, i.e. a few
+    1e-12 of ||C|| for these Gaussian rows) or on the FP64 CUDA cores."""
     d, n, h = case
     H = mg.build_hierarchy(d, n, h)
     N = H.N
@@ -116,7 +128,7 @@ def test_capacitance_and_prec_parity(case, m):
     alpha = 1e-2
     J = rng.standard_normal((m, N)) / np.sqrt(N)
     P = wb.WoodburyPreconditioner(lambda v: mg.vcycle(H, v), J, alpha)
-    S = _gpu(d, n, h, alpha, m, rhs_block=16)
+    S = _gpu(d, n, h, alpha, m, rhs_block=16, cap_gemm=cap_gemm)
     S.capacitance(_t(J))
     C, L = (t.cpu().numpy() for t in S.factors())
     assert np.array_equal(C, C.T)
@@ -241,3 +253,22 @@ def test_status_codes():
     # zero right-hand side: x = 0, no iterations
     x, info = S.pcg(torch.zeros_like(b), 1e-8)
     assert info.iters == 0 and float(x.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("n,m", [((72, 64, 64), 150), ((40, 36, 20), 300)], ids=["2panels_m150", "m300"])
+def test_tensor_capacitance_matches_fp64(n, m):
+    """Line C on the tensor cores against the FP64 CUDA-core GEMM on the same
+    GPU-built H (more than one 262144-wide K panel, ragged tiles): the digit
+    split keeps 42 bits of every row, so C agrees to ~1e-11 of ||C||."""
+    h = tuple(1.0 / v for v in n)
+    N = int(np.prod(n))
+    rng = np.random.default_rng(41)
+    J = _t(rng.standard_normal((m, N)) * rng.uniform(0.1, 10.0, size=(m, 1)) / np.sqrt(N))
+    Cs = []
+    for mode in (0, 1):
+        S = _gpu("fv", n, h, 1e-3, m, cap_gemm=mode)
+        S.capacitance(J)
+        C, L = S.factors()
+        Cs.append(C.cpu().numpy())
+    assert np.array_equal(Cs[0], Cs[0].T)
+    assert np.linalg.norm(Cs[0] - Cs[1]) <= 1e-11 * np.linalg.norm(Cs[1])
