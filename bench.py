@@ -233,6 +233,7 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         phase = {"t_H_ms": [], "t_C_ms": [], "t_chol_ms": [], "t_pcg_ms": []}
+        kern = {k_: [0.0, 0] for k_ in ("gemm_kernel", "jdot", "op", "hdot", "hupd")}
         launches = 0
         iters = []
         e0.record(stream)
@@ -242,6 +243,9 @@ def run_ours(args):
             t = S.timings()
             for k_ in phase:
                 phase[k_].append(getattr(t, k_))
+            for k_ in kern:
+                kern[k_][0] += getattr(t, "t_" + k_ + "_ms")
+                kern[k_][1] += getattr(t, "n_" + k_)
             launches += t.launches_capacitance + t.launches_pcg
             iters.append(info.iters)
         e1.record(stream)
@@ -283,20 +287,41 @@ def run_ours(args):
 
     value = world * args.steps / (ms_max / 1e3)
     mean = {k_: float(np.mean(v_)) for k_, v_ in phase.items()}
-    # dominant kernel: the capacitance GEMM (line C), FP64 on the CUDA cores
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             peaks = json.load(f)
     except OSError:
         pass
-    gemm_flops = float(m) * (m + 1) * N          # symmetric C: m(m+1)/2 entries x 2N flops
-    fp64_peak = 152 * 4 * 2.07e9 / 1e12          # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-    achieved = gemm_flops / (mean["t_C_ms"] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_cap_gemm (line C, FP64 CUDA cores)",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz",
-                "share_of_step": mean["t_C_ms"] / (ms_max / args.steps)}
+    hbm = float(peaks.get("hbm_gbs", 6746.0))
+    bf16_sus = float(peaks.get("bf16_tflops_sustained", 1715.2))
+    # per-kernel rates from CUDA events on the library's stream (h1w_get_timings)
+    tiles = sum(max(0, (m + 63) // 64 - 2 * I) for I in range((m + 127) // 128))
+    kp = min(((N + 2047) // 2048) * 2048, 262144)
+    panels = (N + kp - 1) // kp
+    gemm_flops_launch = tiles * 36 * 2.0 * 128 * 64 * kp        # digit-pair products per panel launch
+    table = {}
+    def rate(name, total_ms, n, per_launch, unit, bound, peak, note):
+        if n == 0 or total_ms <= 0:
+            return
+        avg = total_ms / n
+        ach = per_launch / (avg / 1e3) / (1e12 if unit == "TFLOP/s" else 1e9)
+        table[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                       "avg_launch_ms": avg, "launches_per_step": n / args.steps,
+                       "ms_per_step": total_ms / args.steps, "algorithmic_per_launch": per_launch, "note": note}
+    mat = 8.0 * m * N
+    rate("k_ozaki_gemm", kern["gemm_kernel"][0], kern["gemm_kernel"][1], gemm_flops_launch, "TFLOP/s", "tensor",
+         bf16_sus, "BF16 digit-pair products of one 262144-wide K panel; peak = measured sustained BF16")
+    rate("k_rows_dot (J z, FP64)", kern["jdot"][0], kern["jdot"][1], mat + 8.0 * N, "GB/s", "hbm", hbm,
+         "bytes of J and z per pass; FP64 pipe limits it to ~1 FMA per 8 bytes")
+    rate("k_apply_op<FV> (stencil + J^T w, FP64)", kern["op"][0], kern["op"][1], mat + 16.0 * N, "GB/s", "hbm", hbm,
+         "bytes of J, p and q per pass")
+    rate("k_rows_dot_df (H^T r)", kern["hdot"][0], kern["hdot"][1], mat + 8.0 * N, "GB/s", "hbm", hbm,
+         "bytes of H (double-float) and r per pass")
+    rate("k_woodbury_update_df (z update)", kern["hupd"][0], kern["hupd"][1], mat + 32.0 * N, "GB/s", "hbm", hbm,
+         "bytes of H, z0, r and z per pass")
+    dom = max(table, key=lambda k_: table[k_]["ms_per_step"]) if table else None
+    roofline = dict(table[dom], kernel=dom, traffic=None) if dom else None
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -306,7 +331,11 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (J is %.1f GB)" % (J.numel() * 8 / 1e9)},
         "phases_ms": mean, "pcg_iters": iters, "rel_res_true": rel_true,
         "mg_dof_per_s": float(m) * N / (mean["t_H_ms"] / 1e3),
-        "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
+        "arith": {"operator_and_krylov": "f64", "true_residual": "f64",
+                  "vcycle": "double-float (FP32 pairs, ~48 bits)",
+                  "capacitance_gemm": "BF16 tensor cores on an exact 48-bit digit split, FP64 accumulation",
+                  "cholesky": "f64", "woodbury_passes": "double-float"},
+        "roofline": roofline, "kernels": table, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
         "impl": "ours",
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -89,11 +89,18 @@ typedef struct {
  * the library launched in them. */
 typedef struct {
   float t_H_ms;                 /* line H: batched V-cycles of the last h1w_capacitance */
-  float t_C_ms;                 /* line C: the capacitance GEMM kernel */
+  float t_C_ms;                 /* line C: operand preparation and the capacitance GEMM */
   float t_chol_ms;              /* forming C from the GEMM partials and its Cholesky factor */
   float t_pcg_ms;               /* the last h1w_pcg, launch to convergence */
   int64_t launches_capacitance; /* kernels launched by the last h1w_capacitance */
   int64_t launches_pcg;         /* kernels launched by the last h1w_pcg */
+  /* device time and launch count of individual kernels in those two calls */
+  float t_gemm_kernel_ms;       /* capacitance GEMM kernel launches (line C) */
+  float t_jdot_ms;              /* FP64 passes J z over J inside PCG */
+  float t_op_ms;                /* FP64 operator kernel (stencil + J^T w) inside PCG */
+  float t_hdot_ms;              /* passes H^T r over H inside PCG */
+  float t_hupd_ms;              /* passes z = (z0 - H v / alpha) / alpha over H inside PCG */
+  int32_t n_gemm_kernel, n_jdot, n_op, n_hdot, n_hupd, reserved;
 } h1w_timings;
 
 typedef struct h1w_ctx h1w_ctx;

@@ -60,6 +60,8 @@ struct h1w_ctx {
   int m;                 // current number of measurements (-1: none yet)
   const double* J;       // borrowed
   double* H;             // m_max x N
+  df* Hdf;               // m_max x N, the same as double-floats (double-float V-cycle only)
+  df* vdf;               // N, a vector converted to double-floats
   double* C;             // m_max x m_max
   double* Lc;            // m_max x m_max
   double* gemm_partial;
@@ -75,6 +77,14 @@ struct h1w_ctx {
   // phase timing: 0 H start, 1 H end / C start, 2 C end, 3 chol end, 4 pcg start, 5 pcg end
   cudaEvent_t ev[6];
   bool have_ev;
+  // per-kernel timing: event pairs around selected launches, summed per category
+  static constexpr int kTimed = 1024;
+  cudaEvent_t kev[kTimed][2];
+  int kcat[kTimed];
+  int nk;
+  bool timing_on;
+  float cat_ms[8];
+  int cat_n[8];
   long long launches_cap, launches_pcg;
   std::string err;
 };
@@ -89,6 +99,33 @@ h1w_status h1w::set_global_error(h1w_status st, const std::string& msg) {
 }
 
 namespace {
+
+enum { kCatGemm = 0, kCatJdot = 1, kCatOp = 2, kCatHdot = 3, kCatHupd = 4, kCatCount = 5 };
+
+void timed_begin(h1w_ctx* c) {
+  if (c->timing_on && c->have_ev && c->nk < h1w_ctx::kTimed) cudaEventRecord(c->kev[c->nk][0], c->stream);
+}
+void timed_end(h1w_ctx* c, int cat) {
+  if (c->timing_on && c->have_ev && c->nk < h1w_ctx::kTimed) {
+    cudaEventRecord(c->kev[c->nk][1], c->stream);
+    c->kcat[c->nk++] = cat;
+  }
+}
+// after the stream has been synchronized: add the recorded pairs into the
+// category sums, first clearing the categories in reset_mask
+void timed_collect(h1w_ctx* c, unsigned reset_mask) {
+  for (int k = 0; k < kCatCount; ++k)
+    if (reset_mask & (1u << k)) { c->cat_ms[k] = 0.f; c->cat_n[k] = 0; }
+  for (int t = 0; t < c->nk; ++t) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->kev[t][0], c->kev[t][1]) == cudaSuccess) {
+      c->cat_ms[c->kcat[t]] += ms;
+      c->cat_n[c->kcat[t]] += 1;
+    }
+  }
+  c->nk = 0;
+  cudaGetLastError();
+}
 
 h1w_status fail(h1w_ctx* c, h1w_status st, const std::string& msg) {
   if (c) c->err = msg;
@@ -261,6 +298,9 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   int* dstatus = B.take<int>(4);
   unsigned long long* dbits = B.take<unsigned long long>(4);
   double* H = B.take<double>((int64_t)m_max * N0);
+  const bool use_df = (g.disc == H1W_FV_CELL) && (o.mg_arith == 0);
+  df* Hdf = use_df ? B.take<df>((int64_t)m_max * N0) : nullptr;
+  df* vdf = use_df ? B.take<df>(N0) : nullptr;
   double* C = B.take<double>((int64_t)m_max * m_max);
   double* Lc = B.take<double>((int64_t)m_max * m_max);
   const bool oz = (o.cap_gemm == 0) && m_max > 0;
@@ -294,6 +334,7 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
     for (int k = 0; k < P.nlev; ++k) c->buf[k] = bufs[k];
     c->coarse_X = cX; c->coarse_L = cL; c->dstatus = dstatus; c->dbits = dbits;
     c->H = H; c->C = C; c->Lc = Lc; c->gemm_partial = gp; c->gemm_partial_len = gpl;
+    c->Hdf = Hdf; c->vdf = vdf;
     c->oz = ow;
     c->oz.partial = gp;
     c->oz.status = dstatus;
@@ -366,7 +407,7 @@ void smooth_df(h1w_ctx* c, int l, int nrhs, bool zero_x) {
   if (pending) launch_add_df((int64_t)nrhs * L.N, da, x, c->stream);
 }
 
-void vcycle_block_df(h1w_ctx* c, int nrhs, const double* b0, double* x0) {
+void vcycle_block_df(h1w_ctx* c, int nrhs, const double* b0, double* x0, df* x0df) {
   const int nl = c->nlev;
   const int64_t n0 = (int64_t)nrhs * c->lev[0].N;
   launch_d2df(n0, b0, dfp(c->buf[0].b), c->stream);
@@ -381,15 +422,17 @@ void vcycle_block_df(h1w_ctx* c, int nrhs, const double* b0, double* x0) {
     launch_prolong_add_df(c->lev[l], c->lev[l + 1], nrhs, dfp(c->buf[l + 1].x), dfp(c->buf[l].x), c->stream);
     smooth_df(c, l, nrhs, false);
   }
-  launch_df2d(n0, dfp(c->buf[0].x), x0, c->stream);
+  launch_df2d(n0, dfp(c->buf[0].x), x0, x0df, c->stream);
 }
 
-void vcycle_many(h1w_ctx* c, int nrhs, const double* b, double* x) {
+bool uses_df(const h1w_ctx* c) { return (c->disc == H1W_FV_CELL) && (c->opt.mg_arith == 0); }
+
+// x = L-hat^-1 b for nrhs vectors; xdf (double-float cycle only, may be null) gets x as double-floats
+void vcycle_many(h1w_ctx* c, int nrhs, const double* b, double* x, df* xdf = nullptr) {
   const int64_t N = c->lev[0].N;
-  const bool use_df = (c->disc == H1W_FV_CELL) && (c->opt.mg_arith == 0);
   for (int r0 = 0; r0 < nrhs; r0 += c->opt.rhs_block) {
     const int nr = std::min(c->opt.rhs_block, nrhs - r0);
-    if (use_df) vcycle_block_df(c, nr, b + (int64_t)r0 * N, x + (int64_t)r0 * N);
+    if (uses_df(c)) vcycle_block_df(c, nr, b + (int64_t)r0 * N, x + (int64_t)r0 * N, xdf ? xdf + (int64_t)r0 * N : nullptr);
     else vcycle_block(c, nr, b + (int64_t)r0 * N, x + (int64_t)r0 * N);
   }
 }
@@ -398,7 +441,9 @@ void vcycle_many(h1w_ctx* c, int nrhs, const double* b, double* x) {
 void j_times(h1w_ctx* c, const double* A, const double* v, double* out, double scale = 1.0) {
   const int64_t N = c->lev[0].N;
   if (c->m <= 0) return;
+  timed_begin(c);
   launch_rows_dot(A, c->m, N, v, c->partial, c->stream);
+  timed_end(c, kCatJdot);
   launch_reduce_partials(c->partial, rows_dot_chunks(N), c->m, scale, out, c->stream);
 }
 
@@ -407,21 +452,41 @@ void apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
   const int64_t N = c->lev[0].N;
   vcycle_many(c, 1, r, c->z0);
   const int m = c->m;
+  const bool dfp_ = uses_df(c) && m > 0;
   if (m > 0) {
-    j_times(c, c->H, r, c->svec);                   // s = H^T r
+    if (dfp_) {                                     // s = H^T r (double-float pass)
+      launch_d2df(N, r, c->vdf, c->stream);
+      timed_begin(c);
+      launch_rows_dot_df(c->Hdf, m, N, c->vdf, c->partial, c->stream);
+      timed_end(c, kCatHdot);
+      launch_reduce_partials(c->partial, rows_dot_chunks(N), m, 1.0, c->svec, c->stream);
+    } else {
+      timed_begin(c);
+      launch_rows_dot(c->H, m, N, r, c->partial, c->stream);  // s = H^T r
+      timed_end(c, kCatHdot);
+      launch_reduce_partials(c->partial, rows_dot_chunks(N), m, 1.0, c->svec, c->stream);
+    }
     launch_trsv_lower(c->Lc, m, c->svec, 1, c->stream);
     launch_trsv_upper_t(c->Lc, m, c->svec, 1, c->stream);  // v = C^-1 s
   }
-  launch_woodbury_update(c->H, m, N, c->svec, c->z0, c->grid.alpha, z, rz_slot >= 0 ? r : nullptr,
-                         rz_slot >= 0 ? c->partial : nullptr, c->stream);
+  timed_begin(c);
+  if (dfp_)
+    launch_woodbury_update_df(c->Hdf, m, N, c->svec, c->z0, c->grid.alpha, z, rz_slot >= 0 ? r : nullptr,
+                              rz_slot >= 0 ? c->partial : nullptr, c->stream);
+  else
+    launch_woodbury_update(c->H, m, N, c->svec, c->z0, c->grid.alpha, z, rz_slot >= 0 ? r : nullptr,
+                           rz_slot >= 0 ? c->partial : nullptr, c->stream);
+  timed_end(c, kCatHupd);
   if (rz_slot >= 0) launch_sum_to_scalar(c->partial, colsum_blocks(N), c->scal + rz_slot, c->stream);
 }
 
 // q = alpha (K+M) p + J^T w with w = J p given; scal[pq_slot] = p . q when pq_slot >= 0
 void apply_op_w(h1w_ctx* c, const double* p, const double* w, double* q, int pq_slot) {
   int nb = 0;
+  timed_begin(c);
   launch_apply_op(c->disc, c->lev[0], c->grid.alpha, p, 1.0, c->J, w, c->m > 0 ? c->m : 0, q,
                   pq_slot >= 0 ? c->partial : nullptr, &nb, c->stream);
+  timed_end(c, kCatOp);
   if (pq_slot >= 0) launch_sum_to_scalar(c->partial, nb, c->scal + pq_slot, c->stream);
 }
 
@@ -488,6 +553,12 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
   c->have_ev = true;
   for (int e = 0; e < 6; ++e)
     if (cudaEventCreate(&c->ev[e]) != cudaSuccess) c->have_ev = false;
+  for (int t = 0; t < h1w_ctx::kTimed && c->have_ev; ++t)
+    for (int e = 0; e < 2; ++e)
+      if (cudaEventCreate(&c->kev[t][e]) != cudaSuccess) c->have_ev = false;
+  c->nk = 0;
+  c->timing_on = false;
+  for (int k = 0; k < 8; ++k) { c->cat_ms[k] = 0.f; c->cat_n[k] = 0; }
   c->launches_cap = c->launches_pcg = 0;
 
   // level descriptors
@@ -599,7 +670,7 @@ h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
   const long long l0 = g_kernel_launches.load();
   if (m == 0) { c->launches_cap = 0; return H1W_OK; }
   if (c->have_ev) cudaEventRecord(c->ev[0], c->stream);
-  vcycle_many(c, m, J, c->H);                                       // line H
+  vcycle_many(c, m, J, c->H, c->Hdf);                               // line H
   if (c->have_ev) cudaEventRecord(c->ev[1], c->stream);
   cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
   int splits = 0;
@@ -609,11 +680,20 @@ h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
     cudaMemcpyAsync(c->oz.tiles, c->oz_tiles_host.data(), sizeof(int) * c->oz_tiles_host.size(),
                     cudaMemcpyHostToDevice, c->stream);
     splits = ozaki_splits(m, c->oz.klen);
-    if (!launch_ozaki_capacitance(J, c->H, m, N, c->oz, splits, c->stream))
+    c->timing_on = true;
+    const bool ok = launch_ozaki_capacitance(
+        J, c->H, m, N, c->oz, splits, c->stream, [](void* p) { timed_begin(static_cast<h1w_ctx*>(p)); },
+        [](void* p) { timed_end(static_cast<h1w_ctx*>(p), kCatGemm); }, c);
+    c->timing_on = false;
+    if (!ok)
       return fail(c, H1W_ECUDA, "capacitance: tensor map encoding or kernel attribute failed");
   } else {                                                          // line C, FP64 CUDA cores
     splits = cap_gemm_splits(m, N);
+    c->timing_on = true;
+    timed_begin(c);
     launch_cap_gemm(J, c->H, m, N, c->gemm_partial, splits, c->stream);
+    timed_end(c, kCatGemm);
+    c->timing_on = false;
   }
   if (c->have_ev) cudaEventRecord(c->ev[2], c->stream);
   launch_cap_finalize(c->gemm_partial, splits, m, c->grid.alpha, c->C, c->stream);
@@ -625,6 +705,7 @@ h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
   cudaMemcpyAsync(&status, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail(c, H1W_ECUDA, std::string("capacitance: ") + cudaGetErrorString(e));
+  timed_collect(c, 1u << kCatGemm);
   h1w_status st = cuda_check(c, "capacitance");
   if (st != H1W_OK) return st;
   if (status & kStatusTimeout) {
@@ -685,6 +766,8 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
   enum { RZ = 0, PQ = 1, A = 2, RZN = 3, BETA = 4, RR = 5, BB = 6 };
   const long long l0 = g_kernel_launches.load();
   if (c->have_ev) cudaEventRecord(c->ev[4], s);
+  c->nk = 0;
+  c->timing_on = true;
   launch_dot_partial(b, b, N, c->partial, s);
   launch_sum_to_scalar(c->partial, dot_blocks(N), c->scal + BB, s);
   const double bnorm = std::sqrt(read_scalar(c, BB));
@@ -694,6 +777,8 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
     if (info) *info = inf;
     if (c->have_ev) cudaEventRecord(c->ev[5], s);
     cudaStreamSynchronize(s);
+    c->timing_on = false;
+    c->nk = 0;
     c->launches_pcg = g_kernel_launches.load() - l0;
     return cuda_check(c, "pcg");
   }
@@ -741,6 +826,8 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
     cudaEventRecord(c->ev[5], s);
     cudaEventSynchronize(c->ev[5]);
   }
+  c->timing_on = false;
+  timed_collect(c, (1u << kCatJdot) | (1u << kCatOp) | (1u << kCatHdot) | (1u << kCatHupd));
   c->launches_pcg = g_kernel_launches.load() - l0;
   h1w_status st = cuda_check(c, "pcg");
   if (st != H1W_OK) return st;
@@ -776,6 +863,16 @@ h1w_status h1w_get_timings(const h1w_ctx* c, h1w_timings* out) {
   cudaGetLastError();  // elapsed-time queries on unrecorded events are not errors here
   t.launches_capacitance = c->launches_cap;
   t.launches_pcg = c->launches_pcg;
+  t.t_gemm_kernel_ms = c->cat_ms[kCatGemm];
+  t.t_jdot_ms = c->cat_ms[kCatJdot];
+  t.t_op_ms = c->cat_ms[kCatOp];
+  t.t_hdot_ms = c->cat_ms[kCatHdot];
+  t.t_hupd_ms = c->cat_ms[kCatHupd];
+  t.n_gemm_kernel = c->cat_n[kCatGemm];
+  t.n_jdot = c->cat_n[kCatJdot];
+  t.n_op = c->cat_n[kCatOp];
+  t.n_hdot = c->cat_n[kCatHdot];
+  t.n_hupd = c->cat_n[kCatHupd];
   *out = t;
   return H1W_OK;
 }
@@ -797,8 +894,11 @@ const char* h1w_last_error(const h1w_ctx* c) {
 
 void h1w_destroy(h1w_ctx* c) {
   if (!c) return;
-  if (c->have_ev)
+  if (c->have_ev) {
     for (int e = 0; e < 6; ++e) cudaEventDestroy(c->ev[e]);
+    for (int t = 0; t < h1w_ctx::kTimed; ++t)
+      for (int e = 0; e < 2; ++e) cudaEventDestroy(c->kev[t][e]);
+  }
   delete c;
 }
 

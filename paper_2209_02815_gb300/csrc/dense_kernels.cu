@@ -123,6 +123,94 @@ __global__ void __launch_bounds__(kThreads) k_woodbury_update(
   }
 }
 
+// ---- the same two Woodbury passes over H stored as double-floats -----------------
+// (the preconditioner's passes; FP32-pipe arithmetic, so they stream at HBM rate)
+
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    df t;
+    t.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+    t.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, t);
+  }
+  return v;
+}
+
+// partial[c * m + i] = sum_{k in chunk c} A[i * N + k] * v[k], A and v double-floats
+__global__ void __launch_bounds__(kThreads) k_rows_dot_df(const df* __restrict__ A, int m, int64_t N,
+                                                          const df* __restrict__ v, double* __restrict__ partial) {
+  const int64_t k0 = (int64_t)blockIdx.x * kRowsChunk;
+  const int r0 = blockIdx.y * kRowsPerBlock;
+  df vv[kPerThread];
+#pragma unroll
+  for (int e = 0; e < kPerThread; ++e) {
+    const int64_t k = k0 + threadIdx.x + (int64_t)e * kThreads;
+    vv[e] = (k < N) ? v[k] : df_make(0.f, 0.f);
+  }
+  __shared__ df sh[kRowsPerBlock][kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int rr = 0; rr < kRowsPerBlock; ++rr) {
+    const int row = r0 + rr;
+    float s = 0.f, e = 0.f;  // cascaded sum of exact products
+    if (row < m) {
+      const df* a = A + (int64_t)row * N;
+#pragma unroll
+      for (int q = 0; q < kPerThread; ++q) {
+        const int64_t k = k0 + threadIdx.x + (int64_t)q * kThreads;
+        if (k < N) {
+          const df p = df_mul(a[k], vv[q]);
+          const df t = two_sum(s, p.hi);
+          s = t.hi;
+          e = __fadd_rn(e, __fadd_rn(t.lo, p.lo));
+        }
+      }
+    }
+    df acc = warp_sum_df(fast_two_sum(s, e));
+    if (lane == 0) sh[rr][wid] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < kRowsPerBlock) {
+    const int row = r0 + threadIdx.x;
+    if (row < m) {
+      df t = sh[threadIdx.x][0];
+#pragma unroll
+      for (int w = 1; w < kThreads / 32; ++w) t = df_add(t, sh[threadIdx.x][w]);
+      partial[(int64_t)blockIdx.x * m + row] = df_to_double(t);
+    }
+  }
+}
+
+// z_k = (z0_k - (1/alpha) sum_i H[i][k] v_i) / alpha with H double-floats; partial[block] = sum r_k z_k
+__global__ void __launch_bounds__(kThreads) k_woodbury_update_df(
+    const df* __restrict__ H, int m, int64_t N, const double* __restrict__ v, const double* __restrict__ z0,
+    double inv_alpha, double* __restrict__ z, const double* __restrict__ r, double* __restrict__ partial) {
+  extern __shared__ df svd[];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) svd[i] = df_from_double(v[i]);
+  __syncthreads();
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double prod = 0.0;
+  if (k < N) {
+    float s = 0.f, e = 0.f;
+    const df* col = H + k;
+    for (int i = 0; i < m; ++i) {
+      const df p = df_mul(col[(int64_t)i * N], svd[i]);
+      const df t = two_sum(s, p.hi);
+      s = t.hi;
+      e = __fadd_rn(e, __fadd_rn(t.lo, p.lo));
+    }
+    const double hv = df_to_double(fast_two_sum(s, e));
+    const double zk = (z0[k] - hv * inv_alpha) * inv_alpha;
+    z[k] = zk;
+    if (r) prod = r[k] * zk;
+  }
+  if (partial) {
+    const double t = block_sum(prod);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  }
+}
+
 // ---- Cholesky (lower, in place, row-major n x n), 32-wide panels --------------
 
 constexpr int kNB = 32;
@@ -458,6 +546,20 @@ void launch_reduce_partials(const double* partial, int nchunks, int m, double sc
                             cudaStream_t s) {
   if (m <= 0) return;
   k_reduce_partials<<<nblk(m, 128), 128, 0, s>>>(partial, nchunks, m, scale, out);
+  note_launches(1);
+}
+
+void launch_rows_dot_df(const df* A, int m, int64_t N, const df* v, double* partial, cudaStream_t s) {
+  if (m <= 0) return;
+  dim3 g(rows_dot_chunks(N), (m + kRowsPerBlock - 1) / kRowsPerBlock);
+  k_rows_dot_df<<<g, kThreads, 0, s>>>(A, m, N, v, partial);
+  note_launches(1);
+}
+
+void launch_woodbury_update_df(const df* H, int m, int64_t N, const double* v, const double* z0, double alpha,
+                               double* z, const double* r, double* partial, cudaStream_t s) {
+  const size_t smem = sizeof(df) * (size_t)(m > 0 ? m : 1);
+  k_woodbury_update_df<<<nblk(N), kThreads, smem, s>>>(H, m, N, v, z0, 1.0 / alpha, z, r, partial);
   note_launches(1);
 }
 

@@ -73,8 +73,10 @@ long long ozaki_panel_width(long long N);
 int ozaki_num_tiles(int m);
 int ozaki_splits(int m, long long kp);
 bool ozaki_supported();
+// before/after (may be null) are called around each GEMM kernel launch with hook_arg
 bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long N, const OzakiWork& w,
-                              int splits, cudaStream_t s);
+                              int splits, cudaStream_t s, void (*before)(void*), void (*after)(void*),
+                              void* hook_arg);
 void ozaki_tiles(int m, std::vector<int>& out);
 
 // ---- kernel launchers (mg_kernels.cu) --------------------------------------
@@ -110,7 +112,8 @@ void launch_restrict_df(const Level& Lf, const Level& Lc, int nrhs, const df* rf
 void launch_prolong_add_df(const Level& Lf, const Level& Lc, int nrhs, const df* xc, df* xf, cudaStream_t s);
 void launch_coarse_apply_df(const double* X, int n, int nrhs, const df* b, df* x, cudaStream_t s);
 void launch_d2df(int64_t n, const double* src, df* dst, cudaStream_t s);
-void launch_df2d(int64_t n, const df* src, double* dst, cudaStream_t s);
+// dst = src as FP64; dst2 (may be null) receives a copy of the double-floats
+void launch_df2d(int64_t n, const df* src, double* dst, df* dst2, cudaStream_t s);
 
 // ---- dense / Krylov kernels (dense_kernels.cu) ------------------------------
 // partial[c * m + i] = sum_{k in chunk c} A[i * lda + k] v[k]
@@ -125,6 +128,10 @@ int colsum_blocks(int64_t N);
 void launch_woodbury_update(const double* H, int m, int64_t N, const double* v, const double* z0,
                             double alpha, double* z, const double* r, double* partial,
                             cudaStream_t s);
+// the same two preconditioner passes with H (and v) stored as double-floats
+void launch_rows_dot_df(const df* A, int m, int64_t N, const df* v, double* partial, cudaStream_t s);
+void launch_woodbury_update_df(const df* H, int m, int64_t N, const double* v, const double* z0, double alpha,
+                               double* z, const double* r, double* partial, cudaStream_t s);
 void launch_chol(double* A, int n, int* status, cudaStream_t s);
 // in-place triangular solves with the lower factor L (n x n): x <- L^-1 x, x <- L^-T x
 void launch_trsv_lower(const double* L, int n, double* x, int nrhs, cudaStream_t s);

@@ -467,7 +467,7 @@ bool ozaki_supported() {
 // C partials (FP64, [splits][m][m], upper tiles) of J H^T via the digit split.
 // Returns false when a tensor map cannot be encoded.
 bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long N, const OzakiWork& w, int splits,
-                              cudaStream_t s) {
+                              cudaStream_t s, void (*before)(void*), void (*after)(void*), void* hook_arg) {
   const long long kp = w.klen;
   k_col_balance<<<static_cast<unsigned>((N + 255) / 256), 256, 0, s>>>(J, H, m, N, w.colexp);
   {
@@ -502,7 +502,9 @@ bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long
     a.accumulate = panel > 0 ? 1 : 0;
     a.kcta = kcta;
     a.klen = kp;
+    if (before) before(hook_arg);
     k_ozaki_gemm<<<dim3(tiles, splits), kGemmThreads, kSmemBytes, s>>>(a);
+    if (after) after(hook_arg);
     note_launches(3);
   }
   return true;

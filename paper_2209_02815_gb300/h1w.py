@@ -45,7 +45,11 @@ class Options(ctypes.Structure):
 class Timings(ctypes.Structure):
     _fields_ = [("t_H_ms", ctypes.c_float), ("t_C_ms", ctypes.c_float), ("t_chol_ms", ctypes.c_float),
                 ("t_pcg_ms", ctypes.c_float), ("launches_capacitance", ctypes.c_int64),
-                ("launches_pcg", ctypes.c_int64)]
+                ("launches_pcg", ctypes.c_int64), ("t_gemm_kernel_ms", ctypes.c_float),
+                ("t_jdot_ms", ctypes.c_float), ("t_op_ms", ctypes.c_float), ("t_hdot_ms", ctypes.c_float),
+                ("t_hupd_ms", ctypes.c_float), ("n_gemm_kernel", ctypes.c_int32), ("n_jdot", ctypes.c_int32),
+                ("n_op", ctypes.c_int32), ("n_hdot", ctypes.c_int32), ("n_hupd", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
