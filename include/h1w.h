@@ -155,7 +155,10 @@ h1w_status h1w_gn_rhs(h1w_ctx* ctx, const double* dm, const double* d, double* b
  * stopping when ||r_k||_2 <= rtol ||b||_2 (the Euclidean criterion of Sec. 4)
  * on the recursively updated residual; the true residual b - A x is then
  * recomputed in FP64 and, if it fails the test, the iteration restarts from
- * it (at most max_restarts times). info may be NULL. Synchronizes. Returns
+ * it (at most max_restarts times). Vectors and scalars of the iteration are
+ * FP64; on FV grids with mg_arith = 0 the passes over J and H inside the
+ * iteration read double-float copies (about 48 bits), while the exit test
+ * uses the caller's FP64 J. info may be NULL. Synchronizes. Returns
  * H1W_ENOTCONV when maxit is reached first (x holds the last iterate). */
 h1w_status h1w_pcg(h1w_ctx* ctx, const double* b, double* x, double rtol, int32_t maxit,
                    h1w_info* info);

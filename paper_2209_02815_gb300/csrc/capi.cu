@@ -61,6 +61,7 @@ struct h1w_ctx {
   const double* J;       // borrowed
   double* H;             // m_max x N
   df* Hdf;               // m_max x N, the same as double-floats (double-float V-cycle only)
+  df* Jdf;               // m_max x N, J as double-floats for the Krylov operator passes
   df* vdf;               // N, a vector converted to double-floats
   double* C;             // m_max x m_max
   double* Lc;            // m_max x m_max
@@ -300,6 +301,7 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   double* H = B.take<double>((int64_t)m_max * N0);
   const bool use_df = (g.disc == H1W_FV_CELL) && (o.mg_arith == 0);
   df* Hdf = use_df ? B.take<df>((int64_t)m_max * N0) : nullptr;
+  df* Jdf = use_df ? B.take<df>((int64_t)m_max * N0) : nullptr;
   df* vdf = use_df ? B.take<df>(N0) : nullptr;
   double* C = B.take<double>((int64_t)m_max * m_max);
   double* Lc = B.take<double>((int64_t)m_max * m_max);
@@ -334,7 +336,7 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
     for (int k = 0; k < P.nlev; ++k) c->buf[k] = bufs[k];
     c->coarse_X = cX; c->coarse_L = cL; c->dstatus = dstatus; c->dbits = dbits;
     c->H = H; c->C = C; c->Lc = Lc; c->gemm_partial = gp; c->gemm_partial_len = gpl;
-    c->Hdf = Hdf; c->vdf = vdf;
+    c->Hdf = Hdf; c->vdf = vdf; c->Jdf = Jdf;
     c->oz = ow;
     c->oz.partial = gp;
     c->oz.status = dstatus;
@@ -447,6 +449,17 @@ void j_times(h1w_ctx* c, const double* A, const double* v, double* out, double s
   launch_reduce_partials(c->partial, rows_dot_chunks(N), c->m, scale, out, c->stream);
 }
 
+// w = J v through the double-float copy of J (Krylov passes)
+void j_times_df(h1w_ctx* c, const double* v, double* out) {
+  const int64_t N = c->lev[0].N;
+  if (c->m <= 0) return;
+  launch_d2df(N, v, c->vdf, c->stream);
+  timed_begin(c);
+  launch_rows_dot_df(c->Jdf, c->m, N, c->vdf, c->partial, c->stream);
+  timed_end(c, kCatJdot);
+  launch_reduce_partials(c->partial, rows_dot_df_chunks(N), c->m, 1.0, out, c->stream);
+}
+
 // z = P^-1 r; when rz_slot >= 0 also scal[rz_slot] = r . z
 void apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
   const int64_t N = c->lev[0].N;
@@ -459,7 +472,7 @@ void apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
       timed_begin(c);
       launch_rows_dot_df(c->Hdf, m, N, c->vdf, c->partial, c->stream);
       timed_end(c, kCatHdot);
-      launch_reduce_partials(c->partial, rows_dot_chunks(N), m, 1.0, c->svec, c->stream);
+      launch_reduce_partials(c->partial, rows_dot_df_chunks(N), m, 1.0, c->svec, c->stream);
     } else {
       timed_begin(c);
       launch_rows_dot(c->H, m, N, r, c->partial, c->stream);  // s = H^T r
@@ -481,11 +494,15 @@ void apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
 }
 
 // q = alpha (K+M) p + J^T w with w = J p given; scal[pq_slot] = p . q when pq_slot >= 0
-void apply_op_w(h1w_ctx* c, const double* p, const double* w, double* q, int pq_slot) {
+void apply_op_w(h1w_ctx* c, const double* p, const double* w, double* q, int pq_slot, bool krylov = false) {
   int nb = 0;
   timed_begin(c);
-  launch_apply_op(c->disc, c->lev[0], c->grid.alpha, p, 1.0, c->J, w, c->m > 0 ? c->m : 0, q,
-                  pq_slot >= 0 ? c->partial : nullptr, &nb, c->stream);
+  if (krylov && uses_df(c) && c->m > 0)
+    launch_apply_op_df(c->disc, c->lev[0], c->grid.alpha, p, 1.0, c->Jdf, w, c->m, q,
+                       pq_slot >= 0 ? c->partial : nullptr, &nb, c->stream);
+  else
+    launch_apply_op(c->disc, c->lev[0], c->grid.alpha, p, 1.0, c->J, w, c->m > 0 ? c->m : 0, q,
+                    pq_slot >= 0 ? c->partial : nullptr, &nb, c->stream);
   timed_end(c, kCatOp);
   if (pq_slot >= 0) launch_sum_to_scalar(c->partial, nb, c->scal + pq_slot, c->stream);
 }
@@ -670,6 +687,7 @@ h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
   const long long l0 = g_kernel_launches.load();
   if (m == 0) { c->launches_cap = 0; return H1W_OK; }
   if (c->have_ev) cudaEventRecord(c->ev[0], c->stream);
+  if (uses_df(c)) launch_d2df((int64_t)m * N, J, c->Jdf, c->stream);  // J for the Krylov passes
   vcycle_many(c, m, J, c->H, c->Hdf);                               // line H
   if (c->have_ev) cudaEventRecord(c->ev[1], c->stream);
   cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
@@ -789,10 +807,11 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
   double rel_true = 1.0;
   for (int restart = 0; restart <= c->opt.max_restarts; ++restart) {
     apply_prec_impl(c, c->r, c->z, RZ);
-    j_times(c, c->J, c->z, c->jz);
+    if (uses_df(c)) j_times_df(c, c->z, c->jz);
+    else j_times(c, c->J, c->z, c->jz);
     launch_p_update(c->p, c->z, c->w, c->jz, c->scal, N, m > 0 ? m : 0, true, s);
     while (it < maxit && std::sqrt(rr) > tol) {
-      apply_op_w(c, c->p, c->w, c->q, PQ);
+      apply_op_w(c, c->p, c->w, c->q, PQ, true);
       launch_pcg_alpha(c->scal, s);
       launch_xr_update(x, c->r, c->p, c->q, c->scal, N, c->partial, s);
       launch_sum_to_scalar(c->partial, colsum_blocks(N), c->scal + RR, s);
@@ -801,7 +820,8 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
       if (!std::isfinite(rr)) break;
       if (std::sqrt(rr) <= tol) break;
       apply_prec_impl(c, c->r, c->z, RZN);
-      j_times(c, c->J, c->z, c->jz);
+      if (uses_df(c)) j_times_df(c, c->z, c->jz);
+      else j_times(c, c->J, c->z, c->jz);
       launch_pcg_beta(c->scal, s);
       launch_p_update(c->p, c->z, c->w, c->jz, c->scal, N, m > 0 ? m : 0, false, s);
     }

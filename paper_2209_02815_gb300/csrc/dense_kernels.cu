@@ -137,49 +137,31 @@ __device__ __forceinline__ df warp_sum_df(df v) {
   return v;
 }
 
-// partial[c * m + i] = sum_{k in chunk c} A[i * N + k] * v[k], A and v double-floats
+// partial[c * m + i] = sum_{k in segment c} A[i * N + k] * v[k], A and v
+// double-floats. One warp per row of A and segment of kSegDf entries: lanes
+// stride along the row (coalesced), each lane accumulates 256 exact products
+// in a cascaded sum, and the warp reduces once at the end. The 8 warps of a
+// block share the segment of v through L1.
+constexpr int kSegDf = 8192;
+
 __global__ void __launch_bounds__(kThreads) k_rows_dot_df(const df* __restrict__ A, int m, int64_t N,
                                                           const df* __restrict__ v, double* __restrict__ partial) {
-  const int64_t k0 = (int64_t)blockIdx.x * kRowsChunk;
-  const int r0 = blockIdx.y * kRowsPerBlock;
-  df vv[kPerThread];
-#pragma unroll
-  for (int e = 0; e < kPerThread; ++e) {
-    const int64_t k = k0 + threadIdx.x + (int64_t)e * kThreads;
-    vv[e] = (k < N) ? v[k] : df_make(0.f, 0.f);
-  }
-  __shared__ df sh[kRowsPerBlock][kThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll 1
-  for (int rr = 0; rr < kRowsPerBlock; ++rr) {
-    const int row = r0 + rr;
-    float s = 0.f, e = 0.f;  // cascaded sum of exact products
-    if (row < m) {
-      const df* a = A + (int64_t)row * N;
-#pragma unroll
-      for (int q = 0; q < kPerThread; ++q) {
-        const int64_t k = k0 + threadIdx.x + (int64_t)q * kThreads;
-        if (k < N) {
-          const df p = df_mul(a[k], vv[q]);
-          const df t = two_sum(s, p.hi);
-          s = t.hi;
-          e = __fadd_rn(e, __fadd_rn(t.lo, p.lo));
-        }
-      }
-    }
-    df acc = warp_sum_df(fast_two_sum(s, e));
-    if (lane == 0) sh[rr][wid] = acc;
+  const int row = blockIdx.y * (kThreads / 32) + wid;
+  if (row >= m) return;
+  const int64_t k0 = (int64_t)blockIdx.x * kSegDf;
+  const int64_t kend = (k0 + kSegDf < N) ? k0 + kSegDf : N;
+  const df* a = A + (int64_t)row * N;
+  float s = 0.f, e = 0.f;
+#pragma unroll 8
+  for (int64_t k = k0 + lane; k < kend; k += 32) {
+    const df p = df_mul(a[k], v[k]);
+    const df t = two_sum(s, p.hi);
+    s = t.hi;
+    e = __fadd_rn(e, __fadd_rn(t.lo, p.lo));
   }
-  __syncthreads();
-  if (threadIdx.x < kRowsPerBlock) {
-    const int row = r0 + threadIdx.x;
-    if (row < m) {
-      df t = sh[threadIdx.x][0];
-#pragma unroll
-      for (int w = 1; w < kThreads / 32; ++w) t = df_add(t, sh[threadIdx.x][w]);
-      partial[(int64_t)blockIdx.x * m + row] = df_to_double(t);
-    }
-  }
+  const df acc = warp_sum_df(fast_two_sum(s, e));
+  if (lane == 0) partial[(int64_t)blockIdx.x * m + row] = df_to_double(acc);
 }
 
 // z_k = (z0_k - (1/alpha) sum_i H[i][k] v_i) / alpha with H double-floats; partial[block] = sum r_k z_k
@@ -303,24 +285,31 @@ __global__ void k_zero_upper(double* A, int n) {
 
 // ---- triangular solves, one block per right-hand side --------------------------
 
-// x <- L^-1 x (forward substitution), 32-wide blocks; x in shared memory.
+// x <- L^-1 x (forward substitution), 32-wide blocks; x in shared memory. The
+// 32 x 32 diagonal block is staged in shared memory before its sequential
+// solve so that the dependent steps do not wait on global loads.
 __global__ void __launch_bounds__(512) k_trsv_lower(const double* __restrict__ L, int n,
                                                     double* __restrict__ xg) {
   extern __shared__ double x[];
+  __shared__ double D[kNB][kNB + 1];
   double* xr = xg + (int64_t)blockIdx.x * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = xr[i];
-  __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int kb = 0; kb < n; kb += kNB) {
     const int nb = min(kNB, n - kb);
+    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+      const int r = e / kNB, c = e % kNB;
+      D[r][c] = (r < nb && c <= r) ? L[(int64_t)(kb + r) * n + kb + c] : 0.0;
+    }
+    __syncthreads();
     if (wid == 0) {
       double a = (lane < nb) ? x[kb + lane] : 0.0;
+      const double inv = (lane < nb) ? 1.0 / D[lane][lane] : 0.0;
       for (int c = 0; c < nb; ++c) {
-        double yc = 0.0;
-        if (lane == c) yc = a / L[(int64_t)(kb + c) * n + kb + c];
+        double yc = (lane == c) ? a * inv : 0.0;
         yc = __shfl_sync(0xffffffffu, yc, c);
         if (lane == c) a = yc;
-        else if (lane > c && lane < nb) a -= yc * L[(int64_t)(kb + lane) * n + kb + c];
+        else if (lane > c && lane < nb) a -= yc * D[lane][c];
       }
       if (lane < nb) x[kb + lane] = a;
     }
@@ -328,6 +317,7 @@ __global__ void __launch_bounds__(512) k_trsv_lower(const double* __restrict__ L
     for (int i = kb + nb + threadIdx.x; i < n; i += blockDim.x) {
       const double* li = L + (int64_t)i * n + kb;
       double s = 0.0;
+#pragma unroll 8
       for (int c = 0; c < nb; ++c) s += li[c] * x[kb + c];
       x[i] -= s;
     }
@@ -340,28 +330,34 @@ __global__ void __launch_bounds__(512) k_trsv_lower(const double* __restrict__ L
 __global__ void __launch_bounds__(512) k_trsv_upper_t(const double* __restrict__ L, int n,
                                                       double* __restrict__ xg) {
   extern __shared__ double x[];
+  __shared__ double D[kNB][kNB + 1];
   double* xr = xg + (int64_t)blockIdx.x * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = xr[i];
-  __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nblk = (n + kNB - 1) / kNB;
   for (int bi = nblk - 1; bi >= 0; --bi) {
     const int kb = bi * kNB;
     const int nb = min(kNB, n - kb);
+    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+      const int r = e / kNB, c = e % kNB;
+      D[r][c] = (r < nb && c <= r) ? L[(int64_t)(kb + r) * n + kb + c] : 0.0;
+    }
+    __syncthreads();
     if (wid == 0) {
       double a = (lane < nb) ? x[kb + lane] : 0.0;
+      const double inv = (lane < nb) ? 1.0 / D[lane][lane] : 0.0;
       for (int c = nb - 1; c >= 0; --c) {
-        double vc = 0.0;
-        if (lane == c) vc = a / L[(int64_t)(kb + c) * n + kb + c];
+        double vc = (lane == c) ? a * inv : 0.0;
         vc = __shfl_sync(0xffffffffu, vc, c);
         if (lane == c) a = vc;
-        else if (lane < c) a -= vc * L[(int64_t)(kb + c) * n + kb + lane];
+        else if (lane < c) a -= vc * D[c][lane];
       }
       if (lane < nb) x[kb + lane] = a;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kb; i += blockDim.x) {
       double s = 0.0;
+#pragma unroll 8
       for (int c = 0; c < nb; ++c) s += L[(int64_t)(kb + c) * n + i] * x[kb + c];
       x[i] -= s;
     }
@@ -549,9 +545,11 @@ void launch_reduce_partials(const double* partial, int nchunks, int m, double sc
   note_launches(1);
 }
 
+int rows_dot_df_chunks(int64_t N) { return (int)((N + kSegDf - 1) / kSegDf); }
+
 void launch_rows_dot_df(const df* A, int m, int64_t N, const df* v, double* partial, cudaStream_t s) {
   if (m <= 0) return;
-  dim3 g(rows_dot_chunks(N), (m + kRowsPerBlock - 1) / kRowsPerBlock);
+  dim3 g(rows_dot_df_chunks(N), (m + kThreads / 32 - 1) / (kThreads / 32));
   k_rows_dot_df<<<g, kThreads, 0, s>>>(A, m, N, v, partial);
   note_launches(1);
 }

@@ -100,6 +100,9 @@ void launch_apply_op(int disc, const Level& L, double ca, const double* p, doubl
                      const double* J, const double* w, int m, double* out, double* partial,
                      int* nblocks_out, cudaStream_t s);
 int apply_op_blocks(const Level& L);
+// the same with J stored as double-floats (Jd, m x N)
+void launch_apply_op_df(int disc, const Level& L, double ca, const double* p, double cj, const df* Jd,
+                        const double* w, int m, double* out, double* partial, int* nblocks_out, cudaStream_t s);
 
 // ---- double-float V-cycle on FV grids (mg_df64.cu) ----------------------------
 void launch_cheb_first_df(const Level& L, int nrhs, const df* b, df* x, df* r, df* d, bool zero_x, df inv_theta,
@@ -129,6 +132,7 @@ void launch_woodbury_update(const double* H, int m, int64_t N, const double* v, 
                             double alpha, double* z, const double* r, double* partial,
                             cudaStream_t s);
 // the same two preconditioner passes with H (and v) stored as double-floats
+int rows_dot_df_chunks(int64_t N);
 void launch_rows_dot_df(const df* A, int m, int64_t N, const df* v, double* partial, cudaStream_t s);
 void launch_woodbury_update_df(const df* H, int m, int64_t N, const double* v, const double* z0, double alpha,
                                double* z, const double* r, double* partial, cudaStream_t s);

@@ -397,6 +397,44 @@ __global__ void __launch_bounds__(kThreads) k_apply_op(Level L, double ca, const
   }
 }
 
+// out = ca * (A p) + cj * sum_i Jd[i][k] w[i], with J as double-floats (the
+// stencil part in FP64); partial[block] = sum_k p_k out_k when partial != null.
+template <class D>
+__global__ void __launch_bounds__(kThreads) k_apply_op_df(Level L, double ca, const double* __restrict__ p,
+                                                          double cj, const df* __restrict__ Jd,
+                                                          const double* __restrict__ w, int m,
+                                                          double* __restrict__ out,
+                                                          double* __restrict__ partial) {
+  extern __shared__ df swd[];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) swd[i] = df_from_double(w[i]);
+  __syncthreads();
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double prod = 0.0;
+  if (q < L.N) {
+    int i, j, k;
+    decompose(L, q, i, j, k);
+    double dg;
+    double v = ca * D::apply(L, p, i, j, k, q, dg);
+    if (m > 0) {
+      float s = 0.f, e = 0.f;
+      const df* col = Jd + q;
+      for (int r = 0; r < m; ++r) {
+        const df t = df_mul(col[(int64_t)r * L.N], swd[r]);
+        const df u = two_sum(s, t.hi);
+        s = u.hi;
+        e = __fadd_rn(e, __fadd_rn(u.lo, t.lo));
+      }
+      v += cj * df_to_double(fast_two_sum(s, e));
+    }
+    out[q] = v;
+    prod = p[q] * v;
+  }
+  if (partial) {
+    const double t = block_sum(prod);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  }
+}
+
 inline dim3 grid_for(int64_t N, int nrhs) {
   return dim3((unsigned)((N + kThreads - 1) / kThreads), (unsigned)nrhs);
 }
@@ -461,6 +499,15 @@ void launch_assemble_dense(int disc, const Level& L, double* A, cudaStream_t s) 
 }
 
 int apply_op_blocks(const Level& L) { return (int)((L.N + kThreads - 1) / kThreads); }
+
+void launch_apply_op_df(int disc, const Level& L, double ca, const double* p, double cj, const df* Jd,
+                        const double* w, int m, double* out, double* partial, int* nblocks_out, cudaStream_t s) {
+  const int nb = apply_op_blocks(L);
+  if (nblocks_out) *nblocks_out = nb;
+  const size_t smem = sizeof(df) * (size_t)(m > 0 ? m : 1);
+  H1W_DISPATCH(disc, k_apply_op_df, <<<nb, kThreads, smem, s>>>(L, ca, p, cj, Jd, w, m, out, partial));
+  note_launches(1);
+}
 
 void launch_apply_op(int disc, const Level& L, double ca, const double* p, double cj,
                      const double* J, const double* w, int m, double* out, double* partial,

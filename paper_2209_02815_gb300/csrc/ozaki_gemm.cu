@@ -383,39 +383,56 @@ __global__ void k_row_exp_balanced(const double* __restrict__ X, int m, long lon
 //   [row block of R rows][K block of 32][slice p][row r][32 BF16, 64-byte swizzle]
 // where the 16-byte chunk c of row r sits at chunk c ^ ((r >> 1) & 3) (the
 // 64-byte swizzle of the K-major UMMA operand layout, 512-byte atoms).
+__device__ __forceinline__ long long digits_source(double x, int erow, int s) {
+  // Y = round(|x| 2^(sign s) 2^(47 - e)) with the sign of x (integer arithmetic on the bits)
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int ex = static_cast<int>((b >> 52) & 0x7FF);
+  const long long M = static_cast<long long>((b & 0xFFFFFFFFFFFFFull) | (ex ? (1ull << 52) : 0ull));
+  const int sh = 1028 + erow - (ex ? ex : 1) - s;
+  long long Y = 0;
+  if (M != 0 && sh >= 1 && sh <= 54) Y = (M + (1ll << (sh - 1))) >> sh;
+  return (b >> 63) ? -Y : Y;
+}
+
+// One thread per 8 consecutive K entries (one 16-byte swizzle chunk) of one row:
+// reads 8 values, writes one 16-byte chunk per digit slice.
 __global__ void k_split_digits(const double* __restrict__ X, int m, long long N, long long k0, long long kw,
                                long long klen, int R, const int* __restrict__ e, const short* __restrict__ sk,
                                int sign, uint16_t* __restrict__ S) {
-  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long kc = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) * 8;  // first K of the chunk
   const int row = blockIdx.y;
-  if (k >= klen) return;
-  long long Y = 0;
-  if (k < kw && row < m) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(X[row * N + k0 + k]));
-    const int ex = static_cast<int>((b >> 52) & 0x7FF);
-    const long long M = static_cast<long long>((b & 0xFFFFFFFFFFFFFull) | (ex ? (1ull << 52) : 0ull));
-    // |x| 2^(sign s) = M 2^(ex_eff - 1075 + sign s); Y = round(that * 2^(47 - e))
-    const int sh = 1028 + e[row] - (ex ? ex : 1) - sign * sk[k0 + k];
-    if (M != 0 && sh >= 1 && sh <= 54) Y = (M + (1ll << (sh - 1))) >> sh;
-    if (b >> 63) Y = -Y;
-  }
-  int d[kSlices];
+  if (kc >= klen) return;
+  uint32_t packed[kSlices][4];
 #pragma unroll
-  for (int p = kSlices - 1; p >= 1; --p) {
-    const long long r = ((Y + 32) & 63) - 32;
-    d[p] = static_cast<int>(r);
-    Y = (Y - r) >> 6;
+  for (int t = 0; t < 8; ++t) {
+    const long long k = kc + t;
+    long long Y = 0;
+    if (k < kw && row < m) Y = digits_source(X[row * N + k0 + k], e[row], sign * sk[k0 + k]);
+    int d[kSlices];
+#pragma unroll
+    for (int p = kSlices - 1; p >= 1; --p) {
+      const long long r = ((Y + 32) & 63) - 32;
+      d[p] = static_cast<int>(r);
+      Y = (Y - r) >> 6;
+    }
+    d[0] = static_cast<int>(Y);
+#pragma unroll
+    for (int p = 0; p < kSlices; ++p) {
+      const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d[p])));
+      if (t & 1) packed[p][t >> 1] |= h << 16;
+      else packed[p][t >> 1] = h;
+    }
   }
-  d[0] = static_cast<int>(Y);
   const int rb = row / R, ri = row % R;
-  const long long kb = k / kKt;
-  const int kin = static_cast<int>(k % kKt);
-  const int elem = (((kin >> 3) ^ ((ri >> 1) & 3)) << 3) | (kin & 7);
+  const long long kb = kc / kKt;
+  const int chunk = static_cast<int>((kc % kKt) >> 3);
+  const int pchunk = chunk ^ ((ri >> 1) & 3);
   const long long nkb = klen / kKt;
-  uint16_t* base = S + ((static_cast<long long>(rb) * nkb + kb) * kSlices) * (R * kKt) + ri * kKt + elem;
+  uint16_t* base = S + ((static_cast<long long>(rb) * nkb + kb) * kSlices) * (R * kKt) + ri * kKt + pchunk * 8;
 #pragma unroll
   for (int p = 0; p < kSlices; ++p)
-    base[static_cast<long long>(p) * R * kKt] = __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d[p])));
+    *reinterpret_cast<uint4*>(base + static_cast<long long>(p) * R * kKt) =
+        make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
 }
 
 __global__ void k_fill_int(int* p, int n, int v) {
@@ -486,10 +503,11 @@ bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long
   for (long long k0 = 0; k0 < N; k0 += kp, ++panel) {
     const long long kw = (N - k0) < kp ? (N - k0) : kp;
     const int rowsA = (m + kTileM - 1) / kTileM * kTileM, rowsB = (m + kTileN - 1) / kTileN * kTileN;
-    k_split_digits<<<dim3(static_cast<unsigned>((kp + 255) / 256), rowsA), 256, 0, s>>>(
-        J, m, N, k0, kw, kp, kTileM, w.expo, w.colexp, +1, static_cast<uint16_t*>(w.digitsA));
-    k_split_digits<<<dim3(static_cast<unsigned>((kp + 255) / 256), rowsB), 256, 0, s>>>(
-        H, m, N, k0, kw, kp, kTileN, w.expo + m, w.colexp, -1, static_cast<uint16_t*>(w.digitsB));
+    const unsigned gx = static_cast<unsigned>((kp / 8 + 127) / 128);
+    k_split_digits<<<dim3(gx, rowsA), 128, 0, s>>>(J, m, N, k0, kw, kp, kTileM, w.expo, w.colexp, +1,
+                                                   static_cast<uint16_t*>(w.digitsA));
+    k_split_digits<<<dim3(gx, rowsB), 128, 0, s>>>(H, m, N, k0, kw, kp, kTileN, w.expo + m, w.colexp, -1,
+                                                   static_cast<uint16_t*>(w.digitsB));
     OzakiArgs a;
     a.dA = static_cast<const uint16_t*>(w.digitsA);
     a.dB = static_cast<const uint16_t*>(w.digitsB);
