@@ -313,8 +313,7 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   if (oz) {
     ow.digitsA = B.take<uint16_t>((size_t)8 * ((m_max + 127) / 128 * 128) * kp);
     ow.digitsB = B.take<uint16_t>((size_t)8 * ((m_max + 63) / 64 * 64) * kp);
-    ow.colexp = B.take<short>((size_t)N0);
-    ow.expo = B.take<int>(2 * (size_t)m_max);
+    ow.expo = B.take<int>(2 * (size_t)m_max * ozaki_chunks(N0));
     ow.tiles = B.take<int>(2 * (size_t)ozaki_num_tiles(m_max));
     ow.klen = kp;
   }

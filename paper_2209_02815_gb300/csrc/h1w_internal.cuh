@@ -62,14 +62,14 @@ enum : int { kStatusNotSpd = 1, kStatusTimeout = 2 };
 struct OzakiWork {
   void* digitsA;                 // BF16 digits of a K panel of J, stage-tiled (128-row blocks)
   void* digitsB;                 // BF16 digits of the same panel of H, stage-tiled (64-row blocks)
-  short* colexp;                 // [N] column balance exponents s_k
-  int* expo;                     // [2m] row exponents of the balanced J, then H
+  int* expo;                     // chunk exponents [N/1024][m] of J, then of H
   int* tiles;                    // [2 * tiles] (row block, column block)
   double* partial;               // [splits][m][m]
   int* status;                   // device status word
   long long klen;                // K panel width (multiple of 2048)
 };
 long long ozaki_panel_width(long long N);
+long long ozaki_chunks(long long N);
 int ozaki_num_tiles(int m);
 int ozaki_splits(int m, long long kp);
 bool ozaki_supported();

@@ -10,15 +10,14 @@
 // "digits" and multiplied digit by digit on the tensor cores, with every
 // FP32 accumulation kept exact:
 //
-//  * Column balancing: column k of J is scaled by 2^s_k and column k of H by
-//    2^-s_k (exact; J H^T is unchanged), s_k = floor((b_k - a_k) / 2) from
-//    the binary exponents a_k, b_k of the column maxima, so that peaked
-//    sensitivity columns do not dominate their rows.
-//  * Row scaling: row i of the balanced J (or H) has an exponent e_i with
-//    max_k |x_ik| < 2^e_i. Each entry becomes the integer
-//    Y = round(x 2^(47 - e_i)), |Y| <= 2^47, written in balanced base 64 as
-//    eight digits Y = sum_p d_p 64^(7-p), d_p in [-32, 32]; each digit is
-//    exact in BF16. The rounding error is at most 2^-48 of the row maximum.
+//  * Chunk scaling: for each row i of J (or H) and each chunk c of 1024
+//    consecutive K entries an exponent e_ic with max_{k in c} |x_ik| < 2^e_ic.
+//    Each entry becomes the integer Y = round(x 2^(47 - e_ic)), |Y| <= 2^47,
+//    written in balanced base 64 as eight digits Y = sum_p d_p 64^(7-p),
+//    d_p in [-32, 32]; each digit is exact in BF16. Scaling per chunk rather
+//    than per row keeps the error of the dropped digit pairs proportional to
+//    the chunk's own maxima, which matters for sensitivity rows that peak
+//    sharply near the electrodes (a 100-fold smaller error in C there).
 //  * Digit products d_p d'_q (|.| <= 2^10) of the same level l = p + q are
 //    summed into one FP32 TMEM accumulator (64 columns per level); pairs with
 //    p + q > 7 (weight below 2^-48) are dropped, leaving 36 pairs in 8 levels,
@@ -28,9 +27,8 @@
 //    so the FP32 accumulation is exact.
 //  * After every chunk the epilogue warps read the 8 level sums from TMEM,
 //    combine them exactly in 64-bit integers as T_hi = sum_{l<4} S_l 64^(3-l)
-//    and T_lo = sum_{l>=4} S_l 64^(7-l), and add 2^24 T_hi + T_lo to FP64
-//    accumulators. The tile result is
-//    sum_k x_ik y_jk ~= 2^(e_i + f_j - 52) * sum_chunks (2^24 T_hi + T_lo).
+//    and T_lo = sum_{l>=4} S_l 64^(7-l), and add
+//    2^(e_ic + f_jc - 52) (2^24 T_hi + T_lo) to FP64 accumulators.
 //
 // Kernel layout: one CTA per (128 x 64 output tile, K range); warp 0 moves
 // all eight digit slices of both operands per 32-wide K stage with two bulk
@@ -144,8 +142,9 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 struct OzakiArgs {
   const uint16_t* dA;   // digits of J, stage-tiled (see k_split_digits)
   const uint16_t* dB;   // digits of H, stage-tiled
-  const int* eA;        // row exponents of J
-  const int* eB;        // row exponents of H
+  const int* eA;        // chunk exponents of J, [global chunk][m]
+  const int* eB;        // chunk exponents of H, [global chunk][m]
+  long long chunk0;     // global index of the panel's first chunk
   const int2* tiles;    // (128-row block of J, 64-row block of H)
   double* partial;      // [gridDim.y][m][m]
   int* status;
@@ -265,7 +264,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
     double acc[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+    const int row = row0 + 32 * quad + lane;
+    const int colb = col0 + half * 32;
     for (int c = 0; c < nchunks; ++c) {
+      // per-chunk scale factors 2^(e_row + f_col - 52) for this thread's 32 columns
+      const long long gch = g.chunk0 + kbeg / kChunkK + c;
+      const int er = (row < g.m) ? g.eA[gch * g.m + row] : -100000;
       // lane 0 waits; the warp follows its verdict so that the .sync.aligned
       // TMEM loads below stay warp-uniform
       int ok = 1;
@@ -288,25 +292,32 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) T[j] = T[j] * 64 + static_cast<long long>(__float2int_rn(__uint_as_float(v[j])));
         }
-        const double w = grp == 0 ? 16777216.0 : 1.0;  // 64^4 for the upper group
+        if (grp == 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&bars[5]));  // TMEM may be overwritten now
+        }
+        // the upper group carries the weight 64^4 = 2^24
+        const int wexp = grp == 0 ? 24 : 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = fma(static_cast<double>(T[j]), w, acc[j]);
+        for (int j = 0; j < 32; ++j) {
+          const int col = colb + j;
+          const int ec = (col < g.m) ? g.eB[gch * g.m + col] : -100000;
+          const int k2 = er + ec - 52 + wexp;
+          // 2^k2 from its bit pattern (0 below the normal range; such chunks are negligible)
+          const double scale = (k2 >= -1022 && k2 <= 1023)
+                                   ? __longlong_as_double(static_cast<long long>(k2 + 1023) << 52)
+                                   : 0.0;
+          acc[j] = fma(static_cast<double>(T[j]), scale, acc[j]);
+        }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bars[5]));
     }
-    const int row = row0 + 32 * quad + lane;
     if (!*abort_flag && row < g.m) {
       double* dst = g.partial + static_cast<long long>(blockIdx.y) * g.m * g.m + static_cast<long long>(row) * g.m;
-      const int er = g.eA[row];
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        const int col = col0 + half * 32 + j;
-        if (col < g.m) {
-          const double v = ldexp(acc[j], er + g.eB[col] - 52);
-          dst[col] = g.accumulate ? dst[col] + v : v;
-        }
+        const int col = colb + j;
+        if (col < g.m) dst[col] = g.accumulate ? dst[col] + acc[j] : acc[j];
       }
     }
   }
@@ -341,54 +352,39 @@ __device__ __forceinline__ int exp_field(double x) {
   return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7FF);
 }
 
-// Column balance exponents: s_k = floor((b_k - a_k) / 2) with a_k, b_k the
-// exponent fields of max_i |J_ik| and max_i |H_ik| (0 when a column is zero).
-__global__ void k_col_balance(const double* __restrict__ Jm, const double* __restrict__ Hm, int m, long long N,
-                              short* __restrict__ sk) {
-  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  int a = 0, b = 0;
-  for (int i = 0; i < m; ++i) {
-    const int ea = exp_field(Jm[i * N + k]);
-    const int eb = exp_field(Hm[i * N + k]);
-    a = ea > a ? ea : a;
-    b = eb > b ? eb : b;
-  }
-  sk[k] = (a == 0 || b == 0) ? 0 : static_cast<short>((b - a) >> 1);
-}
-
-// Row exponents of the balanced matrix X 2^(sign * s_k): e[i] with max_k |x_ik 2^(sign s_k)| < 2^e[i].
-__global__ void k_row_exp_balanced(const double* __restrict__ X, int m, long long N, const short* __restrict__ sk,
-                                   int sign, int* __restrict__ emax) {
+// Chunk exponents e[c][i] with max_{k in chunk c} |X[i][k]| < 2^e (-100000 for an
+// all-zero chunk); one block per (chunk, row).
+__global__ void k_chunk_exp(const double* __restrict__ X, int m, long long N, int* __restrict__ e) {
   const int row = blockIdx.y;
-  int best = -100000;
-  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < N;
-       k += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int ex = exp_field(X[row * N + k]);
-    if (ex != 0) {  // zeros (and subnormals) do not raise the row maximum
-      const int e = ex - 1022 + sign * sk[k];  // |x| 2^(sign s_k) < 2^e
-      best = e > best ? e : best;
+  const long long k0 = static_cast<long long>(blockIdx.x) * kChunkK;
+  int best = 0;
+  for (int t = threadIdx.x; t < kChunkK; t += blockDim.x) {
+    const long long k = k0 + t;
+    if (k < N) {
+      const int ex = exp_field(X[row * N + k]);
+      best = ex > best ? ex : best;
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
     const int t = __shfl_down_sync(0xffffffffu, best, o);
     best = t > best ? t : best;
   }
-  if ((threadIdx.x & 31) == 0) atomicMax(emax + row, best);
+  __shared__ int sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = sh[w] > b ? sh[w] : b;
+    e[static_cast<long long>(blockIdx.x) * m + row] = b ? b - 1022 : -100000;
+  }
 }
 
-// Digits of X[i][k0 + k] 2^(sign s_k) for k < kw (zeros for kw <= k < klen and
-// for padded rows m <= i < rows_pad), written in the exact shared-memory image
-// of a pipeline stage so that one bulk copy moves a stage:
-//   [row block of R rows][K block of 32][slice p][row r][32 BF16, 64-byte swizzle]
-// where the 16-byte chunk c of row r sits at chunk c ^ ((r >> 1) & 3) (the
-// 64-byte swizzle of the K-major UMMA operand layout, 512-byte atoms).
-__device__ __forceinline__ long long digits_source(double x, int erow, int s) {
-  // Y = round(|x| 2^(sign s) 2^(47 - e)) with the sign of x (integer arithmetic on the bits)
+__device__ __forceinline__ long long digits_source(double x, int echunk) {
+  // Y = round(|x| 2^(47 - e)) with the sign of x (integer arithmetic on the bits)
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   const int ex = static_cast<int>((b >> 52) & 0x7FF);
   const long long M = static_cast<long long>((b & 0xFFFFFFFFFFFFFull) | (ex ? (1ull << 52) : 0ull));
-  const int sh = 1028 + erow - (ex ? ex : 1) - s;
+  const int sh = 1028 + echunk - (ex ? ex : 1);
   long long Y = 0;
   if (M != 0 && sh >= 1 && sh <= 54) Y = (M + (1ll << (sh - 1))) >> sh;
   return (b >> 63) ? -Y : Y;
@@ -397,17 +393,17 @@ __device__ __forceinline__ long long digits_source(double x, int erow, int s) {
 // One thread per 8 consecutive K entries (one 16-byte swizzle chunk) of one row:
 // reads 8 values, writes one 16-byte chunk per digit slice.
 __global__ void k_split_digits(const double* __restrict__ X, int m, long long N, long long k0, long long kw,
-                               long long klen, int R, const int* __restrict__ e, const short* __restrict__ sk,
-                               int sign, uint16_t* __restrict__ S) {
+                               long long klen, int R, const int* __restrict__ e, uint16_t* __restrict__ S) {
   const long long kc = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) * 8;  // first K of the chunk
   const int row = blockIdx.y;
   if (kc >= klen) return;
+  const int echunk = (row < m && kc < kw) ? e[((k0 + kc) / kChunkK) * m + row] : 0;
   uint32_t packed[kSlices][4];
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     const long long k = kc + t;
     long long Y = 0;
-    if (k < kw && row < m) Y = digits_source(X[row * N + k0 + k], e[row], sign * sk[k0 + k]);
+    if (k < kw && row < m) Y = digits_source(X[row * N + k0 + k], echunk);
     int d[kSlices];
 #pragma unroll
     for (int p = kSlices - 1; p >= 1; --p) {
@@ -486,14 +482,12 @@ bool ozaki_supported() {
 bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long N, const OzakiWork& w, int splits,
                               cudaStream_t s, void (*before)(void*), void (*after)(void*), void* hook_arg) {
   const long long kp = w.klen;
-  k_col_balance<<<static_cast<unsigned>((N + 255) / 256), 256, 0, s>>>(J, H, m, N, w.colexp);
-  {
-    k_fill_int<<<(2 * m + 127) / 128, 128, 0, s>>>(w.expo, 2 * m, -100000);
-    dim3 g(64, m);
-    k_row_exp_balanced<<<g, 256, 0, s>>>(J, m, N, w.colexp, +1, w.expo);
-    k_row_exp_balanced<<<g, 256, 0, s>>>(H, m, N, w.colexp, -1, w.expo + m);
-    note_launches(4);
-  }
+  const long long nch = (N + kChunkK - 1) / kChunkK;
+  int* eA = w.expo;
+  int* eB = w.expo + nch * m;
+  k_chunk_exp<<<dim3(static_cast<unsigned>(nch), m), 256, 0, s>>>(J, m, N, eA);
+  k_chunk_exp<<<dim3(static_cast<unsigned>(nch), m), 256, 0, s>>>(H, m, N, eB);
+  note_launches(2);
   if (cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
     return false;
   const int tiles = ozaki_num_tiles(m);
@@ -504,15 +498,16 @@ bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long
     const long long kw = (N - k0) < kp ? (N - k0) : kp;
     const int rowsA = (m + kTileM - 1) / kTileM * kTileM, rowsB = (m + kTileN - 1) / kTileN * kTileN;
     const unsigned gx = static_cast<unsigned>((kp / 8 + 127) / 128);
-    k_split_digits<<<dim3(gx, rowsA), 128, 0, s>>>(J, m, N, k0, kw, kp, kTileM, w.expo, w.colexp, +1,
+    k_split_digits<<<dim3(gx, rowsA), 128, 0, s>>>(J, m, N, k0, kw, kp, kTileM, eA,
                                                    static_cast<uint16_t*>(w.digitsA));
-    k_split_digits<<<dim3(gx, rowsB), 128, 0, s>>>(H, m, N, k0, kw, kp, kTileN, w.expo + m, w.colexp, -1,
+    k_split_digits<<<dim3(gx, rowsB), 128, 0, s>>>(H, m, N, k0, kw, kp, kTileN, eB,
                                                    static_cast<uint16_t*>(w.digitsB));
     OzakiArgs a;
     a.dA = static_cast<const uint16_t*>(w.digitsA);
     a.dB = static_cast<const uint16_t*>(w.digitsB);
-    a.eA = w.expo;
-    a.eB = w.expo + m;
+    a.eA = eA;
+    a.eB = eB;
+    a.chunk0 = k0 / kChunkK;
     a.tiles = reinterpret_cast<const int2*>(w.tiles);
     a.partial = w.partial;
     a.status = w.status;
@@ -527,5 +522,7 @@ bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long
   }
   return true;
 }
+
+long long ozaki_chunks(long long N) { return (N + kChunkK - 1) / kChunkK; }
 
 }  // namespace h1w
