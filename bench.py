@@ -38,6 +38,11 @@ ALPHA = 1e-3
 RTOL = 1e-8
 MAXIT = 1000
 METRIC = "GN linear solves/s at rel-res 1e-8"
+# FP32 instructions per fine cell of the fused double-float legs (isotropic 7-point operator):
+# down 7 (g) + 91 (two Chebyshev steps) + 92 (residual) + 45 (restriction);
+# up 67 (separable prolongation and add) + 99 (r0, d0) + 99 (final update)
+FP32_OPS_DOWN = 235
+FP32_OPS_UP = 265
 WORKLOAD = "3D ERT GN step, 128^3 cell-centred FV, m=496 pole-dipole, alpha=1e-3, FP64"
 
 
@@ -233,7 +238,7 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         phase = {"t_H_ms": [], "t_C_ms": [], "t_chol_ms": [], "t_pcg_ms": []}
-        kern = {k_: [0.0, 0] for k_ in ("gemm_kernel", "jdot", "op", "hdot", "hupd")}
+        kern = {k_: [0.0, 0] for k_ in ("gemm_kernel", "jdot", "op", "hdot", "hupd", "vc_down", "vc_up")}
         launches = 0
         iters = []
         e0.record(stream)
@@ -312,10 +317,21 @@ def run_ours(args):
     mat = 8.0 * m * N
     rate("k_ozaki_gemm", kern["gemm_kernel"][0], kern["gemm_kernel"][1], gemm_flops_launch, "TFLOP/s", "tensor",
          bf16_sus, "BF16 digit-pair products of one 262144-wide K panel; peak = measured sustained BF16")
-    rate("k_rows_dot (J z, FP64)", kern["jdot"][0], kern["jdot"][1], mat + 8.0 * N, "GB/s", "hbm", hbm,
-         "bytes of J and z per pass; FP64 pipe limits it to ~1 FMA per 8 bytes")
-    rate("k_apply_op<FV> (stencil + J^T w, FP64)", kern["op"][0], kern["op"][1], mat + 16.0 * N, "GB/s", "hbm", hbm,
-         "bytes of J, p and q per pass")
+    rate("k_rows_dot_df (J z)", kern["jdot"][0], kern["jdot"][1], mat + 8.0 * N, "GB/s", "hbm", hbm,
+         "bytes of J (double-float) and z per pass")
+    rate("k_apply_op_df<FV> (stencil + J^T w)", kern["op"][0], kern["op"][1], mat + 16.0 * N, "GB/s", "hbm", hbm,
+         "bytes of J (double-float), p and q per pass")
+    # fused V-cycle legs on the finest level: issue-bound double-float arithmetic. Algorithmic
+    # FP32 instructions per fine cell (FMA counted once) of the operations the legs require,
+    # halo recomputation excluded; peak = 152 SMs x 128 FP32 lanes x the maximum SM clock.
+    alu_peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    for key, name, ops in (("vc_down", "k_pre_fused (finest level: smoothing + residual + restriction)",
+                            FP32_OPS_DOWN),
+                           ("vc_up", "k_post_fused (finest level: prolongation + smoothing)", FP32_OPS_UP)):
+        n_ = kern[key][1]
+        if n_:
+            rate(name, kern[key][0], n_, ops * float(m) * N * args.steps / n_, "TFLOP/s", "alu", alu_peak,
+                 "%d FP32 instructions per fine cell and right-hand side; peak = FP32 issue rate" % ops)
     rate("k_rows_dot_df (H^T r)", kern["hdot"][0], kern["hdot"][1], mat + 8.0 * N, "GB/s", "hbm", hbm,
          "bytes of H (double-float) and r per pass")
     rate("k_woodbury_update_df (z update)", kern["hupd"][0], kern["hupd"][1], mat + 32.0 * N, "GB/s", "hbm", hbm,

@@ -73,7 +73,9 @@ typedef struct {
                             operands (48-bit, default), 1 = FP64 CUDA cores */
   int32_t mg_arith;      /* V-cycle arithmetic on FV grids: 0 = double-float (FP32 pairs, about
                             48 bits, default), 1 = FP64. Q1 grids always use FP64. */
-  int32_t reserved;      /* must be 0 */
+  int32_t mg_unfused;    /* double-float cycle: 0 = levels with all axes coarsened and the degree-2
+                            smoother run each leg (smoothing, residual and transfer) as one kernel
+                            (default), 1 = one kernel per step. Both give identical results. */
 } h1w_options;
 
 typedef struct {
@@ -96,11 +98,14 @@ typedef struct {
   int64_t launches_pcg;         /* kernels launched by the last h1w_pcg */
   /* device time and launch count of individual kernels in those two calls */
   float t_gemm_kernel_ms;       /* capacitance GEMM kernel launches (line C) */
-  float t_jdot_ms;              /* FP64 passes J z over J inside PCG */
-  float t_op_ms;                /* FP64 operator kernel (stencil + J^T w) inside PCG */
+  float t_jdot_ms;              /* passes J z over J inside PCG */
+  float t_op_ms;                /* operator kernel (stencil + J^T w) inside PCG */
   float t_hdot_ms;              /* passes H^T r over H inside PCG */
   float t_hupd_ms;              /* passes z = (z0 - H v / alpha) / alpha over H inside PCG */
   int32_t n_gemm_kernel, n_jdot, n_op, n_hdot, n_hupd, reserved;
+  float t_vc_down_ms;           /* fused down-leg kernel of the finest level (line H, double-float cycle) */
+  float t_vc_up_ms;             /* fused up-leg kernel of the finest level (line H, double-float cycle) */
+  int32_t n_vc_down, n_vc_up;
 } h1w_timings;
 
 typedef struct h1w_ctx h1w_ctx;

@@ -49,6 +49,7 @@ struct h1w_ctx {
   int nlev;
   Level lev[kMaxLevels];
   ChebCoef cheb[kMaxLevels];
+  FusedCoef fco[kMaxLevels];
   LevelBufs buf[kMaxLevels];
   std::vector<double> qhost[kMaxLevels][2];  // Q1 1D coefficients (host copy)
   double* qdev;          // Q1 coefficients, all levels
@@ -84,6 +85,7 @@ struct h1w_ctx {
   int kcat[kTimed];
   int nk;
   bool timing_on;
+  bool time_vc = false;  // record the finest-level fused V-cycle kernels (line H only)
   float cat_ms[8];
   int cat_n[8];
   long long launches_cap, launches_pcg;
@@ -101,7 +103,7 @@ h1w_status h1w::set_global_error(h1w_status st, const std::string& msg) {
 
 namespace {
 
-enum { kCatGemm = 0, kCatJdot = 1, kCatOp = 2, kCatHdot = 3, kCatHupd = 4, kCatCount = 5 };
+enum { kCatGemm = 0, kCatJdot = 1, kCatOp = 2, kCatHdot = 3, kCatHupd = 4, kCatDown = 5, kCatUp = 6, kCatCount = 7 };
 
 void timed_begin(h1w_ctx* c) {
   if (c->timing_on && c->have_ev && c->nk < h1w_ctx::kTimed) cudaEventRecord(c->kev[c->nk][0], c->stream);
@@ -259,7 +261,7 @@ h1w_status validate(const h1w_grid* g, int32_t m_max, const h1w_options* o, std:
     if (o->max_restarts < 0 || o->max_restarts > 100) { why = "max_restarts out of range"; return H1W_EINVAL; }
     if (o->cap_gemm != 0 && o->cap_gemm != 1) { why = "cap_gemm must be 0 or 1"; return H1W_EINVAL; }
     if (o->mg_arith != 0 && o->mg_arith != 1) { why = "mg_arith must be 0 or 1"; return H1W_EINVAL; }
-    if (o->reserved != 0) { why = "reserved must be 0"; return H1W_EINVAL; }
+    if (o->mg_unfused != 0 && o->mg_unfused != 1) { why = "mg_unfused must be 0 or 1"; return H1W_EINVAL; }
   }
   return H1W_OK;
 }
@@ -298,8 +300,9 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   double* cL = B.take<double>(Nc * Nc);
   int* dstatus = B.take<int>(4);
   unsigned long long* dbits = B.take<unsigned long long>(4);
-  double* H = B.take<double>((int64_t)m_max * N0);
   const bool use_df = (g.disc == H1W_FV_CELL) && (o.mg_arith == 0);
+  // FP64 H: not needed when the cycle is double-float and C runs on the tensor cores
+  double* H = B.take<double>((use_df && o.cap_gemm == 0) ? 1 : (int64_t)m_max * N0);
   df* Hdf = use_df ? B.take<df>((int64_t)m_max * N0) : nullptr;
   df* Jdf = use_df ? B.take<df>((int64_t)m_max * N0) : nullptr;
   df* vdf = use_df ? B.take<df>(N0) : nullptr;
@@ -391,14 +394,13 @@ void vcycle_block(h1w_ctx* c, int nrhs, const double* b0, double* x0) {
 
 inline df* dfp(double* p) { return reinterpret_cast<df*>(p); }
 
-void smooth_df(h1w_ctx* c, int l, int nrhs, bool zero_x) {
+void smooth_df(h1w_ctx* c, int l, int nrhs, const df* b, df* x, bool zero_x) {
   const Level& L = c->lev[l];
   const ChebCoef& K = c->cheb[l];
-  df* x = dfp(c->buf[l].x);
   df* r = dfp(c->buf[l].r);
   df* da = dfp(c->buf[l].da);
   df* db = dfp(c->buf[l].db);
-  launch_cheb_first_df(L, nrhs, dfp(c->buf[l].b), x, r, da, zero_x, K.inv_theta_df, c->stream);
+  launch_cheb_first_df(L, nrhs, b, x, r, da, zero_x, K.inv_theta_df, c->stream);
   bool pending = !zero_x;
   for (int j = 1; j < c->opt.cheb_degree; ++j) {
     launch_cheb_step_df(L, nrhs, r, da, db, x, K.c1_df[j], K.c2_df[j], pending, c->stream);
@@ -408,34 +410,81 @@ void smooth_df(h1w_ctx* c, int l, int nrhs, bool zero_x) {
   if (pending) launch_add_df((int64_t)nrhs * L.N, da, x, c->stream);
 }
 
-void vcycle_block_df(h1w_ctx* c, int nrhs, const double* b0, double* x0, df* x0df) {
+// level l smooths with the fused down/up kernels (all axes coarsened, degree-2 smoother)
+bool fused_level(const h1w_ctx* c, int l) {
+  return c->opt.mg_unfused == 0 && c->opt.cheb_degree == 2 && l < c->nlev - 1 && fused_level_ok(c->lev[l]);
+}
+
+// x = L-hat^-1 b for nrhs <= rhs_block right-hand sides given as double-floats (b0, level-0
+// sized, contiguous); the result goes to x64 (FP64) and/or xdf (double-floats).
+// Returns false if a fused kernel could not be configured.
+bool vcycle_block_df(h1w_ctx* c, int nrhs, const df* b0, double* x64, df* xdf) {
   const int nl = c->nlev;
-  const int64_t n0 = (int64_t)nrhs * c->lev[0].N;
-  launch_d2df(n0, b0, dfp(c->buf[0].b), c->stream);
+  cudaStream_t s = c->stream;
+  const df* bl[kMaxLevels];
+  const df* xf[kMaxLevels];
+  bl[0] = b0;
+  for (int l = 1; l < nl; ++l) bl[l] = dfp(c->buf[l].b);
   for (int l = 0; l < nl - 1; ++l) {
-    smooth_df(c, l, nrhs, true);
-    launch_residual_df(c->lev[l], nrhs, dfp(c->buf[l].b), dfp(c->buf[l].x), dfp(c->buf[l].r), c->stream);
-    launch_restrict_df(c->lev[l], c->lev[l + 1], nrhs, dfp(c->buf[l].r), dfp(c->buf[l + 1].b), c->stream);
+    df* x = dfp(c->buf[l].x);
+    if (fused_level(c, l)) {
+      if (l == 0 && c->time_vc) timed_begin(c);
+      if (!launch_pre_fused_df(c->lev[l], c->lev[l + 1], c->fco[l], nrhs, bl[l], x, dfp(c->buf[l + 1].b), s))
+        return false;
+      if (l == 0 && c->time_vc) timed_end(c, kCatDown);
+    } else {
+      smooth_df(c, l, nrhs, bl[l], x, true);
+      launch_residual_df(c->lev[l], nrhs, bl[l], x, dfp(c->buf[l].r), s);
+      launch_restrict_df(c->lev[l], c->lev[l + 1], nrhs, dfp(c->buf[l].r), dfp(c->buf[l + 1].b), s);
+    }
   }
-  launch_coarse_apply_df(c->coarse_X, (int)c->lev[nl - 1].N, nrhs, dfp(c->buf[nl - 1].b), dfp(c->buf[nl - 1].x),
-                         c->stream);
+  launch_coarse_apply_df(c->coarse_X, (int)c->lev[nl - 1].N, nrhs, bl[nl - 1], dfp(c->buf[nl - 1].x), s);
+  xf[nl - 1] = dfp(c->buf[nl - 1].x);
+  bool written = false;
   for (int l = nl - 2; l >= 0; --l) {
-    launch_prolong_add_df(c->lev[l], c->lev[l + 1], nrhs, dfp(c->buf[l + 1].x), dfp(c->buf[l].x), c->stream);
-    smooth_df(c, l, nrhs, false);
+    if (fused_level(c, l)) {
+      df* y = (l == 0) ? xdf : dfp(c->buf[l].r);   // r is free on the up leg
+      double* y64 = (l == 0) ? x64 : nullptr;
+      if (l == 0 && c->time_vc) timed_begin(c);
+      if (!launch_post_fused_df(c->lev[l], c->lev[l + 1], c->fco[l], nrhs, dfp(c->buf[l].x), xf[l + 1], bl[l], y,
+                                y64, s))
+        return false;
+      if (l == 0 && c->time_vc) timed_end(c, kCatUp);
+      xf[l] = y;
+      written = (l == 0);
+    } else {
+      df* x = dfp(c->buf[l].x);
+      launch_prolong_add_df(c->lev[l], c->lev[l + 1], nrhs, xf[l + 1], x, s);
+      smooth_df(c, l, nrhs, bl[l], x, false);
+      xf[l] = x;
+    }
   }
-  launch_df2d(n0, dfp(c->buf[0].x), x0, x0df, c->stream);
+  if (!written) launch_df2d((int64_t)nrhs * c->lev[0].N, xf[0], x64, xdf, s);
+  return true;
 }
 
 bool uses_df(const h1w_ctx* c) { return (c->disc == H1W_FV_CELL) && (c->opt.mg_arith == 0); }
 
-// x = L-hat^-1 b for nrhs vectors; xdf (double-float cycle only, may be null) gets x as double-floats
-void vcycle_many(h1w_ctx* c, int nrhs, const double* b, double* x, df* xdf = nullptr) {
+// x = L-hat^-1 b for nrhs vectors. b comes in FP64 (b64) or, on the double-float cycle,
+// as double-floats (bdf, preferred when given). The result goes to x64 and/or, on the
+// double-float cycle, xdf. Returns false if a fused kernel could not be configured.
+bool vcycle_many(h1w_ctx* c, int nrhs, const double* b64, const df* bdf, double* x64, df* xdf) {
   const int64_t N = c->lev[0].N;
   for (int r0 = 0; r0 < nrhs; r0 += c->opt.rhs_block) {
     const int nr = std::min(c->opt.rhs_block, nrhs - r0);
-    if (uses_df(c)) vcycle_block_df(c, nr, b + (int64_t)r0 * N, x + (int64_t)r0 * N, xdf ? xdf + (int64_t)r0 * N : nullptr);
-    else vcycle_block(c, nr, b + (int64_t)r0 * N, x + (int64_t)r0 * N);
+    const int64_t o = (int64_t)r0 * N;
+    if (uses_df(c)) {
+      const df* b = bdf ? bdf + o : nullptr;
+      if (!b) {
+        launch_d2df((int64_t)nr * N, b64 + o, dfp(c->buf[0].b), c->stream);
+        b = dfp(c->buf[0].b);
+      }
+      if (!vcycle_block_df(c, nr, b, x64 ? x64 + o : nullptr, xdf ? xdf + o : nullptr)) return false;
+    } else {
+      vcycle_block(c, nr, b64 + o, x64 + o);
+    }
   }
+  return true;
 }
 
 // w = J v (m-vector), through per-chunk partials
@@ -459,15 +508,19 @@ void j_times_df(h1w_ctx* c, const double* v, double* out) {
   launch_reduce_partials(c->partial, rows_dot_df_chunks(N), c->m, 1.0, out, c->stream);
 }
 
-// z = P^-1 r; when rz_slot >= 0 also scal[rz_slot] = r . z
-void apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
+// z = P^-1 r; when rz_slot >= 0 also scal[rz_slot] = r . z. False if the cycle could not run.
+bool apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
   const int64_t N = c->lev[0].N;
-  vcycle_many(c, 1, r, c->z0);
+  if (uses_df(c)) {                                 // r as double-floats: input of the cycle and of H^T r
+    launch_d2df(N, r, c->vdf, c->stream);
+    if (!vcycle_many(c, 1, nullptr, c->vdf, c->z0, nullptr)) return false;
+  } else {
+    vcycle_many(c, 1, r, nullptr, c->z0, nullptr);
+  }
   const int m = c->m;
   const bool dfp_ = uses_df(c) && m > 0;
   if (m > 0) {
     if (dfp_) {                                     // s = H^T r (double-float pass)
-      launch_d2df(N, r, c->vdf, c->stream);
       timed_begin(c);
       launch_rows_dot_df(c->Hdf, m, N, c->vdf, c->partial, c->stream);
       timed_end(c, kCatHdot);
@@ -490,6 +543,7 @@ void apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
                            rz_slot >= 0 ? c->partial : nullptr, c->stream);
   timed_end(c, kCatHupd);
   if (rz_slot >= 0) launch_sum_to_scalar(c->partial, colsum_blocks(N), c->scal + rz_slot, c->stream);
+  return true;
 }
 
 // q = alpha (K+M) p + J^T w with w = J p given; scal[pq_slot] = p . q when pq_slot >= 0
@@ -524,7 +578,7 @@ void h1w_default_options(h1w_options* opt) {
   opt->max_restarts = 3;
   opt->cap_gemm = 0;
   opt->mg_arith = 0;
-  opt->reserved = 0;
+  opt->mg_unfused = 0;
 }
 
 size_t h1w_workspace_size(const h1w_grid* grid, int32_t m_max, const h1w_options* opt) {
@@ -645,6 +699,25 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
       K.c2_df[j] = df_host(K.c2[j]);
       rho_prev = rho;
     }
+    if (c->disc == H1W_FV_CELL && o.cheb_degree == 2) {   // constants of the fused smoothing legs
+      const Level& L = c->lev[l];
+      FusedCoef& F = c->fco[l];
+      const double it = K.inv_theta, c1 = K.c1[1], c2 = K.c2[1];
+      const double beta = it * (1.0 + c1) + c2 * (1.0 - it);
+      for (int k = 0; k < 27; ++k) {
+        const double d = L.fv_diag[k], di = 1.0 / d;
+        F.d[k] = df_host(d);
+        F.dinv[k] = df_host(di);
+        F.gam[k] = df_host(c2 * it * di);
+        F.del[k] = df_host(it * di);
+        F.eta[k] = df_host(beta * di);
+        F.kap[k] = df_host(c2 * di);
+      }
+      F.T[0] = df_host(L.Tx);
+      F.T[1] = df_host(L.Ty);
+      F.T[2] = df_host(L.Tz);
+      F.beta = df_host(beta);
+    }
   }
   // coarsest level: dense matrix, Cholesky, explicit symmetric inverse
   {
@@ -687,7 +760,14 @@ h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
   if (m == 0) { c->launches_cap = 0; return H1W_OK; }
   if (c->have_ev) cudaEventRecord(c->ev[0], c->stream);
   if (uses_df(c)) launch_d2df((int64_t)m * N, J, c->Jdf, c->stream);  // J for the Krylov passes
-  vcycle_many(c, m, J, c->H, c->Hdf);                               // line H
+  // line H; on the double-float cycle the tensor-core split reads J and H as double-floats,
+  // so the FP64 copy of H is only written for the FP64 paths
+  const bool h_df_only = uses_df(c) && c->opt.cap_gemm == 0;
+  c->nk = 0;
+  c->timing_on = c->time_vc = true;
+  const bool vc_ok = vcycle_many(c, m, J, uses_df(c) ? c->Jdf : nullptr, h_df_only ? nullptr : c->H, c->Hdf);
+  c->timing_on = c->time_vc = false;
+  if (!vc_ok) return fail(c, H1W_ECUDA, "capacitance: multigrid kernel attribute failed");
   if (c->have_ev) cudaEventRecord(c->ev[1], c->stream);
   cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
   int splits = 0;
@@ -699,7 +779,7 @@ h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
     splits = ozaki_splits(m, c->oz.klen);
     c->timing_on = true;
     const bool ok = launch_ozaki_capacitance(
-        J, c->H, m, N, c->oz, splits, c->stream, [](void* p) { timed_begin(static_cast<h1w_ctx*>(p)); },
+        J, c->H, h_df_only ? c->Jdf : nullptr, h_df_only ? c->Hdf : nullptr, m, N, c->oz, splits, c->stream, [](void* p) { timed_begin(static_cast<h1w_ctx*>(p)); },
         [](void* p) { timed_end(static_cast<h1w_ctx*>(p), kCatGemm); }, c);
     c->timing_on = false;
     if (!ok)
@@ -722,7 +802,7 @@ h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
   cudaMemcpyAsync(&status, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail(c, H1W_ECUDA, std::string("capacitance: ") + cudaGetErrorString(e));
-  timed_collect(c, 1u << kCatGemm);
+  timed_collect(c, (1u << kCatGemm) | (1u << kCatDown) | (1u << kCatUp));
   h1w_status st = cuda_check(c, "capacitance");
   if (st != H1W_OK) return st;
   if (status & kStatusTimeout) {
@@ -740,7 +820,7 @@ h1w_status h1w_apply_prec(h1w_ctx* c, const double* r, double* z) {
   if (!c) return H1W_EINVAL;
   if (!r || !z || r == z) return fail(c, H1W_EINVAL, "r and z must be distinct non-NULL pointers");
   if (c->m < 0) return fail(c, H1W_ESTATE, "call h1w_capacitance first");
-  apply_prec_impl(c, r, z, -1);
+  if (!apply_prec_impl(c, r, z, -1)) return fail(c, H1W_ECUDA, "apply_prec: multigrid kernel attribute failed");
   return cuda_check(c, "apply_prec");
 }
 
@@ -757,7 +837,8 @@ h1w_status h1w_vcycle(h1w_ctx* c, int32_t nrhs, const double* b, double* x) {
   if (!c) return H1W_EINVAL;
   if (nrhs < 0 || (nrhs > 0 && (!b || !x))) return fail(c, H1W_EINVAL, "bad vcycle arguments");
   if (nrhs == 0) return H1W_OK;
-  vcycle_many(c, nrhs, b, x);
+  if (!vcycle_many(c, nrhs, b, nullptr, x, nullptr))
+    return fail(c, H1W_ECUDA, "vcycle: multigrid kernel attribute failed");
   return cuda_check(c, "vcycle");
 }
 
@@ -804,8 +885,9 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
   const double tol = rtol * bnorm;
   int it = 0;
   double rel_true = 1.0;
+  bool prec_failed = false;
   for (int restart = 0; restart <= c->opt.max_restarts; ++restart) {
-    apply_prec_impl(c, c->r, c->z, RZ);
+    if (!apply_prec_impl(c, c->r, c->z, RZ)) { prec_failed = true; break; }
     if (uses_df(c)) j_times_df(c, c->z, c->jz);
     else j_times(c, c->J, c->z, c->jz);
     launch_p_update(c->p, c->z, c->w, c->jz, c->scal, N, m > 0 ? m : 0, true, s);
@@ -818,12 +900,13 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
       ++it;
       if (!std::isfinite(rr)) break;
       if (std::sqrt(rr) <= tol) break;
-      apply_prec_impl(c, c->r, c->z, RZN);
+      if (!apply_prec_impl(c, c->r, c->z, RZN)) { prec_failed = true; break; }
       if (uses_df(c)) j_times_df(c, c->z, c->jz);
       else j_times(c, c->J, c->z, c->jz);
       launch_pcg_beta(c->scal, s);
       launch_p_update(c->p, c->z, c->w, c->jz, c->scal, N, m > 0 ? m : 0, false, s);
     }
+    if (prec_failed) break;
     // true residual r = b - A x
     j_times(c, c->J, x, c->wtmp);
     apply_op_w(c, x, c->wtmp, c->q, -1);
@@ -850,6 +933,7 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
   c->launches_pcg = g_kernel_launches.load() - l0;
   h1w_status st = cuda_check(c, "pcg");
   if (st != H1W_OK) return st;
+  if (prec_failed) return fail(c, H1W_ECUDA, "pcg: multigrid kernel attribute failed");
   if (!(rel_true <= rtol)) return fail(c, H1W_ENOTCONV, "PCG did not reach rtol within maxit");
   return H1W_OK;
 }
@@ -892,6 +976,10 @@ h1w_status h1w_get_timings(const h1w_ctx* c, h1w_timings* out) {
   t.n_op = c->cat_n[kCatOp];
   t.n_hdot = c->cat_n[kCatHdot];
   t.n_hupd = c->cat_n[kCatHupd];
+  t.t_vc_down_ms = c->cat_ms[kCatDown];
+  t.t_vc_up_ms = c->cat_ms[kCatUp];
+  t.n_vc_down = c->cat_n[kCatDown];
+  t.n_vc_up = c->cat_n[kCatUp];
   *out = t;
   return H1W_OK;
 }

@@ -41,6 +41,17 @@ struct Level {
   df fvd_T[3];
 };
 
+// Per-class coefficients of the fused degree-2 smoothing legs (mg_fused.cu), class
+// c = cx + 3 cy + 9 cz by neighbour counts: d = diagonal of A, dinv = 1 / d,
+// gam = c2 / (theta d), del = 1 / (theta d), eta = beta / d, kap = c2 / d with
+// beta = (1 + c1) / theta + c2 (1 - 1 / theta) (theta, c1, c2 of the level's smoother);
+// T = face coefficients (Tx, Ty, Tz).
+struct FusedCoef {
+  df d[27], dinv[27], gam[27], del[27], eta[27], kap[27];
+  df T[3];
+  df beta;
+};
+
 struct ChebCoef {
   double inv_theta;   // 1 / theta
   double c1[8];       // rho_j rho_{j-1} for step j (1-based; index 0 unused)
@@ -73,10 +84,12 @@ long long ozaki_chunks(long long N);
 int ozaki_num_tiles(int m);
 int ozaki_splits(int m, long long kp);
 bool ozaki_supported();
-// before/after (may be null) are called around each GEMM kernel launch with hook_arg
-bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long N, const OzakiWork& w,
-                              int splits, cudaStream_t s, void (*before)(void*), void (*after)(void*),
-                              void* hook_arg);
+// Operands as FP64 (J, H) or, when Jdf and Hdf are both given, as double-floats (J and H
+// are then not read). before/after (may be null) are called around each GEMM kernel launch
+// with hook_arg.
+bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, const df* Hdf, int m, long long N,
+                              const OzakiWork& w, int splits, cudaStream_t s, void (*before)(void*),
+                              void (*after)(void*), void* hook_arg);
 void ozaki_tiles(int m, std::vector<int>& out);
 
 // ---- kernel launchers (mg_kernels.cu) --------------------------------------
@@ -117,6 +130,16 @@ void launch_coarse_apply_df(const double* X, int n, int nrhs, const df* b, df* x
 void launch_d2df(int64_t n, const double* src, df* dst, cudaStream_t s);
 // dst = src as FP64; dst2 (may be null) receives a copy of the double-floats
 void launch_df2d(int64_t n, const df* src, double* dst, df* dst2, cudaStream_t s);
+// Fused smoothing passes on a level with all three axes coarsened 2:1 and the degree-2
+// smoother: down leg (x = S(b) from zero, bc = P^T (b - A x)) and up leg (y = S(x + P xc)
+// started from the corrected x; y and/or y64 may be null, not both). False if the level
+// does not qualify or the kernel attribute for its shared memory could not be set
+// (nothing launched).
+bool fused_level_ok(const Level& L);  // all axes coarsened and nx ny < 2^27
+bool launch_pre_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* b, df* x,
+                         df* bc, cudaStream_t s);
+bool launch_post_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* x,
+                          const df* xc, const df* b, df* y, double* y64, cudaStream_t s);
 
 // ---- dense / Krylov kernels (dense_kernels.cu) ------------------------------
 // partial[c * m + i] = sum_{k in chunk c} A[i * lda + k] v[k]

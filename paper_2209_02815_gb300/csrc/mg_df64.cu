@@ -12,38 +12,14 @@
 // dense coarsest solve (kept in FP64).
 #include "df64.cuh"
 #include "h1w_internal.cuh"
+#include "mg_df64_util.cuh"
 
 namespace h1w {
 namespace {
 
+using namespace dfmg;
+
 constexpr int kThreads = 256;
-
-__device__ __forceinline__ int fv_cls(const Level& L, int i, int j, int k) {
-  return ((i > 0) + (i < L.nx - 1)) + 3 * ((j > 0) + (j < L.ny - 1)) + 9 * ((k > 0) + (k < L.nz - 1));
-}
-
-__device__ __forceinline__ void decompose(const Level& L, int64_t p, int& i, int& j, int& k) {
-  i = (int)(p % L.nx);
-  const int64_t t = p / L.nx;
-  j = (int)(t % L.ny);
-  k = (int)(t / L.ny);
-}
-
-__device__ __forceinline__ df dzero() { return df_make(0.f, 0.f); }
-
-// Cascaded summation of double-floats: the high parts are added with TwoSum,
-// their rounding errors and the low parts are collected in one float, and the
-// result is renormalized once. For the handful of terms summed here the
-// error stays near 2^-46 of the largest term.
-struct dsum {
-  float s = 0.f, e = 0.f;
-  __device__ __forceinline__ void add(df v) {
-    const df t = two_sum(s, v.hi);
-    s = t.hi;
-    e = __fadd_rn(e, __fadd_rn(t.lo, v.lo));
-  }
-  __device__ __forceinline__ df get() const { return fast_two_sum(s, e); }
-};
 
 // One thread per cell of one right-hand side: grid (ceil(nx / blockDim.x), ny, nz * nrhs).
 struct Cell {
@@ -125,35 +101,6 @@ __global__ void k_residual_df(Level L, const df* __restrict__ b, const df* __res
   if (!cell_of(L, q)) return;
   const int64_t off = (int64_t)q.rhs * L.N, p = q.p;
   r[off + p] = df_sub(b[off + p], fv_apply_df(L, x + off, q.i, q.j, q.k, p, fv_cls(L, q.i, q.j, q.k)));
-}
-
-// FV 1D transfer weights (rows of P^T and of P), as in mg_kernels.cu
-__device__ __forceinline__ int fv_restrict_1d(int I, int nc, int coarsened, int* f, float* w) {
-  if (!coarsened) { f[0] = I; w[0] = 1.f; return 1; }
-  int c = 0;
-  if (I >= 1) { f[c] = 2 * I - 1; w[c++] = 0.25f; }
-  f[c] = 2 * I;     w[c++] = (I >= 1) ? 0.75f : 1.f;
-  f[c] = 2 * I + 1; w[c++] = (I + 1 < nc) ? 0.75f : 1.f;
-  if (I + 1 < nc) { f[c] = 2 * I + 2; w[c++] = 0.25f; }
-  return c;
-}
-
-__device__ __forceinline__ int fv_prolong_1d(int i, int nc, int coarsened, int* f, float* w) {
-  if (!coarsened) { f[0] = i; w[0] = 1.f; return 1; }
-  const int I = i >> 1;
-  const int J = (i & 1) ? I + 1 : I - 1;
-  if (J >= 0 && J < nc) { f[0] = I; w[0] = 0.75f; f[1] = J; w[1] = 0.25f; return 2; }
-  f[0] = I; w[0] = 1.f;
-  return 1;
-}
-
-// weights of row I of the 1D P^T at fine offsets 2I-1, 2I, 2I+1, 2I+2 (0 where absent)
-__device__ __forceinline__ void fv_rw(int I, int nc, int coarsened, float* w) {
-  if (!coarsened) { w[0] = 0.f; w[1] = 1.f; w[2] = 0.f; w[3] = 0.f; return; }
-  w[0] = (I >= 1) ? 0.25f : 0.f;
-  w[1] = (I >= 1) ? 0.75f : 1.f;
-  w[2] = (I + 1 < nc) ? 0.75f : 1.f;
-  w[3] = (I + 1 < nc) ? 0.25f : 0.f;
 }
 
 __global__ void k_restrict_df(Level Lf, Level Lc, const df* __restrict__ rf, df* __restrict__ bc) {
@@ -245,7 +192,7 @@ __global__ void k_df2d(int64_t n, const df* __restrict__ src, double* __restrict
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const df v = src[p];
-  dst[p] = df_to_double(v);
+  if (dst) dst[p] = df_to_double(v);
   if (dst2) dst2[p] = v;
 }
 

@@ -1,0 +1,595 @@
+// Fused legs of the double-float V-cycle on FV levels whose three axes are all
+// coarsened 2:1, with the degree-2 Chebyshev-Jacobi smoother.
+//
+// Down leg (one kernel): x = S(b), two smoothing steps from x = 0, then the
+// restricted residual bc = P^T (b - A x). Up leg (one kernel): x' = x + P xc,
+// two smoothing steps from x', result y.
+//
+// The double-float V-cycle is bound by instruction issue, not by HBM (about
+// 40 FP32 instructions per double-float addition or product), so the legs are
+// written to need as few double-float operations as possible:
+//  * With A = D - N_T (D the diagonal, N_T(u) = sum over axes of T_a times the
+//    two face neighbours of u along a), the two Chebyshev steps collapse into
+//      down: g = D^-1 b,  x = beta g + gam_c N_T(g),
+//      up:   r0 = b + N_T(x') - d_c x',  d0 = del_c r0,
+//            y = x' + eta_c r0 + kap_c N_T(d0),
+//    with the per-class constants of FusedCoef (exact algebra of the two steps
+//    r1 = r0 - A d0, d1 = c1 d0 + c2 D^-1 r1, x += d0 + d1 with d0 = D^-1 r0 / theta).
+//  * Values outside the domain are stored as exact zeros in the on-chip
+//    buffers, so the stencils sum all six neighbours without boundary tests;
+//    the neighbour counts only select the class of the constants.
+//  * The prolongation is separable: each coarse plane is interpolated along x,
+//    then y, once, and every fine plane combines two such planes along z.
+//
+// A block owns an xy tile of kFX x kFY fine cells and a range of z planes and
+// marches through the planes, keeping the planes each step needs in rings in
+// shared memory; every step works on the tile grown by the halo the later
+// steps read (3, 2, 1 cells), so neighbouring blocks repeat a little work
+// instead of exchanging it. Only b, x and the coarse vectors go through HBM.
+#include <algorithm>
+#include <atomic>
+
+#include "df64.cuh"
+#include "h1w_internal.cuh"
+#include "mg_df64_util.cuh"
+
+namespace h1w {
+namespace {
+
+using namespace dfmg;
+
+constexpr int kFX = 32, kFY = 16;                               // fine cells of a tile
+constexpr int kTX = kFX / 2, kTY = kFY / 2;                     // coarse cells of a tile
+constexpr int kW3 = kFX + 6, kH3 = kFY + 6, kA3 = kW3 * kH3;    // tile + 3
+constexpr int kW2 = kFX + 4, kH2 = kFY + 4, kA2 = kW2 * kH2;    // tile + 2
+constexpr int kW1 = kFX + 2, kH1 = kFY + 2, kA1 = kW1 * kH1;    // tile + 1
+constexpr int kHC = kTY + 4;                                    // coarse rows of tile + 2
+constexpr int kAX = kHC * kW2;                                  // coarse rows x fine columns
+constexpr int kThr = 256;
+constexpr int kP3 = (kA3 + kThr - 1) / kThr;
+constexpr int kP2 = (kA2 + kThr - 1) / kThr;
+constexpr int kP1 = (kA1 + kThr - 1) / kThr;
+constexpr int kTab = 27;
+
+constexpr size_t kPreSmem = sizeof(df) * (3 * kA3 + 3 * kA1 + 3 * kA2 + kA1 + 3 * kTab);
+constexpr size_t kPostSmem = sizeof(df) * (4 * kA2 + 3 * kA2 + kAX + 3 * kA1 + 2 * kA1 + 4 * kTab);
+
+__device__ __forceinline__ bool in_xy(const Level& L, int i, int j) {
+  return i >= 0 && i < L.nx && j >= 0 && j < L.ny;
+}
+
+// (offset in the plane << 5) | (flag << 4) | xy part of the neighbour class, or -1 outside
+// the domain (the launchers require nx ny < 2^26)
+__device__ __forceinline__ int xy_desc(const Level& L, int gx, int gy, bool flag = false) {
+  if (!in_xy(L, gx, gy)) return -1;
+  const int c = ((gx > 0) + (gx < L.nx - 1)) + 3 * ((gy > 0) + (gy < L.ny - 1));
+  return ((gy * L.nx + gx) << 5) | (flag ? 16 : 0) | c;
+}
+__device__ __forceinline__ int desc_off(int d) { return d >> 5; }
+__device__ __forceinline__ int desc_cls(int d) { return d & 15; }
+__device__ __forceinline__ bool desc_flag(int d) { return (d & 16) != 0; }
+
+__device__ __forceinline__ df scale_w(df v, float w) {
+  // weights 1/4 and 1 scale exactly; 3/4 needs a product
+  if (w == 0.25f) return df_make(v.hi * 0.25f, v.lo * 0.25f);
+  if (w == 1.f) return v;
+  return df_mul_f(v, w);
+}
+
+// N_T(u) at idx of a plane buffer with rows of W cells (u0, u2: planes below and above);
+// out-of-domain entries hold zeros.
+template <bool ISO>
+__device__ __forceinline__ df nsum(const df* __restrict__ u0, const df* __restrict__ u1, const df* __restrict__ u2,
+                                   int idx, int W, df T0, df T1, df T2) {
+  if (ISO) {
+    dsum s;
+    s.add(u1[idx - 1]);
+    s.add(u1[idx + 1]);
+    s.add(u1[idx - W]);
+    s.add(u1[idx + W]);
+    s.add(u0[idx]);
+    s.add(u2[idx]);
+    return df_mul(T0, s.get());
+  }
+  dsum sx, sy, sz;
+  sx.add(u1[idx - 1]);
+  sx.add(u1[idx + 1]);
+  sy.add(u1[idx - W]);
+  sy.add(u1[idx + W]);
+  sz.add(u0[idx]);
+  sz.add(u2[idx]);
+  dsum s;
+  s.add(df_mul(T0, sx.get()));
+  s.add(df_mul(T1, sy.get()));
+  s.add(df_mul(T2, sz.get()));
+  return s.get();
+}
+
+// Down leg. Grid: (xy tiles, z segments of segK coarse planes, right-hand sides).
+template <bool ISO>
+__global__ void __launch_bounds__(kThr) k_pre_fused(Level L, Level Lc, FusedCoef F, const df* __restrict__ b,
+                                                    df* __restrict__ x, df* __restrict__ bc, int segK) {
+  extern __shared__ df sm[];
+  df* Gp = sm;               // g = D^-1 b over tile + 3, 3 planes
+  df* Bp = Gp + 3 * kA3;     // b over tile + 1, 3 planes
+  df* Xp = Bp + 3 * kA1;     // smoothed x over tile + 2, 3 planes
+  df* Rs = Xp + 3 * kA2;     // residual of one plane over tile + 1
+  df* td = Rs + kA1;         // d, dinv, gam by class
+  df* tdinv = td + kTab;
+  df* tgam = tdinv + kTab;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kTab; i += kThr) {
+    td[i] = F.d[i];
+    tdinv[i] = F.dinv[i];
+    tgam[i] = F.gam[i];
+  }
+  const df T0 = F.T[0], T1 = F.T[1], T2 = F.T[2], beta = F.beta;
+  const int ntx = (Lc.nx + kTX - 1) / kTX;
+  const int C0x = (int)(blockIdx.x % (unsigned)ntx) * kTX, C0y = (int)(blockIdx.x / (unsigned)ntx) * kTY;
+  const int F0x = 2 * C0x, F0y = 2 * C0y;
+  const int K0 = (int)blockIdx.y * segK, K1 = min(K0 + segK, Lc.nz);
+  const int Z0 = 2 * K0, Z1 = 2 * K1;
+  const int64_t pl = (int64_t)L.nx * L.ny, plc = (int64_t)Lc.nx * Lc.ny;
+  const df* bb = b + (int64_t)blockIdx.z * L.N;
+  df* xx = x + (int64_t)blockIdx.z * L.N;
+  df* cc = bc + (int64_t)blockIdx.z * Lc.N;
+  const int u_beg = Z0 - 3, u_end = Z1 + 2;
+#define SLOT(p) (((p) - u_beg) % 3)
+
+  // element descriptors, the same on every plane
+  int d3[kP3], r3[kP3], d2[kP2], d1[kP1];
+#pragma unroll
+  for (int q = 0; q < kP3; ++q) {
+    const int e = tid + q * kThr;
+    const int lx = e % kW3, ly = e / kW3;
+    d3[q] = e < kA3 ? xy_desc(L, F0x - 3 + lx, F0y - 3 + ly) : -1;
+    r3[q] = (e < kA3 && lx >= 2 && lx < kW3 - 2 && ly >= 2 && ly < kH3 - 2) ? (ly - 2) * kW1 + lx - 2 : -1;
+  }
+  int i3[kP2], i2[kP1];  // shared-memory index of the element in the buffer a step reads
+#pragma unroll
+  for (int q = 0; q < kP2; ++q) {
+    const int e = tid + q * kThr;
+    const int lx = e % kW2, ly = e / kW2;
+    const bool interior = lx >= 2 && lx < 2 + kFX && ly >= 2 && ly < 2 + kFY;
+    d2[q] = e < kA2 ? xy_desc(L, F0x - 2 + lx, F0y - 2 + ly, interior) : -1;
+    i3[q] = (ly + 1) * kW3 + lx + 1;
+  }
+#pragma unroll
+  for (int q = 0; q < kP1; ++q) {
+    const int e = tid + q * kThr;
+    const int lx = e % kW1, ly = e / kW1;
+    d1[q] = e < kA1 ? xy_desc(L, F0x - 1 + lx, F0y - 1 + ly) : -1;
+    i2[q] = (ly + 1) * kW2 + lx + 1;
+  }
+
+  df pf[kP3];
+  auto fetch = [&](int u) {
+    const bool uin = (u >= 0 && u < L.nz);
+#pragma unroll
+    for (int q = 0; q < kP3; ++q) pf[q] = (uin && d3[q] >= 0) ? bb[u * pl + desc_off(d3[q])] : dzero();
+  };
+  fetch(u_beg);
+
+  // restriction: two threads (lanes 2c, 2c + 1) per coarse cell of the tile, each taking two
+  // of the cell's four fine rows 2J - 1 .. 2J + 2
+  static_assert(2 * kTX * kTY == kThr, "two threads per coarse cell");
+  const int half = tid & 1, cell = tid >> 1;
+  const int Ic = cell % kTX, Jc = cell / kTX;
+  const int gI = C0x + Ic, gJ = C0y + Jc;
+  const bool own = gI < Lc.nx && gJ < Lc.ny;
+  float wx[4], wy[2];
+  {
+    float w4[4];
+    fv_rw(min(gI, Lc.nx - 1), Lc.nx, 1, wx);
+    fv_rw(min(gJ, Lc.ny - 1), Lc.ny, 1, w4);
+    wy[0] = w4[2 * half];
+    wy[1] = w4[2 * half + 1];
+  }
+  dsum acc_a, acc_b;  // coarse planes K and K + 1 while fine plane 2K + 1 or 2K + 2 is added
+  __syncthreads();
+
+  for (int u = u_beg; u <= u_end; ++u) {
+    const int t = u - u_beg;
+    // step 1, plane u: g = D^-1 b over tile + 3; b kept over tile + 1
+    {
+      df* Go = Gp + SLOT(u) * kA3;
+      df* Bo = Bp + SLOT(u) * kA1;
+      const bool uin = (u >= 0 && u < L.nz);
+      const int cz = 9 * ((u > 0) + (u < L.nz - 1));
+#pragma unroll
+      for (int q = 0; q < kP3; ++q) {
+        const int e = tid + q * kThr;
+        if (e < kA3) {
+          Go[e] = (uin && d3[q] >= 0) ? df_mul(pf[q], tdinv[desc_cls(d3[q]) + cz]) : dzero();
+          if (r3[q] >= 0) Bo[r3[q]] = pf[q];
+        }
+      }
+      if (u < u_end) fetch(u + 1);
+    }
+    __syncthreads();
+    // step 2, plane v = u - 1: x = beta g + gam_c N_T(g) over tile + 2
+    if (t >= 2) {
+      const int v = u - 1;
+      const df* G0 = Gp + SLOT(v - 1) * kA3;
+      const df* G1 = Gp + SLOT(v) * kA3;
+      const df* G2 = Gp + SLOT(v + 1) * kA3;
+      df* Xo = Xp + SLOT(v) * kA2;
+      const bool vin = (v >= 0 && v < L.nz);
+      const bool vout = (v >= Z0 && v < Z1);
+      const int cz = 9 * ((v > 0) + (v < L.nz - 1));
+#pragma unroll
+      for (int q = 0; q < kP2; ++q) {
+        const int e = tid + q * kThr;
+        if (e < kA2) {
+          df xv = dzero();
+          if (vin && d2[q] >= 0) {
+            const df n = nsum<ISO>(G0, G1, G2, i3[q], kW3, T0, T1, T2);
+            dsum s;
+            s.add(df_mul(beta, G1[i3[q]]));
+            s.add(df_mul(tgam[desc_cls(d2[q]) + cz], n));
+            xv = s.get();
+            if (vout && desc_flag(d2[q])) xx[v * pl + desc_off(d2[q])] = xv;
+          }
+          Xo[e] = xv;
+        }
+      }
+      __syncthreads();
+    }
+    // step 3, plane w = u - 2: residual b + N_T(x) - d_c x over tile + 1, then P^T
+    if (t >= 4) {
+      const int w = u - 2;
+      const df* X0 = Xp + SLOT(w - 1) * kA2;
+      const df* X1 = Xp + SLOT(w) * kA2;
+      const df* X2 = Xp + SLOT(w + 1) * kA2;
+      const df* B1 = Bp + SLOT(w) * kA1;
+      const bool win = (w >= 0 && w < L.nz);
+      const int cz = 9 * ((w > 0) + (w < L.nz - 1));
+#pragma unroll
+      for (int q = 0; q < kP1; ++q) {
+        const int e = tid + q * kThr;
+        if (e < kA1) {
+          df rv = dzero();
+          if (win && d1[q] >= 0) {
+            const df n = nsum<ISO>(X0, X1, X2, i2[q], kW2, T0, T1, T2);
+            dsum s;
+            s.add(B1[e]);
+            s.add(n);
+            s.add(df_neg(df_mul(td[desc_cls(d1[q]) + cz], X1[i2[q]])));
+            rv = s.get();
+          }
+          Rs[e] = rv;
+        }
+      }
+      __syncthreads();
+      // P^T within the plane: coarse column I takes fine columns 2I - 1 .. 2I + 2 (tile + 1
+      // columns 2I .. 2I + 3), coarse row J fine rows 2J - 1 .. 2J + 2 (tile + 1 rows 2J .. 2J + 3)
+      dsum sy;
+      if (own) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          if (wy[r] != 0.f) {
+            const df* row = Rs + (2 * Jc + 2 * half + r) * kW1 + 2 * Ic;
+            dsum sx;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+              if (wx[a] != 0.f) sx.add(scale_w(row[a], wx[a]));
+            sy.add(scale_w(sx.get(), wy[r]));
+          }
+        }
+      }
+      // both lanes of a cell form the same sum, rows 0-1 first
+      const df mine = sy.get();
+      const df other = df_make(__shfl_xor_sync(0xffffffffu, mine.hi, 1), __shfl_xor_sync(0xffffffffu, mine.lo, 1));
+      dsum sc;
+      sc.add(half ? other : mine);
+      sc.add(half ? mine : other);
+      const df S = sc.get();
+      if (own) {
+        float wz[4];
+        if (w & 1) {  // w = 2K + 1: tap 2 of coarse plane K, tap 0 of K + 1 (which starts here)
+          const int K = (w - 1) >> 1;
+          if (K >= 0 && K < Lc.nz) {
+            fv_rw(K, Lc.nz, 1, wz);
+            if (wz[2] != 0.f) acc_a.add(scale_w(S, wz[2]));
+          }
+          acc_b = dsum();
+          if (K + 1 < Lc.nz) {
+            fv_rw(K + 1, Lc.nz, 1, wz);
+            if (wz[0] != 0.f) acc_b.add(scale_w(S, wz[0]));
+          }
+        } else {      // w = 2K: tap 1 of K, tap 3 of K - 1, which is then complete
+          const int K = w >> 1;
+          if (K < Lc.nz) {
+            fv_rw(K, Lc.nz, 1, wz);
+            if (wz[1] != 0.f) acc_b.add(scale_w(S, wz[1]));
+          }
+          if (K - 1 >= 0) {
+            fv_rw(K - 1, Lc.nz, 1, wz);
+            if (wz[3] != 0.f) acc_a.add(scale_w(S, wz[3]));
+          }
+          if (half == 0 && K - 1 >= K0 && K - 1 < K1) cc[(K - 1) * plc + (int64_t)gJ * Lc.nx + gI] = acc_a.get();
+          acc_a = acc_b;
+        }
+      }
+    }
+  }
+#undef SLOT
+}
+
+// Up leg. Grid: (xy tiles, z segments of segZ fine planes (even), right-hand sides).
+// y and y64 (either may be null) must not overlap x, xc or b.
+template <bool ISO>
+__global__ void __launch_bounds__(kThr) k_post_fused(Level L, Level Lc, FusedCoef F, const df* __restrict__ x,
+                                                     const df* __restrict__ xc, const df* __restrict__ b,
+                                                     df* __restrict__ y, double* __restrict__ y64, int segZ) {
+  extern __shared__ df sm[];
+  df* Xp = sm;               // x' over tile + 2, 4 planes
+  df* Pp = Xp + 4 * kA2;     // coarse planes interpolated along x and y, over tile + 2, 3 planes
+  df* Px = Pp + 3 * kA2;     // one coarse plane interpolated along x: kHC coarse rows x kW2 fine columns
+  df* Dp = Px + kAX;         // d0 over tile + 1, 3 planes
+  df* Rp = Dp + 3 * kA1;     // r0 over tile + 1, 2 planes
+  df* td = Rp + 2 * kA1;     // d, del, eta, kap by class
+  df* tdel = td + kTab;
+  df* teta = tdel + kTab;
+  df* tkap = teta + kTab;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kTab; i += kThr) {
+    td[i] = F.d[i];
+    tdel[i] = F.del[i];
+    teta[i] = F.eta[i];
+    tkap[i] = F.kap[i];
+  }
+  const df T0 = F.T[0], T1 = F.T[1], T2 = F.T[2];
+  const int ntx = (Lc.nx + kTX - 1) / kTX;
+  const int C0x = (int)(blockIdx.x % (unsigned)ntx) * kTX, C0y = (int)(blockIdx.x / (unsigned)ntx) * kTY;
+  const int F0x = 2 * C0x, F0y = 2 * C0y;
+  const int Z0 = (int)blockIdx.y * segZ, Z1 = min(Z0 + segZ, L.nz);
+  const int64_t pl = (int64_t)L.nx * L.ny, plc = (int64_t)Lc.nx * Lc.ny;
+  const int64_t off = (int64_t)blockIdx.z * L.N;
+  const df* xx = x + off;
+  const df* bb = b + off;
+  const df* cx = xc + (int64_t)blockIdx.z * Lc.N;
+  const int u_beg = Z0 - 2, u_end = Z1 + 1;
+  const int Kb = (u_beg >> 1) - 1;  // first coarse plane the block reads
+#define SLOT3(p) (((p) - u_beg) % 3)
+#define SLOT4(p) (((p) - u_beg) & 3)
+#define CSLOT(K) (((K) - Kb) % 3)
+
+  constexpr int kPI = kFX * kFY / kThr;  // tile cells per thread in step 3
+  static_assert(kPI * kThr == kFX * kFY, "whole tile rounds");
+  int d2[kP2], d1[kP1], i2[kP1], dI[kPI], iI1[kPI], iI2[kPI];
+#pragma unroll
+  for (int q = 0; q < kP2; ++q) {
+    const int e = tid + q * kThr;
+    d2[q] = e < kA2 ? xy_desc(L, F0x - 2 + e % kW2, F0y - 2 + e / kW2) : -1;
+  }
+#pragma unroll
+  for (int q = 0; q < kP1; ++q) {
+    const int e = tid + q * kThr;
+    const int lx = e % kW1, ly = e / kW1;
+    d1[q] = e < kA1 ? xy_desc(L, F0x - 1 + lx, F0y - 1 + ly) : -1;
+    i2[q] = (ly + 1) * kW2 + lx + 1;
+  }
+#pragma unroll
+  for (int q = 0; q < kPI; ++q) {
+    const int e = tid + q * kThr;
+    const int lx = e % kFX, ly = e / kFX;
+    dI[q] = xy_desc(L, F0x + lx, F0y + ly);
+    iI1[q] = (ly + 1) * kW1 + lx + 1;
+    iI2[q] = (ly + 2) * kW2 + lx + 2;
+  }
+
+  // coarse plane K interpolated to the fine xy cells of tile + 2, x first, then y
+  // (the operand order of the one-kernel prolongation); zeros outside the domain
+  auto interp_x = [&](int K) {
+    const bool kin = (K >= 0 && K < Lc.nz);
+    for (int e = tid; e < kAX; e += kThr) {
+      const int jl = e / kW2, fl = e % kW2;
+      const int gJ = C0y - 2 + jl, gx = F0x - 2 + fl;
+      df v = dzero();
+      if (kin && gJ >= 0 && gJ < Lc.ny && gx >= 0 && gx < L.nx) {
+        int fx[2];
+        float wx[2];
+        const int n_ = fv_prolong_1d(gx, Lc.nx, 1, fx, wx);
+        const df* row = cx + K * plc + (int64_t)gJ * Lc.nx;
+        dsum s;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+          if (a < n_) s.add(scale_w(row[fx[a]], wx[a]));
+        v = s.get();
+      }
+      Px[e] = v;
+    }
+  };
+  auto interp_y = [&](int K) {
+    df* dst = Pp + CSLOT(K) * kA2;
+#pragma unroll
+    for (int q = 0; q < kP2; ++q) {
+      const int e = tid + q * kThr;
+      if (e < kA2) {
+        df v = dzero();
+        if (d2[q] >= 0) {
+          const int gy = F0y - 2 + e / kW2, lx = e % kW2;
+          int fy[2];
+          float wy[2];
+          const int n_ = fv_prolong_1d(gy, Lc.ny, 1, fy, wy);
+          dsum s;
+#pragma unroll
+          for (int a = 0; a < 2; ++a)
+            if (a < n_) s.add(scale_w(Px[(fy[a] - (C0y - 2)) * kW2 + lx], wy[a]));
+          v = s.get();
+        }
+        dst[e] = v;
+      }
+    }
+  };
+  for (int K = Kb; K < Kb + 3; ++K) {
+    interp_x(K);
+    __syncthreads();
+    interp_y(K);
+    __syncthreads();
+  }
+
+  for (int u = u_beg; u <= u_end; ++u) {
+    const int t = u - u_beg;
+    // step 1, plane u: x' = x + P xc over tile + 2
+    {
+      df* Xo = Xp + SLOT4(u) * kA2;
+      const bool uin = (u >= 0 && u < L.nz);
+      int fz[2] = {Kb, Kb};
+      float wz[2] = {0.f, 0.f};
+      const int nz_ = uin ? fv_prolong_1d(u, Lc.nz, 1, fz, wz) : 0;
+      const df* P0 = Pp + CSLOT(fz[0]) * kA2;
+      const df* P1 = Pp + CSLOT(fz[nz_ > 1 ? 1 : 0]) * kA2;
+#pragma unroll
+      for (int q = 0; q < kP2; ++q) {
+        const int e = tid + q * kThr;
+        if (e < kA2) {
+          df v = dzero();
+          if (uin && d2[q] >= 0) {
+            dsum s;
+            s.add(scale_w(P0[e], wz[0]));
+            if (nz_ > 1) s.add(scale_w(P1[e], wz[1]));
+            v = df_add(xx[u * pl + desc_off(d2[q])], s.get());
+          }
+          Xo[e] = v;
+        }
+      }
+      // at u = 2K - 1 the planes K - 1 and K are in use; interpolate K + 1 for u = 2K + 1
+      if ((u & 1) && u < u_end) {
+        interp_x(((u + 1) >> 1) + 1);
+        __syncthreads();
+        interp_y(((u + 1) >> 1) + 1);
+      }
+    }
+    __syncthreads();
+    // step 2, plane v = u - 1: r0 = b + N_T(x') - d_c x', d0 = del_c r0 over tile + 1
+    if (t >= 2) {
+      const int v = u - 1;
+      const df* X0 = Xp + SLOT4(v - 1) * kA2;
+      const df* X1 = Xp + SLOT4(v) * kA2;
+      const df* X2 = Xp + SLOT4(v + 1) * kA2;
+      df* Ro = Rp + ((v - u_beg) & 1) * kA1;
+      df* Do = Dp + SLOT3(v) * kA1;
+      const bool vin = (v >= 0 && v < L.nz);
+      const int cz = 9 * ((v > 0) + (v < L.nz - 1));
+#pragma unroll
+      for (int q = 0; q < kP1; ++q) {
+        const int e = tid + q * kThr;
+        if (e < kA1) {
+          df rv = dzero(), dv = dzero();
+          if (vin && d1[q] >= 0) {
+            const int c = desc_cls(d1[q]) + cz;
+            const df n = nsum<ISO>(X0, X1, X2, i2[q], kW2, T0, T1, T2);
+            dsum s;
+            s.add(bb[v * pl + desc_off(d1[q])]);
+            s.add(n);
+            s.add(df_neg(df_mul(td[c], X1[i2[q]])));
+            rv = s.get();
+            dv = df_mul(tdel[c], rv);
+          }
+          Ro[e] = rv;
+          Do[e] = dv;
+        }
+      }
+      __syncthreads();
+    }
+    // step 3, plane w = u - 2 (in [Z0, Z1)): y = x' + eta_c r0 + kap_c N_T(d0) on the tile
+    if (t >= 4) {
+      const int w = u - 2;
+      const df* D0 = Dp + SLOT3(w - 1) * kA1;
+      const df* D1 = Dp + SLOT3(w) * kA1;
+      const df* D2 = Dp + SLOT3(w + 1) * kA1;
+      const df* R1 = Rp + ((w - u_beg) & 1) * kA1;
+      const df* X1 = Xp + SLOT4(w) * kA2;
+      const int cz = 9 * ((w > 0) + (w < L.nz - 1));
+#pragma unroll
+      for (int q = 0; q < kPI; ++q) {
+        if (dI[q] >= 0) {
+          const int c = desc_cls(dI[q]) + cz;
+          const df n = nsum<ISO>(D0, D1, D2, iI1[q], kW1, T0, T1, T2);
+          dsum s;
+          s.add(X1[iI2[q]]);
+          s.add(df_mul(teta[c], R1[iI1[q]]));
+          s.add(df_mul(tkap[c], n));
+          const df xv = s.get();
+          const int64_t o = off + w * pl + desc_off(dI[q]);
+          if (y) y[o] = xv;
+          if (y64) y64[o] = df_to_double(xv);
+        }
+      }
+    }
+  }
+#undef SLOT3
+#undef SLOT4
+#undef CSLOT
+}
+
+// z segments: enough blocks for about four waves at three blocks per SM, with at least
+// minp planes per segment
+int fused_segments(int tiles, int nrhs, int planes, int minp) {
+  const int64_t base = (int64_t)tiles * nrhs;
+  const int64_t want = 152 * 3 * 4;
+  int nseg = (int)std::max<int64_t>(1, (want + base - 1) / base);
+  nseg = std::min(nseg, std::max(1, planes / minp));
+  return nseg;
+}
+
+// dynamic shared memory above 48 KB is opted into once per device and kernel
+template <typename K>
+bool allow_smem(K kernel, size_t bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  const unsigned long long bit = 1ull << dev;
+  if (done.load() & bit) return true;
+  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(kernel), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes) != cudaSuccess)
+    return false;
+  done.fetch_or(bit);
+  return true;
+}
+std::atomic<unsigned long long> g_attr[4];
+
+}  // namespace
+
+bool fused_level_ok(const Level& L) {
+  return L.cx && L.cy && L.cz && (int64_t)L.nx * L.ny < (int64_t(1) << 26);
+}
+
+bool launch_pre_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* b, df* x,
+                         df* bc, cudaStream_t s) {
+  if (!fused_level_ok(L)) return false;
+  const bool iso = L.iso != 0;
+  if (!(iso ? allow_smem(k_pre_fused<true>, kPreSmem, g_attr[0]) : allow_smem(k_pre_fused<false>, kPreSmem, g_attr[1])))
+    return false;
+  const int ntx = (Lc.nx + kTX - 1) / kTX, nty = (Lc.ny + kTY - 1) / kTY;
+  const int nseg = fused_segments(ntx * nty, nrhs, Lc.nz, 4);
+  const int segK = (Lc.nz + nseg - 1) / nseg;
+  const int nsegs = (Lc.nz + segK - 1) / segK;
+  const dim3 grid((unsigned)(ntx * nty), (unsigned)nsegs, (unsigned)nrhs);
+  if (iso) k_pre_fused<true><<<grid, kThr, kPreSmem, s>>>(L, Lc, F, b, x, bc, segK);
+  else k_pre_fused<false><<<grid, kThr, kPreSmem, s>>>(L, Lc, F, b, x, bc, segK);
+  note_launches(1);
+  return true;
+}
+
+bool launch_post_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* x,
+                          const df* xc, const df* b, df* y, double* y64, cudaStream_t s) {
+  if (!fused_level_ok(L)) return false;
+  const bool iso = L.iso != 0;
+  if (!(iso ? allow_smem(k_post_fused<true>, kPostSmem, g_attr[2])
+            : allow_smem(k_post_fused<false>, kPostSmem, g_attr[3])))
+    return false;
+  const int ntx = (Lc.nx + kTX - 1) / kTX, nty = (Lc.ny + kTY - 1) / kTY;
+  const int nseg = fused_segments(ntx * nty, nrhs, L.nz, 8);
+  int segZ = (L.nz + nseg - 1) / nseg;
+  segZ += segZ & 1;
+  const int nsegs = (L.nz + segZ - 1) / segZ;
+  const dim3 grid((unsigned)(ntx * nty), (unsigned)nsegs, (unsigned)nrhs);
+  if (iso) k_post_fused<true><<<grid, kThr, kPostSmem, s>>>(L, Lc, F, x, xc, b, y, y64, segZ);
+  else k_post_fused<false><<<grid, kThr, kPostSmem, s>>>(L, Lc, F, x, xc, b, y, y64, segZ);
+  note_launches(1);
+  return true;
+}
+
+}  // namespace h1w

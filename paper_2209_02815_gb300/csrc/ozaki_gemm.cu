@@ -41,6 +41,7 @@
 
 #include <vector>
 
+#include "df64.cuh"
 #include "h1w_internal.cuh"
 
 namespace h1w {
@@ -152,6 +153,7 @@ struct OzakiArgs {
   int accumulate;       // add into partial instead of storing
   long long kcta;       // K entries per CTA (multiple of kChunkK)
   long long klen;       // K extent of the digit tensors (multiple of kChunkK)
+  long long kvalid;     // K entries of the panel holding data, rounded up to kChunkK (<= klen)
 };
 
 __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
   const int row0 = tile.x * kTileM, col0 = tile.y * kTileN;
   const long long kbeg = static_cast<long long>(blockIdx.y) * g.kcta;
   long long kend = kbeg + g.kcta;
-  if (kend > g.klen) kend = g.klen;
+  if (kend > g.kvalid) kend = g.kvalid;  // chunks past the data (last panel) are all zero
   const int nchunks = kend > kbeg ? static_cast<int>((kend - kbeg) / kChunkK) : 0;
   const int iters = nchunks * kItersPerChunk;
 
@@ -352,33 +354,6 @@ __device__ __forceinline__ int exp_field(double x) {
   return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7FF);
 }
 
-// Chunk exponents e[c][i] with max_{k in chunk c} |X[i][k]| < 2^e (-100000 for an
-// all-zero chunk); one block per (chunk, row).
-__global__ void k_chunk_exp(const double* __restrict__ X, int m, long long N, int* __restrict__ e) {
-  const int row = blockIdx.y;
-  const long long k0 = static_cast<long long>(blockIdx.x) * kChunkK;
-  int best = 0;
-  for (int t = threadIdx.x; t < kChunkK; t += blockDim.x) {
-    const long long k = k0 + t;
-    if (k < N) {
-      const int ex = exp_field(X[row * N + k]);
-      best = ex > best ? ex : best;
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const int t = __shfl_down_sync(0xffffffffu, best, o);
-    best = t > best ? t : best;
-  }
-  __shared__ int sh[8];
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = best;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int b = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = sh[w] > b ? sh[w] : b;
-    e[static_cast<long long>(blockIdx.x) * m + row] = b ? b - 1022 : -100000;
-  }
-}
-
 __device__ __forceinline__ long long digits_source(double x, int echunk) {
   // Y = round(|x| 2^(47 - e)) with the sign of x (integer arithmetic on the bits)
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
@@ -390,28 +365,52 @@ __device__ __forceinline__ long long digits_source(double x, int echunk) {
   return (b >> 63) ? -Y : Y;
 }
 
-// One thread per 8 consecutive K entries (one 16-byte swizzle chunk) of one row:
-// reads 8 values, writes one 16-byte chunk per digit slice.
-__global__ void k_split_digits(const double* __restrict__ X, int m, long long N, long long k0, long long kw,
-                               long long klen, int R, const int* __restrict__ e, uint16_t* __restrict__ S) {
-  const long long kc = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) * 8;  // first K of the chunk
-  const int row = blockIdx.y;
-  if (kc >= klen) return;
-  const int echunk = (row < m && kc < kw) ? e[((k0 + kc) / kChunkK) * m + row] : 0;
+// The same for one FP32 part of a double-float: |v| < 2^e, so the shift is at least -23
+// and |Y| <= 2^47 (integer arithmetic on the bits).
+__device__ __forceinline__ long long digits_source_f32(float v, int echunk) {
+  const unsigned b = __float_as_uint(v);
+  const int ex = static_cast<int>((b >> 23) & 0xFF);
+  const long long M = static_cast<long long>((b & 0x7FFFFFu) | (ex ? 0x800000u : 0u));
+  const int sh = 103 + echunk - (ex ? ex : 1);
+  long long Y = 0;
+  if (M != 0 && sh <= 24) Y = sh >= 1 ? (M + (1ll << (sh - 1))) >> sh : M << (-sh);
+  return (b >> 31) ? -Y : Y;
+}
+
+// Largest exponent field over the 128-thread block (0 when every value is zero).
+__device__ __forceinline__ int block_max_exp(int v) {
+  __shared__ int sh[4];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t > v ? t : v;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int b = sh[0];
+#pragma unroll
+  for (int w = 1; w < 4; ++w) b = sh[w] > b ? sh[w] : b;
+  return b;
+}
+
+// Eight balanced base-64 digits of each of 8 consecutive K entries, written as one 16-byte
+// chunk per digit slice into the stage-tiled, pre-swizzled layout the GEMM copies from:
+// [row block][K block of kKt][slice][row in block][kKt], 16-byte chunk c of a row stored at
+// c ^ ((row >> 1) & 3) (64-byte swizzle).
+__device__ __forceinline__ void store_digits(long long (&Y)[8], int row, long long kc, long long klen, int R,
+                                             uint16_t* __restrict__ S) {
   uint32_t packed[kSlices][4];
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
-    const long long k = kc + t;
-    long long Y = 0;
-    if (k < kw && row < m) Y = digits_source(X[row * N + k0 + k], echunk);
+    long long y = Y[t];
     int d[kSlices];
 #pragma unroll
     for (int p = kSlices - 1; p >= 1; --p) {
-      const long long r = ((Y + 32) & 63) - 32;
+      const long long r = ((y + 32) & 63) - 32;
       d[p] = static_cast<int>(r);
-      Y = (Y - r) >> 6;
+      y = (y - r) >> 6;
     }
-    d[0] = static_cast<int>(Y);
+    d[0] = static_cast<int>(y);
 #pragma unroll
     for (int p = 0; p < kSlices; ++p) {
       const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d[p])));
@@ -429,6 +428,62 @@ __global__ void k_split_digits(const double* __restrict__ X, int m, long long N,
   for (int p = 0; p < kSlices; ++p)
     *reinterpret_cast<uint4*>(base + static_cast<long long>(p) * R * kKt) =
         make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
+}
+
+// Split of one K panel [k0, k0 + kw) of X (m rows of N, FP64) into digits. A block of 128
+// threads is one chunk of 1024 K entries of one row (8 per thread): it finds the chunk
+// exponent e with max |x| < 2^e (-100000 for an all-zero chunk), stores it at
+// e[(chunk0 + blockIdx.x) m + row] and writes the digits of x 2^(47 - e).
+// Grid: (klen / 1024, rows rounded up to R).
+__global__ void __launch_bounds__(128) k_split_digits(const double* __restrict__ X, int m, long long N, long long k0,
+                                                      long long kw, long long klen, int R, long long chunk0,
+                                                      int* __restrict__ e, uint16_t* __restrict__ S) {
+  const long long kc = (static_cast<long long>(blockIdx.x) * 128 + threadIdx.x) * 8;
+  const int row = blockIdx.y;
+  double x[8];
+  int best = 0;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const long long k = kc + t;
+    x[t] = (k < kw && row < m) ? X[row * N + k0 + k] : 0.0;
+    const int ex = static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x[t])) >> 52) & 0x7FF);
+    best = ex > best ? ex : best;
+  }
+  best = block_max_exp(best);
+  const int ech = best ? best - 1022 : -100000;
+  if (threadIdx.x == 0 && row < m && static_cast<long long>(blockIdx.x) * kChunkK < kw)
+    e[(chunk0 + blockIdx.x) * m + row] = ech;
+  long long Y[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) Y[t] = digits_source(x[t], ech);
+  store_digits(Y, row, kc, klen, R, S);
+}
+
+// The same from double-floats (value hi + lo): the exponent comes from the high parts
+// (|hi + lo| <= |hi| (1 + 2^-24) stays within the digit range) and each part is scaled
+// on its own, so the value is represented to within 2^(e - 47).
+__global__ void __launch_bounds__(128) k_split_digits_df(const df* __restrict__ X, int m, long long N, long long k0,
+                                                         long long kw, long long klen, int R, long long chunk0,
+                                                         int* __restrict__ e, uint16_t* __restrict__ S) {
+  const long long kc = (static_cast<long long>(blockIdx.x) * 128 + threadIdx.x) * 8;
+  const int row = blockIdx.y;
+  df x[8];
+  int best = 0;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const long long k = kc + t;
+    x[t] = (k < kw && row < m) ? X[row * N + k0 + k] : df_make(0.f, 0.f);
+    const int ex = static_cast<int>((__float_as_uint(x[t].hi) >> 23) & 0xFF);
+    best = ex > best ? ex : best;
+  }
+  best = block_max_exp(best);
+  const int ech = best ? best - 126 : -100000;
+  if (threadIdx.x == 0 && row < m && static_cast<long long>(blockIdx.x) * kChunkK < kw)
+    e[(chunk0 + blockIdx.x) * m + row] = ech;
+  long long Y[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) Y[t] = digits_source_f32(x[t].hi, ech) + digits_source_f32(x[t].lo, ech);
+  store_digits(Y, row, kc, klen, R, S);
 }
 
 __global__ void k_fill_int(int* p, int n, int v) {
@@ -477,37 +532,43 @@ bool ozaki_supported() {
   return major == 10;
 }
 
-// C partials (FP64, [splits][m][m], upper tiles) of J H^T via the digit split.
-// Returns false when a tensor map cannot be encoded.
-bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long N, const OzakiWork& w, int splits,
-                              cudaStream_t s, void (*before)(void*), void (*after)(void*), void* hook_arg) {
+// C partials (FP64, [splits][m][m], upper tiles) of J H^T via the digit split. The operands
+// come as FP64 (J, H) or, when Jdf and Hdf are given, as double-floats.
+// Returns false when the kernel attribute cannot be set.
+bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, const df* Hdf, int m, long long N,
+                              const OzakiWork& w, int splits, cudaStream_t s, void (*before)(void*),
+                              void (*after)(void*), void* hook_arg) {
   const long long kp = w.klen;
   const long long nch = (N + kChunkK - 1) / kChunkK;
   int* eA = w.expo;
   int* eB = w.expo + nch * m;
-  k_chunk_exp<<<dim3(static_cast<unsigned>(nch), m), 256, 0, s>>>(J, m, N, eA);
-  k_chunk_exp<<<dim3(static_cast<unsigned>(nch), m), 256, 0, s>>>(H, m, N, eB);
-  note_launches(2);
   if (cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
     return false;
+  const bool use_df = Jdf && Hdf;
   const int tiles = ozaki_num_tiles(m);
   long long kcta = (kp + splits - 1) / splits;
   kcta = (kcta + kChunkK - 1) / kChunkK * kChunkK;
   int panel = 0;
   for (long long k0 = 0; k0 < N; k0 += kp, ++panel) {
     const long long kw = (N - k0) < kp ? (N - k0) : kp;
+    const long long chunk0 = k0 / kChunkK;
     const int rowsA = (m + kTileM - 1) / kTileM * kTileM, rowsB = (m + kTileN - 1) / kTileN * kTileN;
-    const unsigned gx = static_cast<unsigned>((kp / 8 + 127) / 128);
-    k_split_digits<<<dim3(gx, rowsA), 128, 0, s>>>(J, m, N, k0, kw, kp, kTileM, eA,
-                                                   static_cast<uint16_t*>(w.digitsA));
-    k_split_digits<<<dim3(gx, rowsB), 128, 0, s>>>(H, m, N, k0, kw, kp, kTileN, eB,
-                                                   static_cast<uint16_t*>(w.digitsB));
+    const unsigned gx = static_cast<unsigned>(kp / kChunkK);
+    uint16_t* dA = static_cast<uint16_t*>(w.digitsA);
+    uint16_t* dB = static_cast<uint16_t*>(w.digitsB);
+    if (use_df) {
+      k_split_digits_df<<<dim3(gx, rowsA), 128, 0, s>>>(Jdf, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
+      k_split_digits_df<<<dim3(gx, rowsB), 128, 0, s>>>(Hdf, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
+    } else {
+      k_split_digits<<<dim3(gx, rowsA), 128, 0, s>>>(J, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
+      k_split_digits<<<dim3(gx, rowsB), 128, 0, s>>>(H, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
+    }
     OzakiArgs a;
-    a.dA = static_cast<const uint16_t*>(w.digitsA);
-    a.dB = static_cast<const uint16_t*>(w.digitsB);
+    a.dA = dA;
+    a.dB = dB;
     a.eA = eA;
     a.eB = eB;
-    a.chunk0 = k0 / kChunkK;
+    a.chunk0 = chunk0;
     a.tiles = reinterpret_cast<const int2*>(w.tiles);
     a.partial = w.partial;
     a.status = w.status;
@@ -515,6 +576,7 @@ bool launch_ozaki_capacitance(const double* J, const double* H, int m, long long
     a.accumulate = panel > 0 ? 1 : 0;
     a.kcta = kcta;
     a.klen = kp;
+    a.kvalid = (kw + kChunkK - 1) / kChunkK * kChunkK;
     if (before) before(hook_arg);
     k_ozaki_gemm<<<dim3(tiles, splits), kGemmThreads, kSmemBytes, s>>>(a);
     if (after) after(hook_arg);

@@ -39,7 +39,7 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int32), ("rhs_block", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("cap_gemm", ctypes.c_int32),
-                ("mg_arith", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("mg_arith", ctypes.c_int32), ("mg_unfused", ctypes.c_int32)]
 
 
 class Timings(ctypes.Structure):
@@ -49,7 +49,8 @@ class Timings(ctypes.Structure):
                 ("t_jdot_ms", ctypes.c_float), ("t_op_ms", ctypes.c_float), ("t_hdot_ms", ctypes.c_float),
                 ("t_hupd_ms", ctypes.c_float), ("n_gemm_kernel", ctypes.c_int32), ("n_jdot", ctypes.c_int32),
                 ("n_op", ctypes.c_int32), ("n_hdot", ctypes.c_int32), ("n_hupd", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("t_vc_down_ms", ctypes.c_float), ("t_vc_up_ms", ctypes.c_float),
+                ("n_vc_down", ctypes.c_int32), ("n_vc_up", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
