@@ -43,7 +43,19 @@ METRIC = "GN linear solves/s at rel-res 1e-8"
 # up 67 (separable prolongation and add) + 99 (r0, d0) + 99 (final update)
 FP32_OPS_DOWN = 235
 FP32_OPS_UP = 265
-WORKLOAD = "3D ERT GN step, 128^3 cell-centred FV, m=496 pole-dipole, alpha=1e-3, FP64"
+# ncu DRAM read + write bytes per fine cell and right-hand side (64^3, 32 RHS, finest up leg):
+# (142.75 + 42.98) MB / (262144 * 32)
+NCU_BYTES_PER_CELL_RHS = {"k_post_fused": (142.751488e6 + 42.976e6) / (262144 * 32)}
+def workload(n, m, grid=None):
+    proto = "pole-dipole" if grid is None else "dipole-dipole %dx%d grid" % grid
+    return "3D ERT GN step, %d^3 cell-centred FV, m=%d %s, alpha=1e-3, FP64" % (n, m, proto)
+
+
+def electrode_grid(args):
+    if not args.grid:
+        return None
+    ex, ey = (int(v) for v in args.grid.lower().split("x"))
+    return (ex, ey)
 
 
 def parse():
@@ -54,8 +66,16 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_SIDE)
     ap.add_argument("--ne", type=int, default=N_E)
+    ap.add_argument("--grid", default=None,
+                    help="electrode grid EXxEY on the top face with the dipole-dipole protocol (e.g. 8x8)")
+    ap.add_argument("--m-rows", type=int, default=None, help="truncate the protocol to this many measurements")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead of the ERT step: a batch of this many independent 2D Q1 systems "
+                         "(sides 128..1024, m 8..256, alpha log-uniform 1e-4..1e-1) solved by h1w_solve_batch")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-form-steps", type=int, default=1,
+                    help="steps of the plain FP64 GPU form (FP64 V-cycle, CUDA-core GEMM) timed for comparison")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
     return ap.parse_args()
 
@@ -154,7 +174,7 @@ def allmax(world, v: float) -> float:
 # CPU oracle timing on bounded samples (cpu_baseline and --impl reference)
 # ----------------------------------------------------------------------------
 
-def oracle_sample(J_host, logsigma, m_ref, d, n, budget_s: float) -> dict:
+def oracle_sample(J_host, logsigma, m_ref, d, n, budget_s: float, iters_fallback=None, default_case=True) -> dict:
     """Times the oracle's phases on bounded samples and extrapolates to one solve:
     t = m * t_vcycle + t_gemm(m x N x m) + iters * t_iteration. The iteration count
     comes from the oracle's own full solve of this workload (oracle/reference_run.json)."""
@@ -193,15 +213,67 @@ def oracle_sample(J_host, logsigma, m_ref, d, n, budget_s: float) -> dict:
     t_gemm = t_g * (m / k) ** 2
     path = os.path.join(ROOT, "oracle", "reference_run.json")
     iters = None
-    if os.path.exists(path) and n == N_SIDE:
+    iters_from = "oracle"
+    if os.path.exists(path) and n == N_SIDE and default_case:
         with open(path) as f:
             iters = json.load(f).get("iterations")
+    if iters is None and iters_fallback is not None:
+        iters, iters_from = int(iters_fallback), "gpu"
     # one PCG iteration: operator apply + V-cycle + H^T r + H v (two more m x N passes)
     t_it = t_apply + t_v + 2 * t_jpass
     t_solve = m * t_v + t_gemm + (iters or 0) * t_it
     return {"t_vcycle_s": t_v, "t_apply_s": t_apply, "t_jpass_s": t_jpass, "t_gemm_s": t_gemm,
-            "t_iteration_s": t_it, "iterations": iters, "t_solve_s": t_solve,
+            "t_iteration_s": t_it, "iterations": iters, "iterations_from": iters_from, "t_solve_s": t_solve,
             "threads": ccg.threads(), "vcycles_timed": nv, "applies_timed": na}
+
+
+# ----------------------------------------------------------------------------
+# batch of independent 2D systems (multi-instance workload)
+# ----------------------------------------------------------------------------
+
+def run_batch(args):
+    import torch
+    from paper_2209_02815_gb300 import h1w, inputs
+
+    world, rank, local = dist_init(args)
+    dev = torch.device("cuda", local)
+    descs = inputs.batch_instances(args.batch)
+    solvers, Js, bs, xs = [], [], [], []
+    for dsc in descs:
+        n = dsc["n"]
+        J, b = inputs.batch_instance_data(dsc, device=dev)
+        solvers.append(h1w.Solver(h1w.H1W_Q1_VERTEX, (n, n), (1.0 / (n - 1),) * 2, dsc["alpha"], dsc["m"],
+                                  device=dev, stream=torch.cuda.Stream(dev)))
+        Js.append(J)
+        bs.append(b)
+        xs.append(torch.empty_like(b))
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        infos, _ = h1w.solve_batch(solvers, Js, bs, xs, RTOL, MAXIT)
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        infos, _ = h1w.solve_batch(solvers, Js, bs, xs, RTOL, MAXIT)
+    torch.cuda.synchronize()
+    dt = allmax(world, (time.perf_counter() - t0) * 1e3)
+    clocks = clk.stop()
+    value = world * len(descs) * args.steps / (dt / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "%d independent 2D Q1 systems per step (sides 128-1024, m 8-256, "
+                                  "alpha log-uniform 1e-4..1e-1), h1w_solve_batch" % len(descs),
+                      "dof_total": int(sum(d["n"] ** 2 for d in descs)),
+                      "J_entries": int(sum(d["n"] ** 2 * d["m"] for d in descs)),
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "pcg_iters": [int(i.iters) for i in infos], "max_rel_res_true": max(float(i.rel_res_true) for i in infos),
+           "clocks": clocks, "timing": "host wall clock around whole batches (each call synchronizes)",
+           "impl": "ours"}
+    if rank == 0:
+        print(json.dumps(out))
 
 
 # ----------------------------------------------------------------------------
@@ -218,7 +290,8 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)
     n = args.n
     with torch.cuda.stream(stream):
-        pr = inputs.ert_problem(n, n_e_line=args.ne, alpha=ALPHA, device=dev)
+        pr = inputs.ert_problem(n, n_e_line=args.ne, alpha=ALPHA, device=dev, m_rows=args.m_rows,
+                                grid=electrode_grid(args))
         J = pr.J
         m, N = J.shape
         S = h1w.Solver(h1w.H1W_FV_CELL, (n, n, n), (1.0 / n,) * 3, ALPHA, m, device=dev, stream=stream)
@@ -277,9 +350,8 @@ def run_ours(args):
             f1 = torch.cuda.Event(enable_timing=True)
             f0.record(stream)
             for _ in range(args.e2e_steps):
-                J_dev.copy_(J_host, non_blocking=True)
                 b_dev.copy_(b_host, non_blocking=True)
-                S.capacitance(J_dev)
+                S.capacitance_from_host(J_host, J_dev)   # J streamed in row batches under line H
                 S.pcg(b_dev, RTOL, MAXIT, x=x)
                 x_host.copy_(x, non_blocking=True)
             f1.record(stream)
@@ -290,7 +362,36 @@ def run_ours(args):
                    "d2h_bytes_per_step": int(x.numel() * 8), "steps": args.e2e_steps}
             del J_host, J_dev
 
+        # the plain FP64 GPU form of the same step (FP64 V-cycle and Krylov passes, FP64
+        # CUDA-core capacitance GEMM), same inputs, for comparison with the headline
+        fp64_form = None
+        if args.fp64_form_steps > 0:
+            o64 = h1w.h1w_default_options()
+            o64.cap_gemm = 1
+            o64.mg_arith = 1
+            S64 = h1w.Solver(h1w.H1W_FV_CELL, (n, n, n), (1.0 / n,) * 3, ALPHA, m, device=dev, stream=stream,
+                             opt=o64)
+            S64.capacitance(J)
+            S64.pcg(b, RTOL, MAXIT, x=x)
+            torch.cuda.synchronize()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(args.fp64_form_steps):
+                S64.capacitance(J)
+                _, inf64 = S64.pcg(b, RTOL, MAXIT, x=x)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            gms = allmax(world, g0.elapsed_time(g1))
+            fp64_form = {"value": world * args.fp64_form_steps / (gms / 1e3), "unit": "solves/s",
+                         "ms_per_step": gms / args.fp64_form_steps, "steps": args.fp64_form_steps,
+                         "pcg_iters": int(inf64.iters), "rel_res_true": float(inf64.rel_res_true),
+                         "options": "cap_gemm=1 (FP64 CUDA-core GEMM), mg_arith=1 (FP64 V-cycle and passes)"}
+            del S64
+
     value = world * args.steps / (ms_max / 1e3)
+    if fp64_form:
+        fp64_form["headline_over_fp64_form"] = value / fp64_form["value"]
     mean = {k_: float(np.mean(v_)) for k_, v_ in phase.items()}
     peaks = {}
     try:
@@ -325,6 +426,7 @@ def run_ours(args):
     # FP32 instructions per fine cell (FMA counted once) of the operations the legs require,
     # halo recomputation excluded; peak = 152 SMs x 128 FP32 lanes x the maximum SM clock.
     alu_peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    n_up = kern["vc_up"][1]
     for key, name, ops in (("vc_down", "k_pre_fused (finest level: smoothing + residual + restriction)",
                             FP32_OPS_DOWN),
                            ("vc_up", "k_post_fused (finest level: prolongation + smoothing)", FP32_OPS_UP)):
@@ -338,11 +440,19 @@ def run_ours(args):
          "bytes of H, z0, r and z per pass")
     dom = max(table, key=lambda k_: table[k_]["ms_per_step"]) if table else None
     roofline = dict(table[dom], kernel=dom, traffic=None) if dom else None
+    # DRAM bytes per launch from one ncu capture of the same kernel build on the 64^3 case
+    # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_fused_legs_64cube_32rhs.md),
+    # scaled by the cells x right-hand sides of an average launch here; reads equal the
+    # algorithmic x, b and coarse-vector bytes there, so traffic grows in proportion
+    if roofline and dom.startswith("k_post_fused") and n_up:
+        roofline["traffic"] = NCU_BYTES_PER_CELL_RHS["k_post_fused"] * float(m) * N * args.steps / n_up
+        roofline["traffic_note"] = "ncu 64^3 x 32 RHS capture, scaled by cell-RHS per launch"
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": [n, n, n], "N": N, "m": m, "alpha": ALPHA, "rtol": RTOL,
+        "config": {"workload": workload(n, m, electrode_grid(args)), "n": [n, n, n], "N": N, "m": m, "alpha": ALPHA,
+                   "rtol": RTOL,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (J is %.1f GB)" % (J.numel() * 8 / 1e9)},
         "phases_ms": mean, "pcg_iters": iters, "rel_res_true": rel_true,
@@ -352,11 +462,13 @@ def run_ours(args):
                   "capacitance_gemm": "BF16 tensor cores on an exact 48-bit digit split, FP64 accumulation",
                   "cholesky": "f64", "woodbury_passes": "double-float"},
         "roofline": roofline, "kernels": table, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
+        "fp64_form": fp64_form,
         "impl": "ours",
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         J_host = J.cpu().numpy()
-        s = oracle_sample(J_host, pr.logsigma, pr.m_ref, pr.d, n, args.cpu_sample_s)
+        s = oracle_sample(J_host, pr.logsigma, pr.m_ref, pr.d, n, args.cpu_sample_s, iters_fallback=iters[-1],
+                          default_case=(args.grid is None and args.m_rows is None and args.ne == N_E))
         out["cpu_baseline"] = {"value": (1.0 / s["t_solve_s"]) if s["iterations"] else None,
                                "unit": "solves/s", "cores": s["threads"], "kind": "oracle",
                                "sample": ("oracle phases timed on bounded samples and extrapolated: "
@@ -379,7 +491,8 @@ def run_reference(args):
         return
     from paper_2209_02815_gb300 import inputs
     n = args.n
-    pr = inputs.ert_problem(n, n_e_line=args.ne, alpha=ALPHA, device="cpu")
+    pr = inputs.ert_problem(n, n_e_line=args.ne, alpha=ALPHA, device="cpu", m_rows=args.m_rows,
+                            grid=electrode_grid(args))
     J = np.ascontiguousarray(pr.J)
     vals = []
     last = None
@@ -394,7 +507,9 @@ def run_reference(args):
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": [n, n, n], "m": int(J.shape[0]), "alpha": ALPHA, "rtol": RTOL},
+           "config": {"workload": workload(n, int(J.shape[0]), electrode_grid(args)), "n": [n, n, n],
+                      "m": int(J.shape[0]), "alpha": ALPHA,
+                      "rtol": RTOL},
            "impl": "reference",
            "cpu_baseline": {"value": value, "unit": "solves/s", "kind": "oracle", "cores": last["threads"],
                             "sample": "per step: oracle phases timed on bounded samples, extrapolated "
@@ -408,5 +523,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.batch > 0:
+        run_batch(a)
     else:
         run_ours(a)

@@ -128,15 +128,26 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
 /* Lines H, C and chol of Algorithm "MINRES with the Laplace-Woodbury
  * preconditioner": H = L-hat^-1 J^T (m batched V-cycles), C = I + alpha^-1 J H
  * (formed from its upper triangle and mirrored), C = L L^T. With
- * cap_gemm = 0 the product J H^T runs on the tensor cores: each row of J
- * and H is scaled by a power of two, rounded to 42 bits and written exactly
- * as seven BF16 digits; digit products are accumulated exactly in FP32
- * chunks and combined in FP64 (error below 2^-42 of the row maxima). J (m x N,
- * row-major, device) is borrowed: it must stay valid and unchanged until the
- * next h1w_capacitance or h1w_destroy. 0 <= m <= m_max; m = 0 gives the
- * Laplace-only preconditioner. Synchronizes; H1W_ENOTSPD if C is not
- * numerically positive definite. */
+ * cap_gemm = 0 the product J H^T runs on the tensor cores: each chunk of
+ * 1024 consecutive entries of a row of J and of H is scaled by its own power
+ * of two, rounded to 48 bits and written exactly as eight BF16 digits; digit
+ * products are accumulated exactly in FP32 chunks and combined in FP64
+ * (error below 2^-47 of the chunk maxima). J (m x N, row-major, device) is
+ * borrowed: it must stay valid and unchanged until the next h1w_capacitance or
+ * h1w_destroy. 0 <= m <= m_max; m = 0 gives the Laplace-only preconditioner.
+ * Synchronizes; H1W_ENOTSPD if C is not numerically positive definite. */
 h1w_status h1w_capacitance(h1w_ctx* ctx, int32_t m, const double* J);
+
+/* The same lines with J supplied in page-locked HOST memory: J_host (m x N,
+ * row-major, e.g. from cudaHostAlloc) is copied into the caller's DEVICE
+ * buffer J_dev (m x N), which then is the borrowed J of the context, exactly as
+ * J of h1w_capacitance. The copy runs on a second stream of the context in row
+ * batches of rhs_block, and each batch's V-cycles start as soon as its own
+ * rows have arrived, so the copy overlaps line H. No counterpart in the paper
+ * (its data never leave the host). J_host must stay valid until the call
+ * returns; the results equal those of h1w_capacitance on the same J.
+ * Synchronizes. */
+h1w_status h1w_capacitance_from_host(h1w_ctx* ctx, int32_t m, const double* J_host, double* J_dev);
 
 /* z = P^-1 r with P = alpha L-hat + J^T J, evaluated by the Woodbury formula
  * of Sec. 3.2: z = alpha^-1 [ L-hat^-1 r - alpha^-1 H C^-1 H^T r ].
@@ -171,6 +182,20 @@ h1w_status h1w_pcg(h1w_ctx* ctx, const double* b, double* x, double rtol, int32_
 /* Copies the capacitance matrix C and its lower Cholesky factor L (m x m,
  * row-major, DEVICE) into caller buffers (either may be NULL). */
 h1w_status h1w_capacitance_factors(h1w_ctx* ctx, double* C, double* L);
+
+/* Lines H, C, chol and PCG (as h1w_capacitance followed by h1w_pcg) for `count`
+ * independent systems, each with its own context, set up on its own stream (not
+ * the legacy default stream, which would serialise them). System i takes
+ * m[i] measurements with J[i] (borrowed, as in h1w_capacitance), right-hand
+ * side b[i] and solution x[i] (DEVICE). Up to `threads` host threads (<= 0:
+ * 8) work through the systems concurrently, so that the kernels of small systems
+ * overlap on the GPU. info and status (may be NULL) get count entries.
+ * Returns H1W_OK when every system converged, else the first failing status; the
+ * failing context's h1w_last_error has the reason. The paper solves one system
+ * at a time and has no counterpart. Synchronizes. */
+h1w_status h1w_solve_batch(h1w_ctx* const* ctxs, int32_t count, const int32_t* m, const double* const* J,
+                           const double* const* b, double* const* x, double rtol, int32_t maxit,
+                           int32_t threads, h1w_info* info, h1w_status* status);
 
 /* Phase times and launch counts of the last h1w_capacitance / h1w_pcg. */
 h1w_status h1w_get_timings(const h1w_ctx* ctx, h1w_timings* out);

@@ -60,9 +60,9 @@ struct h1w_ctx {
   // capacitance state
   int m;                 // current number of measurements (-1: none yet)
   const double* J;       // borrowed
-  double* H;             // m_max x N
-  df* Hdf;               // m_max x N, the same as double-floats (double-float V-cycle only)
-  df* Jdf;               // m_max x N, J as double-floats for the Krylov operator passes
+  double* H;             // m_max x N (FP64 paths only)
+  df* Hdf;               // m_max x N, H as double-floats (double-float V-cycle only)
+  df* Jdf;               // m_max x N, J as double-floats for the cycle and the Krylov passes
   df* vdf;               // N, a vector converted to double-floats
   double* C;             // m_max x m_max
   double* Lc;            // m_max x m_max
@@ -86,6 +86,11 @@ struct h1w_ctx {
   int nk;
   bool timing_on;
   bool time_vc = false;  // record the finest-level fused V-cycle kernels (line H only)
+  int num_sms = 152;     // SMs of the context's device
+  int* trsv_flags = nullptr;  // per-block flags of the cooperative C^-1 solve
+  int trsv_epoch = 0;
+  cudaStream_t copy_stream = nullptr;   // host-to-device copies of h1w_capacitance_from_host
+  std::vector<cudaEvent_t> cev;          // one per row batch, plus one for ordering
   float cat_ms[8];
   int cat_n[8];
   long long launches_cap, launches_pcg;
@@ -268,10 +273,10 @@ h1w_status validate(const h1w_grid* g, int32_t m_max, const h1w_options* o, std:
 
 int64_t gemm_partial_len(int m_max, int64_t N, bool ozaki) {
   int64_t best = 1;
-  const long long kp = ozaki_panel_width(N);
   for (int m = 1; m <= m_max; ++m) {
     best = std::max(best, (int64_t)cap_gemm_splits(m, N) * m * m);
-    if (ozaki) best = std::max(best, (int64_t)ozaki_splits(m, kp) * m * m);
+    if (ozaki)  // any SM count: the setup uses the device's own
+      best = std::max(best, (int64_t)ozaki_max_splits(m) * m * m);
   }
   return best;
 }
@@ -299,6 +304,7 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   double* cX = B.take<double>(Nc * Nc);
   double* cL = B.take<double>(Nc * Nc);
   int* dstatus = B.take<int>(4);
+  int* tflags = B.take<int>(2 * ((m_max + 31) / 32 + 1));
   unsigned long long* dbits = B.take<unsigned long long>(4);
   const bool use_df = (g.disc == H1W_FV_CELL) && (o.mg_arith == 0);
   // FP64 H: not needed when the cycle is double-float and C runs on the tensor cores
@@ -336,7 +342,7 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   if (c) {
     c->qdev = qdev;
     for (int k = 0; k < P.nlev; ++k) c->buf[k] = bufs[k];
-    c->coarse_X = cX; c->coarse_L = cL; c->dstatus = dstatus; c->dbits = dbits;
+    c->coarse_X = cX; c->coarse_L = cL; c->dstatus = dstatus; c->dbits = dbits; c->trsv_flags = tflags;
     c->H = H; c->C = C; c->Lc = Lc; c->gemm_partial = gp; c->gemm_partial_len = gpl;
     c->Hdf = Hdf; c->vdf = vdf; c->Jdf = Jdf;
     c->oz = ow;
@@ -418,19 +424,29 @@ bool fused_level(const h1w_ctx* c, int l) {
 // x = L-hat^-1 b for nrhs <= rhs_block right-hand sides given as double-floats (b0, level-0
 // sized, contiguous); the result goes to x64 (FP64) and/or xdf (double-floats).
 // Returns false if a fused kernel could not be configured.
-bool vcycle_block_df(h1w_ctx* c, int nrhs, const df* b0, double* x64, df* xdf) {
+bool vcycle_block_df(h1w_ctx* c, int nrhs, const df* b0, const double* b0_64, double* x64, df* xdf) {
   const int nl = c->nlev;
   cudaStream_t s = c->stream;
   const df* bl[kMaxLevels];
   const df* xf[kMaxLevels];
+  // FP64 right-hand sides: the fused finest-level kernels split them on the fly; every other
+  // consumer gets a double-float copy
+  if (b0_64 && !(nl > 1 && fused_level(c, 0))) {
+    launch_d2df((int64_t)nrhs * c->lev[0].N, b0_64, dfp(c->buf[0].b), s);
+    b0 = dfp(c->buf[0].b);
+    b0_64 = nullptr;
+  }
   bl[0] = b0;
   for (int l = 1; l < nl; ++l) bl[l] = dfp(c->buf[l].b);
   for (int l = 0; l < nl - 1; ++l) {
     df* x = dfp(c->buf[l].x);
     if (fused_level(c, l)) {
       if (l == 0 && c->time_vc) timed_begin(c);
-      if (!launch_pre_fused_df(c->lev[l], c->lev[l + 1], c->fco[l], nrhs, bl[l], x, dfp(c->buf[l + 1].b), s))
-        return false;
+      const bool ok = (l == 0 && b0_64)
+                          ? launch_pre_fused_df(c->lev[0], c->lev[1], c->fco[0], nrhs, b0_64, x, dfp(c->buf[1].b), s)
+                          : launch_pre_fused_df(c->lev[l], c->lev[l + 1], c->fco[l], nrhs, bl[l], x,
+                                                dfp(c->buf[l + 1].b), s);
+      if (!ok) return false;
       if (l == 0 && c->time_vc) timed_end(c, kCatDown);
     } else {
       smooth_df(c, l, nrhs, bl[l], x, true);
@@ -446,9 +462,12 @@ bool vcycle_block_df(h1w_ctx* c, int nrhs, const df* b0, double* x64, df* xdf) {
       df* y = (l == 0) ? xdf : dfp(c->buf[l].r);   // r is free on the up leg
       double* y64 = (l == 0) ? x64 : nullptr;
       if (l == 0 && c->time_vc) timed_begin(c);
-      if (!launch_post_fused_df(c->lev[l], c->lev[l + 1], c->fco[l], nrhs, dfp(c->buf[l].x), xf[l + 1], bl[l], y,
-                                y64, s))
-        return false;
+      const bool ok = (l == 0 && b0_64)
+                          ? launch_post_fused_df(c->lev[0], c->lev[1], c->fco[0], nrhs, dfp(c->buf[0].x), xf[1],
+                                                 b0_64, y, y64, s)
+                          : launch_post_fused_df(c->lev[l], c->lev[l + 1], c->fco[l], nrhs, dfp(c->buf[l].x),
+                                                 xf[l + 1], bl[l], y, y64, s);
+      if (!ok) return false;
       if (l == 0 && c->time_vc) timed_end(c, kCatUp);
       xf[l] = y;
       written = (l == 0);
@@ -474,12 +493,9 @@ bool vcycle_many(h1w_ctx* c, int nrhs, const double* b64, const df* bdf, double*
     const int nr = std::min(c->opt.rhs_block, nrhs - r0);
     const int64_t o = (int64_t)r0 * N;
     if (uses_df(c)) {
-      const df* b = bdf ? bdf + o : nullptr;
-      if (!b) {
-        launch_d2df((int64_t)nr * N, b64 + o, dfp(c->buf[0].b), c->stream);
-        b = dfp(c->buf[0].b);
-      }
-      if (!vcycle_block_df(c, nr, b, x64 ? x64 + o : nullptr, xdf ? xdf + o : nullptr)) return false;
+      if (!vcycle_block_df(c, nr, bdf ? bdf + o : nullptr, bdf ? nullptr : b64 + o, x64 ? x64 + o : nullptr,
+                           xdf ? xdf + o : nullptr))
+        return false;
     } else {
       vcycle_block(c, nr, b64 + o, x64 + o);
     }
@@ -531,8 +547,17 @@ bool apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
       timed_end(c, kCatHdot);
       launch_reduce_partials(c->partial, rows_dot_chunks(N), m, 1.0, c->svec, c->stream);
     }
-    launch_trsv_lower(c->Lc, m, c->svec, 1, c->stream);
-    launch_trsv_upper_t(c->Lc, m, c->svec, 1, c->stream);  // v = C^-1 s
+    // y = C^-1 s by the two triangular solves: backward stable, so the Woodbury formula sees
+    // C + dC with |dC| ~ eps |C|. A product with an explicitly formed C^-1 is not (each
+    // column carries its own rounding), which for |C| ~ 1e10 breaks the preconditioner.
+    if (c->trsv_epoch == 0x7FFFFFFF) {  // flags hold epochs 1 .. 2^31 - 1
+      cudaMemsetAsync(c->trsv_flags, 0, sizeof(int) * 2 * ((c->m_max + 31) / 32 + 1), c->stream);
+      c->trsv_epoch = 0;
+    }
+    if (!launch_chol_solve_coop(c->Lc, m, c->svec, c->trsv_flags, ++c->trsv_epoch, c->dstatus, c->stream)) {
+      launch_trsv_lower(c->Lc, m, c->svec, 1, c->stream);
+      launch_trsv_upper_t(c->Lc, m, c->svec, 1, c->stream);
+    }
   }
   timed_begin(c);
   if (dfp_)
@@ -616,10 +641,17 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
   c->disc = grid->disc;
   c->m_max = m_max;
   c->stream = reinterpret_cast<cudaStream_t>(stream);
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      c->num_sms = sms;
+  }
   c->nlev = P.nlev;
   c->m = -1;
   c->J = nullptr;
   layout(c, P, *grid, m_max, o, static_cast<char*>(workspace));
+  cudaMemsetAsync(c->trsv_flags, 0, sizeof(int) * 2 * ((m_max + 31) / 32 + 1), c->stream);
   c->have_ev = true;
   for (int e = 0; e < 6; ++e)
     if (cudaEventCreate(&c->ev[e]) != cudaSuccess) c->have_ev = false;
@@ -749,23 +781,50 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
   return H1W_OK;
 }
 
-h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
-  if (!c) return H1W_EINVAL;
-  if (m < 0 || m > c->m_max) return fail(c, H1W_EINVAL, "m out of range [0, m_max]");
-  if (m > 0 && !J) return fail(c, H1W_EINVAL, "J is NULL");
+// Lines H, C, chol. With J_host given, the rows of J are first copied from it into J
+// (device) on the context's copy stream, one rhs_block batch at a time, each batch's
+// conversion and V-cycles waiting only for that batch's copy.
+static h1w_status capacitance_impl(h1w_ctx* c, int32_t m, const double* J, const double* J_host) {
   const int64_t N = c->lev[0].N;
   c->m = m;
   c->J = J;
   const long long l0 = g_kernel_launches.load();
   if (m == 0) { c->launches_cap = 0; return H1W_OK; }
+  const int nb = c->opt.rhs_block;
+  const int nbatch = (m + nb - 1) / nb;
+  if (J_host) {
+    if (!c->copy_stream && cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create the copy stream");
+    while ((int)c->cev.size() < nbatch + 1) {
+      cudaEvent_t e;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+        return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create an event");
+      c->cev.push_back(e);
+    }
+    // the copy may overwrite J only after work already queued on the context's stream
+    cudaEventRecord(c->cev[nbatch], c->stream);
+    cudaStreamWaitEvent(c->copy_stream, c->cev[nbatch], 0);
+    for (int bi = 0; bi < nbatch; ++bi) {
+      const int64_t r0 = (int64_t)bi * nb, nr = std::min<int64_t>(nb, m - r0);
+      cudaMemcpyAsync(const_cast<double*>(J) + r0 * N, J_host + r0 * N, sizeof(double) * nr * N,
+                      cudaMemcpyHostToDevice, c->copy_stream);
+      cudaEventRecord(c->cev[bi], c->copy_stream);
+    }
+  }
   if (c->have_ev) cudaEventRecord(c->ev[0], c->stream);
-  if (uses_df(c)) launch_d2df((int64_t)m * N, J, c->Jdf, c->stream);  // J for the Krylov passes
-  // line H; on the double-float cycle the tensor-core split reads J and H as double-floats,
-  // so the FP64 copy of H is only written for the FP64 paths
+  // line H; on the double-float cycle the tensor-core split reads H as double-floats, so the
+  // FP64 copy of H is only written for the FP64 paths
   const bool h_df_only = uses_df(c) && c->opt.cap_gemm == 0;
   c->nk = 0;
   c->timing_on = c->time_vc = true;
-  const bool vc_ok = vcycle_many(c, m, J, uses_df(c) ? c->Jdf : nullptr, h_df_only ? nullptr : c->H, c->Hdf);
+  bool vc_ok = true;
+  for (int bi = 0; bi < nbatch && vc_ok; ++bi) {
+    const int64_t r0 = (int64_t)bi * nb, nr = std::min<int64_t>(nb, m - r0), o = r0 * N;
+    if (J_host) cudaStreamWaitEvent(c->stream, c->cev[bi], 0);
+    if (uses_df(c)) launch_d2df(nr * N, J + o, c->Jdf + o, c->stream);  // J for the cycle and the Krylov passes
+    vc_ok = vcycle_many(c, (int)nr, J + o, uses_df(c) ? c->Jdf + o : nullptr, h_df_only ? nullptr : c->H + o,
+                        c->Hdf ? c->Hdf + o : nullptr);
+  }
   c->timing_on = c->time_vc = false;
   if (!vc_ok) return fail(c, H1W_ECUDA, "capacitance: multigrid kernel attribute failed");
   if (c->have_ev) cudaEventRecord(c->ev[1], c->stream);
@@ -776,10 +835,10 @@ h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
     ozaki_tiles(m, c->oz_tiles_host);
     cudaMemcpyAsync(c->oz.tiles, c->oz_tiles_host.data(), sizeof(int) * c->oz_tiles_host.size(),
                     cudaMemcpyHostToDevice, c->stream);
-    splits = ozaki_splits(m, c->oz.klen);
+    splits = ozaki_splits(m, c->oz.klen, c->num_sms);
     c->timing_on = true;
     const bool ok = launch_ozaki_capacitance(
-        J, c->H, h_df_only ? c->Jdf : nullptr, h_df_only ? c->Hdf : nullptr, m, N, c->oz, splits, c->stream, [](void* p) { timed_begin(static_cast<h1w_ctx*>(p)); },
+        J, c->H, nullptr, h_df_only ? c->Hdf : nullptr, m, N, c->oz, splits, c->stream, [](void* p) { timed_begin(static_cast<h1w_ctx*>(p)); },
         [](void* p) { timed_end(static_cast<h1w_ctx*>(p), kCatGemm); }, c);
     c->timing_on = false;
     if (!ok)
@@ -814,6 +873,20 @@ h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
     return fail(c, H1W_ENOTSPD, "capacitance matrix is not numerically positive definite");
   }
   return H1W_OK;
+}
+
+h1w_status h1w_capacitance(h1w_ctx* c, int32_t m, const double* J) {
+  if (!c) return H1W_EINVAL;
+  if (m < 0 || m > c->m_max) return fail(c, H1W_EINVAL, "m out of range [0, m_max]");
+  if (m > 0 && !J) return fail(c, H1W_EINVAL, "J is NULL");
+  return capacitance_impl(c, m, J, nullptr);
+}
+
+h1w_status h1w_capacitance_from_host(h1w_ctx* c, int32_t m, const double* J_host, double* J_dev) {
+  if (!c) return H1W_EINVAL;
+  if (m < 0 || m > c->m_max) return fail(c, H1W_EINVAL, "m out of range [0, m_max]");
+  if (m > 0 && (!J_host || !J_dev)) return fail(c, H1W_EINVAL, "J_host and J_dev must be non-NULL");
+  return capacitance_impl(c, m, J_dev, m > 0 ? J_host : nullptr);
 }
 
 h1w_status h1w_apply_prec(h1w_ctx* c, const double* r, double* z) {
@@ -866,6 +939,7 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
   if (c->have_ev) cudaEventRecord(c->ev[4], s);
   c->nk = 0;
   c->timing_on = true;
+  cudaMemsetAsync(c->dstatus, 0, sizeof(int), s);  // bounded waits of the C^-1 solves report here
   launch_dot_partial(b, b, N, c->partial, s);
   launch_sum_to_scalar(c->partial, dot_blocks(N), c->scal + BB, s);
   const double bnorm = std::sqrt(read_scalar(c, BB));
@@ -934,6 +1008,10 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
   h1w_status st = cuda_check(c, "pcg");
   if (st != H1W_OK) return st;
   if (prec_failed) return fail(c, H1W_ECUDA, "pcg: multigrid kernel attribute failed");
+  int dst = 0;
+  cudaMemcpyAsync(&dst, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (dst & kStatusTimeout) return fail(c, H1W_ETIMEOUT, "pcg: a bounded device wait ran out");
   if (!(rel_true <= rtol)) return fail(c, H1W_ENOTCONV, "PCG did not reach rtol within maxit");
   return H1W_OK;
 }
@@ -1001,6 +1079,11 @@ const char* h1w_last_error(const h1w_ctx* c) {
 
 void h1w_destroy(h1w_ctx* c) {
   if (!c) return;
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (cudaEvent_t e : c->cev) cudaEventDestroy(e);
   if (c->have_ev) {
     for (int e = 0; e < 6; ++e) cudaEventDestroy(c->ev[e]);
     for (int t = 0; t < h1w_ctx::kTimed; ++t)

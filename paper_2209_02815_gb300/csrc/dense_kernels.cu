@@ -144,6 +144,7 @@ __device__ __forceinline__ df warp_sum_df(df v) {
 // block share the segment of v through L1.
 constexpr int kSegDf = 8192;
 
+
 __global__ void __launch_bounds__(kThreads) k_rows_dot_df(const df* __restrict__ A, int m, int64_t N,
                                                           const df* __restrict__ v, double* __restrict__ partial) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -364,6 +365,140 @@ __global__ void __launch_bounds__(512) k_trsv_upper_t(const double* __restrict__
     __syncthreads();
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) xr[i] = x[i];
+}
+
+// ---- both triangular solves of C^-1 s in one cooperative launch ----------------
+//
+// x <- L^-T L^-1 x for one right-hand side. CTA p owns the 32-row block p. Forward:
+// y_p = D_p^-1 (x_p - sum_{J<p} L_pJ y_J), where each update L_pJ y_J is applied as soon
+// as block J has published y_J (flag_f[J] == epoch); backward likewise with z_p =
+// D_p^-T (y_p - sum_{J>p} L_Jp^T z_J) and flag_b. Only the diagonal solves lie on the
+// critical path; the updates of different blocks run on different SMs (a single-block
+// solve is bound by the FP64 pipe of one SM). All CTAs must be resident: the launch is
+// cooperative. Every wait gives up after about a second, sets kStatusTimeout and returns.
+// The flags hold the epoch of the last solve, so they never need resetting.
+
+__device__ __forceinline__ uint64_t trsv_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait until flag == epoch (bounded). Thread 0 polls and decides for the whole block, so
+// that every thread of the block returns the same answer; false on timeout (or when
+// another block already gave up).
+__device__ bool trsv_wait(const int* flag, int epoch, int* status, int* s_ok) {
+  if (threadIdx.x == 0) {
+    const uint64_t t0 = trsv_timer();
+    unsigned n = 0;
+    int ok = 1;
+    while (atomicAdd(const_cast<int*>(flag), 0) != epoch) {
+      if ((++n & 63) == 0 && (trsv_timer() - t0 > 1000000000ull || (atomicAdd(status, 0) & kStatusTimeout))) {
+        atomicOr(status, kStatusTimeout);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(256) k_chol_solve_coop(const double* __restrict__ L, int n, double* x,
+                                                        int* flag_f, int* flag_b, int epoch, int* status) {
+  __shared__ double D[kNB][kNB + 1];
+  __shared__ double acc[kNB];
+  __shared__ int s_ok;
+  const int p = blockIdx.x, nblk = gridDim.x;
+  const int kb = p * kNB, nb = min(kNB, n - kb);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+    const int r = e / kNB, c = e % kNB;
+    D[r][c] = (r < nb && c <= r) ? L[(int64_t)(kb + r) * n + kb + c] : 0.0;
+  }
+  if (threadIdx.x < kNB) acc[threadIdx.x] = (threadIdx.x < nb) ? x[kb + threadIdx.x] : 0.0;
+  __syncthreads();
+  // forward: thread (row r = 4 wid + lane / 8, t = lane % 8) takes columns t, t + 8, t + 16, t + 24
+  {
+    const int r = 4 * wid + (lane >> 3), t = lane & 7;
+    for (int J = 0; J < p; ++J) {
+      if (!trsv_wait(flag_f + J, epoch, status, &s_ok)) return;
+      const int jb = J * kNB;
+      double sacc = 0.0;
+      if (r < nb) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = t + 8 * k;
+          sacc += L[(int64_t)(kb + r) * n + jb + c] * __ldcg(x + jb + c);
+        }
+      }
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
+      if (t == 0 && r < nb) acc[r] -= sacc;
+      __syncthreads();
+    }
+  }
+  if (wid == 0) {
+    double a = (lane < nb) ? acc[lane] : 0.0;
+    const double inv = (lane < nb) ? 1.0 / D[lane][lane] : 0.0;
+    for (int c = 0; c < nb; ++c) {
+      double yc = (lane == c) ? a * inv : 0.0;
+      yc = __shfl_sync(0xffffffffu, yc, c);
+      if (lane == c) a = yc;
+      else if (lane > c && lane < nb) a -= yc * D[lane][c];
+    }
+    if (lane < nb) {
+      acc[lane] = a;
+      x[kb + lane] = a;
+    }
+    __threadfence();  // the published values before the flag, from every writing lane
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(flag_f + p, epoch);
+  }
+  // backward: thread (row r = 4 wid + lane % 4, t = lane / 4); rows of L^T are columns of L
+  {
+    const int r = 4 * wid + (lane & 3), t = lane >> 2;
+    for (int J = nblk - 1; J > p; --J) {
+      if (!trsv_wait(flag_b + J, epoch, status, &s_ok)) return;
+      const int jb = J * kNB, jn = min(kNB, n - jb);
+      double sacc = 0.0;
+      if (r < nb) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = t + 8 * k;
+          if (c < jn) sacc += L[(int64_t)(jb + c) * n + kb + r] * __ldcg(x + jb + c);
+        }
+      }
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 8);
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 16);
+      if (t == 0 && r < nb) acc[r] -= sacc;
+      __syncthreads();
+    }
+  }
+  if (wid == 0) {
+    double a = (lane < nb) ? acc[lane] : 0.0;
+    const double inv = (lane < nb) ? 1.0 / D[lane][lane] : 0.0;
+    for (int c = nb - 1; c >= 0; --c) {
+      double vc = (lane == c) ? a * inv : 0.0;
+      vc = __shfl_sync(0xffffffffu, vc, c);
+      if (lane == c) a = vc;
+      else if (lane < c) a -= vc * D[c][lane];
+    }
+    if (lane < nb) x[kb + lane] = a;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(flag_b + p, epoch);
+  }
 }
 
 // x[r] = X b[r]: one warp per (row, rhs)
@@ -594,6 +729,25 @@ void launch_trsv_lower(const double* L, int n, double* x, int nrhs, cudaStream_t
 void launch_trsv_upper_t(const double* L, int n, double* x, int nrhs, cudaStream_t s) {
   k_trsv_upper_t<<<nrhs, 512, sizeof(double) * n, s>>>(L, n, x);
   note_launches(1);
+}
+
+bool launch_chol_solve_coop(const double* L, int n, double* x, int* flags, int epoch, int* status,
+                            cudaStream_t s) {
+  const int nblk = (n + kNB - 1) / kNB;
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_solve_coop, 256, 0) != cudaSuccess ||
+      nblk > per_sm * sms)
+    return false;
+  int* flag_f = flags;
+  int* flag_b = flags + nblk;
+  void* args[] = {(void*)&L, (void*)&n, (void*)&x, (void*)&flag_f, (void*)&flag_b, (void*)&epoch, (void*)&status};
+  if (cudaLaunchCooperativeKernel((const void*)k_chol_solve_coop, dim3(nblk), dim3(256), args, 0, s) != cudaSuccess)
+    return false;
+  note_launches(1);
+  return true;
 }
 
 void launch_coarse_apply(const double* X, int n, int nrhs, const double* b, double* x,

@@ -10,6 +10,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 namespace h1w {
 
 struct df {
@@ -23,6 +25,7 @@ __host__ __device__ __forceinline__ df df_make(float h, float l) {
   return r;
 }
 
+#ifdef __CUDACC__
 // s + e = a + b exactly (Knuth)
 __device__ __forceinline__ df two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
@@ -78,6 +81,72 @@ __device__ __forceinline__ df df_from_double(double x) {
 __device__ __forceinline__ double df_to_double(df a) {
   return static_cast<double>(a.hi) + static_cast<double>(a.lo);
 }
+
+#endif  // __CUDACC__
+
+// FP64 -> double-float from the IEEE 754 bit fields with integer arithmetic (the FP64 pipe
+// runs at 1/64 of the FP32 rate here). x = m 2^(e - 52) with a 53-bit significand m;
+// hi = m rounded to its top 24 bits (to nearest, ties to even) = x rounded to FP32, and the
+// remainder rem = m - hm 2^29 (|rem| <= 2^28, exact) gives lo = RN_FP32(rem) 2^(e - 52),
+// i.e. x - hi rounded to FP32: the same pair as df_from_double. Exponents outside
+// [-60, 126] (zero, tiny, huge, subnormal, inf, NaN) fall back to df_from_double so that
+// hi and the scale 2^(e - 52) stay normal FP32 numbers.
+__host__ __device__ __forceinline__ unsigned long long df_bits64(double x) {
+#ifdef __CUDA_ARCH__
+  return static_cast<unsigned long long>(__double_as_longlong(x));
+#else
+  unsigned long long b;
+  memcpy(&b, &x, sizeof(b));
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ float df_float_of_bits(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, sizeof(f));
+  return f;
+#endif
+}
+__host__ __device__ __forceinline__ bool df_split_int(double x, df& out) {
+  const unsigned long long b = df_bits64(x);
+  const int e = static_cast<int>((b >> 52) & 0x7FF) - 1023;
+  if (e < -60 || e > 126) return false;
+  const unsigned sign = static_cast<unsigned>(b >> 32) & 0x80000000u;
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  unsigned hm = static_cast<unsigned>(m >> 29);
+  int rem = static_cast<int>(m & ((1ull << 29) - 1));
+  if (rem > (1 << 28) || (rem == (1 << 28) && (hm & 1u))) {
+    hm += 1u;
+    rem -= (1 << 29);
+  }
+  // hm in [2^23, 2^24]; 2^24 means the rounding carried into the next binade
+  const unsigned hbits = (hm == (1u << 24)) ? (static_cast<unsigned>(e + 128) << 23)
+                                            : ((static_cast<unsigned>(e + 127) << 23) | (hm - (1u << 23)));
+  const float scale = df_float_of_bits(static_cast<unsigned>(e - 52 + 127) << 23);
+  const int rs = sign ? -rem : rem;  // exact remainder with the sign of x (+0 when zero)
+#ifdef __CUDA_ARCH__
+  const float lo = __fmul_rn(__int2float_rn(rs), scale);
+#else
+  const float lo = static_cast<float>(rs) * scale;
+#endif
+  out.hi = df_float_of_bits(hbits | sign);
+  out.lo = lo;
+  return true;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ df df_from_double_fast(double x) {
+  df r;
+  if (!df_split_int(x, r)) r = df_from_double(x);
+  return r;
+}
+
+// element k of an array as a double-float: stored so, or FP64 split on the fly
+__device__ __forceinline__ df load_df(const df* a, long long k) { return a[k]; }
+__device__ __forceinline__ df load_df(const double* a, long long k) { return df_from_double_fast(a[k]); }
+#endif  // __CUDACC__
 
 inline df df_host(double x) {
   const float h = static_cast<float>(x);

@@ -82,10 +82,12 @@ struct OzakiWork {
 long long ozaki_panel_width(long long N);
 long long ozaki_chunks(long long N);
 int ozaki_num_tiles(int m);
-int ozaki_splits(int m, long long kp);
+constexpr int kMaxSms = 256;  // SM counts above this are treated as this many
+// K splits per panel for a GPU with sms SMs; never above ozaki_max_splits(m)
+int ozaki_splits(int m, long long kp, int sms);
+int ozaki_max_splits(int m);
 bool ozaki_supported();
-// Operands as FP64 (J, H) or, when Jdf and Hdf are both given, as double-floats (J and H
-// are then not read). before/after (may be null) are called around each GEMM kernel launch
+// Each operand as FP64 (J, H) or, when its double-float copy (Jdf, Hdf) is given, as that. before/after (may be null) are called around each GEMM kernel launch
 // with hook_arg.
 bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, const df* Hdf, int m, long long N,
                               const OzakiWork& w, int splits, cudaStream_t s, void (*before)(void*),
@@ -116,7 +118,6 @@ int apply_op_blocks(const Level& L);
 // the same with J stored as double-floats (Jd, m x N)
 void launch_apply_op_df(int disc, const Level& L, double ca, const double* p, double cj, const df* Jd,
                         const double* w, int m, double* out, double* partial, int* nblocks_out, cudaStream_t s);
-
 // ---- double-float V-cycle on FV grids (mg_df64.cu) ----------------------------
 void launch_cheb_first_df(const Level& L, int nrhs, const df* b, df* x, df* r, df* d, bool zero_x, df inv_theta,
                           cudaStream_t s);
@@ -136,10 +137,15 @@ void launch_df2d(int64_t n, const df* src, double* dst, df* dst2, cudaStream_t s
 // does not qualify or the kernel attribute for its shared memory could not be set
 // (nothing launched).
 bool fused_level_ok(const Level& L);  // all axes coarsened and nx ny < 2^27
+// b (the level's right-hand sides) as double-floats or as FP64 (split on the fly).
 bool launch_pre_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* b, df* x,
+                         df* bc, cudaStream_t s);
+bool launch_pre_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const double* b, df* x,
                          df* bc, cudaStream_t s);
 bool launch_post_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* x,
                           const df* xc, const df* b, df* y, double* y64, cudaStream_t s);
+bool launch_post_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* x,
+                          const df* xc, const double* b, df* y, double* y64, cudaStream_t s);
 
 // ---- dense / Krylov kernels (dense_kernels.cu) ------------------------------
 // partial[c * m + i] = sum_{k in chunk c} A[i * lda + k] v[k]
@@ -163,6 +169,11 @@ void launch_chol(double* A, int n, int* status, cudaStream_t s);
 // in-place triangular solves with the lower factor L (n x n): x <- L^-1 x, x <- L^-T x
 void launch_trsv_lower(const double* L, int n, double* x, int nrhs, cudaStream_t s);
 void launch_trsv_upper_t(const double* L, int n, double* x, int nrhs, cudaStream_t s);
+// x <- L^-T L^-1 x for one right-hand side in one cooperative launch of ceil(n / 32) CTAs.
+// flags: 2 ceil(n / 32) ints, zero before the first call; epoch > 0 and different from the
+// previous call's. False if the device cannot keep all CTAs resident (nothing launched).
+bool launch_chol_solve_coop(const double* L, int n, double* x, int* flags, int epoch, int* status,
+                            cudaStream_t s);
 void launch_coarse_apply(const double* X, int n, int nrhs, const double* b, double* x,
                          cudaStream_t s);
 void launch_symmetrize_identity_solve(double* X, int n, cudaStream_t s);

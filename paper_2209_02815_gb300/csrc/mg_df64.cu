@@ -185,7 +185,7 @@ __global__ void k_coarse_apply_df(const double* __restrict__ X, int n, const df*
 
 __global__ void k_d2df(int64_t n, const double* __restrict__ src, df* __restrict__ dst) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) dst[p] = df_from_double(src[p]);
+  if (p < n) dst[p] = df_from_double_fast(src[p]);
 }
 
 __global__ void k_df2d(int64_t n, const df* __restrict__ src, double* __restrict__ dst, df* __restrict__ dst2) {

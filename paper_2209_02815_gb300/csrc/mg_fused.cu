@@ -106,8 +106,8 @@ __device__ __forceinline__ df nsum(const df* __restrict__ u0, const df* __restri
 }
 
 // Down leg. Grid: (xy tiles, z segments of segK coarse planes, right-hand sides).
-template <bool ISO>
-__global__ void __launch_bounds__(kThr) k_pre_fused(Level L, Level Lc, FusedCoef F, const df* __restrict__ b,
+template <bool ISO, typename TB>
+__global__ void __launch_bounds__(kThr) k_pre_fused(Level L, Level Lc, FusedCoef F, const TB* __restrict__ b,
                                                     df* __restrict__ x, df* __restrict__ bc, int segK) {
   extern __shared__ df sm[];
   df* Gp = sm;               // g = D^-1 b over tile + 3, 3 planes
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kThr) k_pre_fused(Level L, Level Lc, FusedCoef
   const int K0 = (int)blockIdx.y * segK, K1 = min(K0 + segK, Lc.nz);
   const int Z0 = 2 * K0, Z1 = 2 * K1;
   const int64_t pl = (int64_t)L.nx * L.ny, plc = (int64_t)Lc.nx * Lc.ny;
-  const df* bb = b + (int64_t)blockIdx.z * L.N;
+  const TB* bb = b + (int64_t)blockIdx.z * L.N;
   df* xx = x + (int64_t)blockIdx.z * L.N;
   df* cc = bc + (int64_t)blockIdx.z * Lc.N;
   const int u_beg = Z0 - 3, u_end = Z1 + 2;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kThr) k_pre_fused(Level L, Level Lc, FusedCoef
   auto fetch = [&](int u) {
     const bool uin = (u >= 0 && u < L.nz);
 #pragma unroll
-    for (int q = 0; q < kP3; ++q) pf[q] = (uin && d3[q] >= 0) ? bb[u * pl + desc_off(d3[q])] : dzero();
+    for (int q = 0; q < kP3; ++q) pf[q] = (uin && d3[q] >= 0) ? load_df(bb, u * pl + desc_off(d3[q])) : dzero();
   };
   fetch(u_beg);
 
@@ -318,9 +318,9 @@ __global__ void __launch_bounds__(kThr) k_pre_fused(Level L, Level Lc, FusedCoef
 
 // Up leg. Grid: (xy tiles, z segments of segZ fine planes (even), right-hand sides).
 // y and y64 (either may be null) must not overlap x, xc or b.
-template <bool ISO>
+template <bool ISO, typename TB>
 __global__ void __launch_bounds__(kThr) k_post_fused(Level L, Level Lc, FusedCoef F, const df* __restrict__ x,
-                                                     const df* __restrict__ xc, const df* __restrict__ b,
+                                                     const df* __restrict__ xc, const TB* __restrict__ b,
                                                      df* __restrict__ y, double* __restrict__ y64, int segZ) {
   extern __shared__ df sm[];
   df* Xp = sm;               // x' over tile + 2, 4 planes
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kThr) k_post_fused(Level L, Level Lc, FusedCoe
   const int64_t pl = (int64_t)L.nx * L.ny, plc = (int64_t)Lc.nx * Lc.ny;
   const int64_t off = (int64_t)blockIdx.z * L.N;
   const df* xx = x + off;
-  const df* bb = b + off;
+  const TB* bb = b + off;
   const df* cx = xc + (int64_t)blockIdx.z * Lc.N;
   const int u_beg = Z0 - 2, u_end = Z1 + 1;
   const int Kb = (u_beg >> 1) - 1;  // first coarse plane the block reads
@@ -430,6 +430,22 @@ __global__ void __launch_bounds__(kThr) k_post_fused(Level L, Level Lc, FusedCoe
     __syncthreads();
   }
 
+  // x of the plane step 1 reads next and b of the plane step 2 reads next, loaded one
+  // iteration ahead into registers
+  df px[kP2], pb[kP1];
+  auto fetch_x = [&](int u) {
+    const bool in = (u >= 0 && u < L.nz);
+#pragma unroll
+    for (int q = 0; q < kP2; ++q) px[q] = (in && d2[q] >= 0) ? xx[u * pl + desc_off(d2[q])] : dzero();
+  };
+  auto fetch_b = [&](int v) {
+    const bool in = (v >= 0 && v < L.nz);
+#pragma unroll
+    for (int q = 0; q < kP1; ++q) pb[q] = (in && d1[q] >= 0) ? load_df(bb, v * pl + desc_off(d1[q])) : dzero();
+  };
+  fetch_x(u_beg);
+  fetch_b(u_beg + 1);  // the first plane step 2 works on
+
   for (int u = u_beg; u <= u_end; ++u) {
     const int t = u - u_beg;
     // step 1, plane u: x' = x + P xc over tile + 2
@@ -450,11 +466,12 @@ __global__ void __launch_bounds__(kThr) k_post_fused(Level L, Level Lc, FusedCoe
             dsum s;
             s.add(scale_w(P0[e], wz[0]));
             if (nz_ > 1) s.add(scale_w(P1[e], wz[1]));
-            v = df_add(xx[u * pl + desc_off(d2[q])], s.get());
+            v = df_add(px[q], s.get());
           }
           Xo[e] = v;
         }
       }
+      if (u < u_end) fetch_x(u + 1);
       // at u = 2K - 1 the planes K - 1 and K are in use; interpolate K + 1 for u = 2K + 1
       if ((u & 1) && u < u_end) {
         interp_x(((u + 1) >> 1) + 1);
@@ -482,7 +499,7 @@ __global__ void __launch_bounds__(kThr) k_post_fused(Level L, Level Lc, FusedCoe
             const int c = desc_cls(d1[q]) + cz;
             const df n = nsum<ISO>(X0, X1, X2, i2[q], kW2, T0, T1, T2);
             dsum s;
-            s.add(bb[v * pl + desc_off(d1[q])]);
+            s.add(pb[q]);
             s.add(n);
             s.add(df_neg(df_mul(td[c], X1[i2[q]])));
             rv = s.get();
@@ -492,6 +509,7 @@ __global__ void __launch_bounds__(kThr) k_post_fused(Level L, Level Lc, FusedCoe
           Do[e] = dv;
         }
       }
+      if (v < Z1) fetch_b(v + 1);
       __syncthreads();
     }
     // step 3, plane w = u - 2 (in [Z0, Z1)): y = x' + eta_c r0 + kap_c N_T(d0) on the tile
@@ -526,7 +544,8 @@ __global__ void __launch_bounds__(kThr) k_post_fused(Level L, Level Lc, FusedCoe
 }
 
 // z segments: enough blocks for about four waves at three blocks per SM, with at least
-// minp planes per segment
+// minp planes per segment (small levels are latency-bound: there, more and shorter
+// segments help even though each repeats its halo planes)
 int fused_segments(int tiles, int nrhs, int planes, int minp) {
   const int64_t base = (int64_t)tiles * nrhs;
   const int64_t want = 152 * 3 * 4;
@@ -548,7 +567,52 @@ bool allow_smem(K kernel, size_t bytes, std::atomic<unsigned long long>& done) {
   done.fetch_or(bit);
   return true;
 }
-std::atomic<unsigned long long> g_attr[4];
+
+}  // namespace
+
+
+namespace {
+
+template <typename TB>
+bool pre_fused(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const TB* b, df* x, df* bc,
+               cudaStream_t s, std::atomic<unsigned long long>* attr) {
+  if (!fused_level_ok(L)) return false;
+  const bool iso = L.iso != 0;
+  if (!(iso ? allow_smem(k_pre_fused<true, TB>, kPreSmem, attr[0])
+            : allow_smem(k_pre_fused<false, TB>, kPreSmem, attr[1])))
+    return false;
+  const int ntx = (Lc.nx + kTX - 1) / kTX, nty = (Lc.ny + kTY - 1) / kTY;
+  const int nseg = fused_segments(ntx * nty, nrhs, Lc.nz, Lc.nz >= 64 ? 4 : 1);
+  const int segK = (Lc.nz + nseg - 1) / nseg;
+  const int nsegs = (Lc.nz + segK - 1) / segK;
+  const dim3 grid((unsigned)(ntx * nty), (unsigned)nsegs, (unsigned)nrhs);
+  if (iso) k_pre_fused<true, TB><<<grid, kThr, kPreSmem, s>>>(L, Lc, F, b, x, bc, segK);
+  else k_pre_fused<false, TB><<<grid, kThr, kPreSmem, s>>>(L, Lc, F, b, x, bc, segK);
+  note_launches(1);
+  return true;
+}
+
+template <typename TB>
+bool post_fused(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* x, const df* xc,
+                const TB* b, df* y, double* y64, cudaStream_t s, std::atomic<unsigned long long>* attr) {
+  if (!fused_level_ok(L)) return false;
+  const bool iso = L.iso != 0;
+  if (!(iso ? allow_smem(k_post_fused<true, TB>, kPostSmem, attr[0])
+            : allow_smem(k_post_fused<false, TB>, kPostSmem, attr[1])))
+    return false;
+  const int ntx = (Lc.nx + kTX - 1) / kTX, nty = (Lc.ny + kTY - 1) / kTY;
+  const int nseg = fused_segments(ntx * nty, nrhs, L.nz, L.nz >= 128 ? 8 : 2);
+  int segZ = (L.nz + nseg - 1) / nseg;
+  segZ += segZ & 1;
+  const int nsegs = (L.nz + segZ - 1) / segZ;
+  const dim3 grid((unsigned)(ntx * nty), (unsigned)nsegs, (unsigned)nrhs);
+  if (iso) k_post_fused<true, TB><<<grid, kThr, kPostSmem, s>>>(L, Lc, F, x, xc, b, y, y64, segZ);
+  else k_post_fused<false, TB><<<grid, kThr, kPostSmem, s>>>(L, Lc, F, x, xc, b, y, y64, segZ);
+  note_launches(1);
+  return true;
+}
+
+std::atomic<unsigned long long> g_attr_pre[2][2], g_attr_post[2][2];  // [input FP64][iso]
 
 }  // namespace
 
@@ -558,38 +622,19 @@ bool fused_level_ok(const Level& L) {
 
 bool launch_pre_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* b, df* x,
                          df* bc, cudaStream_t s) {
-  if (!fused_level_ok(L)) return false;
-  const bool iso = L.iso != 0;
-  if (!(iso ? allow_smem(k_pre_fused<true>, kPreSmem, g_attr[0]) : allow_smem(k_pre_fused<false>, kPreSmem, g_attr[1])))
-    return false;
-  const int ntx = (Lc.nx + kTX - 1) / kTX, nty = (Lc.ny + kTY - 1) / kTY;
-  const int nseg = fused_segments(ntx * nty, nrhs, Lc.nz, 4);
-  const int segK = (Lc.nz + nseg - 1) / nseg;
-  const int nsegs = (Lc.nz + segK - 1) / segK;
-  const dim3 grid((unsigned)(ntx * nty), (unsigned)nsegs, (unsigned)nrhs);
-  if (iso) k_pre_fused<true><<<grid, kThr, kPreSmem, s>>>(L, Lc, F, b, x, bc, segK);
-  else k_pre_fused<false><<<grid, kThr, kPreSmem, s>>>(L, Lc, F, b, x, bc, segK);
-  note_launches(1);
-  return true;
+  return pre_fused(L, Lc, F, nrhs, b, x, bc, s, g_attr_pre[0]);
 }
-
+bool launch_pre_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const double* b, df* x,
+                         df* bc, cudaStream_t s) {
+  return pre_fused(L, Lc, F, nrhs, b, x, bc, s, g_attr_pre[1]);
+}
 bool launch_post_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* x,
                           const df* xc, const df* b, df* y, double* y64, cudaStream_t s) {
-  if (!fused_level_ok(L)) return false;
-  const bool iso = L.iso != 0;
-  if (!(iso ? allow_smem(k_post_fused<true>, kPostSmem, g_attr[2])
-            : allow_smem(k_post_fused<false>, kPostSmem, g_attr[3])))
-    return false;
-  const int ntx = (Lc.nx + kTX - 1) / kTX, nty = (Lc.ny + kTY - 1) / kTY;
-  const int nseg = fused_segments(ntx * nty, nrhs, L.nz, 8);
-  int segZ = (L.nz + nseg - 1) / nseg;
-  segZ += segZ & 1;
-  const int nsegs = (L.nz + segZ - 1) / segZ;
-  const dim3 grid((unsigned)(ntx * nty), (unsigned)nsegs, (unsigned)nrhs);
-  if (iso) k_post_fused<true><<<grid, kThr, kPostSmem, s>>>(L, Lc, F, x, xc, b, y, y64, segZ);
-  else k_post_fused<false><<<grid, kThr, kPostSmem, s>>>(L, Lc, F, x, xc, b, y, y64, segZ);
-  note_launches(1);
-  return true;
+  return post_fused(L, Lc, F, nrhs, x, xc, b, y, y64, s, g_attr_post[0]);
+}
+bool launch_post_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* x,
+                          const df* xc, const double* b, df* y, double* y64, cudaStream_t s) {
+  return post_fused(L, Lc, F, nrhs, x, xc, b, y, y64, s, g_attr_post[1]);
 }
 
 }  // namespace h1w

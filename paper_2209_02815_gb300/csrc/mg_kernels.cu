@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_op(Level L, double ca, const
 
 // out = ca * (A p) + cj * sum_i Jd[i][k] w[i], with J as double-floats (the
 // stencil part in FP64); partial[block] = sum_k p_k out_k when partial != null.
+
 template <class D>
 __global__ void __launch_bounds__(kThreads) k_apply_op_df(Level L, double ca, const double* __restrict__ p,
                                                           double cj, const df* __restrict__ Jd,

@@ -39,6 +39,7 @@
 // status bit kStatusTimeout, drains what it started and returns.
 #include <cuda_bf16.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "df64.cuh"
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
       // per-chunk scale factors 2^(e_row + f_col - 52) for this thread's 32 columns
       const long long gch = g.chunk0 + kbeg / kChunkK + c;
       const int er = (row < g.m) ? g.eA[gch * g.m + row] : -100000;
-      // lane 0 waits; the warp follows its verdict so that the .sync.aligned
+      // lane 0 waits; the warp follows its result so that the .sync.aligned
       // TMEM loads below stay warp-uniform
       int ok = 1;
       if (lane == 0) ok = mbar_wait(smem_u32(&bars[4]), c & 1, abort_flag) ? 1 : 0;
@@ -377,20 +378,39 @@ __device__ __forceinline__ long long digits_source_f32(float v, int echunk) {
   return (b >> 31) ? -Y : Y;
 }
 
-// Largest exponent field over the 128-thread block (0 when every value is zero).
-__device__ __forceinline__ int block_max_exp(int v) {
-  __shared__ int sh[4];
+// Balanced base-64 digits Y = sum_p d_p 64^(7 - p), d_1..d_7 in [-32, 31], |Y| <= 2^47.
+// The low four digits are fixed by Y modulo 2^24: their value is the representative of
+// Y mod 2^24 in [-32 S, 31 S], S = 1 + 64 + 64^2 + 64^3 (a window of exactly 2^24 values),
+// so Y splits once into that low part and an exact high part, and each is taken apart
+// in 32-bit arithmetic; the digits are those of the digit-by-digit recurrence.
+__device__ __forceinline__ void balanced_digits(long long Y, int (&d)[kSlices]) {
+  constexpr int kS32 = 32 * (1 + 64 + 4096 + 262144);
+  const int lo = static_cast<int>((Y + kS32) & 0xFFFFFF) - kS32;
+  int hi = static_cast<int>((Y - lo) >> 24);
+  int y = lo;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const int t = __shfl_xor_sync(0xffffffffu, v, o);
-    v = t > v ? t : v;
+  for (int p = 7; p >= 4; --p) {
+    const int r = ((y + 32) & 63) - 32;
+    d[p] = r;
+    y = (y - r) >> 6;
   }
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  int b = sh[0];
 #pragma unroll
-  for (int w = 1; w < 4; ++w) b = sh[w] > b ? sh[w] : b;
-  return b;
+  for (int p = 3; p >= 1; --p) {
+    const int r = ((hi + 32) & 63) - 32;
+    d[p] = r;
+    hi = (hi - r) >> 6;
+  }
+  d[0] = hi;
+}
+
+// Two small integers (|d| < 2^22) as a packed pair of BF16 values, exactly: adding d to
+// the bit pattern of 1.5 * 2^23 and subtracting 1.5 * 2^23 gives float(d); a value of at
+// most 6 significant bits leaves the low 16 bits of the float zero, so its upper half is
+// the BF16 encoding.
+__device__ __forceinline__ uint32_t pack_bf16x2(int d0, int d1) {
+  const float f0 = __fsub_rn(__int_as_float(0x4B400000 + d0), 12582912.0f);
+  const float f1 = __fsub_rn(__int_as_float(0x4B400000 + d1), 12582912.0f);
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
 }
 
 // Eight balanced base-64 digits of each of 8 consecutive K entries, written as one 16-byte
@@ -401,22 +421,12 @@ __device__ __forceinline__ void store_digits(long long (&Y)[8], int row, long lo
                                              uint16_t* __restrict__ S) {
   uint32_t packed[kSlices][4];
 #pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    long long y = Y[t];
-    int d[kSlices];
+  for (int t = 0; t < 8; t += 2) {
+    int da[kSlices], db[kSlices];
+    balanced_digits(Y[t], da);
+    balanced_digits(Y[t + 1], db);
 #pragma unroll
-    for (int p = kSlices - 1; p >= 1; --p) {
-      const long long r = ((y + 32) & 63) - 32;
-      d[p] = static_cast<int>(r);
-      y = (y - r) >> 6;
-    }
-    d[0] = static_cast<int>(y);
-#pragma unroll
-    for (int p = 0; p < kSlices; ++p) {
-      const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(static_cast<float>(d[p])));
-      if (t & 1) packed[p][t >> 1] |= h << 16;
-      else packed[p][t >> 1] = h;
-    }
+    for (int p = 0; p < kSlices; ++p) packed[p][t >> 1] = pack_bf16x2(da[p], db[p]);
   }
   const int rb = row / R, ri = row % R;
   const long long kb = kc / kKt;
@@ -430,59 +440,71 @@ __device__ __forceinline__ void store_digits(long long (&Y)[8], int row, long lo
         make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
 }
 
-// Split of one K panel [k0, k0 + kw) of X (m rows of N, FP64) into digits. A block of 128
-// threads is one chunk of 1024 K entries of one row (8 per thread): it finds the chunk
-// exponent e with max |x| < 2^e (-100000 for an all-zero chunk), stores it at
-// e[(chunk0 + blockIdx.x) m + row] and writes the digits of x 2^(47 - e).
-// Grid: (klen / 1024, rows rounded up to R).
-__global__ void __launch_bounds__(128) k_split_digits(const double* __restrict__ X, int m, long long N, long long k0,
-                                                      long long kw, long long klen, int R, long long chunk0,
-                                                      int* __restrict__ e, uint16_t* __restrict__ S) {
-  const long long kc = (static_cast<long long>(blockIdx.x) * 128 + threadIdx.x) * 8;
-  const int row = blockIdx.y;
-  double x[8];
-  int best = 0;
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    const long long k = kc + t;
-    x[t] = (k < kw && row < m) ? X[row * N + k0 + k] : 0.0;
-    const int ex = static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x[t])) >> 52) & 0x7FF);
-    best = ex > best ? ex : best;
-  }
-  best = block_max_exp(best);
-  const int ech = best ? best - 1022 : -100000;
-  if (threadIdx.x == 0 && row < m && static_cast<long long>(blockIdx.x) * kChunkK < kw)
-    e[(chunk0 + blockIdx.x) * m + row] = ech;
-  long long Y[8];
-#pragma unroll
-  for (int t = 0; t < 8; ++t) Y[t] = digits_source(x[t], ech);
-  store_digits(Y, row, kc, klen, R, S);
-}
+// Split of one K panel [k0, k0 + kw) of X (m rows of N) into digits. A block of
+// 128 kSplitRows threads covers kSplitRows consecutive rows and one chunk of 1024 K
+// entries. A warp takes 8 / kSplitRows K stages of 32 entries; in a stage, lane =
+// 4 (row in the group) + 16-byte chunk, so each warp reads row segments of 256 bytes and
+// writes kSplitRows consecutive rows (64 kSplitRows bytes) of a stage image per digit
+// slice. Per row it finds the chunk exponent e with max |x| < 2^e (-100000 for an
+// all-zero chunk), stores it at e[(chunk0 + blockIdx.x) m + row] and writes the digits of
+// x 2^(47 - e). Grid: (klen / 1024, rows rounded up to R / kSplitRows). XS is double
+// (FP64) or df (double-float, value hi + lo: the exponent comes from the high parts, since
+// |hi + lo| <= |hi| (1 + 2^-24) stays within the digit range, and each part is scaled on
+// its own, so the value is represented to within 2^(e - 47)).
+constexpr int kSplitRows = 1;
+constexpr int kSplitThreads = 128 * kSplitRows;
 
-// The same from double-floats (value hi + lo): the exponent comes from the high parts
-// (|hi + lo| <= |hi| (1 + 2^-24) stays within the digit range) and each part is scaled
-// on its own, so the value is represented to within 2^(e - 47).
-__global__ void __launch_bounds__(128) k_split_digits_df(const df* __restrict__ X, int m, long long N, long long k0,
-                                                         long long kw, long long klen, int R, long long chunk0,
-                                                         int* __restrict__ e, uint16_t* __restrict__ S) {
-  const long long kc = (static_cast<long long>(blockIdx.x) * 128 + threadIdx.x) * 8;
-  const int row = blockIdx.y;
-  df x[8];
+template <typename XS>
+__global__ void __launch_bounds__(kSplitThreads) k_split_digits(const XS* __restrict__ X, int m, long long N,
+                                                                long long k0, long long kw, long long klen, int R,
+                                                                long long chunk0, int* __restrict__ e,
+                                                                uint16_t* __restrict__ S) {
+  constexpr int kGroup = 4 * kSplitRows;   // lanes per stage
+  constexpr int kStagesPerWarp = 32 / kGroup;
+  constexpr int kWarps = kSplitThreads / 32;
+  __shared__ int smax[kWarps][kSplitRows];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / kGroup, rg = (lane >> 2) % kSplitRows, ch = lane & 3;
+  const int row = blockIdx.y * kSplitRows + rg;
+  const long long kc =
+      static_cast<long long>(blockIdx.x) * kChunkK + (warp * kStagesPerWarp + sub) * kKt + ch * 8;
+  constexpr bool kDf = std::is_same<XS, df>::value;
+  XS x[8];
   int best = 0;
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     const long long k = kc + t;
-    x[t] = (k < kw && row < m) ? X[row * N + k0 + k] : df_make(0.f, 0.f);
-    const int ex = static_cast<int>((__float_as_uint(x[t].hi) >> 23) & 0xFF);
+    int ex;
+    if constexpr (kDf) {
+      x[t] = (k < kw && row < m) ? X[row * N + k0 + k] : df_make(0.f, 0.f);
+      ex = static_cast<int>((__float_as_uint(x[t].hi) >> 23) & 0xFF);
+    } else {
+      x[t] = (k < kw && row < m) ? X[row * N + k0 + k] : 0.0;
+      ex = static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x[t])) >> 52) & 0x7FF);
+    }
     best = ex > best ? ex : best;
   }
-  best = block_max_exp(best);
-  const int ech = best ? best - 126 : -100000;
-  if (threadIdx.x == 0 && row < m && static_cast<long long>(blockIdx.x) * kChunkK < kw)
+  // max over the row's lanes of this warp (its chunks and stages), then over the warps
+  best = max(best, __shfl_xor_sync(0xffffffffu, best, 1));
+  best = max(best, __shfl_xor_sync(0xffffffffu, best, 2));
+#pragma unroll
+  for (int o = kGroup; o < 32; o <<= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (ch == 0 && sub == 0) smax[warp][rg] = best;
+  __syncthreads();
+  best = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) best = max(best, smax[w][rg]);
+  int ech;
+  if constexpr (kDf) ech = best ? best - 126 : -100000;
+  else ech = best ? best - 1022 : -100000;
+  if (warp == 0 && sub == 0 && ch == 0 && row < m && static_cast<long long>(blockIdx.x) * kChunkK < kw)
     e[(chunk0 + blockIdx.x) * m + row] = ech;
   long long Y[8];
 #pragma unroll
-  for (int t = 0; t < 8; ++t) Y[t] = digits_source_f32(x[t].hi, ech) + digits_source_f32(x[t].lo, ech);
+  for (int t = 0; t < 8; ++t) {
+    if constexpr (kDf) Y[t] = digits_source_f32(x[t].hi, ech) + digits_source_f32(x[t].lo, ech);
+    else Y[t] = digits_source(x[t], ech);
+  }
   store_digits(Y, row, kc, klen, R, S);
 }
 
@@ -517,12 +539,33 @@ void ozaki_tiles(int m, std::vector<int>& out) {
     }
 }
 
-int ozaki_splits(int m, long long kp) {
+// K splits per panel: the tiles x splits CTAs (one per SM) should fill whole waves of
+// the GPU's sms SMs with equal work. Cost = chunks of the busiest CTA x waves, with a
+// small charge per split for the partial outputs and their reduction.
+int ozaki_splits(int m, long long kp, int sms) {
   const int tiles = ozaki_num_tiles(m);
-  int s = (152 + tiles - 1) / tiles;
-  const long long maxs = kp / kChunkK;
-  if (s > maxs) s = static_cast<int>(maxs);
-  return s < 1 ? 1 : s;
+  const long long nch = kp / kChunkK;
+  if (sms < 1) sms = 1;
+  if (sms > kMaxSms) sms = kMaxSms;
+  int best = 1;
+  double best_cost = 1e300;
+  const long long lim = 2LL * ((sms + tiles - 1) / tiles);  // ozaki_max_splits
+  const long long smax = nch < lim ? nch : lim;
+  for (long long sp = 1; sp <= smax; ++sp) {
+    const long long per = (nch + sp - 1) / sp;
+    const long long waves = (tiles * sp + sms - 1) / sms;
+    const double cost = static_cast<double>(per * waves) * (1.0 + 0.01 * static_cast<double>(sp));
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = static_cast<int>(sp);
+    }
+  }
+  return best;
+}
+
+int ozaki_max_splits(int m) {
+  const int tiles = ozaki_num_tiles(m);
+  return 2 * ((kMaxSms + tiles - 1) / tiles);
 }
 
 bool ozaki_supported() {
@@ -532,8 +575,8 @@ bool ozaki_supported() {
   return major == 10;
 }
 
-// C partials (FP64, [splits][m][m], upper tiles) of J H^T via the digit split. The operands
-// come as FP64 (J, H) or, when Jdf and Hdf are given, as double-floats.
+// C partials (FP64, [splits][m][m], upper tiles) of J H^T via the digit split. Each operand
+// comes as FP64 (J, H) or, when its double-float copy (Jdf, Hdf) is given, as that.
 // Returns false when the kernel attribute cannot be set.
 bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, const df* Hdf, int m, long long N,
                               const OzakiWork& w, int splits, cudaStream_t s, void (*before)(void*),
@@ -544,7 +587,7 @@ bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, c
   int* eB = w.expo + nch * m;
   if (cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
     return false;
-  const bool use_df = Jdf && Hdf;
+
   const int tiles = ozaki_num_tiles(m);
   long long kcta = (kp + splits - 1) / splits;
   kcta = (kcta + kChunkK - 1) / kChunkK * kChunkK;
@@ -556,13 +599,11 @@ bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, c
     const unsigned gx = static_cast<unsigned>(kp / kChunkK);
     uint16_t* dA = static_cast<uint16_t*>(w.digitsA);
     uint16_t* dB = static_cast<uint16_t*>(w.digitsB);
-    if (use_df) {
-      k_split_digits_df<<<dim3(gx, rowsA), 128, 0, s>>>(Jdf, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
-      k_split_digits_df<<<dim3(gx, rowsB), 128, 0, s>>>(Hdf, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
-    } else {
-      k_split_digits<<<dim3(gx, rowsA), 128, 0, s>>>(J, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
-      k_split_digits<<<dim3(gx, rowsB), 128, 0, s>>>(H, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
-    }
+    const dim3 ga(gx, rowsA / kSplitRows), gb(gx, rowsB / kSplitRows);
+    if (Jdf) k_split_digits<df><<<ga, kSplitThreads, 0, s>>>(Jdf, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
+    else k_split_digits<double><<<ga, kSplitThreads, 0, s>>>(J, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
+    if (Hdf) k_split_digits<df><<<gb, kSplitThreads, 0, s>>>(Hdf, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
+    else k_split_digits<double><<<gb, kSplitThreads, 0, s>>>(H, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
     OzakiArgs a;
     a.dA = dA;
     a.dB = dB;

@@ -79,6 +79,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "h1w_workspace_size": (SZ, [G, I32, O]),
         "h1w_setup": (I32, [G, I32, O, P, SZ, P, ctypes.POINTER(P)]),
         "h1w_capacitance": (I32, [P, I32, P]),
+        "h1w_capacitance_from_host": (I32, [P, I32, P, P]),
         "h1w_apply_prec": (I32, [P, P, P]),
         "h1w_apply_op": (I32, [P, P, P]),
         "h1w_vcycle": (I32, [P, I32, P, P]),
@@ -88,6 +89,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "h1w_level_info": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "h1w_get_timings": (I32, [P, ctypes.POINTER(Timings)]),
         "h1w_apply_op_static": (I32, [G, I32, P, P, P, P]),
+        "h1w_solve_batch": (I32, [ctypes.POINTER(P), I32, ctypes.POINTER(I32), ctypes.POINTER(P),
+                                  ctypes.POINTER(P), ctypes.POINTER(P), D, I32, I32, IN, ctypes.POINTER(I32)]),
         "h1w_last_error": (ctypes.c_char_p, [P]),
         "h1w_destroy": (None, [P]),
     }
@@ -162,6 +165,39 @@ def h1w_setup(grid: Grid, m_max: int, opt: Options | None, workspace: torch.Tens
 
 def h1w_capacitance(ctx, m: int, J: torch.Tensor | None, N: int) -> None:
     _check(load().h1w_capacitance(ctx, int(m), _ptr(J, m * N, "J") if m > 0 else None), ctx)
+
+
+def h1w_capacitance_from_host(ctx, m: int, J_host: torch.Tensor, J_dev: torch.Tensor, N: int) -> None:
+    if m > 0:
+        if J_host.is_cuda or not J_host.is_pinned():
+            raise ValueError("J_host must be a pinned CPU tensor")
+        if J_host.dtype != torch.float64 or not J_host.is_contiguous() or J_host.numel() < m * N:
+            raise ValueError("J_host must be a contiguous float64 tensor with m x N entries")
+    _check(load().h1w_capacitance_from_host(ctx, int(m), J_host.data_ptr() if m > 0 else None,
+                                            _ptr(J_dev, m * N, "J_dev") if m > 0 else None), ctx)
+
+
+def solve_batch(solvers, Js, bs, xs, rtol: float, maxit: int = 500, threads: int = 8):
+    """Capacitance + PCG for several Solver objects at once (h1w_solve_batch). Each
+    solver must have been created on its own stream. Returns (list of Info, list of
+    status codes); raises H1wError when a system failed."""
+    n = len(solvers)
+    P = ctypes.c_void_p
+    ctxs = (P * n)(*[s.ctx for s in solvers])
+    ms = (ctypes.c_int32 * n)(*[int(J.shape[0]) if J is not None else 0 for J in Js])
+    Jp = (P * n)(*[(_ptr(J, int(J.shape[0]) * s.N, "J") if J is not None and J.shape[0] else None)
+                   for s, J in zip(solvers, Js)])
+    bp = (P * n)(*[_ptr(b, s.N, "b") for s, b in zip(solvers, bs)])
+    xp = (P * n)(*[_ptr(x, s.N, "x") for s, x in zip(solvers, xs)])
+    infos = (Info * n)()
+    sts = (ctypes.c_int32 * n)()
+    for s, J in zip(solvers, Js):
+        s.J = J
+        s.m = int(J.shape[0]) if J is not None else 0
+    st = load().h1w_solve_batch(ctxs, n, ms, Jp, bp, xp, float(rtol), int(maxit), int(threads), infos, sts)
+    if st != H1W_OK:
+        raise H1wError(st, h1w_last_error(None))
+    return list(infos), list(sts)
 
 
 def h1w_apply_prec(ctx, r: torch.Tensor, z: torch.Tensor, N: int) -> None:
@@ -243,6 +279,13 @@ class Solver:
         m = 0 if J is None else int(J.shape[0])
         self.J = J  # keep the borrowed matrix alive
         h1w_capacitance(self.ctx, m, J, self.N)
+        self.m = m
+
+    def capacitance_from_host(self, J_host: torch.Tensor, J_dev: torch.Tensor) -> None:
+        """Copies J_host (pinned) into J_dev while line H runs; J_dev becomes the borrowed J."""
+        m = int(J_host.shape[0])
+        self.J = J_dev
+        h1w_capacitance_from_host(self.ctx, m, J_host, J_dev, self.N)
         self.m = m
 
     def apply_prec(self, r, z=None):

@@ -302,6 +302,19 @@ def batch_instances(count: int = 64, sides=(128, 256, 512, 1024), ms=(8, 32, 64,
     return out
 
 
+def batch_instance_data(desc: dict, device="cpu"):
+    """J (m x N, i.i.d. N(0,1)/sqrt(N)) and b (N, i.i.d. N(0,1)) of one batch
+    instance, N = n^2 vertices, from the instance's own seeds."""
+    n, m = desc["n"], desc["m"]
+    N = n * n
+    g = torch.Generator(device=device)
+    g.manual_seed(desc["seed_j"])
+    J = torch.randn((m, N), generator=g, dtype=torch.float64, device=device) / math.sqrt(N)
+    g.manual_seed(desc["seed_b"])
+    b = torch.randn(N, generator=g, dtype=torch.float64, device=device)
+    return J, b
+
+
 def paper_pole_dipole(n_e: int) -> np.ndarray:
     """The paper's 1D pole-dipole sequence (Fig. 4.1): for spacings s = 2, 4, 8
     and each direction along the line, electrode triples (A, M, N) at positions

@@ -32,7 +32,7 @@ def test_host_side_validation_without_gpu():
     g = h1w.make_grid(h1w.H1W_FV_CELL, (128, 128, 128), (1 / 128,) * 3, 1e-3)
     size = h1w.h1w_workspace_size(g, 496)
     N = 128 ** 3
-    assert size > 2 * 496 * N * 8  # H and J as double-floats plus the multigrid vectors
+    assert size > 496 * N * 8  # H as double-floats plus the multigrid vectors
     bad = h1w.make_grid(h1w.H1W_FV_CELL, (33, 33, 33), (1 / 33,) * 3, 1e-3)
     assert h1w.h1w_workspace_size(bad, 4) == 0  # cannot coarsen to <= 1024 unknowns
     neg = h1w.make_grid(h1w.H1W_Q1_VERTEX, (64, 64), (1 / 63,) * 2, -1.0)

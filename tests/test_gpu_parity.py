@@ -329,3 +329,108 @@ def test_tensor_capacitance_on_peaked_ert_rows():
     E = Cs[0] - Cs[1]
     assert np.linalg.norm(Cs[1], 2) > 1e8          # the ill-conditioned regime
     assert np.linalg.norm(E, 2) <= 2e-2
+
+
+@pytest.mark.parametrize("rhs_block", [32, 5])
+def test_capacitance_from_host_equals_device_path(rhs_block):
+    """J streamed from pinned host memory in row batches under line H gives the
+    same C and Cholesky factor, bit for bit, as the device entry point, and
+    leaves an exact copy of J in the destination buffer."""
+    d, n, h = _fv((24, 24, 24))
+    N = int(np.prod(n))
+    m = 70
+    rng = np.random.default_rng(41)
+    Jh = torch.as_tensor(rng.standard_normal((m, N)) / np.sqrt(N)).pin_memory()
+    Jd = Jh.to(DEV)
+    a = _gpu(d, n, h, 1e-2, m, rhs_block=rhs_block)
+    a.capacitance(Jd)
+    Ca, La = a.factors()
+    b = _gpu(d, n, h, 1e-2, m, rhs_block=rhs_block)
+    Jdst = torch.empty_like(Jd)
+    b.capacitance_from_host(Jh, Jdst)
+    Cb, Lb = b.factors()
+    assert torch.equal(Jdst, Jd)
+    assert torch.equal(Ca, Cb) and torch.equal(La, Lb)
+
+
+def test_solve_batch_matches_individual_solves():
+    """Systems of different grids, discretizations and measurement counts
+    (including m = 0), solved together by h1w_solve_batch on their own streams,
+    give bit for bit the solutions of solving each alone."""
+    cases = [(_q1((64, 64)), 16), (_fv((24, 24, 24)), 30), (_q1((37, 41)), 5), (_fv((16, 8, 12)), 0),
+             (_fv((20, 12, 28)), 9)]
+    rng = np.random.default_rng(51)
+    solvers, Js, bs, xs, refs = [], [], [], [], []
+    for (d, n, h), m in cases:
+        N = int(np.prod(n))
+        J = _t(rng.standard_normal((m, N)) / np.sqrt(N)) if m else None
+        b = _t(rng.standard_normal(N))
+        code = h1w.H1W_Q1_VERTEX if d == "q1" else h1w.H1W_FV_CELL
+        solvers.append(h1w.Solver(code, n, h, 1e-2, max(m, 1), device=DEV, stream=torch.cuda.Stream()))
+        Js.append(J)
+        bs.append(b)
+        xs.append(torch.empty_like(b))
+        R = _gpu(d, n, h, 1e-2, max(m, 1))
+        R.capacitance(J)
+        xr, _ = R.pcg(b, 1e-10)
+        refs.append(xr)
+    torch.cuda.synchronize()
+    infos, sts = h1w.solve_batch(solvers, Js, bs, xs, 1e-10, threads=3)
+    assert all(s == h1w.H1W_OK for s in sts)
+    for x, xr, inf in zip(xs, refs, infos):
+        assert torch.equal(x, xr)
+        assert inf.rel_res_true <= 1e-10
+
+
+@pytest.mark.parametrize("cap_gemm,mg_arith", [(0, 0), (1, 1)], ids=["mixed", "fp64_form"])
+def test_dipole_grid_solution_error_vs_oracle(cap_gemm, mg_arith):
+    """The precision configuration at small size: a 32^3 ERT step with a 4 x 4
+    electrode grid and the dipole-dipole protocol (60 measurements). The default
+    path (double-float cycle and passes, BF16-digit GEMM, FP64 outer residual) and
+    the plain FP64 form are solved to a true residual of 1e-12 and compared with
+    the oracle's FP64 PCG solution (residual 1e-12, near the FP64 floor of this
+    system): relative error at most 1e-7 after refinement, the bound for
+    mixed-precision paths."""
+    pr = inputs.ert_problem(32, grid=(4, 4), m_rows=60, alpha=1e-3)
+    n = (32, 32, 32)
+    h = (pr.h,) * 3
+    A = disc.regularization_operator("fv", n, h)
+    dm = pr.logsigma - pr.m_ref
+    b_ref = wb.gn_rhs(A, pr.alpha, dm, pr.J, pr.d)
+    H = mg.build_hierarchy("fv", n, h)
+    P = wb.WoodburyPreconditioner(lambda v: mg.vcycle(H, v), pr.J, pr.alpha)
+    x_ref, _, rel_ref = wb.pcg(lambda v: wb.apply_operator(A, pr.alpha, pr.J, v), P, b_ref, 1e-12, 400)
+    assert rel_ref <= 1e-12
+    S = _gpu("fv", n, h, pr.alpha, pr.J.shape[0], cap_gemm=cap_gemm, mg_arith=mg_arith)
+    S.capacitance(_t(pr.J))
+    x, info = S.pcg(_t(b_ref), 1e-12, 400)
+    assert info.rel_res_true <= 1e-12
+    err = _rel(x.cpu().numpy(), x_ref)
+    print(f"dipole grid 32^3 m=60 ({'mixed' if cap_gemm == 0 else 'fp64'}): iters {info.iters}, "
+          f"restarts {info.restarts}, rel error vs oracle {err:.2e}")
+    assert err <= 1e-7
+
+
+def test_ert_64cube_m496_converges_like_fp64_form():
+    """A 64^3 ERT step with the full 496-measurement protocol, where C spans ~1e9:
+    the default path (double-float cycle and passes, tensor-core C) reaches a true
+    residual of 1e-8 within one PCG iteration of the plain FP64 form. Catches
+    precision losses that only show when C is ill-conditioned."""
+    pr = inputs.ert_problem(64, n_e_line=32, alpha=1e-3, device=DEV)
+    n = (64, 64, 64)
+    h = (1.0 / 64,) * 3
+    m = pr.J.shape[0]
+    dm = torch.as_tensor(pr.logsigma - pr.m_ref, device=DEV)
+    d = torch.as_tensor(pr.d, device=DEV)
+    its = []
+    for opt in ({}, {"cap_gemm": 1, "mg_arith": 1}):
+        S = _gpu("fv", n, h, pr.alpha, m, **opt)
+        S.capacitance(pr.J)
+        C, _ = S.factors()
+        b = S.gn_rhs(dm, d)
+        x, info = S.pcg(b, 1e-8, 60)
+        assert info.rel_res_true <= 1e-8
+        its.append(info.iters)
+        del S
+    assert float(torch.linalg.matrix_norm(C, 2)) > 1e8
+    assert abs(its[0] - its[1]) <= 1, its
