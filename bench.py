@@ -74,6 +74,9 @@ def parse():
                          "(sides 128..1024, m 8..256, alpha log-uniform 1e-4..1e-1) solved by h1w_solve_batch")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--arith", default="mixed", choices=["mixed", "fp64"],
+                    help="timed path: mixed (double-float cycle and passes, tensor-core C; default) or the "
+                         "plain FP64 form (FP64 cycle and passes, CUDA-core C)")
     ap.add_argument("--fp64-form-steps", type=int, default=1,
                     help="steps of the plain FP64 GPU form (FP64 V-cycle, CUDA-core GEMM) timed for comparison")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
@@ -294,7 +297,13 @@ def run_ours(args):
                                 grid=electrode_grid(args))
         J = pr.J
         m, N = J.shape
-        S = h1w.Solver(h1w.H1W_FV_CELL, (n, n, n), (1.0 / n,) * 3, ALPHA, m, device=dev, stream=stream)
+        o_main = None
+        if args.arith == "fp64":
+            o_main = h1w.h1w_default_options()
+            o_main.cap_gemm = 1
+            o_main.mg_arith = 1
+        S = h1w.Solver(h1w.H1W_FV_CELL, (n, n, n), (1.0 / n,) * 3, ALPHA, m, device=dev, stream=stream,
+                       opt=o_main)
         dm = torch.as_tensor(pr.logsigma - pr.m_ref, device=dev)
         d = torch.as_tensor(pr.d, device=dev)
         S.capacitance(J)
@@ -344,7 +353,14 @@ def run_ours(args):
             x_host = torch.empty_like(b_host).pin_memory()
             J_dev = torch.empty_like(J)
             b_dev = torch.empty_like(b)
+            # the plain host-to-device copy rate of J, for reference
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            J_dev.copy_(J_host, non_blocking=True)
+            c1.record(stream)
             torch.cuda.synchronize()
+            h2d_gbs = J.numel() * 8 / (c0.elapsed_time(c1) / 1e3) / 1e9
             barrier(world)
             f0 = torch.cuda.Event(enable_timing=True)
             f1 = torch.cuda.Event(enable_timing=True)
@@ -359,13 +375,14 @@ def run_ours(args):
             ems = allmax(world, f0.elapsed_time(f1))
             e2e = {"value": world * args.e2e_steps / (ems / 1e3), "unit": "solves/s",
                    "h2d_bytes_per_step": int(J.numel() * 8 + b.numel() * 8),
-                   "d2h_bytes_per_step": int(x.numel() * 8), "steps": args.e2e_steps}
+                   "d2h_bytes_per_step": int(x.numel() * 8), "steps": args.e2e_steps,
+                   "h2d_copy_gb_per_s": h2d_gbs}
             del J_host, J_dev
 
         # the plain FP64 GPU form of the same step (FP64 V-cycle and Krylov passes, FP64
         # CUDA-core capacitance GEMM), same inputs, for comparison with the headline
         fp64_form = None
-        if args.fp64_form_steps > 0:
+        if args.fp64_form_steps > 0 and args.arith == "mixed":
             o64 = h1w.h1w_default_options()
             o64.cap_gemm = 1
             o64.mg_arith = 1
@@ -457,10 +474,12 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (J is %.1f GB)" % (J.numel() * 8 / 1e9)},
         "phases_ms": mean, "pcg_iters": iters, "rel_res_true": rel_true,
         "mg_dof_per_s": float(m) * N / (mean["t_H_ms"] / 1e3),
-        "arith": {"operator_and_krylov": "f64", "true_residual": "f64",
-                  "vcycle": "double-float (FP32 pairs, ~48 bits)",
-                  "capacitance_gemm": "BF16 tensor cores on an exact 48-bit digit split, FP64 accumulation",
-                  "cholesky": "f64", "woodbury_passes": "double-float"},
+        "arith": ({"operator_and_krylov": "f64", "true_residual": "f64",
+                   "vcycle": "double-float (FP32 pairs, ~48 bits)",
+                   "capacitance_gemm": "BF16 tensor cores on an exact 48-bit digit split, FP64 accumulation",
+                   "cholesky": "f64", "woodbury_passes": "double-float", "krylov_J_passes": "double-float"}
+                  if args.arith == "mixed" else
+                  {"everything": "f64 (plain FP64 form: FP64 cycle and passes, CUDA-core C)"}),
         "roofline": roofline, "kernels": table, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
         "fp64_form": fp64_form,
         "impl": "ours",

@@ -784,7 +784,16 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
 // Lines H, C, chol. With J_host given, the rows of J are first copied from it into J
 // (device) on the context's copy stream, one rhs_block batch at a time, each batch's
 // conversion and V-cycles waiting only for that batch's copy.
+static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const double* J_host);
+
+// every return waits for the copies of J_host, so that none outlives the call
 static h1w_status capacitance_impl(h1w_ctx* c, int32_t m, const double* J, const double* J_host) {
+  const h1w_status st = capacitance_core(c, m, J, J_host);
+  if (J_host && c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  return st;
+}
+
+static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const double* J_host) {
   const int64_t N = c->lev[0].N;
   c->m = m;
   c->J = J;
