@@ -74,6 +74,7 @@ def parse():
                          "(sides 128..1024, m 8..256, alpha log-uniform 1e-4..1e-1) solved by h1w_solve_batch")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per batched V-cycle (0: default)")
     ap.add_argument("--arith", default="mixed", choices=["mixed", "fp64"],
                     help="timed path: mixed (double-float cycle and passes, tensor-core C; default) or the "
                          "plain FP64 form (FP64 cycle and passes, CUDA-core C)")
@@ -298,10 +299,13 @@ def run_ours(args):
         J = pr.J
         m, N = J.shape
         o_main = None
-        if args.arith == "fp64":
+        if args.arith == "fp64" or args.rhs_block > 0:
             o_main = h1w.h1w_default_options()
-            o_main.cap_gemm = 1
-            o_main.mg_arith = 1
+            if args.arith == "fp64":
+                o_main.cap_gemm = 1
+                o_main.mg_arith = 1
+            if args.rhs_block > 0:
+                o_main.rhs_block = args.rhs_block
         S = h1w.Solver(h1w.H1W_FV_CELL, (n, n, n), (1.0 / n,) * 3, ALPHA, m, device=dev, stream=stream,
                        opt=o_main)
         dm = torch.as_tensor(pr.logsigma - pr.m_ref, device=dev)
@@ -370,13 +374,15 @@ def run_ours(args):
                 S.capacitance_from_host(J_host, J_dev)   # J streamed in row batches under line H
                 S.pcg(b_dev, RTOL, MAXIT, x=x)
                 x_host.copy_(x, non_blocking=True)
+            te = S.timings()
             f1.record(stream)
             torch.cuda.synchronize()
             ems = allmax(world, f0.elapsed_time(f1))
             e2e = {"value": world * args.e2e_steps / (ems / 1e3), "unit": "solves/s",
                    "h2d_bytes_per_step": int(J.numel() * 8 + b.numel() * 8),
                    "d2h_bytes_per_step": int(x.numel() * 8), "steps": args.e2e_steps,
-                   "h2d_copy_gb_per_s": h2d_gbs}
+                   "h2d_copy_gb_per_s": h2d_gbs,
+                   "last_step_phases_ms": {k_: float(getattr(te, k_)) for k_ in phase}}
             del J_host, J_dev
 
         # the plain FP64 GPU form of the same step (FP64 V-cycle and Krylov passes, FP64

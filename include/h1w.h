@@ -67,7 +67,7 @@ typedef struct {
 
 typedef struct {
   int32_t cheb_degree;   /* Chebyshev smoother degree per half-cycle (1..7, default 2) */
-  int32_t rhs_block;     /* right-hand sides per batched V-cycle while building H (1..64, default 32) */
+  int32_t rhs_block;     /* right-hand sides per batched V-cycle while building H (1..256, default 128) */
   int32_t max_restarts;  /* true-residual restarts allowed in h1w_pcg (default 3) */
   int32_t cap_gemm;      /* line C: 0 = tensor cores on an exact BF16 digit split of the FP64
                             operands (48-bit, default), 1 = FP64 CUDA cores */

@@ -262,7 +262,7 @@ h1w_status validate(const h1w_grid* g, int32_t m_max, const h1w_options* o, std:
   if (m_max < 0 || m_max > kMaxM) { why = "m_max out of range [0, 4096]"; return H1W_EINVAL; }
   if (o) {
     if (o->cheb_degree < 1 || o->cheb_degree > 7) { why = "cheb_degree out of range [1, 7]"; return H1W_EINVAL; }
-    if (o->rhs_block < 1 || o->rhs_block > 64) { why = "rhs_block out of range [1, 64]"; return H1W_EINVAL; }
+    if (o->rhs_block < 1 || o->rhs_block > 256) { why = "rhs_block out of range [1, 256]"; return H1W_EINVAL; }
     if (o->max_restarts < 0 || o->max_restarts > 100) { why = "max_restarts out of range"; return H1W_EINVAL; }
     if (o->cap_gemm != 0 && o->cap_gemm != 1) { why = "cap_gemm must be 0 or 1"; return H1W_EINVAL; }
     if (o->mg_arith != 0 && o->mg_arith != 1) { why = "mg_arith must be 0 or 1"; return H1W_EINVAL; }
@@ -291,13 +291,19 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   for (int l = 0; l < P.nlev; ++l) qlen += 6 * (int64_t)(P.n[l][0] + P.n[l][1]);
   double* qdev = B.take<double>(g.disc == H1W_Q1_VERTEX ? qlen : 1);
   LevelBufs bufs[kMaxLevels];
+  // the fused legs on the finest level read b from the caller and write x only: its r, b
+  // and Chebyshev vectors are then not needed
+  const bool fused0 = (g.disc == H1W_FV_CELL) && o.mg_arith == 0 && o.mg_unfused == 0 && o.cheb_degree == 2 &&
+                      P.nlev > 1 && P.c[0][0] && P.c[0][1] && P.c[0][2] &&
+                      (int64_t)P.n[0][0] * P.n[0][1] < (int64_t(1) << 26);
   for (int l = 0; l < P.nlev; ++l) {
     const int64_t Nl = (int64_t)P.n[l][0] * P.n[l][1] * P.n[l][2];
+    const int64_t nw = (l == 0 && fused0) ? 1 : nb * Nl;
     bufs[l].x = B.take<double>(nb * Nl);  // level 0: used by the double-float cycle
-    bufs[l].b = B.take<double>(nb * Nl);
-    bufs[l].r = B.take<double>(nb * Nl);
-    bufs[l].da = B.take<double>(nb * Nl);
-    bufs[l].db = B.take<double>(nb * Nl);
+    bufs[l].b = B.take<double>(nw);
+    bufs[l].r = B.take<double>(nw);
+    bufs[l].da = B.take<double>(nw);
+    bufs[l].db = B.take<double>(nw);
   }
   const int l = P.nlev - 1;
   const int64_t Nc = (int64_t)P.n[l][0] * P.n[l][1] * P.n[l][2];
@@ -599,7 +605,7 @@ extern "C" {
 void h1w_default_options(h1w_options* opt) {
   if (!opt) return;
   opt->cheb_degree = 2;
-  opt->rhs_block = 32;
+  opt->rhs_block = 128;
   opt->max_restarts = 3;
   opt->cap_gemm = 0;
   opt->mg_arith = 0;
@@ -799,8 +805,13 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
   c->J = J;
   const long long l0 = g_kernel_launches.load();
   if (m == 0) { c->launches_cap = 0; return H1W_OK; }
+  // row batches: rhs_block rows each; with J coming from the host the first batch is at
+  // most 32 rows, so that the cycles start after a short first copy
   const int nb = c->opt.rhs_block;
-  const int nbatch = (m + nb - 1) / nb;
+  std::vector<int> edge{0};
+  const int first = J_host ? std::min(nb, 32) : nb;
+  for (int r0 = 0; r0 < m; r0 += (r0 == 0 ? first : nb)) edge.push_back(std::min(m, r0 + (r0 == 0 ? first : nb)));
+  const int nbatch = (int)edge.size() - 1;
   if (J_host) {
     if (!c->copy_stream && cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
       return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create the copy stream");
@@ -814,7 +825,7 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
     cudaEventRecord(c->cev[nbatch], c->stream);
     cudaStreamWaitEvent(c->copy_stream, c->cev[nbatch], 0);
     for (int bi = 0; bi < nbatch; ++bi) {
-      const int64_t r0 = (int64_t)bi * nb, nr = std::min<int64_t>(nb, m - r0);
+      const int64_t r0 = edge[bi], nr = edge[bi + 1] - edge[bi];
       cudaMemcpyAsync(const_cast<double*>(J) + r0 * N, J_host + r0 * N, sizeof(double) * nr * N,
                       cudaMemcpyHostToDevice, c->copy_stream);
       cudaEventRecord(c->cev[bi], c->copy_stream);
@@ -828,7 +839,7 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
   c->timing_on = c->time_vc = true;
   bool vc_ok = true;
   for (int bi = 0; bi < nbatch && vc_ok; ++bi) {
-    const int64_t r0 = (int64_t)bi * nb, nr = std::min<int64_t>(nb, m - r0), o = r0 * N;
+    const int64_t r0 = edge[bi], nr = edge[bi + 1] - edge[bi], o = r0 * N;
     if (J_host) cudaStreamWaitEvent(c->stream, c->cev[bi], 0);
     if (uses_df(c)) launch_d2df(nr * N, J + o, c->Jdf + o, c->stream);  // J for the cycle and the Krylov passes
     vc_ok = vcycle_many(c, (int)nr, J + o, uses_df(c) ? c->Jdf + o : nullptr, h_df_only ? nullptr : c->H + o,

@@ -38,4 +38,4 @@ def test_host_side_validation_without_gpu():
     neg = h1w.make_grid(h1w.H1W_Q1_VERTEX, (64, 64), (1 / 63,) * 2, -1.0)
     assert h1w.h1w_workspace_size(neg, 4) == 0
     o = h1w.h1w_default_options()
-    assert (o.cheb_degree, o.rhs_block, o.max_restarts) == (2, 32, 3)
+    assert (o.cheb_degree, o.rhs_block, o.max_restarts) == (2, 128, 3)
