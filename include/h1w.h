@@ -67,12 +67,13 @@ typedef struct {
 
 typedef struct {
   int32_t cheb_degree;   /* Chebyshev smoother degree per half-cycle (1..7, default 2) */
-  int32_t rhs_block;     /* right-hand sides per batched V-cycle while building H (1..256, default 128) */
+  int32_t rhs_block;     /* right-hand sides per batched V-cycle while building H (1..256, default 128;
+                            a context uses at most m_max of them and sizes its buffers so) */
   int32_t max_restarts;  /* true-residual restarts allowed in h1w_pcg (default 3) */
   int32_t cap_gemm;      /* line C: 0 = tensor cores on an exact BF16 digit split of the FP64
                             operands (48-bit, default), 1 = FP64 CUDA cores */
-  int32_t mg_arith;      /* V-cycle arithmetic on FV grids: 0 = double-float (FP32 pairs, about
-                            48 bits, default), 1 = FP64. Q1 grids always use FP64. */
+  int32_t mg_arith;      /* arithmetic of the V-cycle and of the passes over J and H inside PCG:
+                            0 = double-float (FP32 pairs, about 48 bits, default), 1 = FP64 */
   int32_t mg_unfused;    /* double-float cycle: 0 = levels with all axes coarsened and the degree-2
                             smoother run each leg (smoothing, residual and transfer) as one kernel
                             (default), 1 = one kernel per step. Both give identical results. */

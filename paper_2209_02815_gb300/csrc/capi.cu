@@ -53,6 +53,7 @@ struct h1w_ctx {
   LevelBufs buf[kMaxLevels];
   std::vector<double> qhost[kMaxLevels][2];  // Q1 1D coefficients (host copy)
   double* qdev;          // Q1 coefficients, all levels
+  df* q1st;              // Q1 double-float stencil tables, all levels
   double* coarse_X;      // dense inverse of the coarsest operator
   double* coarse_L;      // scratch for its factorization
   int* dstatus;          // device status word
@@ -281,15 +282,25 @@ int64_t gemm_partial_len(int m_max, int64_t N, bool ozaki) {
   return best;
 }
 
+// right-hand sides per batched V-cycle: the option, but no more than the capacitance
+// phase ever batches (m_max rows), so small-m contexts do not size buffers for 128
+int block_rhs(const h1w_options& o, int m_max) { return std::max(1, std::min(o.rhs_block, m_max)); }
+
 // Lays out every buffer; with ctx->... pointers filled when base != nullptr.
 size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w_options& o,
               char* base) {
   Bump B{base};
-  const int nb = o.rhs_block;
+  const int nb = block_rhs(o, m_max);
   const int64_t N0 = (int64_t)P.n[0][0] * P.n[0][1] * P.n[0][2];
   int64_t qlen = 0;
   for (int l = 0; l < P.nlev; ++l) qlen += 6 * (int64_t)(P.n[l][0] + P.n[l][1]);
   double* qdev = B.take<double>(g.disc == H1W_Q1_VERTEX ? qlen : 1);
+  int64_t stlen = 1;
+  if (g.disc == H1W_Q1_VERTEX && o.mg_arith == 0) {
+    stlen = 0;
+    for (int l = 0; l < P.nlev; ++l) stlen += 10 * (int64_t)P.n[l][0] * P.n[l][1] * P.n[l][2];
+  }
+  df* q1st = B.take<df>(stlen);
   LevelBufs bufs[kMaxLevels];
   // the fused legs on the finest level read b from the caller and write x only: its r, b
   // and Chebyshev vectors are then not needed
@@ -312,7 +323,7 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   int* dstatus = B.take<int>(4);
   int* tflags = B.take<int>(2 * ((m_max + 31) / 32 + 1));
   unsigned long long* dbits = B.take<unsigned long long>(4);
-  const bool use_df = (g.disc == H1W_FV_CELL) && (o.mg_arith == 0);
+  const bool use_df = o.mg_arith == 0;
   // FP64 H: not needed when the cycle is double-float and C runs on the tensor cores
   double* H = B.take<double>((use_df && o.cap_gemm == 0) ? 1 : (int64_t)m_max * N0);
   df* Hdf = use_df ? B.take<df>((int64_t)m_max * N0) : nullptr;
@@ -347,6 +358,7 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   double* scal = B.take<double>(16);
   if (c) {
     c->qdev = qdev;
+    c->q1st = q1st;
     for (int k = 0; k < P.nlev; ++k) c->buf[k] = bufs[k];
     c->coarse_X = cX; c->coarse_L = cL; c->dstatus = dstatus; c->dbits = dbits; c->trsv_flags = tflags;
     c->H = H; c->C = C; c->Lc = Lc; c->gemm_partial = gp; c->gemm_partial_len = gpl;
@@ -412,10 +424,13 @@ void smooth_df(h1w_ctx* c, int l, int nrhs, const df* b, df* x, bool zero_x) {
   df* r = dfp(c->buf[l].r);
   df* da = dfp(c->buf[l].da);
   df* db = dfp(c->buf[l].db);
-  launch_cheb_first_df(L, nrhs, b, x, r, da, zero_x, K.inv_theta_df, c->stream);
+  const bool q1 = c->disc == H1W_Q1_VERTEX;
+  if (q1) launch_q1_cheb_first_df(L, nrhs, b, x, r, da, zero_x, K.inv_theta_df, c->stream);
+  else launch_cheb_first_df(L, nrhs, b, x, r, da, zero_x, K.inv_theta_df, c->stream);
   bool pending = !zero_x;
   for (int j = 1; j < c->opt.cheb_degree; ++j) {
-    launch_cheb_step_df(L, nrhs, r, da, db, x, K.c1_df[j], K.c2_df[j], pending, c->stream);
+    if (q1) launch_q1_cheb_step_df(L, nrhs, r, da, db, x, K.c1_df[j], K.c2_df[j], pending, c->stream);
+    else launch_cheb_step_df(L, nrhs, r, da, db, x, K.c1_df[j], K.c2_df[j], pending, c->stream);
     pending = false;
     std::swap(da, db);
   }
@@ -456,8 +471,13 @@ bool vcycle_block_df(h1w_ctx* c, int nrhs, const df* b0, const double* b0_64, do
       if (l == 0 && c->time_vc) timed_end(c, kCatDown);
     } else {
       smooth_df(c, l, nrhs, bl[l], x, true);
-      launch_residual_df(c->lev[l], nrhs, bl[l], x, dfp(c->buf[l].r), s);
-      launch_restrict_df(c->lev[l], c->lev[l + 1], nrhs, dfp(c->buf[l].r), dfp(c->buf[l + 1].b), s);
+      if (c->disc == H1W_Q1_VERTEX) {
+        launch_q1_residual_df(c->lev[l], nrhs, bl[l], x, dfp(c->buf[l].r), s);
+        launch_q1_restrict_df(c->lev[l], c->lev[l + 1], nrhs, dfp(c->buf[l].r), dfp(c->buf[l + 1].b), s);
+      } else {
+        launch_residual_df(c->lev[l], nrhs, bl[l], x, dfp(c->buf[l].r), s);
+        launch_restrict_df(c->lev[l], c->lev[l + 1], nrhs, dfp(c->buf[l].r), dfp(c->buf[l + 1].b), s);
+      }
     }
   }
   launch_coarse_apply_df(c->coarse_X, (int)c->lev[nl - 1].N, nrhs, bl[nl - 1], dfp(c->buf[nl - 1].x), s);
@@ -479,7 +499,8 @@ bool vcycle_block_df(h1w_ctx* c, int nrhs, const df* b0, const double* b0_64, do
       written = (l == 0);
     } else {
       df* x = dfp(c->buf[l].x);
-      launch_prolong_add_df(c->lev[l], c->lev[l + 1], nrhs, xf[l + 1], x, s);
+      if (c->disc == H1W_Q1_VERTEX) launch_q1_prolong_add_df(c->lev[l], c->lev[l + 1], nrhs, xf[l + 1], x, s);
+      else launch_prolong_add_df(c->lev[l], c->lev[l + 1], nrhs, xf[l + 1], x, s);
       smooth_df(c, l, nrhs, bl[l], x, false);
       xf[l] = x;
     }
@@ -488,15 +509,16 @@ bool vcycle_block_df(h1w_ctx* c, int nrhs, const df* b0, const double* b0_64, do
   return true;
 }
 
-bool uses_df(const h1w_ctx* c) { return (c->disc == H1W_FV_CELL) && (c->opt.mg_arith == 0); }
+bool uses_df(const h1w_ctx* c) { return c->opt.mg_arith == 0; }
 
 // x = L-hat^-1 b for nrhs vectors. b comes in FP64 (b64) or, on the double-float cycle,
 // as double-floats (bdf, preferred when given). The result goes to x64 and/or, on the
 // double-float cycle, xdf. Returns false if a fused kernel could not be configured.
 bool vcycle_many(h1w_ctx* c, int nrhs, const double* b64, const df* bdf, double* x64, df* xdf) {
   const int64_t N = c->lev[0].N;
-  for (int r0 = 0; r0 < nrhs; r0 += c->opt.rhs_block) {
-    const int nr = std::min(c->opt.rhs_block, nrhs - r0);
+  const int nb = block_rhs(c->opt, c->m_max);
+  for (int r0 = 0; r0 < nrhs; r0 += nb) {
+    const int nr = std::min(nb, nrhs - r0);
     const int64_t o = (int64_t)r0 * N;
     if (uses_df(c)) {
       if (!vcycle_block_df(c, nr, bdf ? bdf + o : nullptr, bdf ? nullptr : b64 + o, x64 ? x64 + o : nullptr,
@@ -670,7 +692,7 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
   c->launches_cap = c->launches_pcg = 0;
 
   // level descriptors
-  int64_t qoff = 0;
+  int64_t qoff = 0, stoff = 0;
   for (int l = 0; l < P.nlev; ++l) {
     Level& L = c->lev[l];
     L = Level{};
@@ -706,6 +728,12 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
       cudaMemcpyAsync(qx, c->qhost[l][0].data(), sizeof(double) * 6 * L.nx, cudaMemcpyHostToDevice, c->stream);
       cudaMemcpyAsync(qy, c->qhost[l][1].data(), sizeof(double) * 6 * L.ny, cudaMemcpyHostToDevice, c->stream);
       L.qx = qx; L.qy = qy;
+      if (o.mg_arith == 0) {
+        df* st = c->q1st + stoff;
+        stoff += 10 * L.N;
+        launch_q1_stencil_df(L, st, c->stream);
+        L.q1st = st;
+      }
     }
   }
   // Gershgorin bounds and Chebyshev coefficients
@@ -807,7 +835,7 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
   if (m == 0) { c->launches_cap = 0; return H1W_OK; }
   // row batches: rhs_block rows each; with J coming from the host the first batch is at
   // most 32 rows, so that the cycles start after a short first copy
-  const int nb = c->opt.rhs_block;
+  const int nb = block_rhs(c->opt, c->m_max);
   std::vector<int> edge{0};
   const int first = J_host ? std::min(nb, 32) : nb;
   for (int r0 = 0; r0 < m; r0 += (r0 == 0 ? first : nb)) edge.push_back(std::min(m, r0 + (r0 == 0 ? first : nb)));

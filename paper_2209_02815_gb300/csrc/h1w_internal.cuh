@@ -29,6 +29,7 @@ struct Level {
   double Tx, Ty, Tz, V;         // FV coefficients
   const double* qx;              // Q1 x-axis coefficients [6][nx] (device)
   const double* qy;              // Q1 y-axis coefficients [6][ny] (device)
+  const df* q1st;                // Q1 double-float cycle: per-vertex stencil [9][N] and 1/diag [N] (device)
   double lam;                    // upper bound of spec(D^-1 A) (Gershgorin)
   int cx, cy, cz;                // axis coarsened towards the next level
   int iso;                       // FV with Tx == Ty == Tz
@@ -131,6 +132,18 @@ void launch_coarse_apply_df(const double* X, int n, int nrhs, const df* b, df* x
 void launch_d2df(int64_t n, const double* src, df* dst, cudaStream_t s);
 // dst = src as FP64; dst2 (may be null) receives a copy of the double-floats
 void launch_df2d(int64_t n, const df* src, double* dst, df* dst2, cudaStream_t s);
+// The double-float cycle on 2D Q1 levels (one kernel per step): per-vertex stencil tables
+// (launch_q1_stencil_df fills L.q1st's storage from L.qx, L.qy), smoothing steps, residual
+// and vertex transfers, as the FV ones above.
+void launch_q1_stencil_df(const Level& L, df* st, cudaStream_t s);
+void launch_q1_cheb_first_df(const Level& L, int nrhs, const df* b, df* x, df* r, df* d, bool zero_x, df inv_theta,
+                             cudaStream_t s);
+void launch_q1_cheb_step_df(const Level& L, int nrhs, df* r, const df* d_old, df* d_new, df* x, df c1, df c2,
+                            bool add_old, cudaStream_t s);
+void launch_q1_residual_df(const Level& L, int nrhs, const df* b, const df* x, df* r, cudaStream_t s);
+void launch_q1_restrict_df(const Level& Lf, const Level& Lc, int nrhs, const df* rf, df* bc, cudaStream_t s);
+void launch_q1_prolong_add_df(const Level& Lf, const Level& Lc, int nrhs, const df* xc, df* xf, cudaStream_t s);
+
 // Fused smoothing passes on a level with all three axes coarsened 2:1 and the degree-2
 // smoother: down leg (x = S(b) from zero, bc = P^T (b - A x)) and up leg (y = S(x + P xc)
 // started from the corrected x; y and/or y64 may be null, not both). False if the level

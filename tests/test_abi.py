@@ -39,3 +39,19 @@ def test_host_side_validation_without_gpu():
     assert h1w.h1w_workspace_size(neg, 4) == 0
     o = h1w.h1w_default_options()
     assert (o.cheb_degree, o.rhs_block, o.max_restarts) == (2, 128, 3)
+
+
+def test_rhs_block_buffers_capped_at_m_max():
+    """A context never batches more right-hand sides than it has rows of J, so its
+    V-cycle block buffers are sized for min(rhs_block, m_max)."""
+    from paper_2209_02815_gb300 import h1w
+    g = h1w.make_grid(h1w.H1W_Q1_VERTEX, (256, 256), (1 / 255,) * 2, 1e-3)
+    sizes = {}
+    for rb in (8, 64, 128):
+        o = h1w.h1w_default_options()
+        o.rhs_block = rb
+        sizes[rb] = h1w.h1w_workspace_size(g, 8, o)
+    assert sizes[8] == sizes[64] == sizes[128] > 0
+    o = h1w.h1w_default_options()
+    o.rhs_block = 4
+    assert 0 < h1w.h1w_workspace_size(g, 8, o) < sizes[8]
