@@ -437,9 +437,10 @@ void smooth_df(h1w_ctx* c, int l, int nrhs, const df* b, df* x, bool zero_x) {
   if (pending) launch_add_df((int64_t)nrhs * L.N, da, x, c->stream);
 }
 
-// level l smooths with the fused down/up kernels (all axes coarsened, degree-2 smoother)
+// level l smooths with the fused down/up kernels (FV, all axes coarsened, degree-2 smoother)
 bool fused_level(const h1w_ctx* c, int l) {
-  return c->opt.mg_unfused == 0 && c->opt.cheb_degree == 2 && l < c->nlev - 1 && fused_level_ok(c->lev[l]);
+  return c->disc == H1W_FV_CELL && c->opt.mg_unfused == 0 && c->opt.cheb_degree == 2 && l < c->nlev - 1 &&
+         fused_level_ok(c->lev[l]);
 }
 
 // x = L-hat^-1 b for nrhs <= rhs_block right-hand sides given as double-floats (b0, level-0
@@ -833,12 +834,18 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
   c->J = J;
   const long long l0 = g_kernel_launches.load();
   if (m == 0) { c->launches_cap = 0; return H1W_OK; }
-  // row batches: rhs_block rows each; with J coming from the host the first batch is at
-  // most 32 rows, so that the cycles start after a short first copy
+  // row batches: rhs_block rows each. With J coming from the host the batches ramp up
+  // from 16 rows by a factor of about 1.25 (rounded up to multiples of 8): the cycles
+  // start after a short first copy, and while a batch runs the copy of the next, slightly
+  // larger one completes (a cycle costs somewhat more per row than the copy of the row
+  // over the host link), so the cycles rarely wait for data.
   const int nb = block_rhs(c->opt, c->m_max);
   std::vector<int> edge{0};
-  const int first = J_host ? std::min(nb, 32) : nb;
-  for (int r0 = 0; r0 < m; r0 += (r0 == 0 ? first : nb)) edge.push_back(std::min(m, r0 + (r0 == 0 ? first : nb)));
+  for (int r0 = 0, bs = J_host ? std::min(nb, 16) : nb; r0 < m;) {
+    r0 = std::min(m, r0 + bs);
+    edge.push_back(r0);
+    if (J_host) bs = std::min(nb, (bs + bs / 4 + 7) / 8 * 8);
+  }
   const int nbatch = (int)edge.size() - 1;
   if (J_host) {
     if (!c->copy_stream && cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)

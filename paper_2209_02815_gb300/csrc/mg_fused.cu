@@ -38,14 +38,37 @@ namespace {
 
 using namespace dfmg;
 
-constexpr int kFX = 32, kFY = 16;                               // fine cells of a tile
+// Tile shape and block size (compile-time). Defaults: 32 x 16 tiles, 256 threads, and
+// launch bounds that hold both legs to 85 registers so that three blocks (24 warps) stay
+// resident per SM; at two blocks per SM both legs run 10-14 % slower. Larger tiles
+// (32 x 32 or 64 x 16 with 512 threads) repeat less halo work but leave the up leg one
+// block per SM, which costs more than the halo saves at 128^3.
+#ifndef H1W_FUSED_FX
+#define H1W_FUSED_FX 32
+#endif
+#ifndef H1W_FUSED_FY
+#define H1W_FUSED_FY 16
+#endif
+#ifndef H1W_FUSED_THREADS
+#define H1W_FUSED_THREADS 256
+#endif
+#ifndef H1W_FUSED_PRE_MINB
+#define H1W_FUSED_PRE_MINB 3
+#endif
+#ifndef H1W_FUSED_POST_MINB
+#define H1W_FUSED_POST_MINB 3
+#endif
+#ifndef H1W_FUSED_BLOCKS_PER_SM
+#define H1W_FUSED_BLOCKS_PER_SM 3
+#endif
+constexpr int kFX = H1W_FUSED_FX, kFY = H1W_FUSED_FY;           // fine cells of a tile
 constexpr int kTX = kFX / 2, kTY = kFY / 2;                     // coarse cells of a tile
 constexpr int kW3 = kFX + 6, kH3 = kFY + 6, kA3 = kW3 * kH3;    // tile + 3
 constexpr int kW2 = kFX + 4, kH2 = kFY + 4, kA2 = kW2 * kH2;    // tile + 2
 constexpr int kW1 = kFX + 2, kH1 = kFY + 2, kA1 = kW1 * kH1;    // tile + 1
 constexpr int kHC = kTY + 4;                                    // coarse rows of tile + 2
 constexpr int kAX = kHC * kW2;                                  // coarse rows x fine columns
-constexpr int kThr = 256;
+constexpr int kThr = H1W_FUSED_THREADS;
 constexpr int kP3 = (kA3 + kThr - 1) / kThr;
 constexpr int kP2 = (kA2 + kThr - 1) / kThr;
 constexpr int kP1 = (kA1 + kThr - 1) / kThr;
@@ -107,7 +130,7 @@ __device__ __forceinline__ df nsum(const df* __restrict__ u0, const df* __restri
 
 // Down leg. Grid: (xy tiles, z segments of segK coarse planes, right-hand sides).
 template <bool ISO, typename TB>
-__global__ void __launch_bounds__(kThr) k_pre_fused(Level L, Level Lc, FusedCoef F, const TB* __restrict__ b,
+__global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L, Level Lc, FusedCoef F, const TB* __restrict__ b,
                                                     df* __restrict__ x, df* __restrict__ bc, int segK) {
   extern __shared__ df sm[];
   df* Gp = sm;               // g = D^-1 b over tile + 3, 3 planes
@@ -319,7 +342,7 @@ __global__ void __launch_bounds__(kThr) k_pre_fused(Level L, Level Lc, FusedCoef
 // Up leg. Grid: (xy tiles, z segments of segZ fine planes (even), right-hand sides).
 // y and y64 (either may be null) must not overlap x, xc or b.
 template <bool ISO, typename TB>
-__global__ void __launch_bounds__(kThr) k_post_fused(Level L, Level Lc, FusedCoef F, const df* __restrict__ x,
+__global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level L, Level Lc, FusedCoef F, const df* __restrict__ x,
                                                      const df* __restrict__ xc, const TB* __restrict__ b,
                                                      df* __restrict__ y, double* __restrict__ y64, int segZ) {
   extern __shared__ df sm[];
@@ -543,12 +566,12 @@ __global__ void __launch_bounds__(kThr) k_post_fused(Level L, Level Lc, FusedCoe
 #undef CSLOT
 }
 
-// z segments: enough blocks for about four waves at three blocks per SM, with at least
+// z segments: enough blocks for about four waves of resident blocks, with at least
 // minp planes per segment (small levels are latency-bound: there, more and shorter
 // segments help even though each repeats its halo planes)
 int fused_segments(int tiles, int nrhs, int planes, int minp) {
   const int64_t base = (int64_t)tiles * nrhs;
-  const int64_t want = 152 * 3 * 4;
+  const int64_t want = 152 * H1W_FUSED_BLOCKS_PER_SM * 4;
   int nseg = (int)std::max<int64_t>(1, (want + base - 1) / base);
   nseg = std::min(nseg, std::max(1, planes / minp));
   return nseg;
