@@ -218,9 +218,9 @@ __device__ void factor_diag_block(double (*Ld)[kNB + 1], int nb, int* status) {
   }
 }
 
-// grid.x = 1 + number of 32-row blocks below the panel; blockDim = 1024
-__global__ void __launch_bounds__(1024) k_chol_panel(double* A, int n, int kb, int* status) {
-  __shared__ double Ld[kNB][kNB + 1];
+// The diagonal block A11 of the panel at kb, factored in shared memory (blockDim = 1024).
+__device__ __forceinline__ int load_factor_diag(const double* A, int n, int kb, double (*Ld)[kNB + 1],
+                                                int* status) {
   const int nb = min(kNB, n - kb);
   const int tid = threadIdx.x;
   {
@@ -228,14 +228,20 @@ __global__ void __launch_bounds__(1024) k_chol_panel(double* A, int n, int kb, i
     if (r < nb && c <= r) Ld[r][c] = A[(int64_t)(kb + r) * n + kb + c];
   }
   __syncthreads();
-  factor_diag_block(Ld, nb, blockIdx.x == 0 ? status : nullptr);
-  if (blockIdx.x == 0) {
-    const int r = tid / kNB, c = tid % kNB;
-    if (r < nb && c <= r) A[(int64_t)(kb + r) * n + kb + c] = Ld[r][c];
-    return;
-  }
+  factor_diag_block(Ld, nb, status);
+  return nb;
+}
+
+// L21: one block per 32-row block below the panel (grid.x = their number, blockDim = 1024).
+// Each block factors A11 again from A and solves its rows against it. A11 must still be
+// unfactored in A while any of these blocks may start, so its factor is written back only
+// by k_chol_diag, launched after this kernel.
+__global__ void __launch_bounds__(1024) k_chol_panel(double* A, int n, int kb) {
+  __shared__ double Ld[kNB][kNB + 1];
+  const int nb = load_factor_diag(A, n, kb, Ld, nullptr);
+  const int tid = threadIdx.x;
   // rows of this block: solve x L11^T = a for each row (warp w -> row w)
-  const int row = kb + kNB * blockIdx.x + (tid >> 5);
+  const int row = kb + kNB * (blockIdx.x + 1) + (tid >> 5);
   const int lane = tid & 31;
   if (row >= n) return;
   double a = (lane < nb) ? A[(int64_t)row * n + kb + lane] : 0.0;
@@ -247,6 +253,15 @@ __global__ void __launch_bounds__(1024) k_chol_panel(double* A, int n, int kb, i
     else if (lane > c && lane < nb) a -= xc * Ld[lane][c];
   }
   if (lane < nb) A[(int64_t)row * n + kb + lane] = a;
+}
+
+// L11 = chol(A11), written back in place; a non-positive pivot sets kStatusNotSpd. One block
+// of 1024 threads.
+__global__ void __launch_bounds__(1024) k_chol_diag(double* A, int n, int kb, int* status) {
+  __shared__ double Ld[kNB][kNB + 1];
+  const int nb = load_factor_diag(A, n, kb, Ld, status);
+  const int r = threadIdx.x / kNB, c = threadIdx.x % kNB;
+  if (r < nb && c <= r) A[(int64_t)(kb + r) * n + kb + c] = Ld[r][c];
 }
 
 // trailing update A22 -= L21 L21^T over lower tiles (ti >= tj) of 32 x 32
@@ -709,7 +724,11 @@ void launch_woodbury_update(const double* H, int m, int64_t N, const double* v, 
 void launch_chol(double* A, int n, int* status, cudaStream_t s) {
   for (int kb = 0; kb < n; kb += kNB) {
     const int below = (n - kb - 1) / kNB;  // 32-row blocks after the diagonal block
-    k_chol_panel<<<1 + below, 1024, 0, s>>>(A, n, kb, status);
+    if (below > 0) {
+      k_chol_panel<<<below, 1024, 0, s>>>(A, n, kb);
+      note_launches(1);
+    }
+    k_chol_diag<<<1, 1024, 0, s>>>(A, n, kb, status);
     note_launches(1);
     if (below > 0) {
       const int tiles = below * (below + 1) / 2;

@@ -149,7 +149,7 @@ void launch_q1_prolong_add_df(const Level& Lf, const Level& Lc, int nrhs, const 
 // started from the corrected x; y and/or y64 may be null, not both). False if the level
 // does not qualify or the kernel attribute for its shared memory could not be set
 // (nothing launched).
-bool fused_level_ok(const Level& L);  // all axes coarsened and nx ny < 2^27
+bool fused_level_ok(const Level& L);  // all axes coarsened and nx ny < 2^26
 // b (the level's right-hand sides) as double-floats or as FP64 (split on the fly).
 bool launch_pre_fused_df(const Level& L, const Level& Lc, const FusedCoef& F, int nrhs, const df* b, df* x,
                          df* bc, cudaStream_t s);

@@ -191,10 +191,15 @@ def solve_batch(solvers, Js, bs, xs, rtol: float, maxit: int = 500, threads: int
     xp = (P * n)(*[_ptr(x, s.N, "x") for s, x in zip(solvers, xs)])
     infos = (Info * n)()
     sts = (ctypes.c_int32 * n)()
-    for s, J in zip(solvers, Js):
+    for s, J, b, x in zip(solvers, Js, bs, xs):
         s.J = J
         s.m = int(J.shape[0]) if J is not None else 0
-    st = load().h1w_solve_batch(ctxs, n, ms, Jp, bp, xp, float(rtol), int(maxit), int(threads), infos, sts)
+        s._enter(J, b, x)
+    try:
+        st = load().h1w_solve_batch(ctxs, n, ms, Jp, bp, xp, float(rtol), int(maxit), int(threads), infos, sts)
+    finally:
+        for s in solvers:
+            s._leave()
     if st != H1W_OK:
         raise H1wError(st, h1w_last_error(None))
     return list(infos), list(sts)
@@ -258,7 +263,15 @@ def h1w_destroy(ctx) -> None:
 
 
 class Solver:
-    """Owns a workspace tensor and a context for one grid (convenience wrapper)."""
+    """Owns a workspace tensor and a context for one grid (convenience wrapper).
+
+    The library runs on the context's stream. When that is not the caller's current
+    stream, every call first makes the context's stream wait for the current one (so
+    inputs produced there, and the reuse of freed memory by the workspace, are ordered
+    before the library's kernels), marks the tensors it hands over as used on the
+    context's stream (so the caching allocator does not recycle them early), and
+    afterwards makes the current stream wait for the context's stream (so the outputs
+    are complete for whatever the caller runs next)."""
 
     def __init__(self, disc: int, n, h, alpha: float, m_max: int, device="cuda",
                  opt: Options | None = None, stream: torch.cuda.Stream | None = None):
@@ -271,54 +284,88 @@ class Solver:
         if size == 0:
             raise H1wError(H1W_EINVAL, "invalid grid/options for h1w_workspace_size")
         self.workspace = torch.empty(size, dtype=torch.uint8, device=device)
-        self.ctx = h1w_setup(self.grid, self.m_max, opt, self.workspace, stream)
+        self.stream = stream or torch.cuda.current_stream(self.workspace.device)
+        self._enter(self.workspace)
+        self.ctx = h1w_setup(self.grid, self.m_max, opt, self.workspace, self.stream)
+        self._leave()
         self.m = None
         self.J = None
+
+    def _enter(self, *tensors) -> None:
+        cur = torch.cuda.current_stream(self.stream.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+            for t in tensors:
+                if t is not None and t.is_cuda:
+                    t.record_stream(self.stream)
+
+    def _leave(self) -> None:
+        cur = torch.cuda.current_stream(self.stream.device)
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
 
     def capacitance(self, J: torch.Tensor | None) -> None:
         m = 0 if J is None else int(J.shape[0])
         self.J = J  # keep the borrowed matrix alive
+        self._enter(J)
         h1w_capacitance(self.ctx, m, J, self.N)
+        self._leave()
         self.m = m
 
     def capacitance_from_host(self, J_host: torch.Tensor, J_dev: torch.Tensor) -> None:
         """Copies J_host (pinned) into J_dev while line H runs; J_dev becomes the borrowed J."""
         m = int(J_host.shape[0])
         self.J = J_dev
+        self._enter(J_dev)
         h1w_capacitance_from_host(self.ctx, m, J_host, J_dev, self.N)
+        self._leave()
         self.m = m
 
     def apply_prec(self, r, z=None):
         z = torch.empty_like(r) if z is None else z
+        self._enter(r, z)
         h1w_apply_prec(self.ctx, r, z, self.N)
+        self._leave()
         return z
 
     def apply_op(self, p, q=None):
         q = torch.empty_like(p) if q is None else q
+        self._enter(p, q)
         h1w_apply_op(self.ctx, p, q, self.N)
+        self._leave()
         return q
 
     def vcycle(self, b, x=None):
         nrhs = b.numel() // self.N
         x = torch.empty_like(b) if x is None else x
+        self._enter(b, x)
         h1w_vcycle(self.ctx, nrhs, b, x, self.N)
+        self._leave()
         return x
 
     def gn_rhs(self, dm, d):
         b = torch.empty_like(dm)
+        self._enter(dm, d, b)
         h1w_gn_rhs(self.ctx, dm, d, b, self.N, self.m or 0)
+        self._leave()
         return b
 
     def pcg(self, b, rtol: float, maxit: int = 500, x=None, raise_on_notconv=True):
         x = torch.empty_like(b) if x is None else x
-        info = h1w_pcg(self.ctx, b, x, rtol, maxit, self.N, raise_on_notconv)
+        self._enter(b, x)
+        try:
+            info = h1w_pcg(self.ctx, b, x, rtol, maxit, self.N, raise_on_notconv)
+        finally:
+            self._leave()
         return x, info
 
     def factors(self):
         m = self.m or 0
         C = torch.empty((m, m), dtype=torch.float64, device=self.workspace.device)
         L = torch.empty_like(C)
+        self._enter(C, L)
         h1w_capacitance_factors(self.ctx, C, L, m)
+        self._leave()
         return C, L
 
     def timings(self) -> Timings:

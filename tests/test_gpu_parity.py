@@ -382,6 +382,54 @@ def test_solve_batch_matches_individual_solves():
         assert inf.rel_res_true <= 1e-10
 
 
+def test_cholesky_under_concurrent_load():
+    """The capacitance Cholesky (several 32-row panels) while another stream keeps the
+    SMs busy, so that the blocks of a panel start at different times: the factor must
+    equal numpy's Cholesky of the returned C every time. (A block that started after
+    the diagonal block was written back would factor L11 instead of A11.)"""
+    d, n, h = _q1((128, 128))
+    m = 256
+    rng = np.random.default_rng(61)
+    J = _t(rng.standard_normal((m, n[0] * n[1])) / n[0])
+    S = _gpu(d, n, h, 1e-3, m, rhs_block=m)
+    side = torch.cuda.Stream()
+    A = torch.randn(4096, 4096, device=DEV)
+    for _ in range(6):
+        with torch.cuda.stream(side):
+            for _ in range(8):
+                A = torch.tanh(A @ A * 1e-3)
+        S.capacitance(J)
+        C, L = (t.cpu().numpy() for t in S.factors())
+        assert _rel(L, np.linalg.cholesky(C)) <= 1e-10
+    torch.cuda.synchronize()
+
+
+def test_solve_batch_orders_streams():
+    """Solvers on their own streams, created right after their J was generated on
+    the current stream (no synchronize in between), and more systems than host
+    threads: every system must succeed and match solving it alone on the same
+    context bit for bit. The binding orders each context's stream after the current
+    one, so neither the inputs nor memory the caching allocator recycles into a
+    workspace can be read or overwritten early."""
+    descs = inputs.batch_instances(12, sides=(128, 256), ms=(32, 256), alpha_range=(1e-4, 1e-3), seed=77)
+    solvers, Js, bs, xs = [], [], [], []
+    for d in descs:
+        n = d["n"]
+        J, b = inputs.batch_instance_data(d, device=DEV)
+        solvers.append(h1w.Solver(h1w.H1W_Q1_VERTEX, (n, n), (1.0 / (n - 1),) * 2, d["alpha"], d["m"], device=DEV,
+                                  stream=torch.cuda.Stream()))
+        Js.append(J)
+        bs.append(b)
+        xs.append(torch.empty_like(b))
+    infos, sts = h1w.solve_batch(solvers, Js, bs, xs, 1e-8, threads=4)
+    assert all(s_ == h1w.H1W_OK for s_ in sts)
+    for S, J, b, x, inf in zip(solvers, Js, bs, xs, infos):
+        assert inf.rel_res_true <= 1e-8
+        S.capacitance(J)
+        xr, _ = S.pcg(b, 1e-8)
+        assert torch.equal(x, xr)
+
+
 @pytest.mark.parametrize("cap_gemm,mg_arith", [(0, 0), (1, 1)], ids=["mixed", "fp64_form"])
 def test_dipole_grid_solution_error_vs_oracle(cap_gemm, mg_arith):
     """The precision configuration at small size: a 32^3 ERT step with a 4 x 4
