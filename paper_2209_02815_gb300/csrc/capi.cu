@@ -589,14 +589,15 @@ bool apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
     }
   }
   timed_begin(c);
+  int nparts = colsum_blocks(N);
   if (dfp_)
-    launch_woodbury_update_df(c->Hdf, m, N, c->svec, c->z0, c->grid.alpha, z, rz_slot >= 0 ? r : nullptr,
-                              rz_slot >= 0 ? c->partial : nullptr, c->stream);
+    nparts = launch_woodbury_update_df(c->Hdf, m, N, c->svec, c->z0, c->grid.alpha, z, rz_slot >= 0 ? r : nullptr,
+                                       rz_slot >= 0 ? c->partial : nullptr, c->stream);
   else
     launch_woodbury_update(c->H, m, N, c->svec, c->z0, c->grid.alpha, z, rz_slot >= 0 ? r : nullptr,
                            rz_slot >= 0 ? c->partial : nullptr, c->stream);
   timed_end(c, kCatHupd);
-  if (rz_slot >= 0) launch_sum_to_scalar(c->partial, colsum_blocks(N), c->scal + rz_slot, c->stream);
+  if (rz_slot >= 0) launch_sum_to_scalar(c->partial, nparts, c->scal + rz_slot, c->stream);
   return true;
 }
 

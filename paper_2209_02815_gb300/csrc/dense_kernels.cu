@@ -138,59 +138,116 @@ __device__ __forceinline__ df warp_sum_df(df v) {
 }
 
 // partial[c * m + i] = sum_{k in segment c} A[i * N + k] * v[k], A and v
-// double-floats. One warp per row of A and segment of kSegDf entries: lanes
-// stride along the row (coalesced), each lane accumulates 256 exact products
-// in a cascaded sum, and the warp reduces once at the end. The 8 warps of a
-// block share the segment of v through L1.
+// double-floats. A warp covers a segment of kSegDf entries of one row or of a few
+// consecutive rows: lanes stride along the rows (coalesced), each lane accumulates its
+// exact products in cascaded sums, and the warp reduces once at the end.
 constexpr int kSegDf = 8192;
 
 
+// one cascaded-sum step: (s, e) += p
+__device__ __forceinline__ void csum_add(float& s, float& e, df p) {
+  const df t = two_sum(s, p.hi);
+  s = t.hi;
+  e = __fadd_rn(e, __fadd_rn(t.lo, p.lo));
+}
+
+// VEC (N even, so that every row starts on a 16-byte boundary): a warp takes kDotRows
+// consecutive rows; each lane loads two consecutive entries of v with one 16-byte load and
+// uses them for all its rows (v is read once per kDotRows rows), and keeps one cascaded sum
+// per row and entry of the pair. Otherwise one row per warp with 8-byte loads.
+constexpr int kDotRows = 4;
+template <bool VEC>
 __global__ void __launch_bounds__(kThreads) k_rows_dot_df(const df* __restrict__ A, int m, int64_t N,
                                                           const df* __restrict__ v, double* __restrict__ partial) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int row = blockIdx.y * (kThreads / 32) + wid;
-  if (row >= m) return;
   const int64_t k0 = (int64_t)blockIdx.x * kSegDf;
   const int64_t kend = (k0 + kSegDf < N) ? k0 + kSegDf : N;
-  const df* a = A + (int64_t)row * N;
-  float s = 0.f, e = 0.f;
+  if (VEC) {
+    const int row0 = (blockIdx.y * (kThreads / 32) + wid) * kDotRows;
+    if (row0 >= m) return;
+    const float4* v4 = reinterpret_cast<const float4*>(v);
+    const float4* a4[kDotRows];
+#pragma unroll
+    for (int r = 0; r < kDotRows; ++r)
+      a4[r] = reinterpret_cast<const float4*>(A + (int64_t)min(row0 + r, m - 1) * N);
+    float s[kDotRows][2], e[kDotRows][2];
+#pragma unroll
+    for (int r = 0; r < kDotRows; ++r) s[r][0] = s[r][1] = e[r][0] = e[r][1] = 0.f;
+#pragma unroll 2
+    for (int64_t j = k0 / 2 + lane; j < kend / 2; j += 32) {
+      const float4 y = v4[j];
+      const df y0 = df_make(y.x, y.y), y1 = df_make(y.z, y.w);
+#pragma unroll
+      for (int r = 0; r < kDotRows; ++r) {
+        const float4 x = a4[r][j];
+        csum_add(s[r][0], e[r][0], df_mul(df_make(x.x, x.y), y0));
+        csum_add(s[r][1], e[r][1], df_mul(df_make(x.z, x.w), y1));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kDotRows; ++r) {
+      float s0 = s[r][0], e0 = e[r][0];
+      csum_add(s0, e0, fast_two_sum(s[r][1], e[r][1]));
+      const df acc = warp_sum_df(fast_two_sum(s0, e0));
+      if (lane == 0 && row0 + r < m) partial[(int64_t)blockIdx.x * m + row0 + r] = df_to_double(acc);
+    }
+  } else {
+    const int row = blockIdx.y * (kThreads / 32) + wid;
+    if (row >= m) return;
+    const df* a = A + (int64_t)row * N;
+    float s = 0.f, e = 0.f;
 #pragma unroll 8
-  for (int64_t k = k0 + lane; k < kend; k += 32) {
-    const df p = df_mul(a[k], v[k]);
-    const df t = two_sum(s, p.hi);
-    s = t.hi;
-    e = __fadd_rn(e, __fadd_rn(t.lo, p.lo));
+    for (int64_t k = k0 + lane; k < kend; k += 32) csum_add(s, e, df_mul(a[k], v[k]));
+    const df acc = warp_sum_df(fast_two_sum(s, e));
+    if (lane == 0) partial[(int64_t)blockIdx.x * m + row] = df_to_double(acc);
   }
-  const df acc = warp_sum_df(fast_two_sum(s, e));
-  if (lane == 0) partial[(int64_t)blockIdx.x * m + row] = df_to_double(acc);
 }
 
-// z_k = (z0_k - (1/alpha) sum_i H[i][k] v_i) / alpha with H double-floats; partial[block] = sum r_k z_k
+// z_k = (z0_k - (1/alpha) sum_i H[i][k] v_i) / alpha with H double-floats; partial[block] = sum r_k z_k.
+// VEC (N even): each thread takes the two columns 2t, 2t + 1 with one 16-byte load per row
+// and two independent cascaded sums.
+template <bool VEC>
 __global__ void __launch_bounds__(kThreads) k_woodbury_update_df(
     const df* __restrict__ H, int m, int64_t N, const double* __restrict__ v, const double* __restrict__ z0,
     double inv_alpha, double* __restrict__ z, const double* __restrict__ r, double* __restrict__ partial) {
   extern __shared__ df svd[];
   for (int i = threadIdx.x; i < m; i += blockDim.x) svd[i] = df_from_double(v[i]);
   __syncthreads();
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double prod = 0.0;
-  if (k < N) {
-    float s = 0.f, e = 0.f;
-    const df* col = H + k;
-    for (int i = 0; i < m; ++i) {
-      const df p = df_mul(col[(int64_t)i * N], svd[i]);
-      const df t = two_sum(s, p.hi);
-      s = t.hi;
-      e = __fadd_rn(e, __fadd_rn(t.lo, p.lo));
+  if (VEC) {
+    const int64_t k = 2 * t;
+    if (k < N) {
+      float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
+      const float4* col = reinterpret_cast<const float4*>(H + k);
+      const int64_t stride = N / 2;
+      for (int i = 0; i < m; ++i) {
+        const float4 x = col[(int64_t)i * stride];
+        const df w = svd[i];
+        csum_add(s0, e0, df_mul(df_make(x.x, x.y), w));
+        csum_add(s1, e1, df_mul(df_make(x.z, x.w), w));
+      }
+      const double h0 = df_to_double(fast_two_sum(s0, e0)), h1 = df_to_double(fast_two_sum(s1, e1));
+      const double z0k = (z0[k] - h0 * inv_alpha) * inv_alpha, z1k = (z0[k + 1] - h1 * inv_alpha) * inv_alpha;
+      z[k] = z0k;
+      z[k + 1] = z1k;
+      if (r) prod = r[k] * z0k + r[k + 1] * z1k;
     }
-    const double hv = df_to_double(fast_two_sum(s, e));
-    const double zk = (z0[k] - hv * inv_alpha) * inv_alpha;
-    z[k] = zk;
-    if (r) prod = r[k] * zk;
+  } else {
+    const int64_t k = t;
+    if (k < N) {
+      float s = 0.f, e = 0.f;
+      const df* col = H + k;
+      for (int i = 0; i < m; ++i) csum_add(s, e, df_mul(col[(int64_t)i * N], svd[i]));
+      const double hv = df_to_double(fast_two_sum(s, e));
+      const double zk = (z0[k] - hv * inv_alpha) * inv_alpha;
+      z[k] = zk;
+      if (r) prod = r[k] * zk;
+    }
   }
   if (partial) {
-    const double t = block_sum(prod);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    const double bs = block_sum(prod);
+    if (threadIdx.x == 0) partial[blockIdx.x] = bs;
   }
 }
 
@@ -198,9 +255,9 @@ __global__ void __launch_bounds__(kThreads) k_woodbury_update_df(
 
 constexpr int kNB = 32;
 
+// Cholesky of the nb x nb lower triangle in Ld, in place, by any block of at least 32 threads.
 __device__ void factor_diag_block(double (*Ld)[kNB + 1], int nb, int* status) {
   const int tid = threadIdx.x;
-  const int r = tid / kNB, c2 = tid % kNB;
   for (int c = 0; c < nb; ++c) {
     if (tid == 0) {
       double piv = Ld[c][c];
@@ -213,18 +270,20 @@ __device__ void factor_diag_block(double (*Ld)[kNB + 1], int nb, int* status) {
     __syncthreads();
     if (tid > c && tid < nb) Ld[tid][c] /= Ld[c][c];
     __syncthreads();
-    if (r > c && r < nb && c2 > c && c2 <= r) Ld[r][c2] -= Ld[r][c] * Ld[c2][c];
+    for (int e = tid; e < kNB * kNB; e += blockDim.x) {
+      const int r = e / kNB, c2 = e % kNB;
+      if (r > c && r < nb && c2 > c && c2 <= r) Ld[r][c2] -= Ld[r][c] * Ld[c2][c];
+    }
     __syncthreads();
   }
 }
 
-// The diagonal block A11 of the panel at kb, factored in shared memory (blockDim = 1024).
+// The diagonal block A11 of the panel at kb, factored in shared memory.
 __device__ __forceinline__ int load_factor_diag(const double* A, int n, int kb, double (*Ld)[kNB + 1],
                                                 int* status) {
   const int nb = min(kNB, n - kb);
-  const int tid = threadIdx.x;
-  {
-    const int r = tid / kNB, c = tid % kNB;
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+    const int r = e / kNB, c = e % kNB;
     if (r < nb && c <= r) Ld[r][c] = A[(int64_t)(kb + r) * n + kb + c];
   }
   __syncthreads();
@@ -234,12 +293,21 @@ __device__ __forceinline__ int load_factor_diag(const double* A, int n, int kb, 
 
 // L21: one block per 32-row block below the panel (grid.x = their number, blockDim = 1024).
 // Each block factors A11 again from A and solves its rows against it. A11 must still be
-// unfactored in A while any of these blocks may start, so its factor is written back only
-// by k_chol_diag, launched after this kernel.
-__global__ void __launch_bounds__(1024) k_chol_panel(double* A, int n, int kb) {
+// unfactored in A while any of these blocks may start (the blocks of a launch need not
+// run together), so block 0 parks L11 where no block of this launch reads (its strict
+// lower part transposed into the upper triangle of A11, its diagonal in column kb + 32 of
+// rows kb .. kb + 31, all above the diagonal of A and zeroed at the end), and the extra
+// block of k_chol_update moves it into place. (The last panel has no rows below it and
+// is factored by k_chol_diag.)
+__global__ void __launch_bounds__(1024) k_chol_panel(double* A, int n, int kb, int* status) {
   __shared__ double Ld[kNB][kNB + 1];
-  const int nb = load_factor_diag(A, n, kb, Ld, nullptr);
+  const int nb = load_factor_diag(A, n, kb, Ld, blockIdx.x == 0 ? status : nullptr);
   const int tid = threadIdx.x;
+  if (blockIdx.x == 0) {
+    const int r = tid / kNB, c = tid % kNB;
+    if (r < nb && c < r) A[(int64_t)(kb + c) * n + kb + r] = Ld[r][c];
+    if (r < nb && c == r) A[(int64_t)(kb + r) * n + kb + kNB] = Ld[r][r];
+  }
   // rows of this block: solve x L11^T = a for each row (warp w -> row w)
   const int row = kb + kNB * (blockIdx.x + 1) + (tid >> 5);
   const int lane = tid & 31;
@@ -255,20 +323,36 @@ __global__ void __launch_bounds__(1024) k_chol_panel(double* A, int n, int kb) {
   if (lane < nb) A[(int64_t)row * n + kb + lane] = a;
 }
 
-// L11 = chol(A11), written back in place; a non-positive pivot sets kStatusNotSpd. One block
-// of 1024 threads.
-__global__ void __launch_bounds__(1024) k_chol_diag(double* A, int n, int kb, int* status) {
-  __shared__ double Ld[kNB][kNB + 1];
+// L11 = chol(A11), written back in place; a non-positive pivot sets kStatusNotSpd.
+__device__ __forceinline__ void write_diag_factor(double* A, int n, int kb, double (*Ld)[kNB + 1], int* status) {
   const int nb = load_factor_diag(A, n, kb, Ld, status);
-  const int r = threadIdx.x / kNB, c = threadIdx.x % kNB;
-  if (r < nb && c <= r) A[(int64_t)(kb + r) * n + kb + c] = Ld[r][c];
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+    const int r = e / kNB, c = e % kNB;
+    if (r < nb && c <= r) A[(int64_t)(kb + r) * n + kb + c] = Ld[r][c];
+  }
 }
 
-// trailing update A22 -= L21 L21^T over lower tiles (ti >= tj) of 32 x 32
+__global__ void __launch_bounds__(1024) k_chol_diag(double* A, int n, int kb, int* status) {
+  __shared__ double Ld[kNB][kNB + 1];
+  write_diag_factor(A, n, kb, Ld, status);
+}
+
+// trailing update A22 -= L21 L21^T over lower tiles (ti >= tj) of 32 x 32; the block after
+// the last tile moves L11 from where k_chol_panel parked it into A11 (none of these
+// locations is in A22)
 __global__ void __launch_bounds__(256) k_chol_update(double* A, int n, int kb) {
   __shared__ double Li[kNB][kNB + 1];
   __shared__ double Lj[kNB][kNB + 1];
   const int t = blockIdx.x;
+  if (t == gridDim.x - 1) {
+    const int nb = min(kNB, n - kb);
+    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+      const int r = e / kNB, c = e % kNB;
+      if (r < nb && c < r) A[(int64_t)(kb + r) * n + kb + c] = A[(int64_t)(kb + c) * n + kb + r];
+      if (r < nb && c == r) A[(int64_t)(kb + r) * n + kb + r] = A[(int64_t)(kb + r) * n + kb + kNB];
+    }
+    return;
+  }
   int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
   while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
   while (ti * (ti + 1) / 2 > t) --ti;
@@ -699,16 +783,22 @@ int rows_dot_df_chunks(int64_t N) { return (int)((N + kSegDf - 1) / kSegDf); }
 
 void launch_rows_dot_df(const df* A, int m, int64_t N, const df* v, double* partial, cudaStream_t s) {
   if (m <= 0) return;
-  dim3 g(rows_dot_df_chunks(N), (m + kThreads / 32 - 1) / (kThreads / 32));
-  k_rows_dot_df<<<g, kThreads, 0, s>>>(A, m, N, v, partial);
+  const int rows_per_block = (kThreads / 32) * ((N % 2 == 0) ? kDotRows : 1);
+  dim3 g(rows_dot_df_chunks(N), (m + rows_per_block - 1) / rows_per_block);
+  if (N % 2 == 0) k_rows_dot_df<true><<<g, kThreads, 0, s>>>(A, m, N, v, partial);
+  else k_rows_dot_df<false><<<g, kThreads, 0, s>>>(A, m, N, v, partial);
   note_launches(1);
 }
 
-void launch_woodbury_update_df(const df* H, int m, int64_t N, const double* v, const double* z0, double alpha,
-                               double* z, const double* r, double* partial, cudaStream_t s) {
+int launch_woodbury_update_df(const df* H, int m, int64_t N, const double* v, const double* z0, double alpha,
+                              double* z, const double* r, double* partial, cudaStream_t s) {
   const size_t smem = sizeof(df) * (size_t)(m > 0 ? m : 1);
-  k_woodbury_update_df<<<nblk(N), kThreads, smem, s>>>(H, m, N, v, z0, 1.0 / alpha, z, r, partial);
+  const bool vec = N % 2 == 0;
+  const unsigned nb = vec ? nblk(N / 2) : nblk(N);
+  if (vec) k_woodbury_update_df<true><<<nb, kThreads, smem, s>>>(H, m, N, v, z0, 1.0 / alpha, z, r, partial);
+  else k_woodbury_update_df<false><<<nb, kThreads, smem, s>>>(H, m, N, v, z0, 1.0 / alpha, z, r, partial);
   note_launches(1);
+  return (int)nb;
 }
 
 int colsum_blocks(int64_t N) { return (int)nblk(N); }
@@ -725,14 +815,12 @@ void launch_chol(double* A, int n, int* status, cudaStream_t s) {
   for (int kb = 0; kb < n; kb += kNB) {
     const int below = (n - kb - 1) / kNB;  // 32-row blocks after the diagonal block
     if (below > 0) {
-      k_chol_panel<<<below, 1024, 0, s>>>(A, n, kb);
-      note_launches(1);
-    }
-    k_chol_diag<<<1, 1024, 0, s>>>(A, n, kb, status);
-    note_launches(1);
-    if (below > 0) {
+      k_chol_panel<<<below, 1024, 0, s>>>(A, n, kb, status);
       const int tiles = below * (below + 1) / 2;
-      k_chol_update<<<tiles, 256, 0, s>>>(A, n, kb);
+      k_chol_update<<<tiles + 1, 256, 0, s>>>(A, n, kb);
+      note_launches(2);
+    } else {
+      k_chol_diag<<<1, 1024, 0, s>>>(A, n, kb, status);
       note_launches(1);
     }
   }

@@ -176,8 +176,9 @@ void launch_woodbury_update(const double* H, int m, int64_t N, const double* v, 
 // the same two preconditioner passes with H (and v) stored as double-floats
 int rows_dot_df_chunks(int64_t N);
 void launch_rows_dot_df(const df* A, int m, int64_t N, const df* v, double* partial, cudaStream_t s);
-void launch_woodbury_update_df(const df* H, int m, int64_t N, const double* v, const double* z0, double alpha,
-                               double* z, const double* r, double* partial, cudaStream_t s);
+// returns the number of block partials of r . z written to partial (at most colsum_blocks(N))
+int launch_woodbury_update_df(const df* H, int m, int64_t N, const double* v, const double* z0, double alpha,
+                              double* z, const double* r, double* partial, cudaStream_t s);
 void launch_chol(double* A, int n, int* status, cudaStream_t s);
 // in-place triangular solves with the lower factor L (n x n): x <- L^-1 x, x <- L^-T x
 void launch_trsv_lower(const double* L, int n, double* x, int nrhs, cudaStream_t s);

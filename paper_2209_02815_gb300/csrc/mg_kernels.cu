@@ -400,7 +400,9 @@ __global__ void __launch_bounds__(kThreads) k_apply_op(Level L, double ca, const
 // out = ca * (A p) + cj * sum_i Jd[i][k] w[i], with J as double-floats (the
 // stencil part in FP64); partial[block] = sum_k p_k out_k when partial != null.
 
-template <class D>
+// VEC (N even): each thread takes the two cells 2t, 2t + 1, reading the two entries of each
+// row of Jd with one 16-byte load, with one cascaded sum per cell.
+template <class D, bool VEC>
 __global__ void __launch_bounds__(kThreads) k_apply_op_df(Level L, double ca, const double* __restrict__ p,
                                                           double cj, const df* __restrict__ Jd,
                                                           const double* __restrict__ w, int m,
@@ -409,26 +411,50 @@ __global__ void __launch_bounds__(kThreads) k_apply_op_df(Level L, double ca, co
   extern __shared__ df swd[];
   for (int i = threadIdx.x; i < m; i += blockDim.x) swd[i] = df_from_double(w[i]);
   __syncthreads();
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int kC = VEC ? 2 : 1;
+  const int64_t q0 = kC * t0;
   double prod = 0.0;
-  if (q < L.N) {
-    int i, j, k;
-    decompose(L, q, i, j, k);
-    double dg;
-    double v = ca * D::apply(L, p, i, j, k, q, dg);
+  if (q0 < L.N) {
+    float s[kC], e[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) s[c] = e[c] = 0.f;
     if (m > 0) {
-      float s = 0.f, e = 0.f;
-      const df* col = Jd + q;
-      for (int r = 0; r < m; ++r) {
-        const df t = df_mul(col[(int64_t)r * L.N], swd[r]);
-        const df u = two_sum(s, t.hi);
-        s = u.hi;
-        e = __fadd_rn(e, __fadd_rn(u.lo, t.lo));
+      if (VEC) {
+        const float4* col = reinterpret_cast<const float4*>(Jd + q0);
+        const int64_t stride = L.N / 2;
+        for (int r = 0; r < m; ++r) {
+          const float4 x = col[(int64_t)r * stride];
+          const df wr = swd[r];
+          const df t0_ = df_mul(df_make(x.x, x.y), wr), t1_ = df_mul(df_make(x.z, x.w), wr);
+          df u = two_sum(s[0], t0_.hi);
+          s[0] = u.hi;
+          e[0] = __fadd_rn(e[0], __fadd_rn(u.lo, t0_.lo));
+          u = two_sum(s[kC - 1], t1_.hi);
+          s[kC - 1] = u.hi;
+          e[kC - 1] = __fadd_rn(e[kC - 1], __fadd_rn(u.lo, t1_.lo));
+        }
+      } else {
+        const df* col = Jd + q0;
+        for (int r = 0; r < m; ++r) {
+          const df t = df_mul(col[(int64_t)r * L.N], swd[r]);
+          const df u = two_sum(s[0], t.hi);
+          s[0] = u.hi;
+          e[0] = __fadd_rn(e[0], __fadd_rn(u.lo, t.lo));
+        }
       }
-      v += cj * df_to_double(fast_two_sum(s, e));
     }
-    out[q] = v;
-    prod = p[q] * v;
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+      const int64_t q = q0 + c;
+      int i, j, k;
+      decompose(L, q, i, j, k);
+      double dg;
+      double v = ca * D::apply(L, p, i, j, k, q, dg);
+      if (m > 0) v += cj * df_to_double(fast_two_sum(s[c], e[c]));
+      out[q] = v;
+      prod += p[q] * v;
+    }
   }
   if (partial) {
     const double t = block_sum(prod);
@@ -503,10 +529,17 @@ int apply_op_blocks(const Level& L) { return (int)((L.N + kThreads - 1) / kThrea
 
 void launch_apply_op_df(int disc, const Level& L, double ca, const double* p, double cj, const df* Jd,
                         const double* w, int m, double* out, double* partial, int* nblocks_out, cudaStream_t s) {
-  const int nb = apply_op_blocks(L);
+  const bool vec = L.N % 2 == 0;
+  const int nb = vec ? (int)((L.N / 2 + kThreads - 1) / kThreads) : apply_op_blocks(L);
   if (nblocks_out) *nblocks_out = nb;
   const size_t smem = sizeof(df) * (size_t)(m > 0 ? m : 1);
-  H1W_DISPATCH(disc, k_apply_op_df, <<<nb, kThreads, smem, s>>>(L, ca, p, cj, Jd, w, m, out, partial));
+  if (disc == H1W_FV_CELL) {
+    if (vec) k_apply_op_df<FV, true><<<nb, kThreads, smem, s>>>(L, ca, p, cj, Jd, w, m, out, partial);
+    else k_apply_op_df<FV, false><<<nb, kThreads, smem, s>>>(L, ca, p, cj, Jd, w, m, out, partial);
+  } else {
+    if (vec) k_apply_op_df<Q1, true><<<nb, kThreads, smem, s>>>(L, ca, p, cj, Jd, w, m, out, partial);
+    else k_apply_op_df<Q1, false><<<nb, kThreads, smem, s>>>(L, ca, p, cj, Jd, w, m, out, partial);
+  }
   note_launches(1);
 }
 
