@@ -39,10 +39,10 @@ RTOL = 1e-8
 MAXIT = 1000
 METRIC = "GN linear solves/s at rel-res 1e-8"
 # FP32 instructions per fine cell of the fused double-float legs (isotropic 7-point operator):
-# down 7 (g) + 91 (two Chebyshev steps) + 92 (residual) + 45 (restriction);
-# up 67 (separable prolongation and add) + 99 (r0, d0) + 99 (final update)
-FP32_OPS_DOWN = 235
-FP32_OPS_UP = 265
+# down 7 (g) + 84 (two Chebyshev steps, T folded into gamma) + 92 (residual) + 45 (restriction);
+# up 67 (separable prolongation and add) + 99 (r0, d0) + 92 (final update, T folded into kappa)
+FP32_OPS_DOWN = 228
+FP32_OPS_UP = 258
 # ncu DRAM read + write bytes per fine cell and right-hand side (64^3, 32 RHS, finest up leg):
 # (142.75 + 42.98) MB / (262144 * 32)
 NCU_BYTES_PER_CELL_RHS = {"k_post_fused": (142.751488e6 + 42.976e6) / (262144 * 32)}
@@ -485,6 +485,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (J is %.1f GB)" % (J.numel() * 8 / 1e9)},
         "phases_ms": mean, "pcg_iters": iters, "rel_res_true": rel_true,
         "mg_dof_per_s": float(m) * N / (mean["t_H_ms"] / 1e3),
+        "pcg_only_solves_per_s": world * 1e3 / mean["t_pcg_ms"],
         "arith": ({"operator_and_krylov": "f64", "true_residual": "f64",
                    "vcycle": "double-float (FP32 pairs, ~48 bits)",
                    "capacitance_gemm": "BF16 tensor cores on an exact 48-bit digit split, FP64 accumulation",

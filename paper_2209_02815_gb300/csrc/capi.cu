@@ -92,6 +92,8 @@ struct h1w_ctx {
   int trsv_epoch = 0;
   cudaStream_t copy_stream = nullptr;   // host-to-device copies of h1w_capacitance_from_host
   std::vector<cudaEvent_t> cev;          // one per row batch, plus one for ordering
+  cudaStream_t split_stream = nullptr;  // digit splits of line C, overlapped with the GEMM
+  cudaEvent_t split_ev[4] = {};
   float cat_ms[8];
   int cat_n[8];
   long long launches_cap, launches_pcg;
@@ -339,6 +341,11 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   if (oz) {
     ow.digitsA = B.take<uint16_t>((size_t)8 * ((m_max + 127) / 128 * 128) * kp);
     ow.digitsB = B.take<uint16_t>((size_t)8 * ((m_max + 63) / 64 * 64) * kp);
+    // with more than one K panel, a second pair lets the split of the next panel run
+    // during the GEMM of this one
+    const bool two = N0 > kp;
+    ow.digitsA2 = two ? B.take<uint16_t>((size_t)8 * ((m_max + 127) / 128 * 128) * kp) : nullptr;
+    ow.digitsB2 = two ? B.take<uint16_t>((size_t)8 * ((m_max + 63) / 64 * 64) * kp) : nullptr;
     ow.expo = B.take<int>(2 * (size_t)m_max * ozaki_chunks(N0));
     ow.tiles = B.take<int>(2 * (size_t)ozaki_num_tiles(m_max));
     ow.klen = kp;
@@ -780,6 +787,8 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
         F.del[k] = df_host(it * di);
         F.eta[k] = df_host(beta * di);
         F.kap[k] = df_host(c2 * di);
+        F.gamT[k] = df_host(c2 * it * di * L.Tx);
+        F.kapT[k] = df_host(c2 * di * L.Tx);
       }
       F.T[0] = df_host(L.Tx);
       F.T[1] = df_host(L.Ty);
@@ -892,10 +901,16 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
     cudaMemcpyAsync(c->oz.tiles, c->oz_tiles_host.data(), sizeof(int) * c->oz_tiles_host.size(),
                     cudaMemcpyHostToDevice, c->stream);
     splits = ozaki_splits(m, c->oz.klen, c->num_sms);
+    if (c->oz.digitsA2 && !c->split_stream) {
+      bool made = cudaStreamCreateWithFlags(&c->split_stream, cudaStreamNonBlocking) == cudaSuccess;
+      for (int e = 0; e < 4 && made; ++e)
+        made = cudaEventCreateWithFlags(&c->split_ev[e], cudaEventDisableTiming) == cudaSuccess;
+      if (!made) return fail(c, H1W_ECUDA, "capacitance: cannot create the split stream or its events");
+    }
     c->timing_on = true;
     const bool ok = launch_ozaki_capacitance(
         J, c->H, nullptr, h_df_only ? c->Hdf : nullptr, m, N, c->oz, splits, c->stream, [](void* p) { timed_begin(static_cast<h1w_ctx*>(p)); },
-        [](void* p) { timed_end(static_cast<h1w_ctx*>(p), kCatGemm); }, c);
+        [](void* p) { timed_end(static_cast<h1w_ctx*>(p), kCatGemm); }, c, c->split_stream, c->split_ev);
     c->timing_on = false;
     if (!ok)
       return fail(c, H1W_ECUDA, "capacitance: tensor map encoding or kernel attribute failed");
@@ -1140,6 +1155,12 @@ void h1w_destroy(h1w_ctx* c) {
     cudaStreamDestroy(c->copy_stream);
   }
   for (cudaEvent_t e : c->cev) cudaEventDestroy(e);
+  if (c->split_stream) {
+    cudaStreamSynchronize(c->split_stream);
+    cudaStreamDestroy(c->split_stream);
+    for (int e = 0; e < 4; ++e)
+      if (c->split_ev[e]) cudaEventDestroy(c->split_ev[e]);
+  }
   if (c->have_ev) {
     for (int e = 0; e < 6; ++e) cudaEventDestroy(c->ev[e]);
     for (int t = 0; t < h1w_ctx::kTimed; ++t)

@@ -49,6 +49,7 @@ struct Level {
 // T = face coefficients (Tx, Ty, Tz).
 struct FusedCoef {
   df d[27], dinv[27], gam[27], del[27], eta[27], kap[27];
+  df gamT[27], kapT[27];  // gam T and kap T on isotropic levels (T = T[0] = T[1] = T[2])
   df T[3];
   df beta;
 };
@@ -74,6 +75,8 @@ enum : int { kStatusNotSpd = 1, kStatusTimeout = 2 };
 struct OzakiWork {
   void* digitsA;                 // BF16 digits of a K panel of J, stage-tiled (128-row blocks)
   void* digitsB;                 // BF16 digits of the same panel of H, stage-tiled (64-row blocks)
+  void* digitsA2;                // second pair of panel buffers (null: one pair, no overlap)
+  void* digitsB2;
   int* expo;                     // chunk exponents [N/1024][m] of J, then of H
   int* tiles;                    // [2 * tiles] (row block, column block)
   double* partial;               // [splits][m][m]
@@ -88,11 +91,16 @@ constexpr int kMaxSms = 256;  // SM counts above this are treated as this many
 int ozaki_splits(int m, long long kp, int sms);
 int ozaki_max_splits(int m);
 bool ozaki_supported();
-// Each operand as FP64 (J, H) or, when its double-float copy (Jdf, Hdf) is given, as that. before/after (may be null) are called around each GEMM kernel launch
-// with hook_arg.
+// Each operand as FP64 (J, H) or, when its double-float copy (Jdf, Hdf) is given, as that.
+// before/after (may be null) are called around each GEMM kernel launch with hook_arg.
+// With a second pair of panel buffers in w and an auxiliary stream aux (with the four
+// events ev, disabled timing), the digit split of panel p + 1 runs on aux while the GEMM
+// of panel p runs on s; otherwise everything runs on s in order. Either way all work is
+// ordered after what s had queued before the call, and s ends after all of it.
 bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, const df* Hdf, int m, long long N,
                               const OzakiWork& w, int splits, cudaStream_t s, void (*before)(void*),
-                              void (*after)(void*), void* hook_arg);
+                              void (*after)(void*), void* hook_arg, cudaStream_t aux = nullptr,
+                              cudaEvent_t* ev = nullptr);
 void ozaki_tiles(int m, std::vector<int>& out);
 
 // ---- kernel launchers (mg_kernels.cu) --------------------------------------

@@ -15,6 +15,8 @@
 //            y = x' + eta_c r0 + kap_c N_T(d0),
 //    with the per-class constants of FusedCoef (exact algebra of the two steps
 //    r1 = r0 - A d0, d1 = c1 d0 + c2 D^-1 r1, x += d0 + d1 with d0 = D^-1 r0 / theta).
+//    On isotropic levels N_T is T times the plain neighbour sum, and gam_c T and kap_c T
+//    are formed once on the host, which saves a product per cell in those two steps.
 //  * Values outside the domain are stored as exact zeros in the on-chip
 //    buffers, so the stencils sum all six neighbours without boundary tests;
 //    the neighbour counts only select the class of the constants.
@@ -99,21 +101,25 @@ __device__ __forceinline__ df scale_w(df v, float w) {
   return df_mul_f(v, w);
 }
 
+// Sum of the six face neighbours at idx (isotropic levels, where N_T = T times it).
+__device__ __forceinline__ df nsum6(const df* __restrict__ u0, const df* __restrict__ u1, const df* __restrict__ u2,
+                                   int idx, int W) {
+  dsum s;
+  s.add(u1[idx - 1]);
+  s.add(u1[idx + 1]);
+  s.add(u1[idx - W]);
+  s.add(u1[idx + W]);
+  s.add(u0[idx]);
+  s.add(u2[idx]);
+  return s.get();
+}
+
 // N_T(u) at idx of a plane buffer with rows of W cells (u0, u2: planes below and above);
 // out-of-domain entries hold zeros.
 template <bool ISO>
 __device__ __forceinline__ df nsum(const df* __restrict__ u0, const df* __restrict__ u1, const df* __restrict__ u2,
                                    int idx, int W, df T0, df T1, df T2) {
-  if (ISO) {
-    dsum s;
-    s.add(u1[idx - 1]);
-    s.add(u1[idx + 1]);
-    s.add(u1[idx - W]);
-    s.add(u1[idx + W]);
-    s.add(u0[idx]);
-    s.add(u2[idx]);
-    return df_mul(T0, s.get());
-  }
+  if (ISO) return df_mul(T0, nsum6(u0, u1, u2, idx, W));
   dsum sx, sy, sz;
   sx.add(u1[idx - 1]);
   sx.add(u1[idx + 1]);
@@ -144,7 +150,7 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L,
   for (int i = tid; i < kTab; i += kThr) {
     td[i] = F.d[i];
     tdinv[i] = F.dinv[i];
-    tgam[i] = F.gam[i];
+    tgam[i] = ISO ? F.gamT[i] : F.gam[i];  // isotropic: T folded in, step 2 sums the neighbours only
   }
   const df T0 = F.T[0], T1 = F.T[1], T2 = F.T[2], beta = F.beta;
   const int ntx = (Lc.nx + kTX - 1) / kTX;
@@ -246,7 +252,7 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L,
         if (e < kA2) {
           df xv = dzero();
           if (vin && d2[q] >= 0) {
-            const df n = nsum<ISO>(G0, G1, G2, i3[q], kW3, T0, T1, T2);
+            const df n = ISO ? nsum6(G0, G1, G2, i3[q], kW3) : nsum<false>(G0, G1, G2, i3[q], kW3, T0, T1, T2);
             dsum s;
             s.add(df_mul(beta, G1[i3[q]]));
             s.add(df_mul(tgam[desc_cls(d2[q]) + cz], n));
@@ -360,7 +366,7 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
     td[i] = F.d[i];
     tdel[i] = F.del[i];
     teta[i] = F.eta[i];
-    tkap[i] = F.kap[i];
+    tkap[i] = ISO ? F.kapT[i] : F.kap[i];  // isotropic: T folded in, step 3 sums the neighbours only
   }
   const df T0 = F.T[0], T1 = F.T[1], T2 = F.T[2];
   const int ntx = (Lc.nx + kTX - 1) / kTX;
@@ -548,7 +554,7 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
       for (int q = 0; q < kPI; ++q) {
         if (dI[q] >= 0) {
           const int c = desc_cls(dI[q]) + cz;
-          const df n = nsum<ISO>(D0, D1, D2, iI1[q], kW1, T0, T1, T2);
+          const df n = ISO ? nsum6(D0, D1, D2, iI1[q], kW1) : nsum<false>(D0, D1, D2, iI1[q], kW1, T0, T1, T2);
           dsum s;
           s.add(X1[iI2[q]]);
           s.add(df_mul(teta[c], R1[iI1[q]]));
