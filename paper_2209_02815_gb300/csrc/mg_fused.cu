@@ -76,7 +76,8 @@ constexpr int kP2 = (kA2 + kThr - 1) / kThr;
 constexpr int kP1 = (kA1 + kThr - 1) / kThr;
 constexpr int kTab = 27;
 
-constexpr size_t kPreSmem = sizeof(df) * (3 * kA3 + 3 * kA1 + 3 * kA2 + kA1 + 3 * kTab);
+constexpr int kRX = kH1 * kTX;                                  // fine rows of tile + 1 x coarse columns
+constexpr size_t kPreSmem = sizeof(df) * (3 * kA3 + 3 * kA1 + 3 * kA2 + kA1 + 3 * kTab + 1 + kRX + 2 * kTX);
 constexpr size_t kPostSmem = sizeof(df) * (4 * kA2 + 3 * kA2 + kAX + 3 * kA1 + 2 * kA1 + 4 * kTab);
 
 __device__ __forceinline__ bool in_xy(const Level& L, int i, int j) {
@@ -146,6 +147,8 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L,
   df* td = Rs + kA1;         // d, dinv, gam by class
   df* tdinv = td + kTab;
   df* tgam = tdinv + kTab;
+  df* RX = tgam + kTab + 1;  // residual restricted along x: [fine row of tile + 1][coarse column]
+  float4* wxt = reinterpret_cast<float4*>(RX + kRX);  // P^T weights of each coarse column of the tile
   const int tid = threadIdx.x;
   for (int i = tid; i < kTab; i += kThr) {
     td[i] = F.d[i];
@@ -199,21 +202,20 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L,
   };
   fetch(u_beg);
 
-  // restriction: two threads (lanes 2c, 2c + 1) per coarse cell of the tile, each taking two
-  // of the cell's four fine rows 2J - 1 .. 2J + 2
-  static_assert(2 * kTX * kTY == kThr, "two threads per coarse cell");
-  const int half = tid & 1, cell = tid >> 1;
-  const int Ic = cell % kTX, Jc = cell / kTX;
-  const int gI = C0x + Ic, gJ = C0y + Jc;
-  const bool own = gI < Lc.nx && gJ < Lc.ny;
-  float wx[4], wy[2];
-  {
-    float w4[4];
-    fv_rw(min(gI, Lc.nx - 1), Lc.nx, 1, wx);
-    fv_rw(min(gJ, Lc.ny - 1), Lc.ny, 1, w4);
-    wy[0] = w4[2 * half];
-    wy[1] = w4[2 * half + 1];
+  // restriction, separably: the x pass restricts every fine row of tile + 1 once per coarse
+  // column (weights from wxt); then thread c < kTX kTY takes coarse cell c along y and z
+  static_assert(kTX * kTY <= kThr, "one thread per coarse cell");
+  static_assert(((3 * kA3 + 3 * kA1 + 3 * kA2 + kA1 + 3 * kTab + 1 + kRX) % 2) == 0, "wxt 16-byte aligned");
+  if (tid < kTX) {
+    float w[4];
+    fv_rw(min(C0x + tid, Lc.nx - 1), Lc.nx, 1, w);
+    wxt[tid] = make_float4(w[0], w[1], w[2], w[3]);
   }
+  const int Ic = tid % kTX, Jc = tid / kTX;
+  const int gI = C0x + Ic, gJ = C0y + Jc;
+  const bool own = tid < kTX * kTY && gI < Lc.nx && gJ < Lc.ny;
+  float wy[4];
+  fv_rw(min(gJ, Lc.ny - 1), Lc.ny, 1, wy);
   dsum acc_a, acc_b;  // coarse planes K and K + 1 while fine plane 2K + 1 or 2K + 2 is added
   __syncthreads();
 
@@ -292,27 +294,25 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L,
       __syncthreads();
       // P^T within the plane: coarse column I takes fine columns 2I - 1 .. 2I + 2 (tile + 1
       // columns 2I .. 2I + 3), coarse row J fine rows 2J - 1 .. 2J + 2 (tile + 1 rows 2J .. 2J + 3)
-      dsum sy;
-      if (own) {
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          if (wy[r] != 0.f) {
-            const df* row = Rs + (2 * Jc + 2 * half + r) * kW1 + 2 * Ic;
-            dsum sx;
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-              if (wx[a] != 0.f) sx.add(scale_w(row[a], wx[a]));
-            sy.add(scale_w(sx.get(), wy[r]));
-          }
-        }
+      for (int e = tid; e < kRX; e += kThr) {
+        const int ly = e / kTX, I = e - ly * kTX;
+        const df* row = Rs + ly * kW1 + 2 * I;
+        const float4 w = wxt[I];
+        dsum sx;
+        sx.add(df_mul_f(row[0], w.x));
+        sx.add(df_mul_f(row[1], w.y));
+        sx.add(df_mul_f(row[2], w.z));
+        sx.add(df_mul_f(row[3], w.w));
+        RX[e] = sx.get();
       }
-      // both lanes of a cell form the same sum, rows 0-1 first
-      const df mine = sy.get();
-      const df other = df_make(__shfl_xor_sync(0xffffffffu, mine.hi, 1), __shfl_xor_sync(0xffffffffu, mine.lo, 1));
-      dsum sc;
-      sc.add(half ? other : mine);
-      sc.add(half ? mine : other);
-      const df S = sc.get();
+      __syncthreads();
+      df S = dzero();
+      if (own) {
+        dsum sy;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) sy.add(df_mul_f(RX[(2 * Jc + b) * kTX + Ic], wy[b]));
+        S = sy.get();
+      }
       if (own) {
         float wz[4];
         if (w & 1) {  // w = 2K + 1: tap 2 of coarse plane K, tap 0 of K + 1 (which starts here)
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L,
             fv_rw(K - 1, Lc.nz, 1, wz);
             if (wz[3] != 0.f) acc_a.add(scale_w(S, wz[3]));
           }
-          if (half == 0 && K - 1 >= K0 && K - 1 < K1) cc[(K - 1) * plc + (int64_t)gJ * Lc.nx + gI] = acc_a.get();
+          if (K - 1 >= K0 && K - 1 < K1) cc[(K - 1) * plc + (int64_t)gJ * Lc.nx + gI] = acc_a.get();
           acc_a = acc_b;
         }
       }
