@@ -38,11 +38,15 @@ ALPHA = 1e-3
 RTOL = 1e-8
 MAXIT = 1000
 METRIC = "GN linear solves/s at rel-res 1e-8"
-# FP32 instructions per fine cell of the fused double-float legs (isotropic 7-point operator):
-# down 7 (g) + 84 (two Chebyshev steps, T folded into gamma) + 92 (residual) + 45 (restriction);
-# up 67 (separable prolongation and add) + 99 (r0, d0) + 92 (final update, T folded into kappa)
-FP32_OPS_DOWN = 228
-FP32_OPS_UP = 258
+# FP32 instructions per fine cell of the fused double-float legs (isotropic 7-point operator;
+# double-float product 7, product with a float 6, cascaded-sum term 8, sum result 3):
+# down 7 (g) + 84 (two Chebyshev steps, T folded into gamma) + 92 (residual)
+#   + 51 (separable restriction: x pass 59 per half cell, y pass 59 per quarter cell, z taps 28
+#   per quarter cell);
+# up 55 (separable prolongation: x pass 27 per quarter cell, y pass 27 per half cell, z taps and
+#   the add 35) + 99 (r0, d0) + 92 (final update, T folded into kappa)
+FP32_OPS_DOWN = 234
+FP32_OPS_UP = 246
 # ncu DRAM read + write bytes per fine cell and right-hand side (64^3, 32 RHS, finest up leg):
 # (142.75 + 42.98) MB / (262144 * 32)
 NCU_BYTES_PER_CELL_RHS = {"k_post_fused": (142.751488e6 + 42.976e6) / (262144 * 32)}

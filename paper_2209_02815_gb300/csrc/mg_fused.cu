@@ -408,23 +408,26 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
     iI2[q] = (ly + 2) * kW2 + lx + 2;
   }
 
-  // coarse plane K interpolated to the fine xy cells of tile + 2, x first, then y
-  // (the operand order of the one-kernel prolongation); zeros outside the domain
+  // coarse plane K interpolated to the fine xy cells of tile + 2, x first, then y (the
+  // operand order of the one-kernel prolongation). The 1D weights are 3/4 on the parent
+  // coarse cell and 1/4 on the next one towards the fine cell; clamping that neighbour
+  // to the grid gives the boundary rule (all weight on the parent) without a branch.
+  // Entries for fine cells outside the domain are computed from clamped indices too and
+  // never used: step 1 zeroes them.
   auto interp_x = [&](int K) {
     const bool kin = (K >= 0 && K < Lc.nz);
     for (int e = tid; e < kAX; e += kThr) {
-      const int jl = e / kW2, fl = e % kW2;
-      const int gJ = C0y - 2 + jl, gx = F0x - 2 + fl;
+      const int jl = e / kW2, fl = e - jl * kW2;
+      const int gJ = min(max(C0y - 2 + jl, 0), Lc.ny - 1), gx = F0x - 2 + fl;
+      const int I0 = gx >> 1, I1 = (gx & 1) ? I0 + 1 : I0 - 1;
+      const int c0 = min(max(I0, 0), Lc.nx - 1), c1 = min(max(I1, 0), Lc.nx - 1);
       df v = dzero();
-      if (kin && gJ >= 0 && gJ < Lc.ny && gx >= 0 && gx < L.nx) {
-        int fx[2];
-        float wx[2];
-        const int n_ = fv_prolong_1d(gx, Lc.nx, 1, fx, wx);
+      if (kin) {
         const df* row = cx + K * plc + (int64_t)gJ * Lc.nx;
+        const df a = row[c0], b1 = row[c1];
         dsum s;
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-          if (a < n_) s.add(scale_w(row[fx[a]], wx[a]));
+        s.add(df_mul_f(a, 0.75f));
+        s.add(df_make(b1.hi * 0.25f, b1.lo * 0.25f));
         v = s.get();
       }
       Px[e] = v;
@@ -436,19 +439,15 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
     for (int q = 0; q < kP2; ++q) {
       const int e = tid + q * kThr;
       if (e < kA2) {
-        df v = dzero();
-        if (d2[q] >= 0) {
-          const int gy = F0y - 2 + e / kW2, lx = e % kW2;
-          int fy[2];
-          float wy[2];
-          const int n_ = fv_prolong_1d(gy, Lc.ny, 1, fy, wy);
-          dsum s;
-#pragma unroll
-          for (int a = 0; a < 2; ++a)
-            if (a < n_) s.add(scale_w(Px[(fy[a] - (C0y - 2)) * kW2 + lx], wy[a]));
-          v = s.get();
-        }
-        dst[e] = v;
+        const int ey = e / kW2, lx = e - ey * kW2;
+        const int gy = F0y - 2 + ey;
+        const int J0 = gy >> 1, J1 = (gy & 1) ? J0 + 1 : J0 - 1;
+        const int r0 = min(max(J0, 0), Lc.ny - 1) - (C0y - 2), r1 = min(max(J1, 0), Lc.ny - 1) - (C0y - 2);
+        const df a = Px[r0 * kW2 + lx], b1 = Px[r1 * kW2 + lx];
+        dsum s;
+        s.add(df_mul_f(a, 0.75f));
+        s.add(df_make(b1.hi * 0.25f, b1.lo * 0.25f));
+        dst[e] = s.get();
       }
     }
   };
@@ -493,9 +492,10 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
           df v = dzero();
           if (uin && d2[q] >= 0) {
             dsum s;
+            s.add(px[q]);
             s.add(scale_w(P0[e], wz[0]));
             if (nz_ > 1) s.add(scale_w(P1[e], wz[1]));
-            v = df_add(px[q], s.get());
+            v = s.get();
           }
           Xo[e] = v;
         }
