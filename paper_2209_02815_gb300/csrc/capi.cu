@@ -92,8 +92,8 @@ struct h1w_ctx {
   int trsv_epoch = 0;
   cudaStream_t copy_stream = nullptr;   // host-to-device copies of h1w_capacitance_from_host
   std::vector<cudaEvent_t> cev;          // one per row batch, plus one for ordering
-  cudaStream_t split_stream = nullptr;  // digit splits of line C, overlapped with the GEMM
-  cudaEvent_t split_ev[4] = {};
+  cudaStream_t cycle_stream = nullptr;  // the preconditioner's V-cycle, beside its H^T r pass
+  cudaEvent_t cycle_ev[2] = {};
   float cat_ms[8];
   int cat_n[8];
   long long launches_cap, launches_pcg;
@@ -341,11 +341,6 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   if (oz) {
     ow.digitsA = B.take<uint16_t>((size_t)8 * ((m_max + 127) / 128 * 128) * kp);
     ow.digitsB = B.take<uint16_t>((size_t)8 * ((m_max + 63) / 64 * 64) * kp);
-    // with more than one K panel, a second pair lets the split of the next panel run
-    // during the GEMM of this one
-    const bool two = N0 > kp;
-    ow.digitsA2 = two ? B.take<uint16_t>((size_t)8 * ((m_max + 127) / 128 * 128) * kp) : nullptr;
-    ow.digitsB2 = two ? B.take<uint16_t>((size_t)8 * ((m_max + 63) / 64 * 64) * kp) : nullptr;
     ow.expo = B.take<int>(2 * (size_t)m_max * ozaki_chunks(N0));
     ow.tiles = B.take<int>(2 * (size_t)ozaki_num_tiles(m_max));
     ow.klen = kp;
@@ -563,14 +558,32 @@ void j_times_df(h1w_ctx* c, const double* v, double* out) {
 // z = P^-1 r; when rz_slot >= 0 also scal[rz_slot] = r . z. False if the cycle could not run.
 bool apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
   const int64_t N = c->lev[0].N;
+  const int m = c->m;
+  const bool dfp_ = uses_df(c) && m > 0;
+  // z0 = L-hat^-1 r and s = H^T r (with y = C^-1 s) do not depend on each other: on the
+  // double-float path the cycle, bound by latency, runs on a second stream while the pass,
+  // bound by HBM, runs on the context's; the update z = (z0 - H y / alpha) / alpha joins them
+  const bool side = dfp_ && c->cycle_stream;
   if (uses_df(c)) {                                 // r as double-floats: input of the cycle and of H^T r
     launch_d2df(N, r, c->vdf, c->stream);
-    if (!vcycle_many(c, 1, nullptr, c->vdf, c->z0, nullptr)) return false;
+    if (side) {
+      cudaEventRecord(c->cycle_ev[0], c->stream);
+      cudaStreamWaitEvent(c->cycle_stream, c->cycle_ev[0], 0);
+      const cudaStream_t main = c->stream;
+      c->stream = c->cycle_stream;  // every launch of the cycle goes to the context's stream
+      const bool ok = vcycle_many(c, 1, nullptr, c->vdf, c->z0, nullptr);
+      c->stream = main;
+      cudaEventRecord(c->cycle_ev[1], c->cycle_stream);
+      if (!ok) {
+        cudaStreamWaitEvent(c->stream, c->cycle_ev[1], 0);
+        return false;
+      }
+    } else if (!vcycle_many(c, 1, nullptr, c->vdf, c->z0, nullptr)) {
+      return false;
+    }
   } else {
     vcycle_many(c, 1, r, nullptr, c->z0, nullptr);
   }
-  const int m = c->m;
-  const bool dfp_ = uses_df(c) && m > 0;
   if (m > 0) {
     if (dfp_) {                                     // s = H^T r (double-float pass)
       timed_begin(c);
@@ -595,6 +608,7 @@ bool apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
       launch_trsv_upper_t(c->Lc, m, c->svec, 1, c->stream);
     }
   }
+  if (side) cudaStreamWaitEvent(c->stream, c->cycle_ev[1], 0);  // z0 is ready
   timed_begin(c);
   int nparts = colsum_blocks(N);
   if (dfp_)
@@ -901,16 +915,10 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
     cudaMemcpyAsync(c->oz.tiles, c->oz_tiles_host.data(), sizeof(int) * c->oz_tiles_host.size(),
                     cudaMemcpyHostToDevice, c->stream);
     splits = ozaki_splits(m, c->oz.klen, c->num_sms);
-    if (c->oz.digitsA2 && !c->split_stream) {
-      bool made = cudaStreamCreateWithFlags(&c->split_stream, cudaStreamNonBlocking) == cudaSuccess;
-      for (int e = 0; e < 4 && made; ++e)
-        made = cudaEventCreateWithFlags(&c->split_ev[e], cudaEventDisableTiming) == cudaSuccess;
-      if (!made) return fail(c, H1W_ECUDA, "capacitance: cannot create the split stream or its events");
-    }
     c->timing_on = true;
     const bool ok = launch_ozaki_capacitance(
         J, c->H, nullptr, h_df_only ? c->Hdf : nullptr, m, N, c->oz, splits, c->stream, [](void* p) { timed_begin(static_cast<h1w_ctx*>(p)); },
-        [](void* p) { timed_end(static_cast<h1w_ctx*>(p), kCatGemm); }, c, c->split_stream, c->split_ev);
+        [](void* p) { timed_end(static_cast<h1w_ctx*>(p), kCatGemm); }, c);
     c->timing_on = false;
     if (!ok)
       return fail(c, H1W_ECUDA, "capacitance: tensor map encoding or kernel attribute failed");
@@ -1006,6 +1014,16 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
   const int m = c->m;
   cudaStream_t s = c->stream;
   enum { RZ = 0, PQ = 1, A = 2, RZN = 3, BETA = 4, RR = 5, BB = 6 };
+  if (uses_df(c) && m > 0 && !c->cycle_stream) {
+    // highest priority, so that the cycle's small kernels are not queued behind the blocks
+    // of the pass beside them
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    bool made = cudaStreamCreateWithPriority(&c->cycle_stream, cudaStreamNonBlocking, hi) == cudaSuccess;
+    for (int e = 0; e < 2 && made; ++e)
+      made = cudaEventCreateWithFlags(&c->cycle_ev[e], cudaEventDisableTiming) == cudaSuccess;
+    if (!made) return fail(c, H1W_ECUDA, "pcg: cannot create the cycle stream or its events");
+  }
   const long long l0 = g_kernel_launches.load();
   if (c->have_ev) cudaEventRecord(c->ev[4], s);
   c->nk = 0;
@@ -1155,11 +1173,11 @@ void h1w_destroy(h1w_ctx* c) {
     cudaStreamDestroy(c->copy_stream);
   }
   for (cudaEvent_t e : c->cev) cudaEventDestroy(e);
-  if (c->split_stream) {
-    cudaStreamSynchronize(c->split_stream);
-    cudaStreamDestroy(c->split_stream);
-    for (int e = 0; e < 4; ++e)
-      if (c->split_ev[e]) cudaEventDestroy(c->split_ev[e]);
+  if (c->cycle_stream) {
+    cudaStreamSynchronize(c->cycle_stream);
+    cudaStreamDestroy(c->cycle_stream);
+    for (int e = 0; e < 2; ++e)
+      if (c->cycle_ev[e]) cudaEventDestroy(c->cycle_ev[e]);
   }
   if (c->have_ev) {
     for (int e = 0; e < 6; ++e) cudaEventDestroy(c->ev[e]);

@@ -75,8 +75,6 @@ enum : int { kStatusNotSpd = 1, kStatusTimeout = 2 };
 struct OzakiWork {
   void* digitsA;                 // BF16 digits of a K panel of J, stage-tiled (128-row blocks)
   void* digitsB;                 // BF16 digits of the same panel of H, stage-tiled (64-row blocks)
-  void* digitsA2;                // second pair of panel buffers (null: one pair, no overlap)
-  void* digitsB2;
   int* expo;                     // chunk exponents [N/1024][m] of J, then of H
   int* tiles;                    // [2 * tiles] (row block, column block)
   double* partial;               // [splits][m][m]
@@ -93,14 +91,9 @@ int ozaki_max_splits(int m);
 bool ozaki_supported();
 // Each operand as FP64 (J, H) or, when its double-float copy (Jdf, Hdf) is given, as that.
 // before/after (may be null) are called around each GEMM kernel launch with hook_arg.
-// With a second pair of panel buffers in w and an auxiliary stream aux (with the four
-// events ev, disabled timing), the digit split of panel p + 1 runs on aux while the GEMM
-// of panel p runs on s; otherwise everything runs on s in order. Either way all work is
-// ordered after what s had queued before the call, and s ends after all of it.
 bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, const df* Hdf, int m, long long N,
                               const OzakiWork& w, int splits, cudaStream_t s, void (*before)(void*),
-                              void (*after)(void*), void* hook_arg, cudaStream_t aux = nullptr,
-                              cudaEvent_t* ev = nullptr);
+                              void (*after)(void*), void* hook_arg);
 void ozaki_tiles(int m, std::vector<int>& out);
 
 // ---- kernel launchers (mg_kernels.cu) --------------------------------------

@@ -454,11 +454,8 @@ __device__ __forceinline__ void store_digits(long long (&Y)[8], int row, long lo
 constexpr int kSplitRows = 1;
 constexpr int kSplitThreads = 128 * kSplitRows;
 
-// The launch bound keeps the split at 40 registers per thread, so that two of its blocks fit
-// in the registers a GEMM CTA leaves free on an SM (the split of the next panel runs beside
-// the GEMM of this one).
 template <typename XS>
-__global__ void __launch_bounds__(kSplitThreads, 11) k_split_digits(const XS* __restrict__ X, int m, long long N,
+__global__ void __launch_bounds__(kSplitThreads) k_split_digits(const XS* __restrict__ X, int m, long long N,
                                                                 long long k0, long long kw, long long klen, int R,
                                                                 long long chunk0, int* __restrict__ e,
                                                                 uint16_t* __restrict__ S) {
@@ -583,7 +580,7 @@ bool ozaki_supported() {
 // Returns false when the kernel attribute cannot be set.
 bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, const df* Hdf, int m, long long N,
                               const OzakiWork& w, int splits, cudaStream_t s, void (*before)(void*),
-                              void (*after)(void*), void* hook_arg, cudaStream_t aux, cudaEvent_t* ev) {
+                              void (*after)(void*), void* hook_arg) {
   const long long kp = w.klen;
   const long long nch = (N + kChunkK - 1) / kChunkK;
   int* eA = w.expo;
@@ -594,33 +591,19 @@ bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, c
   const int tiles = ozaki_num_tiles(m);
   long long kcta = (kp + splits - 1) / splits;
   kcta = (kcta + kChunkK - 1) / kChunkK * kChunkK;
-  // ev[0..1]: splits of the panels using buffer pair 0/1 done (on aux); ev[2..3]: GEMMs
-  // using buffer pair 0/1 done (on s). The buffer pair of panel p is p & 1.
-  const bool overlap = aux && ev && w.digitsA2 && w.digitsB2 && N > kp;
-  if (overlap) {
-    cudaEventRecord(ev[0], s);  // the operands are complete once s gets here
-    cudaStreamWaitEvent(aux, ev[0], 0);
-  }
-  const cudaStream_t ss = overlap ? aux : s;
   int panel = 0;
   for (long long k0 = 0; k0 < N; k0 += kp, ++panel) {
     const long long kw = (N - k0) < kp ? (N - k0) : kp;
     const long long chunk0 = k0 / kChunkK;
     const int rowsA = (m + kTileM - 1) / kTileM * kTileM, rowsB = (m + kTileN - 1) / kTileN * kTileN;
     const unsigned gx = static_cast<unsigned>(kp / kChunkK);
-    const int pb = overlap ? (panel & 1) : 0;
-    uint16_t* dA = static_cast<uint16_t*>(pb ? w.digitsA2 : w.digitsA);
-    uint16_t* dB = static_cast<uint16_t*>(pb ? w.digitsB2 : w.digitsB);
-    if (overlap && panel >= 2) cudaStreamWaitEvent(aux, ev[2 + pb], 0);  // GEMM panel - 2 read this pair
+    uint16_t* dA = static_cast<uint16_t*>(w.digitsA);
+    uint16_t* dB = static_cast<uint16_t*>(w.digitsB);
     const dim3 ga(gx, rowsA / kSplitRows), gb(gx, rowsB / kSplitRows);
-    if (Jdf) k_split_digits<df><<<ga, kSplitThreads, 0, ss>>>(Jdf, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
-    else k_split_digits<double><<<ga, kSplitThreads, 0, ss>>>(J, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
-    if (Hdf) k_split_digits<df><<<gb, kSplitThreads, 0, ss>>>(Hdf, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
-    else k_split_digits<double><<<gb, kSplitThreads, 0, ss>>>(H, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
-    if (overlap) {
-      cudaEventRecord(ev[pb], aux);
-      cudaStreamWaitEvent(s, ev[pb], 0);
-    }
+    if (Jdf) k_split_digits<df><<<ga, kSplitThreads, 0, s>>>(Jdf, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
+    else k_split_digits<double><<<ga, kSplitThreads, 0, s>>>(J, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
+    if (Hdf) k_split_digits<df><<<gb, kSplitThreads, 0, s>>>(Hdf, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
+    else k_split_digits<double><<<gb, kSplitThreads, 0, s>>>(H, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
     OzakiArgs a;
     a.dA = dA;
     a.dB = dB;
@@ -638,7 +621,6 @@ bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, c
     if (before) before(hook_arg);
     k_ozaki_gemm<<<dim3(tiles, splits), kGemmThreads, kSmemBytes, s>>>(a);
     if (after) after(hook_arg);
-    if (overlap) cudaEventRecord(ev[2 + pb], s);
     note_launches(3);
   }
   return true;

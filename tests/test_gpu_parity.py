@@ -297,10 +297,8 @@ def test_status_codes():
                          ids=["2panels_m150", "m300", "4panels_m40"])
 def test_tensor_capacitance_matches_fp64(n, m):
     """Line C on the tensor cores against the FP64 CUDA-core GEMM on the same
-    GPU-built H (more than one 262144-wide K panel, ragged tiles; with four panels
-    the split of each panel overlaps the GEMM of the previous one and the two
-    buffer pairs are each reused): the digit split keeps 42 bits of every row, so
-    C agrees to ~1e-11 of ||C||."""
+    GPU-built H (more than one 262144-wide K panel, up to four, ragged tiles): the
+    digit split keeps 42 bits of every row, so C agrees to ~1e-11 of ||C||."""
     h = tuple(1.0 / v for v in n)
     N = int(np.prod(n))
     rng = np.random.default_rng(41)
