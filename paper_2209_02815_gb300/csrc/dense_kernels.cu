@@ -140,7 +140,9 @@ __device__ __forceinline__ df warp_sum_df(df v) {
 // partial[c * m + i] = sum_{k in segment c} A[i * N + k] * v[k], A and v
 // double-floats. A warp covers a segment of kSegDf entries of one row or of a few
 // consecutive rows: lanes stride along the rows (coalesced), each lane accumulates its
-// exact products in cascaded sums, and the warp reduces once at the end.
+// exact products in cascaded sums, and the warp reduces once at the end. Grid: (row
+// groups, segments), row groups fastest, so that blocks running together read the same
+// segment of neighbouring rows (and of v); the other order was 4 % slower.
 constexpr int kSegDf = 8192;
 
 
@@ -160,10 +162,10 @@ template <bool VEC>
 __global__ void __launch_bounds__(kThreads) k_rows_dot_df(const df* __restrict__ A, int m, int64_t N,
                                                           const df* __restrict__ v, double* __restrict__ partial) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t k0 = (int64_t)blockIdx.x * kSegDf;
+  const int64_t k0 = (int64_t)blockIdx.y * kSegDf;
   const int64_t kend = (k0 + kSegDf < N) ? k0 + kSegDf : N;
   if (VEC) {
-    const int row0 = (blockIdx.y * (kThreads / 32) + wid) * kDotRows;
+    const int row0 = (blockIdx.x * (kThreads / 32) + wid) * kDotRows;
     if (row0 >= m) return;
     const float4* v4 = reinterpret_cast<const float4*>(v);
     const float4* a4[kDotRows];
@@ -189,17 +191,17 @@ __global__ void __launch_bounds__(kThreads) k_rows_dot_df(const df* __restrict__
       float s0 = s[r][0], e0 = e[r][0];
       csum_add(s0, e0, fast_two_sum(s[r][1], e[r][1]));
       const df acc = warp_sum_df(fast_two_sum(s0, e0));
-      if (lane == 0 && row0 + r < m) partial[(int64_t)blockIdx.x * m + row0 + r] = df_to_double(acc);
+      if (lane == 0 && row0 + r < m) partial[(int64_t)blockIdx.y * m + row0 + r] = df_to_double(acc);
     }
   } else {
-    const int row = blockIdx.y * (kThreads / 32) + wid;
+    const int row = blockIdx.x * (kThreads / 32) + wid;
     if (row >= m) return;
     const df* a = A + (int64_t)row * N;
     float s = 0.f, e = 0.f;
 #pragma unroll 8
     for (int64_t k = k0 + lane; k < kend; k += 32) csum_add(s, e, df_mul(a[k], v[k]));
     const df acc = warp_sum_df(fast_two_sum(s, e));
-    if (lane == 0) partial[(int64_t)blockIdx.x * m + row] = df_to_double(acc);
+    if (lane == 0) partial[(int64_t)blockIdx.y * m + row] = df_to_double(acc);
   }
 }
 
@@ -784,7 +786,7 @@ int rows_dot_df_chunks(int64_t N) { return (int)((N + kSegDf - 1) / kSegDf); }
 void launch_rows_dot_df(const df* A, int m, int64_t N, const df* v, double* partial, cudaStream_t s) {
   if (m <= 0) return;
   const int rows_per_block = (kThreads / 32) * ((N % 2 == 0) ? kDotRows : 1);
-  dim3 g(rows_dot_df_chunks(N), (m + rows_per_block - 1) / rows_per_block);
+  dim3 g((m + rows_per_block - 1) / rows_per_block, rows_dot_df_chunks(N));
   if (N % 2 == 0) k_rows_dot_df<true><<<g, kThreads, 0, s>>>(A, m, N, v, partial);
   else k_rows_dot_df<false><<<g, kThreads, 0, s>>>(A, m, N, v, partial);
   note_launches(1);
