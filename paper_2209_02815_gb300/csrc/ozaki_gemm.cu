@@ -49,7 +49,6 @@ namespace h1w {
 namespace {
 
 constexpr int kSlices = 8;
-constexpr int kLevels = 8;                 // p + q in 0..7
 constexpr int kTileM = 128;                // rows of J per tile (TMEM lanes)
 constexpr int kTileN = 64;                 // rows of H per tile (columns per level)
 constexpr int kKt = 32;                    // K per stage: 64-byte rows
@@ -351,10 +350,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
 
 // ---- operand split ---------------------------------------------------------------
 
-__device__ __forceinline__ int exp_field(double x) {
-  return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7FF);
-}
-
 __device__ __forceinline__ long long digits_source(double x, int echunk) {
   // Y = round(|x| 2^(47 - e)) with the sign of x (integer arithmetic on the bits)
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
@@ -446,8 +441,9 @@ __device__ __forceinline__ void store_digits(long long (&Y)[8], int row, long lo
 // 4 (row in the group) + 16-byte chunk, so each warp reads row segments of 256 bytes and
 // writes kSplitRows consecutive rows (64 kSplitRows bytes) of a stage image per digit
 // slice. Per row it finds the chunk exponent e with max |x| < 2^e (-100000 for an
-// all-zero chunk), stores it at e[(chunk0 + blockIdx.x) m + row] and writes the digits of
-// x 2^(47 - e). Grid: (klen / 1024, rows rounded up to R / kSplitRows). XS is double
+// all-zero chunk), stores it at e[(chunk0 + blockIdx.y) m + row] and writes the digits of
+// x 2^(47 - e). Grid: (rows rounded up to R / kSplitRows, klen / 1024), rows fastest, so
+// that blocks running together fill neighbouring rows of the same stage images. XS is double
 // (FP64) or df (double-float, value hi + lo: the exponent comes from the high parts, since
 // |hi + lo| <= |hi| (1 + 2^-24) stays within the digit range, and each part is scaled on
 // its own, so the value is represented to within 2^(e - 47)).
@@ -465,9 +461,9 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_digits(const XS* __rest
   __shared__ int smax[kWarps][kSplitRows];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / kGroup, rg = (lane >> 2) % kSplitRows, ch = lane & 3;
-  const int row = blockIdx.y * kSplitRows + rg;
+  const int row = blockIdx.x * kSplitRows + rg;
   const long long kc =
-      static_cast<long long>(blockIdx.x) * kChunkK + (warp * kStagesPerWarp + sub) * kKt + ch * 8;
+      static_cast<long long>(blockIdx.y) * kChunkK + (warp * kStagesPerWarp + sub) * kKt + ch * 8;
   constexpr bool kDf = std::is_same<XS, df>::value;
   XS x[8];
   int best = 0;
@@ -497,8 +493,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_digits(const XS* __rest
   int ech;
   if constexpr (kDf) ech = best ? best - 126 : -100000;
   else ech = best ? best - 1022 : -100000;
-  if (warp == 0 && sub == 0 && ch == 0 && row < m && static_cast<long long>(blockIdx.x) * kChunkK < kw)
-    e[(chunk0 + blockIdx.x) * m + row] = ech;
+  if (warp == 0 && sub == 0 && ch == 0 && row < m && static_cast<long long>(blockIdx.y) * kChunkK < kw)
+    e[(chunk0 + blockIdx.y) * m + row] = ech;
   long long Y[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
@@ -506,11 +502,6 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_digits(const XS* __rest
     else Y[t] = digits_source(x[t], ech);
   }
   store_digits(Y, row, kc, klen, R, S);
-}
-
-__global__ void k_fill_int(int* p, int n, int v) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = v;
 }
 
 }  // namespace
@@ -599,7 +590,7 @@ bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, c
     const unsigned gx = static_cast<unsigned>(kp / kChunkK);
     uint16_t* dA = static_cast<uint16_t*>(w.digitsA);
     uint16_t* dB = static_cast<uint16_t*>(w.digitsB);
-    const dim3 ga(gx, rowsA / kSplitRows), gb(gx, rowsB / kSplitRows);
+    const dim3 ga(rowsA / kSplitRows, gx), gb(rowsB / kSplitRows, gx);
     if (Jdf) k_split_digits<df><<<ga, kSplitThreads, 0, s>>>(Jdf, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
     else k_split_digits<double><<<ga, kSplitThreads, 0, s>>>(J, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
     if (Hdf) k_split_digits<df><<<gb, kSplitThreads, 0, s>>>(Hdf, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
