@@ -47,9 +47,9 @@ METRIC = "GN linear solves/s at rel-res 1e-8"
 #   the add 35) + 99 (r0, d0) + 92 (final update, T folded into kappa)
 FP32_OPS_DOWN = 234
 FP32_OPS_UP = 246
-# ncu DRAM read + write bytes per fine cell and right-hand side (64^3, 32 RHS, finest up leg):
-# (142.75 + 42.98) MB / (262144 * 32)
-NCU_BYTES_PER_CELL_RHS = {"k_post_fused": (142.751488e6 + 42.976e6) / (262144 * 32)}
+# ncu DRAM read + write bytes per fine cell and right-hand side (64^3, 128 RHS, finest up leg
+# of the current build): (599.29 + 242.93) MB / (262144 * 128)
+NCU_BYTES_PER_CELL_RHS = {"k_post_fused": (599.294464e6 + 242.928896e6) / (262144 * 128)}
 def workload(n, m, grid=None):
     proto = "pole-dipole" if grid is None else "dipole-dipole %dx%d grid" % grid
     return "3D ERT GN step, %d^3 cell-centred FV, m=%d %s, alpha=1e-3, FP64" % (n, m, proto)
@@ -473,12 +473,12 @@ def run_ours(args):
     dom = max(table, key=lambda k_: table[k_]["ms_per_step"]) if table else None
     roofline = dict(table[dom], kernel=dom, traffic=None) if dom else None
     # DRAM bytes per launch from one ncu capture of the same kernel build on the 64^3 case
-    # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_fused_legs_64cube_32rhs.md),
+    # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_fused_legs_64cube_128rhs.md),
     # scaled by the cells x right-hand sides of an average launch here; reads equal the
     # algorithmic x, b and coarse-vector bytes there, so traffic grows in proportion
     if roofline and dom.startswith("k_post_fused") and n_up:
         roofline["traffic"] = NCU_BYTES_PER_CELL_RHS["k_post_fused"] * float(m) * N * args.steps / n_up
-        roofline["traffic_note"] = "ncu 64^3 x 32 RHS capture, scaled by cell-RHS per launch"
+        roofline["traffic_note"] = "ncu 64^3 x 128 RHS capture, scaled by cell-RHS per launch"
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
