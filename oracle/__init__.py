@@ -19,6 +19,10 @@ plain (no blocking, fusion or reordering beyond what the definitions state):
   (Algorithm "MINRES with the Laplace-Woodbury preconditioner", lines H/C/chol)
   and the Sherman-Morrison-Woodbury preconditioner apply (Sec. 3.2), the dense
   direct Woodbury solve of Sec. 3.1, and PCG with the Euclidean stopping rule.
+* ``ert``: the ERT forward model of Sec. 4.1 on a cell-centred finite-volume
+  grid (harmonic-mean face conductances, Dirichlet ghosts, unit point
+  currents), its measurements (Eqs. 4.3, 4.5) and Jacobian (Eq. 4.4), by
+  sparse LU solves.
 * ``ccg``: a plain C + OpenMP operator apply and unpreconditioned CG on the
   assembled CSR operator plus the two dense J products (the timed CPU
   baseline).
