@@ -230,6 +230,58 @@ h1w_status h1w_level_info(const h1w_ctx* ctx, int32_t level, int32_t* nlevels, i
 h1w_status h1w_apply_op_static(const h1w_grid* grid, int32_t m, const double* J, const double* p,
                                double* q, void* stream);
 
+/* ---- ERT forward model and Jacobian (Sec. 4.1, Eqs. 4.1-4.5) ------------------
+ *
+ * On the context's H1W_FV_CELL grid, with conductivity sigma = exp(m) per cell:
+ * -div(sigma grad u) = f, face conductance G_k 2 s_a s_b / (s_a + s_b) between
+ * neighbours along axis k (G_k = face area / centre distance), u = 0 on the
+ * box faces marked Dirichlet (the paper's gamma_D; a ghost at half a cell,
+ * conductance 2 G_k s_a) and zero flux on the others. Electrode e injects a unit
+ * current into cell cell[e]; its pole field is u_e = A^-1 e_{cell[e]}.
+ * Measurement i with electrodes abmn[i] = (A, B, M, N), any of them -1 for "at
+ * infinity" (the paper's B electrode of the pole-dipole survey), is
+ *     g_i = k_i (v(cell[M]) - v(cell[N])),  v = u_A - u_B      (Eqs. 4.3, 4.5),
+ * and the Jacobian J = dg/dm of Eq. 4.4 in its discrete form is
+ *     J_ic = -k_i w^T (dA/dm_c) v,  w = u_M - u_N  (reciprocity),
+ * i.e. the exact derivative of the discrete g. */
+#define H1W_ERT_MAX_ELECTRODES 128
+
+typedef struct {
+  int32_t n_e;              /* electrodes, 1..H1W_ERT_MAX_ELECTRODES */
+  const int32_t* cell;      /* HOST [n_e]: level-0 cell index under each electrode */
+  int32_t m;                /* measurements (>= 0) */
+  const int32_t* abmn;      /* HOST [m][4]: electrode indices A, B, M, N (-1 = at infinity) */
+  const double* k;          /* HOST [m]: geometric factors k_i (Eq. 4.5) */
+  uint32_t dirichlet;       /* bit f marks box face f Dirichlet, f = 0..5: x-, x+, y-, y+, z-, z+;
+                               at least one bit (the operator must be definite) */
+} h1w_survey;
+
+/* Bytes of device workspace (256-byte aligned) that h1w_forward and h1w_adjoint
+ * need for n_e electrodes and m measurements on this context's grid: about
+ * (4 FP64 + 5 FP32) vectors per electrode plus the coefficients of every level.
+ * 0 for invalid input or a context that is not H1W_FV_CELL. */
+size_t h1w_ert_workspace_size(const h1w_ctx* ctx, int32_t n_e, int32_t m);
+
+/* Pole fields and measurements for the log-conductivity logsigma (N, DEVICE).
+ * U (DEVICE, [n_e][N], caller-owned) receives the fields u_e, g (DEVICE, [m])
+ * the measurements. The fields are solved together by PCG in FP64 to
+ * ||e_c - A u_e||_2 <= rtol (unit sources), preconditioned by one FP32 V-cycle
+ * on the same operator over the context's hierarchy. The survey's host arrays
+ * are copied before the call returns. info (may be NULL): iterations, and the
+ * worst field's FP64 true and recursive residuals. H1W_ENOTCONV when maxit
+ * iterations do not reach rtol (U holds the iterates), H1W_ENOTSPD when the
+ * coarsest operator fails its Cholesky factorization. Synchronizes. */
+h1w_status h1w_forward(h1w_ctx* ctx, const h1w_survey* survey, const double* logsigma, double* U, double* g,
+                       void* workspace, size_t ws_bytes, double rtol, int32_t maxit, h1w_info* info);
+
+/* The Jacobian from the fields U of h1w_forward (same survey and logsigma):
+ * J (DEVICE, [m][N] row-major, may be NULL) receives every row, and JTr
+ * (DEVICE, [N], may be NULL) receives J^T r for r (DEVICE, [m]), formed without
+ * storing J. At least one of J, JTr. Uses the workspace of h1w_forward (its
+ * fields are not touched). Synchronizes. */
+h1w_status h1w_adjoint(h1w_ctx* ctx, const h1w_survey* survey, const double* logsigma, const double* U,
+                       const double* r, double* JTr, double* J, void* workspace, size_t ws_bytes);
+
 /* Text of the last error on this context (ctx = NULL: the last error of
  * h1w_setup on this thread). Never NULL. */
 const char* h1w_last_error(const h1w_ctx* ctx);

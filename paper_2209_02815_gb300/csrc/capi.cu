@@ -1166,6 +1166,31 @@ const char* h1w_last_error(const h1w_ctx* c) {
   return c->err.c_str();
 }
 
+size_t h1w_ert_workspace_size(const h1w_ctx* c, int32_t n_e, int32_t m) {
+  if (!c || c->disc != H1W_FV_CELL) return 0;
+  return h1w::ert_workspace_bytes(c->lev, c->nlev, n_e, m);
+}
+
+h1w_status h1w_forward(h1w_ctx* c, const h1w_survey* survey, const double* logsigma, double* U, double* g,
+                       void* workspace, size_t ws_bytes, double rtol, int32_t maxit, h1w_info* info) {
+  if (!c) return h1w::set_global_error(H1W_EINVAL, "h1w_forward: NULL context");
+  if (c->disc != H1W_FV_CELL) return fail(c, H1W_EUNSUPPORTED, "h1w_forward: needs an H1W_FV_CELL grid");
+  std::string err;
+  const h1w_status st = h1w::ert_forward(c->lev, c->nlev, c->stream, survey, logsigma, U, g, workspace, ws_bytes,
+                                         rtol, maxit, info, err);
+  return st == H1W_OK ? st : fail(c, st, err);
+}
+
+h1w_status h1w_adjoint(h1w_ctx* c, const h1w_survey* survey, const double* logsigma, const double* U,
+                       const double* r, double* JTr, double* J, void* workspace, size_t ws_bytes) {
+  if (!c) return h1w::set_global_error(H1W_EINVAL, "h1w_adjoint: NULL context");
+  if (c->disc != H1W_FV_CELL) return fail(c, H1W_EUNSUPPORTED, "h1w_adjoint: needs an H1W_FV_CELL grid");
+  std::string err;
+  const h1w_status st =
+      h1w::ert_adjoint(c->lev, c->nlev, c->stream, survey, logsigma, U, r, JTr, J, workspace, ws_bytes, err);
+  return st == H1W_OK ? st : fail(c, st, err);
+}
+
 void h1w_destroy(h1w_ctx* c) {
   if (!c) return;
   if (c->copy_stream) {

@@ -1,0 +1,888 @@
+// The ERT forward model and its Jacobian on the context's finite-volume grid (Sec. 4.1,
+// Eqs. 4.1-4.5): h1w_forward and h1w_adjoint.
+//
+// Model. sigma = exp(m) per cell; the conductance of the face between neighbours a, b
+// along axis k is G_k 2 s_a s_b / (s_a + s_b) (G_k = face area / centre distance, the
+// level's Tx, Ty, Tz); a box face marked Dirichlet (the paper's gamma_D) couples its
+// boundary cells to a ghost value 0 at distance h_k / 2 (conductance 2 G_k s_a), the
+// other box faces are zero-flux. Electrode e injects a unit current into its cell c_e,
+// so the pole field is u_e = A^-1 e_{c_e}, and measurement i with electrodes (A, B, M, N)
+// (-1: at infinity) is g_i = k_i (v(c_M) - v(c_N)), v = u_A - u_B (Eq. 4.3 with the
+// geometric factor of Eq. 4.5). By reciprocity A^-1 (e_M - e_N) = u_M - u_N = w, so the
+// derivative of Eq. 4.4 is J_ic = -k_i w^T (dA / dm_c) v: a sum over the faces of cell c
+// of d(conductance)/dm_c times the jumps of v and w across the face.
+//
+// Forward solve. All n_e pole fields at once by PCG in FP64 (flexible beta, since the
+// preconditioner is applied in FP32) on A, preconditioned by one FP32 V-cycle on the same
+// operator: the context's hierarchy and its trilinear transfers (R = P^T), Chebyshev-
+// Jacobi smoothing of degree 2 on [lambda / 30, lambda] with the Gershgorin bound
+// lambda = 2 of D^-1 A, and coarse operators rediscretized from the geometric mean of
+// the children's conductivities; the coarsest level is solved with a dense inverse from
+// the FP64 Cholesky factor. The operator kernels run one thread per cell over all fields,
+// so the coefficients are read once per sweep.
+//
+// Jacobian. One block takes 32 consecutive cells: it stages the jumps of every field
+// across the six faces of each cell, and the conductance derivatives, in shared memory,
+// then every warp forms J_ic for its measurements with the 32 cells on its lanes. The
+// same kernel accumulates J^T r without storing J.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "h1w_internal.cuh"
+
+namespace h1w {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kJacCells = 32;
+constexpr int kJacWarps = 8;
+constexpr int kDotBlocks = 64;   // partial sums per field in the dot kernels
+constexpr double kLambda = 2.0;  // Gershgorin bound of D^-1 A for this operator
+
+struct Bump {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += sizeof(T) * (count ? count : 1);
+    return p;
+  }
+};
+
+struct Coef32 {
+  const float *tx, *ty, *tz, *dg, *dinv;  // t*: conductance to the + neighbour (0 at the last cell)
+};
+
+struct Layout {
+  int* cell;
+  int4* abmn;
+  double* k;
+  double* sig[kMaxLevels];
+  double *tx64, *ty64, *tz64, *dg64;
+  float *tx[kMaxLevels], *ty[kMaxLevels], *tz[kMaxLevels], *dg[kMaxLevels], *dinv[kMaxLevels];
+  float *x[kMaxLevels], *b[kMaxLevels], *r[kMaxLevels], *da[kMaxLevels], *db[kMaxLevels];
+  double *Ac, *Xc;
+  float* Xf;
+  int* status;
+  double *r64, *z64, *p64, *q64;
+  double* partial;  // [2][n_e][kDotBlocks]
+  double* scal;     // [kScal][n_e]
+};
+
+enum { kRho = 0, kAlpha, kBeta, kRR, kActive, kScal };
+
+size_t layout(Layout& W, char* base, const Level* lev, int nlev, int n_e, int m) {
+  Bump B{base};
+  const int64_t N = lev[0].N;
+  W.cell = B.take<int>(n_e);
+  W.abmn = B.take<int4>(m);
+  W.k = B.take<double>(m);
+  for (int l = 0; l < nlev; ++l) W.sig[l] = B.take<double>(lev[l].N);
+  W.tx64 = B.take<double>(N);
+  W.ty64 = B.take<double>(N);
+  W.tz64 = B.take<double>(N);
+  W.dg64 = B.take<double>(N);
+  for (int l = 0; l < nlev; ++l) {
+    const int64_t n = lev[l].N;
+    W.tx[l] = B.take<float>(n);
+    W.ty[l] = B.take<float>(n);
+    W.tz[l] = B.take<float>(n);
+    W.dg[l] = B.take<float>(n);
+    W.dinv[l] = B.take<float>(n);
+    W.x[l] = B.take<float>(n * n_e);
+    W.b[l] = B.take<float>(n * n_e);
+    W.r[l] = B.take<float>(n * n_e);
+    W.da[l] = B.take<float>(n * n_e);
+    W.db[l] = B.take<float>(n * n_e);
+  }
+  const int64_t nc = lev[nlev - 1].N;
+  W.Ac = B.take<double>(nc * nc);
+  W.Xc = B.take<double>(nc * nc);
+  W.Xf = B.take<float>(nc * nc);
+  W.status = B.take<int>(1);
+  W.r64 = B.take<double>(N * n_e);
+  W.z64 = B.take<double>(N * n_e);
+  W.p64 = B.take<double>(N * n_e);
+  W.q64 = B.take<double>(N * n_e);
+  W.partial = B.take<double>(2 * (size_t)n_e * kDotBlocks);
+  W.scal = B.take<double>((size_t)kScal * n_e);
+  return B.off + 256;
+}
+
+__device__ __forceinline__ void cell_ijk(const Level& L, int64_t p, int& i, int& j, int& k) {
+  i = (int)(p % L.nx);
+  const int64_t q = p / L.nx;
+  j = (int)(q % L.ny);
+  k = (int)(q / L.ny);
+}
+
+__device__ __forceinline__ double harmonic_face(double G, double a, double b) { return G * 2.0 * a * b / (a + b); }
+
+inline unsigned nblk(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+// ---- conductivities and coefficients --------------------------------------------
+
+__global__ void k_exp(int64_t N, const double* __restrict__ m, double* __restrict__ s) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < N) s[p] = exp(m[p]);
+}
+
+// coarse conductivity = geometric mean of the children's
+__global__ void k_coarsen_sigma(Level Lf, Level Lc, const double* __restrict__ sf, double* __restrict__ sc) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Lc.N) return;
+  int I, J, K;
+  cell_ijk(Lc, p, I, J, K);
+  const int nx = Lf.cx ? 2 : 1, ny = Lf.cy ? 2 : 1, nz = Lf.cz ? 2 : 1;
+  double acc = 0.0;
+  for (int c = 0; c < nz; ++c)
+    for (int b = 0; b < ny; ++b)
+      for (int a = 0; a < nx; ++a) {
+        const int64_t f = ((int64_t)(K * nz + c) * Lf.ny + (J * ny + b)) * Lf.nx + (I * nx + a);
+        acc += log(sf[f]);
+      }
+  sc[p] = exp(acc / (nx * ny * nz));
+}
+
+// Conductances to the + neighbours and the diagonal of one level; FP64 copies and the
+// dense matrix (coarsest level) when asked.
+__global__ void k_coef(Level L, const double* __restrict__ sig, unsigned dirichlet, float* tx, float* ty, float* tz,
+                       float* dg, float* dinv, double* tx64, double* ty64, double* tz64, double* dg64, double* A) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  int i, j, k;
+  cell_ijk(L, p, i, j, k);
+  const double s = sig[p];
+  const int64_t sx = 1, sy = L.nx, sz = (int64_t)L.nx * L.ny;
+  const double G[3] = {L.Tx, L.Ty, L.Tz};
+  const int idx[3] = {i, j, k}, n[3] = {L.nx, L.ny, L.nz};
+  const int64_t st[3] = {sx, sy, sz};
+  double tplus[3], d = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double tm = 0.0, tp = 0.0;
+    if (idx[a] > 0) tm = harmonic_face(G[a], s, sig[p - st[a]]);
+    else if (dirichlet >> (2 * a) & 1) d += 2.0 * G[a] * s;
+    if (idx[a] < n[a] - 1) tp = harmonic_face(G[a], s, sig[p + st[a]]);
+    else if (dirichlet >> (2 * a + 1) & 1) d += 2.0 * G[a] * s;
+    d += tm + tp;
+    tplus[a] = tp;
+    if (A) {
+      if (idx[a] > 0) A[p * L.N + p - st[a]] = -tm;
+      if (idx[a] < n[a] - 1) A[p * L.N + p + st[a]] = -tp;
+    }
+  }
+  tx[p] = (float)tplus[0];
+  ty[p] = (float)tplus[1];
+  tz[p] = (float)tplus[2];
+  dg[p] = (float)d;
+  dinv[p] = (float)(1.0 / d);
+  if (tx64) {
+    tx64[p] = tplus[0];
+    ty64[p] = tplus[1];
+    tz64[p] = tplus[2];
+    dg64[p] = d;
+  }
+  if (A) A[p * L.N + p] = d;
+}
+
+// ---- the operator ------------------------------------------------------------------
+
+template <class T>
+struct Stencil {
+  T c, xm, xp, ym, yp, zm, zp;  // diagonal and the six couplings (0 where there is no face)
+  int64_t sy, sz;
+  bool hxm, hxp, hym, hyp, hzm, hzp;
+};
+
+template <class T>
+__device__ __forceinline__ Stencil<T> load_stencil(const Level& L, const T* tx, const T* ty, const T* tz, const T* dg,
+                                                   int64_t p) {
+  int i, j, k;
+  cell_ijk(L, p, i, j, k);
+  Stencil<T> S;
+  S.sy = L.nx;
+  S.sz = (int64_t)L.nx * L.ny;
+  S.hxm = i > 0; S.hxp = i < L.nx - 1;
+  S.hym = j > 0; S.hyp = j < L.ny - 1;
+  S.hzm = k > 0; S.hzp = k < L.nz - 1;
+  S.c = dg[p];
+  S.xp = tx[p]; S.yp = ty[p]; S.zp = tz[p];
+  S.xm = S.hxm ? tx[p - 1] : T(0);
+  S.ym = S.hym ? ty[p - S.sy] : T(0);
+  S.zm = S.hzm ? tz[p - S.sz] : T(0);
+  return S;
+}
+
+template <class T>
+__device__ __forceinline__ T stencil_apply(const Stencil<T>& S, const T* __restrict__ x, int64_t p) {
+  T y = S.c * x[p];
+  if (S.hxm) y -= S.xm * x[p - 1];
+  if (S.hxp) y -= S.xp * x[p + 1];
+  if (S.hym) y -= S.ym * x[p - S.sy];
+  if (S.hyp) y -= S.yp * x[p + S.sy];
+  if (S.hzm) y -= S.zm * x[p - S.sz];
+  if (S.hzp) y -= S.zp * x[p + S.sz];
+  return y;
+}
+
+// y_e = A x_e (FP64, level 0), one thread per cell over all fields
+__global__ void k_apply64(Level L, const double* tx, const double* ty, const double* tz, const double* dg, int nrhs,
+                          const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  const Stencil<double> S = load_stencil<double>(L, tx, ty, tz, dg, p);
+  for (int e = 0; e < nrhs; ++e) y[e * L.N + p] = stencil_apply(S, x + e * L.N, p);
+}
+
+// ---- FP32 V-cycle -------------------------------------------------------------------
+
+__global__ void k_cheb_first32(Level L, Coef32 C, int nrhs, const float* __restrict__ b, float* __restrict__ x,
+                               float* __restrict__ r, float* __restrict__ d, int zero_x, float inv_theta) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
+  const float di = C.dinv[p] * inv_theta;
+  for (int e = 0; e < nrhs; ++e) {
+    const int64_t o = e * L.N;
+    float rv = b[o + p];
+    if (!zero_x) rv -= stencil_apply(S, x + o, p);
+    r[o + p] = rv;
+    d[o + p] = di * rv;
+    if (zero_x) x[o + p] = di * rv;
+  }
+}
+
+__global__ void k_cheb_step32(Level L, Coef32 C, int nrhs, float* __restrict__ r, const float* __restrict__ dold,
+                              float* __restrict__ dnew, float* __restrict__ x, float c1, float c2, int add_old) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
+  const float di = C.dinv[p];
+  for (int e = 0; e < nrhs; ++e) {
+    const int64_t o = e * L.N;
+    const float d0 = dold[o + p];
+    const float rv = r[o + p] - stencil_apply(S, dold + o, p);
+    const float dv = c1 * d0 + c2 * di * rv;
+    r[o + p] = rv;
+    dnew[o + p] = dv;
+    x[o + p] += add_old ? d0 + dv : dv;
+  }
+}
+
+__global__ void k_resid32(Level L, Coef32 C, int nrhs, const float* __restrict__ b, const float* __restrict__ x,
+                          float* __restrict__ r) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
+  for (int e = 0; e < nrhs; ++e) r[e * L.N + p] = b[e * L.N + p] - stencil_apply(S, x + e * L.N, p);
+}
+
+__global__ void k_add32(int64_t n, const float* __restrict__ d, float* __restrict__ x) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) x[p] += d[p];
+}
+
+// Cell-centred trilinear transfer weights of one axis (2:1 agglomeration), as in the
+// context's cycle: prolongation 3/4 from the parent and 1/4 from the parent's
+// neighbour on the child's side (the parent alone at the boundary); R = P^T.
+__device__ __forceinline__ int rst_1d(int I, int nc, int coarsened, int* f, float* w) {
+  if (!coarsened) { f[0] = I; w[0] = 1.f; return 1; }
+  int c = 0;
+  if (I >= 1) { f[c] = 2 * I - 1; w[c++] = 0.25f; }
+  f[c] = 2 * I;     w[c++] = (I >= 1) ? 0.75f : 1.f;
+  f[c] = 2 * I + 1; w[c++] = (I + 1 < nc) ? 0.75f : 1.f;
+  if (I + 1 < nc) { f[c] = 2 * I + 2; w[c++] = 0.25f; }
+  return c;
+}
+
+__device__ __forceinline__ int prl_1d(int i, int nc, int coarsened, int* f, float* w) {
+  if (!coarsened) { f[0] = i; w[0] = 1.f; return 1; }
+  const int I = i >> 1;
+  const int J = (i & 1) ? I + 1 : I - 1;
+  if (J >= 0 && J < nc) { f[0] = I; w[0] = 0.75f; f[1] = J; w[1] = 0.25f; return 2; }
+  f[0] = I; w[0] = 1.f;
+  return 1;
+}
+
+__global__ void k_restrict32(Level Lf, Level Lc, int nrhs, const float* __restrict__ rf, float* __restrict__ bc) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Lc.N) return;
+  int I, J, K;
+  cell_ijk(Lc, p, I, J, K);
+  int fx[4], fy[4], fz[4];
+  float wx[4], wy[4], wz[4];
+  const int nx_ = rst_1d(I, Lc.nx, Lf.cx, fx, wx);
+  const int ny_ = rst_1d(J, Lc.ny, Lf.cy, fy, wy);
+  const int nz_ = rst_1d(K, Lc.nz, Lf.cz, fz, wz);
+  for (int e = 0; e < nrhs; ++e) {
+    const float* r = rf + e * Lf.N;
+    float acc = 0.f;
+    for (int c = 0; c < nz_; ++c)
+      for (int b = 0; b < ny_; ++b) {
+        const float* row = r + ((int64_t)fz[c] * Lf.ny + fy[b]) * Lf.nx;
+        float s = 0.f;
+        for (int a = 0; a < nx_; ++a) s += wx[a] * row[fx[a]];
+        acc += wy[b] * wz[c] * s;
+      }
+    bc[e * Lc.N + p] = acc;
+  }
+}
+
+__global__ void k_prolong_add32(Level Lf, Level Lc, int nrhs, const float* __restrict__ xc, float* __restrict__ xf) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Lf.N) return;
+  int i, j, k;
+  cell_ijk(Lf, p, i, j, k);
+  int fx[2], fy[2], fz[2];
+  float wx[2], wy[2], wz[2];
+  const int nx_ = prl_1d(i, Lc.nx, Lf.cx, fx, wx);
+  const int ny_ = prl_1d(j, Lc.ny, Lf.cy, fy, wy);
+  const int nz_ = prl_1d(k, Lc.nz, Lf.cz, fz, wz);
+  for (int e = 0; e < nrhs; ++e) {
+    const float* c = xc + e * Lc.N;
+    float acc = 0.f;
+    for (int cc = 0; cc < nz_; ++cc)
+      for (int b = 0; b < ny_; ++b) {
+        const float* row = c + ((int64_t)fz[cc] * Lc.ny + fy[b]) * Lc.nx;
+        float s = 0.f;
+        for (int a = 0; a < nx_; ++a) s += wx[a] * row[fx[a]];
+        acc += wy[b] * wz[cc] * s;
+      }
+    xf[e * Lf.N + p] += acc;
+  }
+}
+
+// x_e = X b_e on the coarsest level (X: dense inverse, n x n, FP32)
+__global__ void k_dense_apply32(const float* __restrict__ X, int n, const float* __restrict__ b, float* __restrict__ x) {
+  extern __shared__ float sb[];
+  const int e = blockIdx.y;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) sb[j] = b[(int64_t)e * n + j];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* row = X + (int64_t)i * n;
+  float acc = 0.f;
+  for (int j = 0; j < n; ++j) acc += row[j] * sb[j];
+  x[(int64_t)e * n + i] = acc;
+}
+
+__global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) b[p] = (float)a[p];
+}
+
+// ---- PCG vector kernels (FP64, grid: (kDotBlocks, fields)) ---------------------------
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+  __syncthreads();
+  return s;
+}
+
+// x = 0, r = e_{c_e}, b32 = (float) r
+__global__ void k_init(int64_t N, const int* __restrict__ cell, double* __restrict__ x, double* __restrict__ r,
+                       float* __restrict__ b32) {
+  const int e = blockIdx.y;
+  const int c = cell[e];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (p == c) ? 1.0 : 0.0;
+    x[e * N + p] = 0.0;
+    r[e * N + p] = v;
+    b32[e * N + p] = (float)v;
+  }
+}
+
+// partial[0] = a . b, partial[1] = c . d (when c is given), per field
+__global__ void k_dots(int64_t N, const double* __restrict__ a, const double* __restrict__ b,
+                       const double* __restrict__ c, const double* __restrict__ d, double* __restrict__ partial) {
+  __shared__ double red[kThreads / 32];
+  const int e = blockIdx.y, ne = gridDim.y;
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = e * N + p;
+    s0 += a[o] * b[o];
+    if (c) s1 += c[o] * d[o];
+  }
+  s0 = block_sum(s0, red);
+  s1 = block_sum(s1, red);
+  if (threadIdx.x == 0) {
+    partial[(int64_t)e * gridDim.x + blockIdx.x] = s0;
+    partial[((int64_t)ne + e) * gridDim.x + blockIdx.x] = s1;
+  }
+}
+
+// z = (double) z32; partials r . z and z . q
+__global__ void k_z_dots(int64_t N, const float* __restrict__ z32, double* __restrict__ z, const double* __restrict__ r,
+                         const double* __restrict__ q, double* __restrict__ partial) {
+  __shared__ double red[kThreads / 32];
+  const int e = blockIdx.y, ne = gridDim.y;
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = e * N + p;
+    const double zv = (double)z32[o];
+    z[o] = zv;
+    s0 += r[o] * zv;
+    if (q) s1 += zv * q[o];
+  }
+  s0 = block_sum(s0, red);
+  s1 = block_sum(s1, red);
+  if (threadIdx.x == 0) {
+    partial[(int64_t)e * gridDim.x + blockIdx.x] = s0;
+    partial[((int64_t)ne + e) * gridDim.x + blockIdx.x] = s1;
+  }
+}
+
+// x += alpha p; r -= alpha q; b32 = (float) r; partial r . r
+__global__ void k_xr(int64_t N, const double* __restrict__ scal, double* __restrict__ x, double* __restrict__ r,
+                     const double* __restrict__ p_, const double* __restrict__ q, float* __restrict__ b32,
+                     double* __restrict__ partial) {
+  __shared__ double red[kThreads / 32];
+  const int e = blockIdx.y, ne = gridDim.y;
+  const double a = scal[kAlpha * ne + e];
+  double s0 = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = e * N + p;
+    x[o] += a * p_[o];
+    const double rv = r[o] - a * q[o];
+    r[o] = rv;
+    b32[o] = (float)rv;
+    s0 += rv * rv;
+  }
+  s0 = block_sum(s0, red);
+  if (threadIdx.x == 0) partial[(int64_t)e * gridDim.x + blockIdx.x] = s0;
+}
+
+// p = z + beta p
+__global__ void k_pupd(int64_t N, const double* __restrict__ scal, const double* __restrict__ z, double* __restrict__ p_) {
+  const int e = blockIdx.y, ne = gridDim.y;
+  const double be = scal[kBeta * ne + e];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = e * N + p;
+    p_[o] = z[o] + be * p_[o];
+  }
+}
+
+// Per-field scalar updates from the partial sums (one thread per field).
+// mode 0: rho = r.z (start); 1: alpha = rho / p.q (0 once converged or at breakdown);
+// 2: rr = r.r, active = rr > tol2; 3: beta = z.(r - r_old) / rho = -alpha z.q / rho (the
+// flexible form, since r - r_old = -alpha q), rho = r.z.
+__global__ void k_scalars(int mode, int ne, int nb, const double* __restrict__ partial, double* __restrict__ scal,
+                          double tol2) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    s0 += partial[(int64_t)e * nb + b];
+    s1 += partial[((int64_t)ne + e) * nb + b];
+  }
+  double* S = scal;
+  if (mode == 0) {
+    S[kRho * ne + e] = s0;
+    S[kActive * ne + e] = 1.0;
+  } else if (mode == 1) {
+    const double rho = S[kRho * ne + e];
+    S[kAlpha * ne + e] = (S[kActive * ne + e] != 0.0 && s0 > 0.0 && rho > 0.0) ? rho / s0 : 0.0;
+  } else if (mode == 2) {
+    S[kRR * ne + e] = s0;
+    if (!(s0 > tol2)) S[kActive * ne + e] = 0.0;
+  } else {
+    const double rho = S[kRho * ne + e];
+    const double a = S[kAlpha * ne + e];
+    S[kBeta * ne + e] = (rho > 0.0 && S[kActive * ne + e] != 0.0) ? -a * s1 / rho : 0.0;
+    S[kRho * ne + e] = s0;
+  }
+}
+
+// ---- measurements and the Jacobian ---------------------------------------------------
+
+__device__ __forceinline__ double field_at(const double* U, int64_t N, const int* cell, int e, int f) {
+  return (e >= 0 && f >= 0) ? U[(int64_t)e * N + cell[f]] : 0.0;
+}
+
+__global__ void k_measure(const double* __restrict__ U, int64_t N, const int* __restrict__ cell,
+                          const int4* __restrict__ abmn, const double* __restrict__ k, int m, double* __restrict__ g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int4 q = abmn[i];
+  const double vm = field_at(U, N, cell, q.x, q.z) - field_at(U, N, cell, q.y, q.z);
+  const double vn = field_at(U, N, cell, q.x, q.w) - field_at(U, N, cell, q.y, q.w);
+  g[i] = k[i] * (vm - vn);
+}
+
+// Shared layout: D[e][face][cell] jumps u_e(c) - u_e(neighbour) (u_e(c) across a Dirichlet
+// face, 0 across a zero-flux one), then W[face][cell] = d(conductance)/dm_c, then the
+// warps' partial sums of J^T r.
+template <bool ROWS>
+__global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const double* __restrict__ U, int ne,
+                                                             const double* __restrict__ sig, unsigned dirichlet,
+                                                             const int4* __restrict__ abmn, const double* __restrict__ kf,
+                                                             int m, const double* __restrict__ rv, double* __restrict__ J,
+                                                             double* __restrict__ JTr) {
+  extern __shared__ double sm[];
+  double* D = sm;
+  double* Wf = D + (size_t)ne * 6 * kJacCells;
+  double* red = Wf + 6 * kJacCells;
+  const int64_t N = L.N;
+  const int64_t p0 = (int64_t)blockIdx.x * kJacCells;
+  const int64_t st[3] = {1, L.nx, (int64_t)L.nx * L.ny};
+  const int nn[3] = {L.nx, L.ny, L.nz};
+  const double G[3] = {L.Tx, L.Ty, L.Tz};
+  for (int t = threadIdx.x; t < 6 * kJacCells; t += blockDim.x) {
+    const int f = t / kJacCells, c = t % kJacCells;
+    const int64_t p = p0 + c;
+    double w = 0.0;
+    if (p < N) {
+      int ijk[3];
+      cell_ijk(L, p, ijk[0], ijk[1], ijk[2]);
+      const int a = f >> 1, side = f & 1;
+      const bool inside = side ? ijk[a] < nn[a] - 1 : ijk[a] > 0;
+      const double s = sig[p];
+      if (inside) {
+        const double o = sig[side ? p + st[a] : p - st[a]];
+        const double den = s + o;
+        w = G[a] * 2.0 * s * o * o / (den * den);
+      } else if (dirichlet >> f & 1) {
+        w = 2.0 * G[a] * s;
+      }
+    }
+    Wf[t] = w;
+  }
+  for (int t = threadIdx.x; t < ne * kJacCells; t += blockDim.x) {
+    const int e = t / kJacCells, c = t % kJacCells;
+    const int64_t p = p0 + c;
+    double* De = D + (size_t)e * 6 * kJacCells;
+    if (p < N) {
+      int ijk[3];
+      cell_ijk(L, p, ijk[0], ijk[1], ijk[2]);
+      const double* u = U + (int64_t)e * N;
+      const double up = u[p];
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        const int a = f >> 1, side = f & 1;
+        const bool inside = side ? ijk[a] < nn[a] - 1 : ijk[a] > 0;
+        De[f * kJacCells + c] = inside ? up - u[side ? p + st[a] : p - st[a]] : up;  // W is 0 on zero-flux faces
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < 6; ++f) De[f * kJacCells + c] = 0.0;
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, c = threadIdx.x & 31;
+  const int64_t p = p0 + c;
+  double w6[6];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) w6[f] = Wf[f * kJacCells + c];
+  double acc_r = 0.0;
+  for (int i = warp; i < m; i += kJacWarps) {
+    const int4 q = abmn[i];
+    const double* DA = q.x >= 0 ? D + (size_t)q.x * 6 * kJacCells + c : nullptr;
+    const double* DB = q.y >= 0 ? D + (size_t)q.y * 6 * kJacCells + c : nullptr;
+    const double* DM = q.z >= 0 ? D + (size_t)q.z * 6 * kJacCells + c : nullptr;
+    const double* DN = q.w >= 0 ? D + (size_t)q.w * 6 * kJacCells + c : nullptr;
+    double acc = 0.0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const double dv = (DA ? DA[f * kJacCells] : 0.0) - (DB ? DB[f * kJacCells] : 0.0);
+      const double dw = (DM ? DM[f * kJacCells] : 0.0) - (DN ? DN[f * kJacCells] : 0.0);
+      acc += w6[f] * dv * dw;
+    }
+    const double val = -kf[i] * acc;
+    if (ROWS) {
+      if (p < N) J[(int64_t)i * N + p] = val;
+    } else {
+      acc_r += rv[i] * val;
+    }
+  }
+  if (!ROWS) {
+    red[warp * kJacCells + c] = acc_r;
+    __syncthreads();
+    if (warp == 0 && p < N) {
+      double s = 0.0;
+      for (int w = 0; w < kJacWarps; ++w) s += red[w * kJacCells + c];
+      JTr[p] = s;
+    }
+  }
+}
+
+size_t jac_smem(int ne) { return sizeof(double) * ((size_t)ne * 6 * kJacCells + 6 * kJacCells + kJacWarps * kJacCells); }
+
+// ---- host driver ---------------------------------------------------------------------
+
+struct Cheb {
+  float inv_theta, c1, c2;
+};
+
+Cheb cheb_coefs() {
+  const double lo = kLambda / 30.0, hi = kLambda;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sg = theta / delta;
+  const double rho0 = 1.0 / sg;
+  const double rho1 = 1.0 / (2.0 * sg - rho0);
+  return Cheb{(float)(1.0 / theta), (float)(rho1 * rho0), (float)(2.0 * rho1 / delta)};
+}
+
+Coef32 coef_of(const Layout& W, int l) { return Coef32{W.tx[l], W.ty[l], W.tz[l], W.dg[l], W.dinv[l]}; }
+
+void smooth32(const Layout& W, const Level* lev, int l, int ne, const Cheb& K, const float* b, float* x, bool zero_x,
+              cudaStream_t s) {
+  const Level& L = lev[l];
+  const Coef32 C = coef_of(W, l);
+  k_cheb_first32<<<nblk(L.N), kThreads, 0, s>>>(L, C, ne, b, x, W.r[l], W.da[l], zero_x ? 1 : 0, K.inv_theta);
+  k_cheb_step32<<<nblk(L.N), kThreads, 0, s>>>(L, C, ne, W.r[l], W.da[l], W.db[l], x, K.c1, K.c2, zero_x ? 0 : 1);
+  note_launches(2);
+}
+
+// x0 = one V-cycle on b0 (level-0 buffers W.b[0] -> W.x[0])
+void vcycle32(const Layout& W, const Level* lev, int nl, int ne, cudaStream_t s) {
+  const Cheb K = cheb_coefs();
+  for (int l = 0; l < nl - 1; ++l) {
+    smooth32(W, lev, l, ne, K, W.b[l], W.x[l], true, s);
+    k_resid32<<<nblk(lev[l].N), kThreads, 0, s>>>(lev[l], coef_of(W, l), ne, W.b[l], W.x[l], W.r[l]);
+    k_restrict32<<<nblk(lev[l + 1].N), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
+    note_launches(2);
+  }
+  const int nc = (int)lev[nl - 1].N;
+  k_dense_apply32<<<dim3((nc + kThreads - 1) / kThreads, ne), kThreads, sizeof(float) * nc, s>>>(W.Xf, nc, W.b[nl - 1],
+                                                                                                  W.x[nl - 1]);
+  note_launches(1);
+  for (int l = nl - 2; l >= 0; --l) {
+    k_prolong_add32<<<nblk(lev[l].N), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.x[l + 1], W.x[l]);
+    note_launches(1);
+    smooth32(W, lev, l, ne, K, W.b[l], W.x[l], false, s);
+  }
+}
+
+h1w_status validate_survey(const Level* lev, const h1w_survey* sv, std::string& err) {
+  if (!sv || sv->n_e < 1 || sv->n_e > H1W_ERT_MAX_ELECTRODES || sv->m < 0 || !sv->cell ||
+      (sv->m > 0 && (!sv->abmn || !sv->k))) {
+    err = "survey: need 1..H1W_ERT_MAX_ELECTRODES electrodes, m >= 0 and non-NULL arrays";
+    return H1W_EINVAL;
+  }
+  if (sv->dirichlet == 0 || sv->dirichlet >= 64u) {
+    err = "survey: dirichlet must mark at least one of the six box faces (bits 0..5)";
+    return H1W_EINVAL;
+  }
+  for (int e = 0; e < sv->n_e; ++e)
+    if (sv->cell[e] < 0 || sv->cell[e] >= lev[0].N) {
+      err = "survey: electrode cell out of range";
+      return H1W_EINVAL;
+    }
+  for (int64_t q = 0; q < 4 * (int64_t)sv->m; ++q)
+    if (sv->abmn[q] < -1 || sv->abmn[q] >= sv->n_e) {
+      err = "survey: electrode index out of range in abmn";
+      return H1W_EINVAL;
+    }
+  return H1W_OK;
+}
+
+h1w_status check_cuda(cudaStream_t s, std::string& err, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return H1W_ECUDA;
+  }
+  return H1W_OK;
+}
+
+h1w_status upload_survey(const Layout& W, const h1w_survey* sv, cudaStream_t s) {
+  cudaMemcpyAsync(W.cell, sv->cell, sizeof(int) * sv->n_e, cudaMemcpyHostToDevice, s);
+  if (sv->m > 0) {
+    cudaMemcpyAsync(W.abmn, sv->abmn, sizeof(int4) * sv->m, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(W.k, sv->k, sizeof(double) * sv->m, cudaMemcpyHostToDevice, s);
+  }
+  return H1W_OK;
+}
+
+// Conductivities and operator coefficients of every level; the coarsest level's dense inverse.
+h1w_status build_operator(const Layout& W, const Level* lev, int nl, const double* logsigma, unsigned dirichlet,
+                          cudaStream_t s, std::string& err) {
+  k_exp<<<nblk(lev[0].N), kThreads, 0, s>>>(lev[0].N, logsigma, W.sig[0]);
+  note_launches(1);
+  for (int l = 1; l < nl; ++l) {
+    k_coarsen_sigma<<<nblk(lev[l].N), kThreads, 0, s>>>(lev[l - 1], lev[l], W.sig[l - 1], W.sig[l]);
+    note_launches(1);
+  }
+  const int nc = (int)lev[nl - 1].N;
+  cudaMemsetAsync(W.Ac, 0, sizeof(double) * nc * nc, s);
+  for (int l = 0; l < nl; ++l) {
+    const bool top = l == 0, bottom = l == nl - 1;
+    k_coef<<<nblk(lev[l].N), kThreads, 0, s>>>(lev[l], W.sig[l], dirichlet, W.tx[l], W.ty[l], W.tz[l], W.dg[l],
+                                               W.dinv[l], top ? W.tx64 : nullptr, top ? W.ty64 : nullptr,
+                                               top ? W.tz64 : nullptr, top ? W.dg64 : nullptr, bottom ? W.Ac : nullptr);
+    note_launches(1);
+  }
+  cudaMemsetAsync(W.status, 0, sizeof(int), s);
+  launch_chol(W.Ac, nc, W.status, s);
+  launch_set_identity(W.Xc, nc, s);
+  launch_trsv_lower(W.Ac, nc, W.Xc, nc, s);
+  launch_trsv_upper_t(W.Ac, nc, W.Xc, nc, s);
+  launch_symmetrize_identity_solve(W.Xc, nc, s);
+  k_d2f<<<nblk((int64_t)nc * nc), kThreads, 0, s>>>((int64_t)nc * nc, W.Xc, W.Xf);
+  note_launches(1);
+  int status = 0;
+  cudaMemcpyAsync(&status, W.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  h1w_status st = check_cuda(s, err, "ert operator");
+  if (st != H1W_OK) return st;
+  if (status & kStatusNotSpd) {
+    err = "ert: coarsest-level matrix is not positive definite";
+    return H1W_ENOTSPD;
+  }
+  return H1W_OK;
+}
+
+}  // namespace
+
+size_t ert_workspace_bytes(const Level* lev, int nlev, int n_e, int m) {
+  if (n_e < 1 || n_e > H1W_ERT_MAX_ELECTRODES || m < 0) return 0;
+  Layout W;
+  return layout(W, nullptr, lev, nlev, n_e, m);
+}
+
+h1w_status ert_forward(const Level* lev, int nl, cudaStream_t s, const h1w_survey* sv, const double* logsigma,
+                       double* U, double* g, void* ws, size_t ws_bytes, double rtol, int maxit, h1w_info* info,
+                       std::string& err) {
+  h1w_status st = validate_survey(lev, sv, err);
+  if (st != H1W_OK) return st;
+  if (!logsigma || !U || (sv->m > 0 && !g) || !ws || !(rtol > 0.0) || maxit < 1) {
+    err = "h1w_forward: NULL logsigma/U/g/workspace, rtol <= 0 or maxit < 1";
+    return H1W_EINVAL;
+  }
+  const int ne = sv->n_e;
+  Layout W;
+  if (layout(W, nullptr, lev, nl, ne, sv->m) > ws_bytes) {
+    err = "h1w_forward: workspace smaller than h1w_ert_workspace_size";
+    return H1W_EINVAL;
+  }
+  layout(W, static_cast<char*>(ws), lev, nl, ne, sv->m);
+  upload_survey(W, sv, s);
+  st = build_operator(W, lev, nl, logsigma, sv->dirichlet, s, err);
+  if (st != H1W_OK) return st;
+
+  const Level& L0 = lev[0];
+  const int64_t N = L0.N;
+  const dim3 vg(kDotBlocks, ne);
+  const unsigned sb = (unsigned)((ne + 127) / 128);
+  const double tol2 = rtol * rtol;  // ||f_e|| = 1
+  std::vector<double> rr(ne);
+  k_init<<<vg, kThreads, 0, s>>>(N, W.cell, U, W.r64, W.b[0]);
+  vcycle32(W, lev, nl, ne, s);
+  k_z_dots<<<vg, kThreads, 0, s>>>(N, W.x[0], W.z64, W.r64, nullptr, W.partial);
+  k_scalars<<<sb, 128, 0, s>>>(0, ne, kDotBlocks, W.partial, W.scal, tol2);
+  cudaMemcpyAsync(W.p64, W.z64, sizeof(double) * N * ne, cudaMemcpyDeviceToDevice, s);
+  note_launches(3);
+  int it = 0;
+  bool done = false;
+  double worst = 1.0;
+  while (!done && it < maxit) {
+    ++it;
+    k_apply64<<<nblk(N), kThreads, 0, s>>>(L0, W.tx64, W.ty64, W.tz64, W.dg64, ne, W.p64, W.q64);
+    k_dots<<<vg, kThreads, 0, s>>>(N, W.p64, W.q64, nullptr, nullptr, W.partial);
+    k_scalars<<<sb, 128, 0, s>>>(1, ne, kDotBlocks, W.partial, W.scal, tol2);
+    k_xr<<<vg, kThreads, 0, s>>>(N, W.scal, U, W.r64, W.p64, W.q64, W.b[0], W.partial);
+    k_scalars<<<sb, 128, 0, s>>>(2, ne, kDotBlocks, W.partial, W.scal, tol2);
+    note_launches(5);
+    cudaMemcpyAsync(rr.data(), W.scal + kRR * ne, sizeof(double) * ne, cudaMemcpyDeviceToHost, s);
+    st = check_cuda(s, err, "h1w_forward");
+    if (st != H1W_OK) return st;
+    worst = 0.0;
+    for (int e = 0; e < ne; ++e) worst = std::max(worst, rr[e]);
+    if (!(worst == worst)) {
+      err = "h1w_forward: NaN residual";
+      return H1W_ENOTCONV;
+    }
+    if (worst <= tol2) {
+      done = true;
+      break;
+    }
+    vcycle32(W, lev, nl, ne, s);
+    k_z_dots<<<vg, kThreads, 0, s>>>(N, W.x[0], W.z64, W.r64, W.q64, W.partial);
+    k_scalars<<<sb, 128, 0, s>>>(3, ne, kDotBlocks, W.partial, W.scal, tol2);
+    k_pupd<<<vg, kThreads, 0, s>>>(N, W.scal, W.z64, W.p64);
+    note_launches(3);
+  }
+  if (sv->m > 0) {
+    k_measure<<<(sv->m + 127) / 128, 128, 0, s>>>(U, N, W.cell, W.abmn, W.k, sv->m, g);
+    note_launches(1);
+  }
+  if (info) {
+    // true residual ||e_{c_e} - A u_e|| in FP64, worst field
+    k_apply64<<<nblk(N), kThreads, 0, s>>>(L0, W.tx64, W.ty64, W.tz64, W.dg64, ne, U, W.q64);
+    k_init<<<vg, kThreads, 0, s>>>(N, W.cell, W.z64, W.r64, W.b[0]);
+    note_launches(2);
+    cudaMemcpyAsync(W.p64, W.q64, sizeof(double) * N * ne, cudaMemcpyDeviceToDevice, s);
+    launch_axpby(W.p64, 1.0, W.r64, -1.0, N * ne, s);  // p = r - q
+    k_dots<<<vg, kThreads, 0, s>>>(N, W.p64, W.p64, nullptr, nullptr, W.partial);
+    k_scalars<<<sb, 128, 0, s>>>(2, ne, kDotBlocks, W.partial, W.scal, 0.0);
+    note_launches(2);
+    cudaMemcpyAsync(rr.data(), W.scal + kRR * ne, sizeof(double) * ne, cudaMemcpyDeviceToHost, s);
+    st = check_cuda(s, err, "h1w_forward");
+    if (st != H1W_OK) return st;
+    double tw = 0.0;
+    for (int e = 0; e < ne; ++e) tw = std::max(tw, rr[e]);
+    info->iters = it;
+    info->restarts = 0;
+    info->rel_res_true = std::sqrt(tw);
+    info->rel_res_rec = std::sqrt(worst);
+  } else {
+    st = check_cuda(s, err, "h1w_forward");
+    if (st != H1W_OK) return st;
+  }
+  if (!done) {
+    err = "h1w_forward: PCG did not reach rtol within maxit";
+    return H1W_ENOTCONV;
+  }
+  return H1W_OK;
+}
+
+h1w_status ert_adjoint(const Level* lev, int nl, cudaStream_t s, const h1w_survey* sv, const double* logsigma,
+                       const double* U, const double* r, double* JTr, double* J, void* ws, size_t ws_bytes,
+                       std::string& err) {
+  h1w_status st = validate_survey(lev, sv, err);
+  if (st != H1W_OK) return st;
+  if (!logsigma || !U || !ws || (JTr && !r) || (!JTr && !J)) {
+    err = "h1w_adjoint: NULL logsigma/U/workspace, JTr without r, or neither JTr nor J";
+    return H1W_EINVAL;
+  }
+  const int ne = sv->n_e;
+  Layout W;
+  if (layout(W, nullptr, lev, nl, ne, sv->m) > ws_bytes) {
+    err = "h1w_adjoint: workspace smaller than h1w_ert_workspace_size";
+    return H1W_EINVAL;
+  }
+  layout(W, static_cast<char*>(ws), lev, nl, ne, sv->m);
+  upload_survey(W, sv, s);
+  const Level& L0 = lev[0];
+  k_exp<<<nblk(L0.N), kThreads, 0, s>>>(L0.N, logsigma, W.sig[0]);
+  note_launches(1);
+  const size_t smem = jac_smem(ne);
+  const unsigned grid = (unsigned)((L0.N + kJacCells - 1) / kJacCells);
+  if (J) {
+    cudaFuncSetAttribute(k_jacobian<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobian<true><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.k, sv->m,
+                                                        nullptr, J, nullptr);
+    note_launches(1);
+  }
+  if (JTr) {
+    cudaFuncSetAttribute(k_jacobian<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobian<false><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.k, sv->m, r,
+                                                         nullptr, JTr);
+    note_launches(1);
+  }
+  return check_cuda(s, err, "h1w_adjoint");
+}
+
+}  // namespace h1w

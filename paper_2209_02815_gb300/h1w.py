@@ -58,6 +58,12 @@ class Info(ctypes.Structure):
                 ("rel_res_true", ctypes.c_double), ("rel_res_rec", ctypes.c_double)]
 
 
+class SurveyC(ctypes.Structure):
+    _fields_ = [("n_e", ctypes.c_int32), ("cell", ctypes.POINTER(ctypes.c_int32)), ("m", ctypes.c_int32),
+                ("abmn", ctypes.POINTER(ctypes.c_int32)), ("k", ctypes.POINTER(ctypes.c_double)),
+                ("dirichlet", ctypes.c_uint32)]
+
+
 _lib = None
 
 
@@ -91,6 +97,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "h1w_apply_op_static": (I32, [G, I32, P, P, P, P]),
         "h1w_solve_batch": (I32, [ctypes.POINTER(P), I32, ctypes.POINTER(I32), ctypes.POINTER(P),
                                   ctypes.POINTER(P), ctypes.POINTER(P), D, I32, I32, IN, ctypes.POINTER(I32)]),
+        "h1w_ert_workspace_size": (SZ, [P, I32, I32]),
+        "h1w_forward": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, SZ, D, I32, IN]),
+        "h1w_adjoint": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, SZ]),
         "h1w_last_error": (ctypes.c_char_p, [P]),
         "h1w_destroy": (None, [P]),
     }
@@ -257,6 +266,61 @@ def h1w_apply_op_static(grid: Grid, m: int, J: torch.Tensor | None, p: torch.Ten
                                       _ptr(p, N, "p"), _ptr(q, N, "q"), s), None)
 
 
+class Survey:
+    """An ERT survey in the layout of h1w_survey: electrode cells (n_e,), measurements
+    abmn (m, 4) with -1 for an electrode at infinity, geometric factors k (m,), and
+    the Dirichlet box faces as a bit mask (bit f: x-, x+, y-, y+, z-, z+)."""
+
+    def __init__(self, cells, abmn, k, dirichlet: int):
+        import numpy as np
+        self.cells = np.ascontiguousarray(np.asarray(cells, dtype=np.int32))
+        self.abmn = np.ascontiguousarray(np.asarray(abmn, dtype=np.int32).reshape(-1, 4))
+        self.k = np.ascontiguousarray(np.asarray(k, dtype=np.float64))
+        if self.k.shape[0] != self.abmn.shape[0]:
+            raise ValueError("k needs one entry per measurement")
+        self.dirichlet = int(dirichlet)
+        c = SurveyC()
+        c.n_e = self.cells.size
+        c.cell = self.cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        c.m = self.abmn.shape[0]
+        c.abmn = self.abmn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        c.k = self.k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        c.dirichlet = self.dirichlet
+        self.c = c
+
+    @property
+    def n_e(self) -> int:
+        return int(self.cells.size)
+
+    @property
+    def m(self) -> int:
+        return int(self.abmn.shape[0])
+
+
+def h1w_ert_workspace_size(ctx, n_e: int, m: int) -> int:
+    return int(load().h1w_ert_workspace_size(ctx, n_e, m))
+
+
+def h1w_forward(ctx, survey: Survey, logsigma: torch.Tensor, U: torch.Tensor, g: torch.Tensor | None,
+                ws: torch.Tensor, rtol: float, maxit: int, N: int, raise_on_notconv: bool = True) -> Info:
+    info = Info()
+    st = load().h1w_forward(ctx, ctypes.byref(survey.c), _ptr(logsigma, N, "logsigma"),
+                            _ptr(U, N * survey.n_e, "U"), _ptr(g, survey.m, "g"), ws.data_ptr(), ws.numel(),
+                            rtol, maxit, ctypes.byref(info))
+    if st == H1W_ENOTCONV and not raise_on_notconv:
+        return info
+    _check(st, ctx)
+    return info
+
+
+def h1w_adjoint(ctx, survey: Survey, logsigma: torch.Tensor, U: torch.Tensor, r: torch.Tensor | None,
+                JTr: torch.Tensor | None, J: torch.Tensor | None, ws: torch.Tensor, N: int) -> None:
+    st = load().h1w_adjoint(ctx, ctypes.byref(survey.c), _ptr(logsigma, N, "logsigma"),
+                            _ptr(U, N * survey.n_e, "U"), _ptr(r, survey.m, "r"), _ptr(JTr, N, "JTr"),
+                            _ptr(J, N * survey.m, "J"), ws.data_ptr(), ws.numel())
+    _check(st, ctx)
+
+
 def h1w_destroy(ctx) -> None:
     if ctx:
         load().h1w_destroy(ctx)
@@ -359,6 +423,36 @@ class Solver:
             self._leave()
         return x, info
 
+    def ert_workspace(self, survey: Survey) -> torch.Tensor:
+        size = h1w_ert_workspace_size(self.ctx, survey.n_e, survey.m)
+        if size == 0:
+            raise H1wError(H1W_EINVAL, "invalid survey size or grid for h1w_ert_workspace_size")
+        return torch.empty(size, dtype=torch.uint8, device=self.workspace.device)
+
+    def forward(self, survey: Survey, logsigma, rtol: float = 1e-10, maxit: int = 200, ws=None, U=None):
+        """Pole fields U (n_e, N) and measurements g (m,) of the ERT model (h1w_forward)."""
+        ws = self.ert_workspace(survey) if ws is None else ws
+        U = torch.empty((survey.n_e, self.N), dtype=torch.float64, device=logsigma.device) if U is None else U
+        g = torch.empty(survey.m, dtype=torch.float64, device=logsigma.device)
+        self._enter(logsigma, U, g, ws)
+        try:
+            info = h1w_forward(self.ctx, survey, logsigma, U, g, ws, rtol, maxit, self.N)
+        finally:
+            self._leave()
+        return g, U, info
+
+    def adjoint(self, survey: Survey, logsigma, U, r=None, rows: bool = False, ws=None):
+        """J^T r (when r is given) and the rows of J (when rows) from the fields U (h1w_adjoint)."""
+        ws = self.ert_workspace(survey) if ws is None else ws
+        JTr = torch.empty(self.N, dtype=torch.float64, device=U.device) if r is not None else None
+        J = torch.empty((survey.m, self.N), dtype=torch.float64, device=U.device) if rows else None
+        self._enter(logsigma, U, r, JTr, J, ws)
+        try:
+            h1w_adjoint(self.ctx, survey, logsigma, U, r, JTr, J, ws, self.N)
+        finally:
+            self._leave()
+        return JTr, J
+
     def factors(self):
         m = self.m or 0
         C = torch.empty((m, m), dtype=torch.float64, device=self.workspace.device)
@@ -385,3 +479,22 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class ErtForward(torch.autograd.Function):
+    """g = ERT measurements of logsigma (h1w_forward); the backward pass is J^T grad_g
+    (h1w_adjoint), formed from the saved pole fields without storing J."""
+
+    @staticmethod
+    def forward(ctx, logsigma, solver: Solver, survey: Survey, rtol: float = 1e-10, maxit: int = 200):
+        ls = logsigma.detach().contiguous()
+        g, U, _ = solver.forward(survey, ls, rtol=rtol, maxit=maxit)
+        ctx.solver, ctx.survey = solver, survey
+        ctx.save_for_backward(ls, U)
+        return g
+
+    @staticmethod
+    def backward(ctx, grad_g):
+        ls, U = ctx.saved_tensors
+        JTr, _ = ctx.solver.adjoint(ctx.survey, ls, U, r=grad_g.detach().contiguous())
+        return JTr, None, None, None, None

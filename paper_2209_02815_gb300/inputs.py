@@ -166,6 +166,37 @@ def dipole_dipole_grid(ex: int, ey: int, m_max: int) -> np.ndarray:
     return np.asarray(rows, dtype=np.int64)
 
 
+def electrode_cells(n_cells: int, electrodes: np.ndarray, h: float) -> np.ndarray:
+    """Index of the top-layer (z = 0) cell under each surface electrode (x, y, 0)."""
+    i = np.minimum((electrodes[:, 0] / h).astype(np.int64), n_cells - 1)
+    j = np.minimum((electrodes[:, 1] / h).astype(np.int64), n_cells - 1)
+    return (j * n_cells + i).astype(np.int32)
+
+
+# Dirichlet (u = 0) on every box face but the surface z = 0 (bits x-, x+, y-, y+, z+)
+ERT_DIRICHLET_ALL_BUT_TOP = 0b101111
+
+
+def ert_survey(n: int, n_e_line: int = 32, grid: tuple[int, int] | None = None,
+               m_rows: int | None = None):
+    """Electrode cells, (A, B, M, N) rows (-1 = at infinity) and geometric factors of
+    the surveys used by ``ert_problem``: the line pair protocol (B at infinity) or
+    the dipole-dipole grid. Returns (cells, abmn, k, electrodes)."""
+    h = 1.0 / n
+    if grid is None:
+        el = line_electrodes(n, n_e_line, h)
+        prot = pair_protocol(n_e_line)
+        if m_rows is not None:
+            prot = prot[:m_rows]
+        abmn = np.stack([prot[:, 0], np.full(len(prot), -1), prot[:, 1], prot[:, 2]], axis=1)
+        k = geometric_factor_pole_dipole(el[prot[:, 0]], el[prot[:, 1]], el[prot[:, 2]])
+    else:
+        el = grid_electrodes(n, grid[0], grid[1], h)
+        abmn = dipole_dipole_grid(grid[0], grid[1], m_rows or 10 ** 9)
+        k = geometric_factor_dipole_dipole(el[abmn[:, 0]], el[abmn[:, 1]], el[abmn[:, 2]], el[abmn[:, 3]])
+    return electrode_cells(n, el, h), abmn.astype(np.int32), k, el
+
+
 def geometric_factor_pole_dipole(xa, xm, xn) -> np.ndarray:
     """3D geometric factor with B at infinity (limit of Eq. 4.5)."""
     am = np.linalg.norm(xa - xm, axis=-1)
