@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--grid", default=None,
                     help="electrode grid EXxEY on the top face with the dipole-dipole protocol (e.g. 8x8)")
     ap.add_argument("--m-rows", type=int, default=None, help="truncate the protocol to this many measurements")
+    ap.add_argument("--ert", action="store_true",
+                    help="time the ERT model evaluation (h1w_forward + h1w_adjoint J rows) instead")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of the ERT step: a batch of this many independent 2D Q1 systems "
                          "(sides 128..1024, m 8..256, alpha log-uniform 1e-4..1e-1) solved by h1w_solve_batch")
@@ -280,6 +282,142 @@ def run_batch(args):
            "pcg_iters": [int(i.iters) for i in infos], "max_rel_res_true": max(float(i.rel_res_true) for i in infos),
            "clocks": clocks, "timing": "host wall clock around whole batches (each call synchronizes)",
            "impl": "ours"}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+# ----------------------------------------------------------------------------
+# ERT model evaluation: pole fields, measurements and all rows of J (Sec. 4.1)
+# ----------------------------------------------------------------------------
+
+ERT_RTOL = 1e-10
+# nominal FP64 rate of the recipe's table (1.25 TFLOP/s), as FP64 instructions (FMA = 1)
+FP64_INST_PEAK_T = 1.25 / 2
+
+
+def ert_oracle_sample(n_side: int, ne: int, budget_s: float) -> dict:
+    """The oracle's evaluation (sparse LU pole fields, g, J rows) on an n_side^3 grid
+    with the same survey design, timed on the host cores."""
+    import numpy as np
+    from oracle import ert as oert
+    from paper_2209_02815_gb300 import inputs
+    cells, abmn, k, _ = inputs.ert_survey(n_side, n_e_line=ne)
+    field, _ = inputs.gaussian_random_field((n_side,) * 3, (1.0 / n_side,) * 3, 0.1, math.log(0.01), 1.0, 0)
+    ls = field.reshape(-1)
+    h = (1.0 / n_side,) * 3
+    t0 = time.perf_counter()
+    g, U = oert.forward((n_side,) * 3, h, ls, cells, abmn, k, inputs.ERT_DIRICHLET_ALL_BUT_TOP)
+    t1 = time.perf_counter()
+    rows = max(1, min(len(abmn), int(len(abmn) * budget_s / max(1e-3, 4 * (t1 - t0)))))
+    oert.jacobian((n_side,) * 3, h, ls, U, abmn[:rows], k[:rows], inputs.ERT_DIRICHLET_ALL_BUT_TOP)
+    t2 = time.perf_counter()
+    return {"fields_s": t1 - t0, "rows_timed": rows, "rows_s": t2 - t1,
+            "eval_s": (t1 - t0) + (t2 - t1) * len(abmn) / rows, "m": int(len(abmn)), "n": n_side}
+
+
+def run_ert(args):
+    import numpy as np
+    import torch
+    from paper_2209_02815_gb300 import h1w, inputs
+
+    world, rank, local = dist_init(args)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    n = args.n
+    N = n ** 3
+    grid = electrode_grid(args)
+    cells, abmn, k, _ = inputs.ert_survey(n, n_e_line=args.ne, grid=grid, m_rows=args.m_rows)
+    sv = h1w.Survey(cells, abmn, k, inputs.ERT_DIRICHLET_ALL_BUT_TOP)
+    field, _ = inputs.gaussian_random_field((n,) * 3, (1.0 / n,) * 3, 0.1, math.log(0.01), 1.0, inputs.SEED_FIELD)
+    with torch.cuda.stream(stream):
+        S = h1w.Solver(h1w.H1W_FV_CELL, (n, n, n), (1.0 / n,) * 3, ALPHA, 1, device=dev, stream=stream)
+        ls = torch.as_tensor(field.reshape(-1), device=dev)
+        ws = S.ert_workspace(sv)
+        U = torch.empty((sv.n_e, N), dtype=torch.float64, device=dev)
+        J = torch.empty((sv.m, N), dtype=torch.float64, device=dev)
+        g = torch.empty(sv.m, dtype=torch.float64, device=dev)
+
+        def step():
+            info = h1w.h1w_forward(S.ctx, sv, ls, U, g, ws, ERT_RTOL, 200, N)
+            h1w.h1w_adjoint(S.ctx, sv, ls, U, None, None, J, ws, N)
+            return info
+
+        for _ in range(args.warmup):
+            info = step()
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = ClockSampler(local)
+        clk.start()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+        ev[0].record(stream)
+        iters = []
+        for i in range(args.steps):
+            info = h1w.h1w_forward(S.ctx, sv, ls, U, g, ws, ERT_RTOL, 200, N)
+            ev[2 * i + 1].record(stream)
+            h1w.h1w_adjoint(S.ctx, sv, ls, U, None, None, J, ws, N)
+            ev[2 * i + 2].record(stream)
+            iters.append(int(info.iters))
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        ms = allmax(world, ev[0].elapsed_time(ev[-1]))
+        fwd = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)]
+        jac = [ev[2 * i + 1].elapsed_time(ev[2 * i + 2]) for i in range(args.steps)]
+
+        # end to end through the public API: logsigma from pinned host memory, g back to it
+        ls_host = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        ls_host.copy_(ls)
+        g_host = torch.empty(sv.m, dtype=torch.float64, pin_memory=True)
+        ls_dev = torch.empty_like(ls)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            ls_dev.copy_(ls_host, non_blocking=True)
+            h1w.h1w_forward(S.ctx, sv, ls_dev, U, g, ws, ERT_RTOL, 200, N)
+            h1w.h1w_adjoint(S.ctx, sv, ls_dev, U, None, None, J, ws, N)
+            g_host.copy_(g, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = allmax(world, e0.elapsed_time(e1)) if args.e2e_steps else None
+
+    m = sv.m
+    groups = int(np.sum(np.any(np.diff(abmn[:, :2], axis=0) != 0, axis=1)) + 1)
+    n_full = int(np.sum((abmn[:, 2] >= 0) & (abmn[:, 3] >= 0)))
+    # FP64 instructions of the J-row kernel: per row and cell 6 faces x (subtraction + FMA)
+    # (one electrode of the receiver pair at infinity: no subtraction) + the scaling by -k_i;
+    # per source and cell 6 products W_f (D_A - D_B)
+    fp64_inst = N * (n_full * 13 + (m - n_full) * 7 + groups * 6)
+    jac_ms = float(np.median(jac))
+    ach = fp64_inst / (jac_ms / 1e3) / 1e12
+    value = world * args.steps / (ms / 1e3)
+    out = {"metric": "ERT model evaluations/s (pole fields, g and all rows of J)", "value": value,
+           "unit": "evaluations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "ERT forward model and Jacobian, %d^3 FV cells, %d electrodes, m = %d "
+                                  "(%s), GRF log-conductivity, PCG rtol %g" %
+                                  (n, sv.n_e, m, "dipole-dipole grid" if grid else "line pair protocol",
+                                   ERT_RTOL),
+                      "n": [n, n, n], "n_e": sv.n_e, "m": m, "l2": "inputs larger than L2 (fields "
+                      "%.1f GB, J %.1f GB)" % (sv.n_e * N * 8 / 1e9, m * N * 8 / 1e9)},
+           "forward_ms": float(np.median(fwd)), "jacobian_rows_ms": jac_ms, "pcg_iters": iters,
+           "rel_res_true": float(info.rel_res_true),
+           "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_INST_PEAK_T, "unit": "T FP64 inst/s",
+                        "frac": ach / FP64_INST_PEAK_T, "traffic": None, "kernel": "k_jacobian<rows>",
+                        "note": "FP64 instructions of the J-row kernel (%d per launch) / its event time; "
+                                "peak = nominal 1.25 TFLOP/s FP64 as FMA instructions" % fp64_inst},
+           "clocks": clocks, "impl": "ours"}
+    if e2e_ms:
+        out["e2e"] = {"value": world * args.e2e_steps / (e2e_ms / 1e3), "unit": "evaluations/s",
+                      "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": m * 8, "steps": args.e2e_steps}
+    if rank == 0 and not args.no_cpu_baseline:
+        smp = ert_oracle_sample(32, args.ne if grid is None else args.ne, args.cpu_sample_s)
+        out["cpu_baseline"] = {"value": 1.0 / (smp["eval_s"] * N / 32 ** 3), "unit": "evaluations/s",
+                               "kind": "oracle", "cores": os.cpu_count(),
+                               "sample": "oracle on a 32^3 grid with the same survey design (sparse LU "
+                                         "fields, g, %d of %d J rows timed), scaled linearly in cells to "
+                                         "%d^3: an upper bound, since the LU grows faster than linearly"
+                                         % (smp["rows_timed"], smp["m"], n), "detail": smp}
     if rank == 0:
         print(json.dumps(out))
 
@@ -558,6 +696,8 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.ert:
+        run_ert(a)
     elif a.batch > 0:
         run_batch(a)
     else:

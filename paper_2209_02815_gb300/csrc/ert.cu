@@ -290,72 +290,81 @@ __global__ void k_add32(int64_t n, const float* __restrict__ d, float* __restric
 
 // Cell-centred trilinear transfer weights of one axis (2:1 agglomeration), as in the
 // context's cycle: prolongation 3/4 from the parent and 1/4 from the parent's
-// neighbour on the child's side (the parent alone at the boundary); R = P^T.
-__device__ __forceinline__ int rst_1d(int I, int nc, int coarsened, int* f, float* w) {
-  if (!coarsened) { f[0] = I; w[0] = 1.f; return 1; }
-  int c = 0;
-  if (I >= 1) { f[c] = 2 * I - 1; w[c++] = 0.25f; }
-  f[c] = 2 * I;     w[c++] = (I >= 1) ? 0.75f : 1.f;
-  f[c] = 2 * I + 1; w[c++] = (I + 1 < nc) ? 0.75f : 1.f;
-  if (I + 1 < nc) { f[c] = 2 * I + 2; w[c++] = 0.25f; }
-  return c;
+// neighbour on the child's side (the parent alone at the boundary); R = P^T. Both
+// footprints have a fixed size (4 fine cells per coarse cell, 2 coarse cells per fine
+// cell) with in-range indices and weight 0 where a point does not exist, so the loops
+// unroll and all loads of a thread are independent.
+__device__ __forceinline__ void rst_1d(int I, int nc, int coarsened, int f[4], float w[4]) {
+  if (!coarsened) {
+    f[0] = f[1] = f[2] = f[3] = I;
+    w[0] = 1.f; w[1] = w[2] = w[3] = 0.f;
+    return;
+  }
+  const bool lo = I >= 1, hi = I + 1 < nc;
+  f[0] = lo ? 2 * I - 1 : 2 * I;
+  f[1] = 2 * I;
+  f[2] = 2 * I + 1;
+  f[3] = hi ? 2 * I + 2 : 2 * I + 1;
+  w[0] = lo ? 0.25f : 0.f;
+  w[1] = lo ? 0.75f : 1.f;
+  w[2] = hi ? 0.75f : 1.f;
+  w[3] = hi ? 0.25f : 0.f;
 }
 
-__device__ __forceinline__ int prl_1d(int i, int nc, int coarsened, int* f, float* w) {
-  if (!coarsened) { f[0] = i; w[0] = 1.f; return 1; }
+__device__ __forceinline__ void prl_1d(int i, int nc, int coarsened, int f[2], float w[2]) {
+  if (!coarsened) { f[0] = f[1] = i; w[0] = 1.f; w[1] = 0.f; return; }
   const int I = i >> 1;
   const int J = (i & 1) ? I + 1 : I - 1;
-  if (J >= 0 && J < nc) { f[0] = I; w[0] = 0.75f; f[1] = J; w[1] = 0.25f; return 2; }
-  f[0] = I; w[0] = 1.f;
-  return 1;
+  const bool has = J >= 0 && J < nc;
+  f[0] = I; f[1] = has ? J : I;
+  w[0] = has ? 0.75f : 1.f; w[1] = has ? 0.25f : 0.f;
 }
 
-__global__ void k_restrict32(Level Lf, Level Lc, int nrhs, const float* __restrict__ rf, float* __restrict__ bc) {
+// grid: (coarse cells / 256, fields)
+__global__ void k_restrict32(Level Lf, Level Lc, const float* __restrict__ rf, float* __restrict__ bc) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= Lc.N) return;
   int I, J, K;
   cell_ijk(Lc, p, I, J, K);
   int fx[4], fy[4], fz[4];
   float wx[4], wy[4], wz[4];
-  const int nx_ = rst_1d(I, Lc.nx, Lf.cx, fx, wx);
-  const int ny_ = rst_1d(J, Lc.ny, Lf.cy, fy, wy);
-  const int nz_ = rst_1d(K, Lc.nz, Lf.cz, fz, wz);
-  for (int e = 0; e < nrhs; ++e) {
-    const float* r = rf + e * Lf.N;
-    float acc = 0.f;
-    for (int c = 0; c < nz_; ++c)
-      for (int b = 0; b < ny_; ++b) {
-        const float* row = r + ((int64_t)fz[c] * Lf.ny + fy[b]) * Lf.nx;
-        float s = 0.f;
-        for (int a = 0; a < nx_; ++a) s += wx[a] * row[fx[a]];
-        acc += wy[b] * wz[c] * s;
-      }
-    bc[e * Lc.N + p] = acc;
-  }
+  rst_1d(I, Lc.nx, Lf.cx, fx, wx);
+  rst_1d(J, Lc.ny, Lf.cy, fy, wy);
+  rst_1d(K, Lc.nz, Lf.cz, fz, wz);
+  const float* r = rf + (int64_t)blockIdx.y * Lf.N;
+  float acc = 0.f;
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float* row = r + ((int64_t)fz[c] * Lf.ny + fy[b]) * Lf.nx;
+      const float s = wx[0] * row[fx[0]] + wx[1] * row[fx[1]] + wx[2] * row[fx[2]] + wx[3] * row[fx[3]];
+      acc += wy[b] * wz[c] * s;
+    }
+  bc[(int64_t)blockIdx.y * Lc.N + p] = acc;
 }
 
-__global__ void k_prolong_add32(Level Lf, Level Lc, int nrhs, const float* __restrict__ xc, float* __restrict__ xf) {
+// grid: (fine cells / 256, fields)
+__global__ void k_prolong_add32(Level Lf, Level Lc, const float* __restrict__ xc, float* __restrict__ xf) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= Lf.N) return;
   int i, j, k;
   cell_ijk(Lf, p, i, j, k);
   int fx[2], fy[2], fz[2];
   float wx[2], wy[2], wz[2];
-  const int nx_ = prl_1d(i, Lc.nx, Lf.cx, fx, wx);
-  const int ny_ = prl_1d(j, Lc.ny, Lf.cy, fy, wy);
-  const int nz_ = prl_1d(k, Lc.nz, Lf.cz, fz, wz);
-  for (int e = 0; e < nrhs; ++e) {
-    const float* c = xc + e * Lc.N;
-    float acc = 0.f;
-    for (int cc = 0; cc < nz_; ++cc)
-      for (int b = 0; b < ny_; ++b) {
-        const float* row = c + ((int64_t)fz[cc] * Lc.ny + fy[b]) * Lc.nx;
-        float s = 0.f;
-        for (int a = 0; a < nx_; ++a) s += wx[a] * row[fx[a]];
-        acc += wy[b] * wz[cc] * s;
-      }
-    xf[e * Lf.N + p] += acc;
-  }
+  prl_1d(i, Lc.nx, Lf.cx, fx, wx);
+  prl_1d(j, Lc.ny, Lf.cy, fy, wy);
+  prl_1d(k, Lc.nz, Lf.cz, fz, wz);
+  const float* c = xc + (int64_t)blockIdx.y * Lc.N;
+  float acc = 0.f;
+#pragma unroll
+  for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float* row = c + ((int64_t)fz[cc] * Lc.ny + fy[b]) * Lc.nx;
+      acc += wy[b] * wz[cc] * (wx[0] * row[fx[0]] + wx[1] * row[fx[1]]);
+    }
+  xf[(int64_t)blockIdx.y * Lf.N + p] += acc;
 }
 
 // x_e = X b_e on the coarsest level (X: dense inverse, n x n, FP32)
@@ -586,25 +595,43 @@ __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const doub
   double w6[6];
 #pragma unroll
   for (int f = 0; f < 6; ++f) w6[f] = Wf[f * kJacCells + c];
+  // The measurements of a warp mostly share their source (A, B) with the previous one
+  // (survey rows are ordered by source), so t_f = W_f (D_A - D_B) is formed once per
+  // source and each row costs one subtraction and one FMA per face.
   double acc_r = 0.0;
+  int la = -2, lb = -2;
+  double t6[6];
   for (int i = warp; i < m; i += kJacWarps) {
     const int4 q = abmn[i];
-    const double* DA = q.x >= 0 ? D + (size_t)q.x * 6 * kJacCells + c : nullptr;
-    const double* DB = q.y >= 0 ? D + (size_t)q.y * 6 * kJacCells + c : nullptr;
+    if (q.x != la || q.y != lb) {  // warp-uniform
+      la = q.x;
+      lb = q.y;
+      const double* DA = la >= 0 ? D + (size_t)la * 6 * kJacCells + c : nullptr;
+      const double* DB = lb >= 0 ? D + (size_t)lb * 6 * kJacCells + c : nullptr;
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        const double dv = DA ? (DB ? DA[f * kJacCells] - DB[f * kJacCells] : DA[f * kJacCells])
+                             : (DB ? -DB[f * kJacCells] : 0.0);
+        t6[f] = w6[f] * dv;
+      }
+    }
     const double* DM = q.z >= 0 ? D + (size_t)q.z * 6 * kJacCells + c : nullptr;
     const double* DN = q.w >= 0 ? D + (size_t)q.w * 6 * kJacCells + c : nullptr;
     double acc = 0.0;
+    if (DM && DN) {
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      const double dv = (DA ? DA[f * kJacCells] : 0.0) - (DB ? DB[f * kJacCells] : 0.0);
-      const double dw = (DM ? DM[f * kJacCells] : 0.0) - (DN ? DN[f * kJacCells] : 0.0);
-      acc += w6[f] * dv * dw;
+      for (int f = 0; f < 6; ++f) acc = fma(t6[f], DM[f * kJacCells] - DN[f * kJacCells], acc);
+    } else if (DM || DN) {
+      const double* D1 = DM ? DM : DN;
+#pragma unroll
+      for (int f = 0; f < 6; ++f) acc = fma(t6[f], D1[f * kJacCells], acc);
+      if (!DM) acc = -acc;
     }
     const double val = -kf[i] * acc;
     if (ROWS) {
       if (p < N) J[(int64_t)i * N + p] = val;
     } else {
-      acc_r += rv[i] * val;
+      acc_r = fma(rv[i], val, acc_r);
     }
   }
   if (!ROWS) {
@@ -651,7 +678,7 @@ void vcycle32(const Layout& W, const Level* lev, int nl, int ne, cudaStream_t s)
   for (int l = 0; l < nl - 1; ++l) {
     smooth32(W, lev, l, ne, K, W.b[l], W.x[l], true, s);
     k_resid32<<<nblk(lev[l].N), kThreads, 0, s>>>(lev[l], coef_of(W, l), ne, W.b[l], W.x[l], W.r[l]);
-    k_restrict32<<<nblk(lev[l + 1].N), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
+    k_restrict32<<<dim3(nblk(lev[l + 1].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], W.r[l], W.b[l + 1]);
     note_launches(2);
   }
   const int nc = (int)lev[nl - 1].N;
@@ -659,7 +686,7 @@ void vcycle32(const Layout& W, const Level* lev, int nl, int ne, cudaStream_t s)
                                                                                                   W.x[nl - 1]);
   note_launches(1);
   for (int l = nl - 2; l >= 0; --l) {
-    k_prolong_add32<<<nblk(lev[l].N), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.x[l + 1], W.x[l]);
+    k_prolong_add32<<<dim3(nblk(lev[l].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], W.x[l + 1], W.x[l]);
     note_launches(1);
     smooth32(W, lev, l, ne, K, W.b[l], W.x[l], false, s);
   }
