@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--m-rows", type=int, default=None, help="truncate the protocol to this many measurements")
     ap.add_argument("--ert", action="store_true",
                     help="time the ERT model evaluation (h1w_forward + h1w_adjoint J rows) instead")
+    ap.add_argument("--gn-steps", type=int, default=0,
+                    help="time this many Gauss-Newton steps of the ERT inversion workload instead")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of the ERT step: a batch of this many independent 2D Q1 systems "
                          "(sides 128..1024, m 8..256, alpha log-uniform 1e-4..1e-1) solved by h1w_solve_batch")
@@ -291,6 +293,10 @@ def run_batch(args):
 # ----------------------------------------------------------------------------
 
 ERT_RTOL = 1e-10
+# regularization weight of the inversion workload: on the 16^3 oracle inversion of the same
+# design, full Gauss-Newton steps diverge for alpha <= 0.1 and reach the noise level in 3-4
+# steps for alpha = 10..100 (100: smallest model error)
+GN_ALPHA = 100.0
 # nominal FP64 rate of the recipe's table (1.25 TFLOP/s), as FP64 instructions (FMA = 1)
 FP64_INST_PEAK_T = 1.25 / 2
 
@@ -418,6 +424,67 @@ def run_ert(args):
                                          "fields, g, %d of %d J rows timed), scaled linearly in cells to "
                                          "%d^3: an upper bound, since the LU grows faster than linearly"
                                          % (smp["rows_timed"], smp["m"], n), "detail": smp}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+# ----------------------------------------------------------------------------
+# Gauss-Newton inversion: Algorithm "Gauss-Newton with iterative solver"
+# ----------------------------------------------------------------------------
+
+def run_gn(args):
+    import numpy as np
+    import torch
+    from paper_2209_02815_gb300 import h1w, inputs
+
+    world, rank, local = dist_init(args)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    n = args.n
+    N = n ** 3
+    cells, abmn, k, _ = inputs.gn_survey(n, m_rows=args.m_rows or 1000)
+    sv = h1w.Survey(cells, abmn, k, inputs.ERT_DIRICHLET_ALL_BUT_TOP)
+    with torch.cuda.stream(stream):
+        S = h1w.Solver(h1w.H1W_FV_CELL, (n, n, n), (1.0 / n,) * 3, GN_ALPHA, sv.m, device=dev, stream=stream)
+        ls_true = torch.as_tensor(inputs.gn_truth(n), device=dev)
+        g_true, _, _ = S.forward(sv, ls_true, rtol=1e-12)
+        g_obs = torch.as_tensor(inputs.noisy(g_true.cpu().numpy()), device=dev)
+        m_ref = torch.full((N,), math.log(0.01), dtype=torch.float64, device=dev)
+        m = m_ref.clone()
+        if args.warmup:
+            S.gn_inversion(sv, g_obs, m_ref, m, min(args.warmup, 2), rtol_fwd=ERT_RTOL, rtol=RTOL, maxit=MAXIT)
+        m.copy_(m_ref)
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = ClockSampler(local)
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hist, g, _ = S.gn_inversion(sv, g_obs, m_ref, m, args.gn_steps, rtol_fwd=ERT_RTOL, rtol=RTOL, maxit=MAXIT)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        ms = allmax(world, e0.elapsed_time(e1))
+        t = S.timings()
+        err_true = float(torch.linalg.norm(m - ls_true) / torch.linalg.norm(ls_true - m_ref))
+    value = world * args.gn_steps / (ms / 1e3)
+    out = {"metric": "Gauss-Newton steps/s (ERT inversion: forward, J, Laplace-Woodbury PCG, update)",
+           "value": value, "unit": "GN steps/s", "n_gpus": world, "steps": args.gn_steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.gn_steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "ERT inversion, %d^3 FV cells, two Gaussian anomalies (10x and 0.1x of "
+                                  "0.01 S/m), %d surface electrodes (6 x 8), pair protocol m = %d, 2 %% noise, "
+                                  "alpha = %g, m_0 = m_ref" % (n, sv.n_e, sv.m, GN_ALPHA),
+                      "n": [n, n, n], "n_e": sv.n_e, "m": sv.m, "rtol_forward": ERT_RTOL, "rtol_gn": RTOL},
+           "misfit": [float(h_.misfit) for h_ in hist], "final_misfit": float(torch.linalg.norm(
+               S.forward(sv, m, rtol=ERT_RTOL)[0] - g_obs)),
+           "noise_level": float(torch.linalg.norm(g_obs - g_true)),
+           "rel_model_error": err_true,
+           "fwd_iters": [int(h_.fwd_iters) for h_ in hist], "gn_iters": [int(h_.gn_iters) for h_ in hist],
+           "last_step_phases_ms": {"t_H_ms": t.t_H_ms, "t_C_ms": t.t_C_ms, "t_chol_ms": t.t_chol_ms,
+                                   "t_pcg_ms": t.t_pcg_ms},
+           "clocks": clocks, "impl": "ours"}
     if rank == 0:
         print(json.dumps(out))
 
@@ -698,6 +765,8 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.ert:
         run_ert(a)
+    elif a.gn_steps > 0:
+        run_gn(a)
     elif a.batch > 0:
         run_batch(a)
     else:

@@ -282,6 +282,31 @@ h1w_status h1w_forward(h1w_ctx* ctx, const h1w_survey* survey, const double* log
 h1w_status h1w_adjoint(h1w_ctx* ctx, const h1w_survey* survey, const double* logsigma, const double* U,
                        const double* r, double* JTr, double* J, void* workspace, size_t ws_bytes);
 
+/* ---- Gauss-Newton step (Algorithm "Gauss-Newton with iterative solver") --------
+ *
+ * One pass of the algorithm's loop on an ERT model: evaluate g_m and J_m at m
+ * (h1w_forward, h1w_adjoint), solve the linearized system
+ *     (alpha (K + M) + J^T J) dm = -alpha (K + M)(m - m_ref) - J^T (g_m - g_obs)
+ * with the Laplace-Woodbury PCG (h1w_capacitance, h1w_gn_rhs, h1w_pcg), and
+ * update m := m + dm. Every step runs in this library's kernels.
+ * m (DEVICE, N) is updated in place; m_ref (DEVICE, N) and g_obs (DEVICE,
+ * survey->m) are inputs; U ([n_e][N]), J ([m][N]) and g ([m]) receive the
+ * fields, Jacobian and measurements at the incoming m (DEVICE); scratch
+ * (DEVICE) holds 3 N + m doubles; ert_ws is the workspace of h1w_forward.
+ * survey->m must not exceed the context's m_max. rtol_fwd and rtol are the
+ * forward and GN PCG tolerances; maxit bounds both. Synchronizes. */
+typedef struct {
+  int32_t fwd_iters;     /* PCG iterations of the forward solve */
+  int32_t gn_iters;      /* PCG iterations of the GN solve */
+  double misfit;         /* ||g_m - g_obs||_2 at the incoming m */
+  double rel_res_true;   /* the GN solve's FP64 true relative residual */
+  double step_norm;      /* ||dm||_2 */
+} h1w_gn_info;
+
+h1w_status h1w_gn_step(h1w_ctx* ctx, const h1w_survey* survey, const double* g_obs, const double* m_ref,
+                       double* m, double* U, double* J, double* g, double* scratch, void* ert_ws,
+                       size_t ert_ws_bytes, double rtol_fwd, double rtol, int32_t maxit, h1w_gn_info* info);
+
 /* Text of the last error on this context (ctx = NULL: the last error of
  * h1w_setup on this thread). Never NULL. */
 const char* h1w_last_error(const h1w_ctx* ctx);

@@ -1191,6 +1191,56 @@ h1w_status h1w_adjoint(h1w_ctx* c, const h1w_survey* survey, const double* logsi
   return st == H1W_OK ? st : fail(c, st, err);
 }
 
+h1w_status h1w_gn_step(h1w_ctx* c, const h1w_survey* survey, const double* g_obs, const double* m_ref,
+                       double* mvec, double* U, double* J, double* g, double* scratch, void* ert_ws,
+                       size_t ert_ws_bytes, double rtol_fwd, double rtol, int32_t maxit, h1w_gn_info* info) {
+  if (!c) return h1w::set_global_error(H1W_EINVAL, "h1w_gn_step: NULL context");
+  if (!survey || !g_obs || !m_ref || !mvec || !J || !g || !scratch)
+    return fail(c, H1W_EINVAL, "h1w_gn_step: NULL argument");
+  if (survey->m < 1 || survey->m > c->m_max) return fail(c, H1W_EINVAL, "h1w_gn_step: need 1 <= survey->m <= m_max");
+  const int64_t N = c->lev[0].N;
+  const int m = survey->m;
+  double* dmr = scratch;        // m - m_ref
+  double* b = scratch + N;      // GN right-hand side
+  double* dm = scratch + 2 * N;  // the step
+  double* d = scratch + 3 * N;  // g_m - g_obs
+  h1w_info fi{}, pi{};
+  h1w_status st = h1w_forward(c, survey, mvec, U, g, ert_ws, ert_ws_bytes, rtol_fwd, maxit, &fi);
+  if (st != H1W_OK) return st;
+  st = h1w_adjoint(c, survey, mvec, U, nullptr, nullptr, J, ert_ws, ert_ws_bytes);
+  if (st != H1W_OK) return st;
+  cudaMemcpyAsync(d, g, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->stream);
+  h1w::launch_axpby(d, -1.0, g_obs, 1.0, m, c->stream);
+  cudaMemcpyAsync(dmr, mvec, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream);
+  h1w::launch_axpby(dmr, -1.0, m_ref, 1.0, N, c->stream);
+  std::vector<double> dh(m);
+  cudaMemcpyAsync(dh.data(), d, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream);
+  st = h1w_capacitance(c, m, J);
+  if (st != H1W_OK) return st;
+  st = h1w_gn_rhs(c, dmr, d, b);
+  if (st != H1W_OK) return st;
+  st = h1w_pcg(c, b, dm, rtol, maxit, &pi);
+  if (st != H1W_OK) return st;
+  h1w::launch_axpby(mvec, 1.0, dm, 1.0, N, c->stream);
+  h1w::launch_dot_partial(dm, dm, N, c->partial, c->stream);
+  std::vector<double> part(h1w::dot_blocks(N));
+  cudaMemcpyAsync(part.data(), c->partial, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "h1w_gn_step");
+  st = cuda_check(c, "h1w_gn_step");
+  if (st != H1W_OK) return st;
+  if (info) {
+    double mis = 0.0, sn = 0.0;
+    for (double v : dh) mis += v * v;
+    for (double v : part) sn += v;
+    info->fwd_iters = fi.iters;
+    info->gn_iters = pi.iters;
+    info->misfit = std::sqrt(mis);
+    info->rel_res_true = pi.rel_res_true;
+    info->step_norm = std::sqrt(sn);
+  }
+  return H1W_OK;
+}
+
 void h1w_destroy(h1w_ctx* c) {
   if (!c) return;
   if (c->copy_stream) {

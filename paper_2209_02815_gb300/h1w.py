@@ -64,6 +64,11 @@ class SurveyC(ctypes.Structure):
                 ("dirichlet", ctypes.c_uint32)]
 
 
+class GnInfo(ctypes.Structure):
+    _fields_ = [("fwd_iters", ctypes.c_int32), ("gn_iters", ctypes.c_int32), ("misfit", ctypes.c_double),
+                ("rel_res_true", ctypes.c_double), ("step_norm", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -100,6 +105,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "h1w_ert_workspace_size": (SZ, [P, I32, I32]),
         "h1w_forward": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, SZ, D, I32, IN]),
         "h1w_adjoint": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, SZ]),
+        "h1w_gn_step": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, P, P, SZ, D, D, I32,
+                              ctypes.POINTER(GnInfo)]),
         "h1w_last_error": (ctypes.c_char_p, [P]),
         "h1w_destroy": (None, [P]),
     }
@@ -321,6 +328,18 @@ def h1w_adjoint(ctx, survey: Survey, logsigma: torch.Tensor, U: torch.Tensor, r:
     _check(st, ctx)
 
 
+def h1w_gn_step(ctx, survey: Survey, g_obs: torch.Tensor, m_ref: torch.Tensor, m: torch.Tensor, U: torch.Tensor,
+                J: torch.Tensor, g: torch.Tensor, scratch: torch.Tensor, ws: torch.Tensor, rtol_fwd: float,
+                rtol: float, maxit: int, N: int) -> GnInfo:
+    info = GnInfo()
+    st = load().h1w_gn_step(ctx, ctypes.byref(survey.c), _ptr(g_obs, survey.m, "g_obs"), _ptr(m_ref, N, "m_ref"),
+                            _ptr(m, N, "m"), _ptr(U, N * survey.n_e, "U"), _ptr(J, N * survey.m, "J"),
+                            _ptr(g, survey.m, "g"), _ptr(scratch, 3 * N + survey.m, "scratch"), ws.data_ptr(),
+                            ws.numel(), rtol_fwd, rtol, maxit, ctypes.byref(info))
+    _check(st, ctx)
+    return info
+
+
 def h1w_destroy(ctx) -> None:
     if ctx:
         load().h1w_destroy(ctx)
@@ -452,6 +471,28 @@ class Solver:
         finally:
             self._leave()
         return JTr, J
+
+    def gn_inversion(self, survey: Survey, g_obs, m_ref, m, steps: int, rtol_fwd: float = 1e-10,
+                     rtol: float = 1e-8, maxit: int = 500):
+        """Algorithm "Gauss-Newton with iterative solver": `steps` passes of h1w_gn_step
+        from m (updated in place). Returns the per-step GnInfo list and the last g, J."""
+        dev = m.device
+        ws = self.ert_workspace(survey)
+        U = torch.empty((survey.n_e, self.N), dtype=torch.float64, device=dev)
+        J = torch.empty((survey.m, self.N), dtype=torch.float64, device=dev)
+        g = torch.empty(survey.m, dtype=torch.float64, device=dev)
+        scratch = torch.empty(3 * self.N + survey.m, dtype=torch.float64, device=dev)
+        self.J = J
+        hist = []
+        self._enter(g_obs, m_ref, m, U, J, g, scratch, ws)
+        try:
+            for _ in range(steps):
+                hist.append(h1w_gn_step(self.ctx, survey, g_obs, m_ref, m, U, J, g, scratch, ws, rtol_fwd, rtol,
+                                        maxit, self.N))
+        finally:
+            self._leave()
+        self.m = survey.m
+        return hist, g, J
 
     def factors(self):
         m = self.m or 0

@@ -197,6 +197,44 @@ def ert_survey(n: int, n_e_line: int = 32, grid: tuple[int, int] | None = None,
     return electrode_cells(n, el, h), abmn.astype(np.int32), k, el
 
 
+def gn_truth(n: int, sigma_bg: float = 0.01, factors=(10.0, 0.1),
+             centres=((0.35, 0.5, 0.18), (0.65, 0.5, 0.18)), width: float = 0.08) -> np.ndarray:
+    """Log-conductivity of the inversion workload: a background of sigma_bg with two
+    Gaussian anomalies of peak conductivity factors ``factors`` (one conductive, one
+    resistive) below the surface z = 0; cell centres of an n^3 grid on the unit cube,
+    x fastest."""
+    c = (np.arange(n) + 0.5) / n
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    ls = np.full(x.shape, math.log(sigma_bg))
+    for f, (cx, cy, cz) in zip(factors, centres):
+        ls += math.log(f) * np.exp(-((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) / (2 * width ** 2))
+    return ls.reshape(-1)
+
+
+def gn_survey(n: int, ex: int = 6, ey: int = 8, m_rows: int | None = 1000):
+    """Surface electrodes on an ex x ey grid with the pair protocol over them (A, B at
+    infinity, M, N), the first m_rows rows whose geometric factor is defined: on a grid
+    the protocol's N can be as far from A as M is, which makes 1/|AM| - 1/|AN| vanish,
+    and those rows are skipped. Returns (cells, abmn, k, electrodes)."""
+    h = 1.0 / n
+    el = grid_electrodes(n, ex, ey, h)
+    prot = pair_protocol(len(el))
+    am = np.linalg.norm(el[prot[:, 0]] - el[prot[:, 1]], axis=1)
+    an = np.linalg.norm(el[prot[:, 0]] - el[prot[:, 2]], axis=1)
+    prot = prot[np.abs(1.0 / am - 1.0 / an) > 1e-9 / am]
+    if m_rows is not None:
+        prot = prot[:m_rows]
+    abmn = np.stack([prot[:, 0], np.full(len(prot), -1), prot[:, 1], prot[:, 2]], axis=1)
+    k = geometric_factor_pole_dipole(el[prot[:, 0]], el[prot[:, 1]], el[prot[:, 2]])
+    return electrode_cells(n, el, h), abmn.astype(np.int32), k, el
+
+
+def noisy(g_true: np.ndarray, noise: float = 0.02, seed: int = SEED_RHS) -> np.ndarray:
+    """Observed data g_true (1 + noise eps), eps ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    return g_true * (1.0 + noise * rng.standard_normal(g_true.shape))
+
+
 def geometric_factor_pole_dipole(xa, xm, xn) -> np.ndarray:
     """3D geometric factor with B at infinity (limit of Eq. 4.5)."""
     am = np.linalg.norm(xa - xm, axis=-1)

@@ -93,3 +93,52 @@ def test_half_space_apparent_resistivity(n):
     k = 2 * np.pi / (1 / np.linalg.norm(P[0] - P[1]) - 1 / np.linalg.norm(P[0] - P[2]))
     g, _ = ert.forward((n, n, n), h, ls, cells, np.array([[0, -1, 1, 2]]), [k], ALL_BUT_TOP)
     assert abs(g[0] * s0 - 1.0) < 0.05
+
+
+# ---- Gauss-Newton steps (Algorithm "Gauss-Newton with iterative solver") ----------
+
+from oracle import discretization as odisc  # noqa: E402
+from oracle import gn as ogn  # noqa: E402
+
+
+def _gn_case(alpha):
+    n, h = (6, 5, 4), (1 / 6, 1 / 5, 1 / 4)
+    N = int(np.prod(n))
+    rng = np.random.default_rng(21)
+    m_ref = np.full(N, np.log(0.01))
+    m = m_ref + 0.3 * rng.standard_normal(N)
+    m_true = m_ref + 0.5 * rng.standard_normal(N)
+    cells = [0, 2, 4, 12, 16, 27]
+    abmn = np.array([(p, -1, q, (q + 1) % 6 if (q + 1) % 6 != p else (q + 2) % 6)
+                     for p in range(6) for q in range(p + 1, 6)])
+    k = np.linspace(1.0, 2.0, len(abmn))
+    g_true, _ = ert.forward(n, h, m_true, cells, abmn, k, ALL_BUT_TOP)
+    return n, h, alpha, m, m_ref, cells, abmn, k, ALL_BUT_TOP, g_true * 1.01
+
+
+def test_gn_step_is_the_least_squares_minimizer():
+    """The step minimizes 1/2||d + J dm||^2 + alpha/2 ||R (m - m_ref + dm)||^2 with
+    K + M = R^T R: solved here as a stacked least-squares problem by QR (numpy lstsq)
+    instead of the normal equations."""
+    n, h, alpha, m, m_ref, cells, abmn, k, dm_, g_obs = _gn_case(1e-3)
+    dm, g, J = ogn.gn_step(n, h, alpha, m, m_ref, cells, abmn, k, dm_, g_obs)
+    R = np.linalg.cholesky(odisc.regularization_operator("fv", n, h).toarray()).T
+    A = np.vstack([J, np.sqrt(alpha) * R])
+    rhs = -np.concatenate([g - g_obs, np.sqrt(alpha) * R @ (m - m_ref)])
+    ls = np.linalg.lstsq(A, rhs, rcond=None)[0]
+    assert np.abs(dm - ls).max() / np.abs(ls).max() < 1e-9
+
+
+def test_gn_step_descends():
+    n, h, alpha, m, m_ref, cells, abmn, k, dm_, g_obs = _gn_case(1e-3)
+    dm, _, _ = ogn.gn_step(n, h, alpha, m, m_ref, cells, abmn, k, dm_, g_obs)
+    f0 = ogn.objective(n, h, alpha, m, m_ref, cells, abmn, k, dm_, g_obs)
+    f1 = ogn.objective(n, h, alpha, m + 1e-3 * dm, m_ref, cells, abmn, k, dm_, g_obs)
+    assert f1 < f0
+
+
+def test_gn_step_large_alpha_returns_to_reference():
+    """With the regularization dominating, the step is m_ref - m."""
+    n, h, alpha, m, m_ref, cells, abmn, k, dm_, g_obs = _gn_case(1e8)
+    dm, _, _ = ogn.gn_step(n, h, alpha, m, m_ref, cells, abmn, k, dm_, g_obs)
+    assert np.abs(dm + (m - m_ref)).max() / np.abs(m - m_ref).max() < 1e-6
