@@ -266,13 +266,18 @@ size_t h1w_ert_workspace_size(const h1w_ctx* ctx, int32_t n_e, int32_t m);
  * U (DEVICE, [n_e][N], caller-owned) receives the fields u_e, g (DEVICE, [m])
  * the measurements. The fields are solved together by PCG in FP64 to
  * ||e_c - A u_e||_2 <= rtol (unit sources), preconditioned by one FP32 V-cycle
- * on the same operator over the context's hierarchy. The survey's host arrays
+ * on the same operator over the context's hierarchy, from u_e = 0 or, with
+ * H1W_FORWARD_WARM_START, from the fields already in U (e.g. those of the previous
+ * Gauss-Newton iterate). The survey's host arrays
  * are copied before the call returns. info (may be NULL): iterations, and the
  * worst field's FP64 true and recursive residuals. H1W_ENOTCONV when maxit
  * iterations do not reach rtol (U holds the iterates), H1W_ENOTSPD when the
  * coarsest operator fails its Cholesky factorization. Synchronizes. */
+#define H1W_FORWARD_WARM_START 1u  /* flags: start PCG from the fields already in U (else from 0) */
+
 h1w_status h1w_forward(h1w_ctx* ctx, const h1w_survey* survey, const double* logsigma, double* U, double* g,
-                       void* workspace, size_t ws_bytes, double rtol, int32_t maxit, h1w_info* info);
+                       void* workspace, size_t ws_bytes, double rtol, int32_t maxit, uint32_t flags,
+                       h1w_info* info);
 
 /* The Jacobian from the fields U of h1w_forward (same survey and logsigma):
  * J (DEVICE, [m][N] row-major, may be NULL) receives every row, and JTr
@@ -294,7 +299,8 @@ h1w_status h1w_adjoint(h1w_ctx* ctx, const h1w_survey* survey, const double* log
  * fields, Jacobian and measurements at the incoming m (DEVICE); scratch
  * (DEVICE) holds 3 N + m doubles; ert_ws is the workspace of h1w_forward.
  * survey->m must not exceed the context's m_max. rtol_fwd and rtol are the
- * forward and GN PCG tolerances; maxit bounds both. Synchronizes. */
+ * forward and GN PCG tolerances; maxit bounds both; fwd_flags goes to h1w_forward
+ * (H1W_FORWARD_WARM_START once U holds the previous iterate's fields). Synchronizes. */
 typedef struct {
   int32_t fwd_iters;     /* PCG iterations of the forward solve */
   int32_t gn_iters;      /* PCG iterations of the GN solve */
@@ -305,7 +311,8 @@ typedef struct {
 
 h1w_status h1w_gn_step(h1w_ctx* ctx, const h1w_survey* survey, const double* g_obs, const double* m_ref,
                        double* m, double* U, double* J, double* g, double* scratch, void* ert_ws,
-                       size_t ert_ws_bytes, double rtol_fwd, double rtol, int32_t maxit, h1w_gn_info* info);
+                       size_t ert_ws_bytes, double rtol_fwd, double rtol, int32_t maxit, uint32_t fwd_flags,
+                       h1w_gn_info* info);
 
 /* Text of the last error on this context (ctx = NULL: the last error of
  * h1w_setup on this thread). Never NULL. */

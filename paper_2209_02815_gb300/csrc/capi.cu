@@ -1172,12 +1172,14 @@ size_t h1w_ert_workspace_size(const h1w_ctx* c, int32_t n_e, int32_t m) {
 }
 
 h1w_status h1w_forward(h1w_ctx* c, const h1w_survey* survey, const double* logsigma, double* U, double* g,
-                       void* workspace, size_t ws_bytes, double rtol, int32_t maxit, h1w_info* info) {
+                       void* workspace, size_t ws_bytes, double rtol, int32_t maxit, uint32_t flags,
+                       h1w_info* info) {
   if (!c) return h1w::set_global_error(H1W_EINVAL, "h1w_forward: NULL context");
   if (c->disc != H1W_FV_CELL) return fail(c, H1W_EUNSUPPORTED, "h1w_forward: needs an H1W_FV_CELL grid");
   std::string err;
+  if (flags & ~H1W_FORWARD_WARM_START) return fail(c, H1W_EINVAL, "h1w_forward: unknown flags");
   const h1w_status st = h1w::ert_forward(c->lev, c->nlev, c->stream, survey, logsigma, U, g, workspace, ws_bytes,
-                                         rtol, maxit, info, err);
+                                         rtol, maxit, (flags & H1W_FORWARD_WARM_START) != 0, info, err);
   return st == H1W_OK ? st : fail(c, st, err);
 }
 
@@ -1193,7 +1195,8 @@ h1w_status h1w_adjoint(h1w_ctx* c, const h1w_survey* survey, const double* logsi
 
 h1w_status h1w_gn_step(h1w_ctx* c, const h1w_survey* survey, const double* g_obs, const double* m_ref,
                        double* mvec, double* U, double* J, double* g, double* scratch, void* ert_ws,
-                       size_t ert_ws_bytes, double rtol_fwd, double rtol, int32_t maxit, h1w_gn_info* info) {
+                       size_t ert_ws_bytes, double rtol_fwd, double rtol, int32_t maxit, uint32_t fwd_flags,
+                       h1w_gn_info* info) {
   if (!c) return h1w::set_global_error(H1W_EINVAL, "h1w_gn_step: NULL context");
   if (!survey || !g_obs || !m_ref || !mvec || !J || !g || !scratch)
     return fail(c, H1W_EINVAL, "h1w_gn_step: NULL argument");
@@ -1205,7 +1208,7 @@ h1w_status h1w_gn_step(h1w_ctx* c, const h1w_survey* survey, const double* g_obs
   double* dm = scratch + 2 * N;  // the step
   double* d = scratch + 3 * N;  // g_m - g_obs
   h1w_info fi{}, pi{};
-  h1w_status st = h1w_forward(c, survey, mvec, U, g, ert_ws, ert_ws_bytes, rtol_fwd, maxit, &fi);
+  h1w_status st = h1w_forward(c, survey, mvec, U, g, ert_ws, ert_ws_bytes, rtol_fwd, maxit, fwd_flags, &fi);
   if (st != H1W_OK) return st;
   st = h1w_adjoint(c, survey, mvec, U, nullptr, nullptr, J, ert_ws, ert_ws_bytes);
   if (st != H1W_OK) return st;

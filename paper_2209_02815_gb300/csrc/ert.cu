@@ -414,6 +414,18 @@ __global__ void k_init(int64_t N, const int* __restrict__ cell, double* __restri
   }
 }
 
+// r = e_{c_e} - q (q = A u), b32 = (float) r; u is left as it is
+__global__ void k_init_warm(int64_t N, const int* __restrict__ cell, const double* __restrict__ q,
+                            double* __restrict__ r, float* __restrict__ b32) {
+  const int e = blockIdx.y;
+  const int c = cell[e];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const double v = ((p == c) ? 1.0 : 0.0) - q[e * N + p];
+    r[e * N + p] = v;
+    b32[e * N + p] = (float)v;
+  }
+}
+
 // partial[0] = a . b, partial[1] = c . d (when c is given), per field
 __global__ void k_dots(int64_t N, const double* __restrict__ a, const double* __restrict__ b,
                        const double* __restrict__ c, const double* __restrict__ d, double* __restrict__ partial) {
@@ -780,8 +792,8 @@ size_t ert_workspace_bytes(const Level* lev, int nlev, int n_e, int m) {
 }
 
 h1w_status ert_forward(const Level* lev, int nl, cudaStream_t s, const h1w_survey* sv, const double* logsigma,
-                       double* U, double* g, void* ws, size_t ws_bytes, double rtol, int maxit, h1w_info* info,
-                       std::string& err) {
+                       double* U, double* g, void* ws, size_t ws_bytes, double rtol, int maxit, bool warm,
+                       h1w_info* info, std::string& err) {
   h1w_status st = validate_survey(lev, sv, err);
   if (st != H1W_OK) return st;
   if (!logsigma || !U || (sv->m > 0 && !g) || !ws || !(rtol > 0.0) || maxit < 1) {
@@ -805,12 +817,19 @@ h1w_status ert_forward(const Level* lev, int nl, cudaStream_t s, const h1w_surve
   const unsigned sb = (unsigned)((ne + 127) / 128);
   const double tol2 = rtol * rtol;  // ||f_e|| = 1
   std::vector<double> rr(ne);
-  k_init<<<vg, kThreads, 0, s>>>(N, W.cell, U, W.r64, W.b[0]);
+  if (warm) {  // r = e_c - A u from the fields in U
+    k_apply64<<<nblk(N), kThreads, 0, s>>>(L0, W.tx64, W.ty64, W.tz64, W.dg64, ne, U, W.q64);
+    k_init_warm<<<vg, kThreads, 0, s>>>(N, W.cell, W.q64, W.r64, W.b[0]);
+    note_launches(2);
+  } else {
+    k_init<<<vg, kThreads, 0, s>>>(N, W.cell, U, W.r64, W.b[0]);
+    note_launches(1);
+  }
   vcycle32(W, lev, nl, ne, s);
   k_z_dots<<<vg, kThreads, 0, s>>>(N, W.x[0], W.z64, W.r64, nullptr, W.partial);
   k_scalars<<<sb, 128, 0, s>>>(0, ne, kDotBlocks, W.partial, W.scal, tol2);
   cudaMemcpyAsync(W.p64, W.z64, sizeof(double) * N * ne, cudaMemcpyDeviceToDevice, s);
-  note_launches(3);
+  note_launches(2);
   int it = 0;
   bool done = false;
   double worst = 1.0;

@@ -103,9 +103,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "h1w_solve_batch": (I32, [ctypes.POINTER(P), I32, ctypes.POINTER(I32), ctypes.POINTER(P),
                                   ctypes.POINTER(P), ctypes.POINTER(P), D, I32, I32, IN, ctypes.POINTER(I32)]),
         "h1w_ert_workspace_size": (SZ, [P, I32, I32]),
-        "h1w_forward": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, SZ, D, I32, IN]),
+        "h1w_forward": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, SZ, D, I32, ctypes.c_uint32, IN]),
         "h1w_adjoint": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, SZ]),
-        "h1w_gn_step": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, P, P, SZ, D, D, I32,
+        "h1w_gn_step": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, P, P, SZ, D, D, I32, ctypes.c_uint32,
                               ctypes.POINTER(GnInfo)]),
         "h1w_last_error": (ctypes.c_char_p, [P]),
         "h1w_destroy": (None, [P]),
@@ -308,12 +308,16 @@ def h1w_ert_workspace_size(ctx, n_e: int, m: int) -> int:
     return int(load().h1w_ert_workspace_size(ctx, n_e, m))
 
 
+H1W_FORWARD_WARM_START = 1
+
+
 def h1w_forward(ctx, survey: Survey, logsigma: torch.Tensor, U: torch.Tensor, g: torch.Tensor | None,
-                ws: torch.Tensor, rtol: float, maxit: int, N: int, raise_on_notconv: bool = True) -> Info:
+                ws: torch.Tensor, rtol: float, maxit: int, N: int, raise_on_notconv: bool = True,
+                flags: int = 0) -> Info:
     info = Info()
     st = load().h1w_forward(ctx, ctypes.byref(survey.c), _ptr(logsigma, N, "logsigma"),
                             _ptr(U, N * survey.n_e, "U"), _ptr(g, survey.m, "g"), ws.data_ptr(), ws.numel(),
-                            rtol, maxit, ctypes.byref(info))
+                            rtol, maxit, flags, ctypes.byref(info))
     if st == H1W_ENOTCONV and not raise_on_notconv:
         return info
     _check(st, ctx)
@@ -330,12 +334,12 @@ def h1w_adjoint(ctx, survey: Survey, logsigma: torch.Tensor, U: torch.Tensor, r:
 
 def h1w_gn_step(ctx, survey: Survey, g_obs: torch.Tensor, m_ref: torch.Tensor, m: torch.Tensor, U: torch.Tensor,
                 J: torch.Tensor, g: torch.Tensor, scratch: torch.Tensor, ws: torch.Tensor, rtol_fwd: float,
-                rtol: float, maxit: int, N: int) -> GnInfo:
+                rtol: float, maxit: int, N: int, fwd_flags: int = 0) -> GnInfo:
     info = GnInfo()
     st = load().h1w_gn_step(ctx, ctypes.byref(survey.c), _ptr(g_obs, survey.m, "g_obs"), _ptr(m_ref, N, "m_ref"),
                             _ptr(m, N, "m"), _ptr(U, N * survey.n_e, "U"), _ptr(J, N * survey.m, "J"),
                             _ptr(g, survey.m, "g"), _ptr(scratch, 3 * N + survey.m, "scratch"), ws.data_ptr(),
-                            ws.numel(), rtol_fwd, rtol, maxit, ctypes.byref(info))
+                            ws.numel(), rtol_fwd, rtol, maxit, fwd_flags, ctypes.byref(info))
     _check(st, ctx)
     return info
 
@@ -448,14 +452,17 @@ class Solver:
             raise H1wError(H1W_EINVAL, "invalid survey size or grid for h1w_ert_workspace_size")
         return torch.empty(size, dtype=torch.uint8, device=self.workspace.device)
 
-    def forward(self, survey: Survey, logsigma, rtol: float = 1e-10, maxit: int = 200, ws=None, U=None):
-        """Pole fields U (n_e, N) and measurements g (m,) of the ERT model (h1w_forward)."""
+    def forward(self, survey: Survey, logsigma, rtol: float = 1e-10, maxit: int = 200, ws=None, U=None,
+                warm: bool = False):
+        """Pole fields U (n_e, N) and measurements g (m,) of the ERT model (h1w_forward);
+        warm: start from the fields already in U."""
         ws = self.ert_workspace(survey) if ws is None else ws
         U = torch.empty((survey.n_e, self.N), dtype=torch.float64, device=logsigma.device) if U is None else U
         g = torch.empty(survey.m, dtype=torch.float64, device=logsigma.device)
         self._enter(logsigma, U, g, ws)
         try:
-            info = h1w_forward(self.ctx, survey, logsigma, U, g, ws, rtol, maxit, self.N)
+            info = h1w_forward(self.ctx, survey, logsigma, U, g, ws, rtol, maxit, self.N,
+                               flags=H1W_FORWARD_WARM_START if warm else 0)
         finally:
             self._leave()
         return g, U, info
@@ -473,9 +480,11 @@ class Solver:
         return JTr, J
 
     def gn_inversion(self, survey: Survey, g_obs, m_ref, m, steps: int, rtol_fwd: float = 1e-10,
-                     rtol: float = 1e-8, maxit: int = 500):
+                     rtol: float = 1e-8, maxit: int = 500, warm: bool = True):
         """Algorithm "Gauss-Newton with iterative solver": `steps` passes of h1w_gn_step
-        from m (updated in place). Returns the per-step GnInfo list and the last g, J."""
+        from m (updated in place); from the second step on, each forward solve starts from
+        the previous iterate's fields when warm. Returns the per-step GnInfo list and the
+        last g, J."""
         dev = m.device
         ws = self.ert_workspace(survey)
         U = torch.empty((survey.n_e, self.N), dtype=torch.float64, device=dev)
@@ -486,9 +495,10 @@ class Solver:
         hist = []
         self._enter(g_obs, m_ref, m, U, J, g, scratch, ws)
         try:
-            for _ in range(steps):
+            for i in range(steps):
+                flags = H1W_FORWARD_WARM_START if (warm and i > 0) else 0
                 hist.append(h1w_gn_step(self.ctx, survey, g_obs, m_ref, m, U, J, g, scratch, ws, rtol_fwd, rtol,
-                                        maxit, self.N))
+                                        maxit, self.N, fwd_flags=flags))
         finally:
             self._leave()
         self.m = survey.m
