@@ -299,6 +299,9 @@ ERT_RTOL = 1e-10
 GN_ALPHA = 100.0
 # nominal FP64 rate of the recipe's table (1.25 TFLOP/s), as FP64 instructions (FMA = 1)
 FP64_INST_PEAK_T = 1.25 / 2
+# ncu DRAM read + write bytes per J entry of k_jacobian<rows> (64^3, 32 electrodes, m = 496):
+# (1102.422 + 70.367) MB / (496 * 262144)
+NCU_BYTES_PER_J_ENTRY = (1102.422e6 + 70.366976e6) / (496 * 262144)
 
 
 def ert_oracle_sample(n_side: int, ne: int, budget_s: float) -> dict:
@@ -409,7 +412,9 @@ def run_ert(args):
            "forward_ms": float(np.median(fwd)), "jacobian_rows_ms": jac_ms, "pcg_iters": iters,
            "rel_res_true": float(info.rel_res_true),
            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_INST_PEAK_T, "unit": "T FP64 inst/s",
-                        "frac": ach / FP64_INST_PEAK_T, "traffic": None, "kernel": "k_jacobian<rows>",
+                        "frac": ach / FP64_INST_PEAK_T, "traffic": NCU_BYTES_PER_J_ENTRY * m * N,
+                        "traffic_note": "ncu 64^3 capture (32 electrodes, m = 496), scaled by J entries per launch",
+                        "kernel": "k_jacobian<rows>",
                         "note": "FP64 instructions of the J-row kernel (%d per launch) / its event time; "
                                 "peak = nominal 1.25 TFLOP/s FP64 as FMA instructions" % fp64_inst},
            "clocks": clocks, "impl": "ours"}
