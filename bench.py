@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--m-rows", type=int, default=None, help="truncate the protocol to this many measurements")
     ap.add_argument("--ert", action="store_true",
                     help="time the ERT model evaluation (h1w_forward + h1w_adjoint J rows) instead")
+    ap.add_argument("--precond", default="woodbury", choices=["woodbury", "laplace"],
+                    help="laplace: the paper's variant without the capacitance matrix (comparison only)")
+    ap.add_argument("--maxit", type=int, default=MAXIT)
     ap.add_argument("--gn-steps", type=int, default=0,
                     help="time this many Gauss-Newton steps of the ERT inversion workload instead")
     ap.add_argument("--batch", type=int, default=0,
@@ -513,8 +516,10 @@ def run_ours(args):
         J = pr.J
         m, N = J.shape
         o_main = None
-        if args.arith == "fp64" or args.rhs_block > 0:
+        if args.arith == "fp64" or args.rhs_block > 0 or args.precond == "laplace":
             o_main = h1w.h1w_default_options()
+            if args.precond == "laplace":
+                o_main.precond = 1
             if args.arith == "fp64":
                 o_main.cap_gemm = 1
                 o_main.mg_arith = 1
@@ -529,7 +534,7 @@ def run_ours(args):
         x = torch.empty_like(b)
         for _ in range(args.warmup):
             S.capacitance(J)
-            _, info = S.pcg(b, RTOL, MAXIT, x=x)
+            _, info = S.pcg(b, RTOL, args.maxit, x=x, raise_on_notconv=args.precond != "laplace")
         stream.synchronize()
         barrier(world)
         torch.cuda.synchronize()
@@ -544,7 +549,7 @@ def run_ours(args):
         e0.record(stream)
         for _ in range(args.steps):
             S.capacitance(J)
-            _, info = S.pcg(b, RTOL, MAXIT, x=x)
+            _, info = S.pcg(b, RTOL, args.maxit, x=x, raise_on_notconv=args.precond != "laplace")
             t = S.timings()
             for k_ in phase:
                 phase[k_].append(getattr(t, k_))
@@ -694,7 +699,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload(n, m, electrode_grid(args)), "n": [n, n, n], "N": N, "m": m, "alpha": ALPHA,
-                   "rtol": RTOL,
+                   "rtol": RTOL, "precond": args.precond,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (J is %.1f GB)" % (J.numel() * 8 / 1e9)},
         "phases_ms": mean, "pcg_iters": iters, "rel_res_true": rel_true,

@@ -77,6 +77,10 @@ typedef struct {
   int32_t mg_unfused;    /* double-float cycle: 0 = levels with all axes coarsened and the degree-2
                             smoother run each leg (smoothing, residual and transfer) as one kernel
                             (default), 1 = one kernel per step. Both give identical results. */
+  int32_t precond;       /* preconditioner of h1w_pcg / h1w_apply_prec: 0 = Laplace-Woodbury
+                            alpha^-1 [L^-1 - alpha^-1 H C^-1 H^T] (default); 1 = Laplace only,
+                            alpha^-1 L^-1, the paper's variant without the capacitance matrix
+                            (Sec. 3.2), for which h1w_capacitance skips lines H, C and chol */
 } h1w_options;
 
 typedef struct {

@@ -270,6 +270,7 @@ h1w_status validate(const h1w_grid* g, int32_t m_max, const h1w_options* o, std:
     if (o->cap_gemm != 0 && o->cap_gemm != 1) { why = "cap_gemm must be 0 or 1"; return H1W_EINVAL; }
     if (o->mg_arith != 0 && o->mg_arith != 1) { why = "mg_arith must be 0 or 1"; return H1W_EINVAL; }
     if (o->mg_unfused != 0 && o->mg_unfused != 1) { why = "mg_unfused must be 0 or 1"; return H1W_EINVAL; }
+    if (o->precond != 0 && o->precond != 1) { why = "precond must be 0 or 1"; return H1W_EINVAL; }
   }
   return H1W_OK;
 }
@@ -558,7 +559,7 @@ void j_times_df(h1w_ctx* c, const double* v, double* out) {
 // z = P^-1 r; when rz_slot >= 0 also scal[rz_slot] = r . z. False if the cycle could not run.
 bool apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
   const int64_t N = c->lev[0].N;
-  const int m = c->m;
+  const int m = c->opt.precond == 1 ? 0 : c->m;  // Laplace only: z = alpha^-1 L-hat^-1 r
   const bool dfp_ = uses_df(c) && m > 0;
   // z0 = L-hat^-1 r and s = H^T r (with y = C^-1 s) do not depend on each other: on the
   // double-float path the cycle, bound by latency, runs on a second stream while the pass,
@@ -655,6 +656,7 @@ void h1w_default_options(h1w_options* opt) {
   opt->cap_gemm = 0;
   opt->mg_arith = 0;
   opt->mg_unfused = 0;
+  opt->precond = 0;
 }
 
 size_t h1w_workspace_size(const h1w_grid* grid, int32_t m_max, const h1w_options* opt) {
@@ -891,6 +893,18 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
     }
   }
   if (c->have_ev) cudaEventRecord(c->ev[0], c->stream);
+  if (c->opt.precond == 1) {  // Laplace-only preconditioner: J for the operator, no lines H, C, chol
+    for (int bi = 0; bi < nbatch; ++bi) {
+      const int64_t r0 = edge[bi], nr = edge[bi + 1] - edge[bi], o = r0 * N;
+      if (J_host) cudaStreamWaitEvent(c->stream, c->cev[bi], 0);
+      if (uses_df(c)) launch_d2df(nr * N, J + o, c->Jdf + o, c->stream);
+    }
+    for (int k = 1; k < 4 && c->have_ev; ++k) cudaEventRecord(c->ev[k], c->stream);
+    c->launches_cap = g_kernel_launches.load() - l0;
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, H1W_ECUDA, std::string("capacitance: ") + cudaGetErrorString(e));
+    return cuda_check(c, "capacitance");
+  }
   // line H; on the double-float cycle the tensor-core split reads H as double-floats, so the
   // FP64 copy of H is only written for the FP64 paths
   const bool h_df_only = uses_df(c) && c->opt.cap_gemm == 0;
@@ -1108,6 +1122,7 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
 h1w_status h1w_capacitance_factors(h1w_ctx* c, double* C, double* L) {
   if (!c) return H1W_EINVAL;
   if (c->m < 0) return fail(c, H1W_ESTATE, "call h1w_capacitance first");
+  if (c->opt.precond == 1) return fail(c, H1W_ESTATE, "precond = 1 forms no capacitance matrix");
   const size_t bytes = sizeof(double) * c->m * c->m;
   if (C && bytes) cudaMemcpyAsync(C, c->C, bytes, cudaMemcpyDeviceToDevice, c->stream);
   if (L && bytes) cudaMemcpyAsync(L, c->Lc, bytes, cudaMemcpyDeviceToDevice, c->stream);

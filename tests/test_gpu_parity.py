@@ -483,3 +483,43 @@ def test_ert_64cube_m496_converges_like_fp64_form():
         del S
     assert float(torch.linalg.matrix_norm(C, 2)) > 1e8
     assert abs(its[0] - its[1]) <= 1, its
+
+
+@pytest.mark.parametrize("case", [_q1((65, 65)), _fv((32, 32, 32))], ids=["q1_65", "fv32"])
+def test_laplace_only_preconditioner(case):
+    """The paper's variant without the capacitance matrix (precond = 1, P^-1 = alpha^-1
+    L-hat^-1): the same solution as with the Laplace-Woodbury preconditioner, iteration
+    counts as the oracle's PCG with that preconditioner, and the behaviour Sec. 3.2 and the
+    timing experiments describe: its iterations grow with m and as alpha falls, while the
+    Laplace-Woodbury counts stay flat."""
+    d, n, h = case
+    A = disc.regularization_operator(d, n, h)
+    N = A.shape[0]
+    H = mg.build_hierarchy(d, n, h)
+    rng = np.random.default_rng(41)
+    J_all = rng.standard_normal((32, N)) / np.sqrt(N)
+    b = rng.standard_normal(N)
+    its = {}
+    for m in (4, 32):
+        J = J_all[:m]
+        for alpha in (1e-1, 1e-2):
+            S0 = _gpu(d, n, h, alpha, m)
+            S0.capacitance(_t(J))
+            x0, i0 = S0.pcg(_t(b), 1e-11, 3000)
+            S1 = _gpu(d, n, h, alpha, m, precond=1)
+            S1.capacitance(_t(J))
+            x1, i1 = S1.pcg(_t(b), 1e-11, 3000)
+            assert i0.rel_res_true <= 1e-11 and i1.rel_res_true <= 1e-11
+            assert _rel(x1.cpu().numpy(), x0.cpu().numpy()) <= 1e-8
+            _, it_ref, _ = wb.pcg(lambda v: wb.apply_operator(A, alpha, J, v), lambda v: mg.vcycle(H, v) / alpha,
+                                  b, 1e-11, 3000)
+            # without the capacitance term the preconditioned system is far worse conditioned,
+            # and at rtol 1e-11 the 48-bit cycle and the oracle's FP64 one part by a few
+            # iterations (35 against 32 for m = 4, alpha = 1e-2 on the Q1 grid)
+            assert abs(i1.iters - it_ref) <= max(3, it_ref // 10), (m, alpha, i1.iters, it_ref)
+            its[(m, alpha)] = (i0.iters, i1.iters)
+    assert its[(32, 1e-2)][1] > its[(4, 1e-2)][1] and its[(32, 1e-2)][1] > its[(32, 1e-1)][1], its
+    wood = [v[0] for v in its.values()]
+    assert max(wood) <= min(wood) + 3, its
+    with pytest.raises(h1w.H1wError):
+        S1.factors()

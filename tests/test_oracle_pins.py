@@ -297,3 +297,19 @@ def test_woodbury_pcg_iterations_bounded_by_mg_pcg(alpha):
     _, it_w, rel = wb.pcg(lambda v: wb.apply_operator(A, alpha, pr.J, v), P, pr.b, 1e-8, 200)
     assert rel <= 1e-8
     assert it_w <= it_mg + 2
+
+
+@pytest.mark.parametrize("d", ["q1", "fv"])
+def test_laplace_only_exact_inverse_terminates_within_m_plus_1(d):
+    """The preconditioner without the capacitance matrix, alpha^-1 A^-1 (the paper's
+    comparison variant): P^-1 (alpha A + J^T J) = I + alpha^-1 A^-1 J^T J is the identity
+    plus a rank-m term, so it has at most m + 1 distinct eigenvalues and CG stops within
+    m + 1 iterations, where the Woodbury preconditioner needs one. (The bound is one of
+    exact arithmetic; with alpha = 1 the spectrum is narrow enough that rounding does not
+    delay it, while at alpha = 1e-3 the oracle takes m + 2.)"""
+    A, J, b = _tiny(d)
+    alpha = 1.0
+    Aop = alpha * A + J.T @ J
+    Ainv = np.linalg.inv(A)
+    x, it, rel = wb.pcg(lambda v: Aop @ v, lambda v: Ainv @ v / alpha, b, 1e-10, 50)
+    assert 1 < it <= J.shape[0] + 1 and rel <= 1e-10, it
