@@ -300,11 +300,9 @@ ERT_RTOL = 1e-10
 # design, full Gauss-Newton steps diverge for alpha <= 0.1 and reach the noise level in 3-4
 # steps for alpha = 10..100 (100: smallest model error)
 GN_ALPHA = 100.0
-# nominal FP64 rate of the recipe's table (1.25 TFLOP/s), as FP64 instructions (FMA = 1)
-FP64_INST_PEAK_T = 1.25 / 2
 # ncu DRAM read + write bytes per J entry of k_jacobian<rows> (64^3, 32 electrodes, m = 496):
-# (1102.422 + 70.367) MB / (496 * 262144)
-NCU_BYTES_PER_J_ENTRY = (1102.422e6 + 70.366976e6) / (496 * 262144)
+# (1102.789 + 69.838) MB / (496 * 262144)
+NCU_BYTES_PER_J_ENTRY = (1102.789e6 + 69.83808e6) / (496 * 262144)
 
 
 def ert_oracle_sample(n_side: int, ne: int, budget_s: float) -> dict:
@@ -393,14 +391,24 @@ def run_ert(args):
         e2e_ms = allmax(world, e0.elapsed_time(e1)) if args.e2e_steps else None
 
     m = sv.m
-    groups = int(np.sum(np.any(np.diff(abmn[:, :2], axis=0) != 0, axis=1)) + 1)
+    new_src = np.concatenate([[True], np.any(np.diff(abmn[:, :2], axis=0) != 0, axis=1)])
+    src_b = int(np.sum(new_src & (abmn[:, 1] >= 0)))
+    src_a = int(np.sum(new_src)) - src_b
     n_full = int(np.sum((abmn[:, 2] >= 0) & (abmn[:, 3] >= 0)))
-    # FP64 instructions of the J-row kernel: per row and cell 6 faces x (subtraction + FMA)
-    # (one electrode of the receiver pair at infinity: no subtraction) + the scaling by -k_i;
-    # per source and cell 6 products W_f (D_A - D_B)
-    fp64_inst = N * (n_full * 13 + (m - n_full) * 7 + groups * 6)
+    # FP32 instructions of the double-float J-row kernel (FMA counted once): per row and cell
+    # 6 faces x (difference 20 + product 7 + sum term 8) + 3 to renormalize (6 x (7 + 8) + 3
+    # when one receiver electrode is at infinity); per new source and cell 6 x (20 + 7), or
+    # 6 x 7 without a B electrode
+    fp32_inst = N * (n_full * 213 + (m - n_full) * 93 + src_b * 162 + src_a * 42)
     jac_ms = float(np.median(jac))
-    ach = fp64_inst / (jac_ms / 1e3) / 1e12
+    ach = fp32_inst / (jac_ms / 1e3) / 1e12
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    alu_peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     value = world * args.steps / (ms / 1e3)
     out = {"metric": "ERT model evaluations/s (pole fields, g and all rows of J)", "value": value,
            "unit": "evaluations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -414,12 +422,13 @@ def run_ert(args):
                       "%.1f GB, J %.1f GB)" % (sv.n_e * N * 8 / 1e9, m * N * 8 / 1e9)},
            "forward_ms": float(np.median(fwd)), "jacobian_rows_ms": jac_ms, "pcg_iters": iters,
            "rel_res_true": float(info.rel_res_true),
-           "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_INST_PEAK_T, "unit": "T FP64 inst/s",
-                        "frac": ach / FP64_INST_PEAK_T, "traffic": NCU_BYTES_PER_J_ENTRY * m * N,
+           "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "T FP32 inst/s",
+                        "frac": ach / alu_peak, "traffic": NCU_BYTES_PER_J_ENTRY * m * N,
                         "traffic_note": "ncu 64^3 capture (32 electrodes, m = 496), scaled by J entries per launch",
                         "kernel": "k_jacobian<rows>",
-                        "note": "FP64 instructions of the J-row kernel (%d per launch) / its event time; "
-                                "peak = nominal 1.25 TFLOP/s FP64 as FMA instructions" % fp64_inst},
+                        "note": "FP32 instructions of the double-float J-row kernel (%d per launch) / its "
+                                "event time; peak = FP32 issue rate (152 SMs x 128 lanes x max SM clock)"
+                                % fp32_inst},
            "clocks": clocks, "impl": "ours"}
     if e2e_ms:
         out["e2e"] = {"value": world * args.e2e_steps / (e2e_ms / 1e3), "unit": "evaluations/s",

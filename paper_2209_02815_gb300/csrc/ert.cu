@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "h1w_internal.cuh"
+#include "mg_df64_util.cuh"
 
 namespace h1w {
 namespace {
@@ -544,8 +545,10 @@ __global__ void k_measure(const double* __restrict__ U, int64_t N, const int* __
 }
 
 // Shared layout: D[e][face][cell] jumps u_e(c) - u_e(neighbour) (u_e(c) across a Dirichlet
-// face, 0 across a zero-flux one), then W[face][cell] = d(conductance)/dm_c, then the
-// warps' partial sums of J^T r.
+// face, 0 across a zero-flux one), then W[face][cell] = d(conductance)/dm_c, both formed in
+// FP64 and stored as double-floats, then the warps' partial sums of J^T r. The products
+// and sums of a row run in double-float arithmetic (about 48 bits) on the FP32 pipes, which
+// GB300 issues at 64 times its FP64 rate; only the scaling by -k_i is FP64.
 template <bool ROWS>
 __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const double* __restrict__ U, int ne,
                                                              const double* __restrict__ sig, unsigned dirichlet,
@@ -553,9 +556,9 @@ __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const doub
                                                              int m, const double* __restrict__ rv, double* __restrict__ J,
                                                              double* __restrict__ JTr) {
   extern __shared__ double sm[];
-  double* D = sm;
-  double* Wf = D + (size_t)ne * 6 * kJacCells;
-  double* red = Wf + 6 * kJacCells;
+  df* D = reinterpret_cast<df*>(sm);
+  df* Wf = D + (size_t)ne * 6 * kJacCells;
+  double* red = reinterpret_cast<double*>(Wf + 6 * kJacCells);
   const int64_t N = L.N;
   const int64_t p0 = (int64_t)blockIdx.x * kJacCells;
   const int64_t st[3] = {1, L.nx, (int64_t)L.nx * L.ny};
@@ -579,12 +582,12 @@ __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const doub
         w = 2.0 * G[a] * s;
       }
     }
-    Wf[t] = w;
+    Wf[t] = df_from_double_fast(w);
   }
   for (int t = threadIdx.x; t < ne * kJacCells; t += blockDim.x) {
     const int e = t / kJacCells, c = t % kJacCells;
     const int64_t p = p0 + c;
-    double* De = D + (size_t)e * 6 * kJacCells;
+    df* De = D + (size_t)e * 6 * kJacCells;
     if (p < N) {
       int ijk[3];
       cell_ijk(L, p, ijk[0], ijk[1], ijk[2]);
@@ -594,52 +597,54 @@ __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const doub
       for (int f = 0; f < 6; ++f) {
         const int a = f >> 1, side = f & 1;
         const bool inside = side ? ijk[a] < nn[a] - 1 : ijk[a] > 0;
-        De[f * kJacCells + c] = inside ? up - u[side ? p + st[a] : p - st[a]] : up;  // W is 0 on zero-flux faces
+        // W is 0 on zero-flux faces
+        De[f * kJacCells + c] = df_from_double_fast(inside ? up - u[side ? p + st[a] : p - st[a]] : up);
       }
     } else {
 #pragma unroll
-      for (int f = 0; f < 6; ++f) De[f * kJacCells + c] = 0.0;
+      for (int f = 0; f < 6; ++f) De[f * kJacCells + c] = df_make(0.f, 0.f);
     }
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, c = threadIdx.x & 31;
   const int64_t p = p0 + c;
-  double w6[6];
+  df w6[6];
 #pragma unroll
   for (int f = 0; f < 6; ++f) w6[f] = Wf[f * kJacCells + c];
   // The measurements of a warp mostly share their source (A, B) with the previous one
   // (survey rows are ordered by source), so t_f = W_f (D_A - D_B) is formed once per
-  // source and each row costs one subtraction and one FMA per face.
+  // source and each row costs one difference, one product and one sum term per face.
   double acc_r = 0.0;
   int la = -2, lb = -2;
-  double t6[6];
+  df t6[6];
   for (int i = warp; i < m; i += kJacWarps) {
     const int4 q = abmn[i];
     if (q.x != la || q.y != lb) {  // warp-uniform
       la = q.x;
       lb = q.y;
-      const double* DA = la >= 0 ? D + (size_t)la * 6 * kJacCells + c : nullptr;
-      const double* DB = lb >= 0 ? D + (size_t)lb * 6 * kJacCells + c : nullptr;
+      const df* DA = la >= 0 ? D + (size_t)la * 6 * kJacCells + c : nullptr;
+      const df* DB = lb >= 0 ? D + (size_t)lb * 6 * kJacCells + c : nullptr;
 #pragma unroll
       for (int f = 0; f < 6; ++f) {
-        const double dv = DA ? (DB ? DA[f * kJacCells] - DB[f * kJacCells] : DA[f * kJacCells])
-                             : (DB ? -DB[f * kJacCells] : 0.0);
-        t6[f] = w6[f] * dv;
+        const df dv = DA ? (DB ? df_sub(DA[f * kJacCells], DB[f * kJacCells]) : DA[f * kJacCells])
+                         : (DB ? df_neg(DB[f * kJacCells]) : df_make(0.f, 0.f));
+        t6[f] = df_mul(w6[f], dv);
       }
     }
-    const double* DM = q.z >= 0 ? D + (size_t)q.z * 6 * kJacCells + c : nullptr;
-    const double* DN = q.w >= 0 ? D + (size_t)q.w * 6 * kJacCells + c : nullptr;
-    double acc = 0.0;
+    const df* DM = q.z >= 0 ? D + (size_t)q.z * 6 * kJacCells + c : nullptr;
+    const df* DN = q.w >= 0 ? D + (size_t)q.w * 6 * kJacCells + c : nullptr;
+    dfmg::dsum acc;
     if (DM && DN) {
 #pragma unroll
-      for (int f = 0; f < 6; ++f) acc = fma(t6[f], DM[f * kJacCells] - DN[f * kJacCells], acc);
+      for (int f = 0; f < 6; ++f) acc.add(df_mul(t6[f], df_sub(DM[f * kJacCells], DN[f * kJacCells])));
     } else if (DM || DN) {
-      const double* D1 = DM ? DM : DN;
+      const df* D1 = DM ? DM : DN;
 #pragma unroll
-      for (int f = 0; f < 6; ++f) acc = fma(t6[f], D1[f * kJacCells], acc);
-      if (!DM) acc = -acc;
+      for (int f = 0; f < 6; ++f) acc.add(df_mul(t6[f], D1[f * kJacCells]));
     }
-    const double val = -kf[i] * acc;
+    double sum = df_to_double(acc.get());
+    if (!DM && DN) sum = -sum;
+    const double val = -kf[i] * sum;
     if (ROWS) {
       if (p < N) J[(int64_t)i * N + p] = val;
     } else {
