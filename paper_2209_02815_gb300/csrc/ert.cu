@@ -115,11 +115,14 @@ size_t layout(Layout& W, char* base, const Level* lev, int nlev, int n_e, int m)
   return B.off + 256;
 }
 
+// (i, j, k) of cell p in 32-bit unsigned arithmetic (the forward checks N < 2^31): 64-bit
+// division is a long software sequence, and the one-field-per-thread kernels pay it per field
 __device__ __forceinline__ void cell_ijk(const Level& L, int64_t p, int& i, int& j, int& k) {
-  i = (int)(p % L.nx);
-  const int64_t q = p / L.nx;
-  j = (int)(q % L.ny);
-  k = (int)(q / L.ny);
+  const unsigned u = (unsigned)p, nx = (unsigned)L.nx, ny = (unsigned)L.ny;
+  const unsigned q = u / nx;
+  i = (int)(u - q * nx);
+  k = (int)(q / ny);
+  j = (int)(q - (unsigned)k * ny);
 }
 
 __device__ __forceinline__ double harmonic_face(double G, double a, double b) { return G * 2.0 * a * b / (a + b); }
@@ -243,45 +246,45 @@ __global__ void k_apply64(Level L, const double* tx, const double* ty, const dou
 
 // ---- FP32 V-cycle -------------------------------------------------------------------
 
-__global__ void k_cheb_first32(Level L, Coef32 C, int nrhs, const float* __restrict__ b, float* __restrict__ x,
+// The FP32 cycle kernels take one field per thread (grid y = field): the blocks in flight
+// then work on the same field, whose neighbouring planes stay in L2, where a loop over the
+// fields inside each thread spread the working set over all of them.
+__global__ void k_cheb_first32(Level L, Coef32 C, const float* __restrict__ b, float* __restrict__ x,
                                float* __restrict__ r, float* __restrict__ d, int zero_x, float inv_theta) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
   const float di = C.dinv[p] * inv_theta;
-  for (int e = 0; e < nrhs; ++e) {
-    const int64_t o = e * L.N;
-    float rv = b[o + p];
-    if (!zero_x) rv -= stencil_apply(S, x + o, p);
-    r[o + p] = rv;
-    d[o + p] = di * rv;
-    if (zero_x) x[o + p] = di * rv;
-  }
+  const int64_t o = (int64_t)blockIdx.y * L.N;
+  float rv = b[o + p];
+  if (!zero_x) rv -= stencil_apply(S, x + o, p);
+  r[o + p] = rv;
+  d[o + p] = di * rv;
+  if (zero_x) x[o + p] = di * rv;
 }
 
-__global__ void k_cheb_step32(Level L, Coef32 C, int nrhs, float* __restrict__ r, const float* __restrict__ dold,
+__global__ void k_cheb_step32(Level L, Coef32 C, float* __restrict__ r, const float* __restrict__ dold,
                               float* __restrict__ dnew, float* __restrict__ x, float c1, float c2, int add_old) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
   const float di = C.dinv[p];
-  for (int e = 0; e < nrhs; ++e) {
-    const int64_t o = e * L.N;
-    const float d0 = dold[o + p];
-    const float rv = r[o + p] - stencil_apply(S, dold + o, p);
-    const float dv = c1 * d0 + c2 * di * rv;
-    r[o + p] = rv;
-    dnew[o + p] = dv;
-    x[o + p] += add_old ? d0 + dv : dv;
-  }
+  const int64_t o = (int64_t)blockIdx.y * L.N;
+  const float d0 = dold[o + p];
+  const float rv = r[o + p] - stencil_apply(S, dold + o, p);
+  const float dv = c1 * d0 + c2 * di * rv;
+  r[o + p] = rv;
+  dnew[o + p] = dv;
+  x[o + p] += add_old ? d0 + dv : dv;
 }
 
-__global__ void k_resid32(Level L, Coef32 C, int nrhs, const float* __restrict__ b, const float* __restrict__ x,
+__global__ void k_resid32(Level L, Coef32 C, const float* __restrict__ b, const float* __restrict__ x,
                           float* __restrict__ r) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
-  for (int e = 0; e < nrhs; ++e) r[e * L.N + p] = b[e * L.N + p] - stencil_apply(S, x + e * L.N, p);
+  const int64_t o = (int64_t)blockIdx.y * L.N;
+  r[o + p] = b[o + p] - stencil_apply(S, x + o, p);
 }
 
 __global__ void k_add32(int64_t n, const float* __restrict__ d, float* __restrict__ x) {
@@ -684,8 +687,9 @@ void smooth32(const Layout& W, const Level* lev, int l, int ne, const Cheb& K, c
               cudaStream_t s) {
   const Level& L = lev[l];
   const Coef32 C = coef_of(W, l);
-  k_cheb_first32<<<nblk(L.N), kThreads, 0, s>>>(L, C, ne, b, x, W.r[l], W.da[l], zero_x ? 1 : 0, K.inv_theta);
-  k_cheb_step32<<<nblk(L.N), kThreads, 0, s>>>(L, C, ne, W.r[l], W.da[l], W.db[l], x, K.c1, K.c2, zero_x ? 0 : 1);
+  const dim3 grid(nblk(L.N), ne);
+  k_cheb_first32<<<grid, kThreads, 0, s>>>(L, C, b, x, W.r[l], W.da[l], zero_x ? 1 : 0, K.inv_theta);
+  k_cheb_step32<<<grid, kThreads, 0, s>>>(L, C, W.r[l], W.da[l], W.db[l], x, K.c1, K.c2, zero_x ? 0 : 1);
   note_launches(2);
 }
 
@@ -694,7 +698,7 @@ void vcycle32(const Layout& W, const Level* lev, int nl, int ne, cudaStream_t s)
   const Cheb K = cheb_coefs();
   for (int l = 0; l < nl - 1; ++l) {
     smooth32(W, lev, l, ne, K, W.b[l], W.x[l], true, s);
-    k_resid32<<<nblk(lev[l].N), kThreads, 0, s>>>(lev[l], coef_of(W, l), ne, W.b[l], W.x[l], W.r[l]);
+    k_resid32<<<dim3(nblk(lev[l].N), ne), kThreads, 0, s>>>(lev[l], coef_of(W, l), W.b[l], W.x[l], W.r[l]);
     k_restrict32<<<dim3(nblk(lev[l + 1].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], W.r[l], W.b[l + 1]);
     note_launches(2);
   }
@@ -710,6 +714,10 @@ void vcycle32(const Layout& W, const Level* lev, int nl, int ne, cudaStream_t s)
 }
 
 h1w_status validate_survey(const Level* lev, const h1w_survey* sv, std::string& err) {
+  if (lev[0].N >= (int64_t(1) << 31)) {
+    err = "ert: grids of 2^31 cells or more are not supported";
+    return H1W_EUNSUPPORTED;
+  }
   if (!sv || sv->n_e < 1 || sv->n_e > H1W_ERT_MAX_ELECTRODES || sv->m < 0 || !sv->cell ||
       (sv->m > 0 && (!sv->abmn || !sv->k))) {
     err = "survey: need 1..H1W_ERT_MAX_ELECTRODES electrodes, m >= 0 and non-NULL arrays";
