@@ -234,6 +234,21 @@ h1w_status h1w_level_info(const h1w_ctx* ctx, int32_t level, int32_t* nlevels, i
 h1w_status h1w_apply_op_static(const h1w_grid* grid, int32_t m, const double* J, const double* p,
                                double* q, void* stream);
 
+/* ---- Direct solve (the paper's Gauss-Newton step with an exact inverse) --------
+ *
+ * The comparison variant of Sec. 3.1 for small grids: x = (alpha (K + M) + J^T J)^-1 b
+ * with the J of the last h1w_capacitance, by forming the N x N matrix densely in FP64
+ * and factorizing it with the library's blocked Cholesky (the algorithm "Gauss-Newton
+ * with direct solver" uses a dense factorization in place of the iterative solve).
+ * The workspace (DEVICE, 256-byte aligned) holds the matrix: h1w_direct_workspace_size
+ * bytes, 0 when N exceeds H1W_DIRECT_MAX_N (the triangular solves keep x in one
+ * block's shared memory). b, x: DEVICE, N entries, may coincide. H1W_ENOTSPD when a
+ * pivot is not positive. Synchronizes. */
+#define H1W_DIRECT_MAX_N 6144
+
+size_t h1w_direct_workspace_size(const h1w_ctx* ctx);
+h1w_status h1w_solve_direct(h1w_ctx* ctx, const double* b, double* x, void* workspace, size_t ws_bytes);
+
 /* ---- ERT forward model and Jacobian (Sec. 4.1, Eqs. 4.1-4.5) ------------------
  *
  * On the context's H1W_FV_CELL grid, with conductivity sigma = exp(m) per cell:

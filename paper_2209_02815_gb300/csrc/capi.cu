@@ -1181,6 +1181,38 @@ const char* h1w_last_error(const h1w_ctx* c) {
   return c->err.c_str();
 }
 
+size_t h1w_direct_workspace_size(const h1w_ctx* c) {
+  if (!c || c->lev[0].N > H1W_DIRECT_MAX_N) return 0;
+  return sizeof(double) * (size_t)c->lev[0].N * (size_t)c->lev[0].N + 256;
+}
+
+h1w_status h1w_solve_direct(h1w_ctx* c, const double* b, double* x, void* workspace, size_t ws_bytes) {
+  if (!c) return h1w::set_global_error(H1W_EINVAL, "h1w_solve_direct: NULL context");
+  if (!b || !x || !workspace) return fail(c, H1W_EINVAL, "h1w_solve_direct: NULL argument");
+  const size_t need = h1w_direct_workspace_size(c);
+  if (need == 0) return fail(c, H1W_EUNSUPPORTED, "h1w_solve_direct: grid larger than H1W_DIRECT_MAX_N");
+  if (ws_bytes < need - 256) return fail(c, H1W_EINVAL, "h1w_solve_direct: workspace too small");
+  if (c->m < 0) return fail(c, H1W_ESTATE, "call h1w_capacitance first");
+  const int n = (int)c->lev[0].N;
+  double* A = static_cast<double*>(workspace);
+  cudaMemsetAsync(A, 0, sizeof(double) * (size_t)n * n, c->stream);
+  launch_assemble_dense(c->disc, c->lev[0], A, c->stream);          // K + M
+  launch_dense_gn(A, n, c->grid.alpha, c->J, c->m, c->stream);       // alpha (K + M) + J^T J
+  cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
+  launch_chol(A, n, c->dstatus, c->stream);
+  if (x != b) cudaMemcpyAsync(x, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+  launch_trsv_lower(A, n, x, 1, c->stream);
+  launch_trsv_upper_t(A, n, x, 1, c->stream);
+  int status = 0;
+  cudaMemcpyAsync(&status, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  const cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, H1W_ECUDA, std::string("h1w_solve_direct: ") + cudaGetErrorString(e));
+  const h1w_status st = cuda_check(c, "h1w_solve_direct");
+  if (st != H1W_OK) return st;
+  if (status & kStatusNotSpd) return fail(c, H1W_ENOTSPD, "h1w_solve_direct: matrix is not numerically positive definite");
+  return H1W_OK;
+}
+
 size_t h1w_ert_workspace_size(const h1w_ctx* c, int32_t n_e, int32_t m) {
   if (!c || c->disc != H1W_FV_CELL) return 0;
   return h1w::ert_workspace_bytes(c->lev, c->nlev, n_e, m);

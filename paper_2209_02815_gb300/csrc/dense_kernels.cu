@@ -813,6 +813,45 @@ void launch_woodbury_update(const double* H, int m, int64_t N, const double* v, 
   note_launches(1);
 }
 
+// A = alpha A + J^T J for the dense direct solve: J (m x n, row-major) in 32-row slices
+// staged in shared memory, one 32 x 32 tile of A per block, each thread four entries of it.
+__global__ void __launch_bounds__(256) k_dense_gn(double* __restrict__ A, int n, double alpha,
+                                                  const double* __restrict__ J, int m) {
+  __shared__ double Jp[32][33];
+  __shared__ double Jq[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int p0 = blockIdx.y * 32, q0 = blockIdx.x * 32;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i0 = 0; i0 < m; i0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const int i = i0 + r;
+      Jp[r][tx] = (i < m && p0 + tx < n) ? J[(int64_t)i * n + p0 + tx] : 0.0;
+      Jq[r][tx] = (i < m && q0 + tx < n) ? J[(int64_t)i * n + q0 + tx] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+      const double a = Jq[r][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fma(Jp[r][ty + 8 * u], a, acc[u]);
+    }
+    __syncthreads();
+  }
+  const int q = q0 + tx;
+  if (q >= n) return;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int p = p0 + ty + 8 * u;
+    if (p < n) A[(int64_t)p * n + q] = alpha * A[(int64_t)p * n + q] + acc[u];
+  }
+}
+
+void launch_dense_gn(double* A, int n, double alpha, const double* J, int m, cudaStream_t s) {
+  const dim3 grid((n + 31) / 32, (n + 31) / 32);
+  k_dense_gn<<<grid, dim3(32, 8), 0, s>>>(A, n, alpha, J, m);
+  note_launches(1);
+}
+
 void launch_chol(double* A, int n, int* status, cudaStream_t s) {
   for (int kb = 0; kb < n; kb += kNB) {
     const int below = (n - kb - 1) / kNB;  // 32-row blocks after the diagonal block

@@ -287,11 +287,6 @@ __global__ void k_resid32(Level L, Coef32 C, const float* __restrict__ b, const 
   r[o + p] = b[o + p] - stencil_apply(S, x + o, p);
 }
 
-__global__ void k_add32(int64_t n, const float* __restrict__ d, float* __restrict__ x) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) x[p] += d[p];
-}
-
 // Cell-centred trilinear transfer weights of one axis (2:1 agglomeration), as in the
 // context's cycle: prolongation 3/4 from the parent and 1/4 from the parent's
 // neighbour on the child's side (the parent alone at the boundary); R = P^T. Both

@@ -181,6 +181,8 @@ void launch_rows_dot_df(const df* A, int m, int64_t N, const df* v, double* part
 int launch_woodbury_update_df(const df* H, int m, int64_t N, const double* v, const double* z0, double alpha,
                               double* z, const double* r, double* partial, cudaStream_t s);
 void launch_chol(double* A, int n, int* status, cudaStream_t s);
+// A = alpha A + J^T J (A n x n, J m x n, row-major)
+void launch_dense_gn(double* A, int n, double alpha, const double* J, int m, cudaStream_t s);
 // in-place triangular solves with the lower factor L (n x n): x <- L^-1 x, x <- L^-T x
 void launch_trsv_lower(const double* L, int n, double* x, int nrhs, cudaStream_t s);
 void launch_trsv_upper_t(const double* L, int n, double* x, int nrhs, cudaStream_t s);

@@ -107,6 +107,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "h1w_adjoint": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, SZ]),
         "h1w_gn_step": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, P, P, SZ, D, D, I32, ctypes.c_uint32,
                               ctypes.POINTER(GnInfo)]),
+        "h1w_direct_workspace_size": (SZ, [P]),
+        "h1w_solve_direct": (I32, [P, P, P, P, SZ]),
         "h1w_last_error": (ctypes.c_char_p, [P]),
         "h1w_destroy": (None, [P]),
     }
@@ -445,6 +447,22 @@ class Solver:
         finally:
             self._leave()
         return x, info
+
+    def solve_direct(self, b, x=None):
+        """x = (alpha (K + M) + J^T J)^-1 b by a dense Cholesky factorization (small grids;
+        the J of the last capacitance call)."""
+        size = int(load().h1w_direct_workspace_size(self.ctx))
+        if size == 0:
+            raise H1wError(H1W_EUNSUPPORTED, "grid too large for h1w_solve_direct")
+        ws = torch.empty(size, dtype=torch.uint8, device=self.workspace.device)
+        x = torch.empty_like(b) if x is None else x
+        self._enter(b, x, ws)
+        try:
+            _check(load().h1w_solve_direct(self.ctx, _ptr(b, self.N, "b"), _ptr(x, self.N, "x"), ws.data_ptr(),
+                                           ws.numel()), self.ctx)
+        finally:
+            self._leave()
+        return x
 
     def ert_workspace(self, survey: Survey) -> torch.Tensor:
         size = h1w_ert_workspace_size(self.ctx, survey.n_e, survey.m)

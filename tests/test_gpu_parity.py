@@ -523,3 +523,38 @@ def test_laplace_only_preconditioner(case):
     assert max(wood) <= min(wood) + 3, its
     with pytest.raises(h1w.H1wError):
         S1.factors()
+
+
+@pytest.mark.parametrize("case", [_q1((33, 33)), _q1((64, 64)), _fv((16, 12, 8)), _fv((16, 16, 16))],
+                         ids=["q1_33", "q1_64", "fv16x12x8", "fv16"])
+def test_direct_solve_matches_oracle(case):
+    """h1w_solve_direct (dense alpha (K + M) + J^T J, blocked Cholesky, two triangular
+    solves) against the oracle's dense solve, and against the PCG solution."""
+    d, n, h = case
+    A = disc.regularization_operator(d, n, h).toarray()
+    N = A.shape[0]
+    rng = np.random.default_rng(51)
+    m, alpha = 24, 1e-2
+    J = rng.standard_normal((m, N)) / np.sqrt(N)
+    b = rng.standard_normal(N)
+    x_ref = np.linalg.solve(alpha * A + J.T @ J, b)
+    S = _gpu(d, n, h, alpha, m)
+    S.capacitance(_t(J))
+    x = S.solve_direct(_t(b))
+    assert _rel(x.cpu().numpy(), x_ref) <= 1e-10
+    xp, _ = S.pcg(_t(b), 1e-12, 300)
+    assert _rel(xp.cpu().numpy(), x.cpu().numpy()) <= 1e-9
+    # m = 0: the regularization operator alone; b and x may coincide
+    S0 = _gpu(d, n, h, alpha, 1)
+    S0.capacitance(None)
+    bb = _t(b)
+    S0.solve_direct(bb, bb)
+    assert _rel(bb.cpu().numpy(), np.linalg.solve(alpha * A, b)) <= 1e-10
+
+
+def test_direct_solve_refuses_large_grids():
+    S = _gpu("fv", (32, 32, 32), (1 / 32,) * 3, 1e-2, 1)
+    S.capacitance(None)
+    with pytest.raises(h1w.H1wError) as ei:
+        S.solve_direct(_t(np.ones(32 ** 3)))
+    assert ei.value.status == h1w.H1W_EUNSUPPORTED
