@@ -154,9 +154,14 @@ __global__ void k_coarsen_sigma(Level Lf, Level Lc, const double* __restrict__ s
 }
 
 // Conductances to the + neighbours and the diagonal of one level; FP64 copies and the
-// dense matrix (coarsest level) when asked.
-__global__ void k_coef(Level L, const double* __restrict__ sig, unsigned dirichlet, float* tx, float* ty, float* tz,
-                       float* dg, float* dinv, double* tx64, double* ty64, double* tz64, double* dg64, double* A) {
+// dense matrix (coarsest level) when asked. A Dirichlet face adds ghost * G_k * sigma to the
+// diagonal: ghost = 2 on the fine level (the model: u = 0 half a cell away). The coarse
+// levels only precondition, and there ghost = 4, so that the coarse operator matches P^T A P
+// on constants (a coarse boundary cell collects four fine ghost faces of 2 G_k sigma with
+// prolongation weight 1, while its own G_k is twice the fine one).
+__global__ void k_coef(Level L, const double* __restrict__ sig, unsigned dirichlet, double ghost, float* tx,
+                       float* ty, float* tz, float* dg, float* dinv, double* tx64, double* ty64, double* tz64,
+                       double* dg64, double* A) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   int i, j, k;
@@ -171,9 +176,9 @@ __global__ void k_coef(Level L, const double* __restrict__ sig, unsigned dirichl
   for (int a = 0; a < 3; ++a) {
     double tm = 0.0, tp = 0.0;
     if (idx[a] > 0) tm = harmonic_face(G[a], s, sig[p - st[a]]);
-    else if (dirichlet >> (2 * a) & 1) d += 2.0 * G[a] * s;
+    else if (dirichlet >> (2 * a) & 1) d += ghost * G[a] * s;
     if (idx[a] < n[a] - 1) tp = harmonic_face(G[a], s, sig[p + st[a]]);
-    else if (dirichlet >> (2 * a + 1) & 1) d += 2.0 * G[a] * s;
+    else if (dirichlet >> (2 * a + 1) & 1) d += ghost * G[a] * s;
     d += tm + tp;
     tplus[a] = tp;
     if (A) {
@@ -767,7 +772,8 @@ h1w_status build_operator(const Layout& W, const Level* lev, int nl, const doubl
   cudaMemsetAsync(W.Ac, 0, sizeof(double) * nc * nc, s);
   for (int l = 0; l < nl; ++l) {
     const bool top = l == 0, bottom = l == nl - 1;
-    k_coef<<<nblk(lev[l].N), kThreads, 0, s>>>(lev[l], W.sig[l], dirichlet, W.tx[l], W.ty[l], W.tz[l], W.dg[l],
+    k_coef<<<nblk(lev[l].N), kThreads, 0, s>>>(lev[l], W.sig[l], dirichlet, top ? 2.0 : 4.0, W.tx[l], W.ty[l],
+                                               W.tz[l], W.dg[l],
                                                W.dinv[l], top ? W.tx64 : nullptr, top ? W.ty64 : nullptr,
                                                top ? W.tz64 : nullptr, top ? W.dg64 : nullptr, bottom ? W.Ac : nullptr);
     note_launches(1);
