@@ -494,7 +494,10 @@ __device__ bool trsv_wait(const int* flag, int epoch, int* status, int* s_ok) {
     unsigned n = 0;
     int ok = 1;
     while (atomicAdd(const_cast<int*>(flag), 0) != epoch) {
-      if ((++n & 63) == 0 && (trsv_timer() - t0 > 1000000000ull || (atomicAdd(status, 0) & kStatusTimeout))) {
+      // about a second, or 2^22 polls should the global timer not advance (a legitimate wait,
+      // for the blocks before this one, lasts well under a millisecond)
+      if ((++n & 63) == 0 && (trsv_timer() - t0 > 1000000000ull || n >= (1u << 22) ||
+                              (atomicAdd(status, 0) & kStatusTimeout))) {
         atomicOr(status, kStatusTimeout);
         ok = 0;
         break;

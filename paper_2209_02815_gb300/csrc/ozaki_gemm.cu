@@ -62,6 +62,9 @@ constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 128;
 constexpr int kGemmThreads = 320;
 constexpr int kEpiWarps = 8;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // one second per wait
+// and at most this many polls per wait, should the global timer not advance (a legitimate
+// wait, for one copy or one MMA, lasts microseconds)
+constexpr uint32_t kWaitPolls = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -97,7 +100,7 @@ __device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag)
     if (mbar_try(a, parity)) return true;
     if ((n & 255) == 0) {
       if (*abort_flag) return false;
-      if (gtimer() - t0 > kWaitNs) return false;
+      if (gtimer() - t0 > kWaitNs || n >= kWaitPolls) return false;
     }
   }
 }
@@ -331,13 +334,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
     const int n = *issued;
     for (int it = (n > 2 ? n - 2 : 0); it < n; ++it) {
       const uint64_t t0 = gtimer();
-      while (!mbar_try(smem_u32(&bars[it & 1]), (it >> 1) & 1) && gtimer() - t0 < kWaitNs) {
+      for (uint32_t k = 0; !mbar_try(smem_u32(&bars[it & 1]), (it >> 1) & 1) && gtimer() - t0 < kWaitNs &&
+                           k < kWaitPolls;
+           ++k) {
       }
     }
     const int cc = *committed;
     if (cc > 0) {
       const uint64_t t0 = gtimer();
-      while (!mbar_try(smem_u32(&bars[4]), (cc - 1) & 1) && gtimer() - t0 < kWaitNs) {
+      for (uint32_t k = 0; !mbar_try(smem_u32(&bars[4]), (cc - 1) & 1) && gtimer() - t0 < kWaitNs && k < kWaitPolls;
+           ++k) {
       }
     }
   }
