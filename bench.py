@@ -501,6 +501,9 @@ def run_gn(args):
            "fwd_iters": [int(h_.fwd_iters) for h_ in hist], "gn_iters": [int(h_.gn_iters) for h_ in hist],
            "last_step_phases_ms": {"t_H_ms": t.t_H_ms, "t_C_ms": t.t_C_ms, "t_chol_ms": t.t_chol_ms,
                                    "t_pcg_ms": t.t_pcg_ms},
+           "roofline": None,
+           "roofline_note": "a GN step runs the kernels of the default line (GN solve, about 70 % of the step) "
+                            "and of --ert (forward and J rows); their rooflines are reported there",
            "clocks": clocks, "impl": "ours"}
     if rank == 0:
         print(json.dumps(out))

@@ -220,3 +220,22 @@ def test_forward_warm_start():
     gc = g_cold.cpu().numpy()
     np.testing.assert_allclose(g_warm.cpu().numpy(), gc, rtol=1e-9, atol=1e-9 * np.abs(gc).max())
     assert float(torch.abs(U_warm - U_cold).max() / torch.abs(U_cold).max()) < 1e-9
+
+
+def test_gn_step_and_direct_argument_checks():
+    n, h = (12, 10, 8), (0.1, 0.1, 0.1)
+    N = int(np.prod(n))
+    sv = _random_survey(n, 4, 6, seed=31)
+    s = h1w.Solver(h1w.H1W_FV_CELL, n, h, 1.0, 3, device=DEV)   # m_max = 3 < survey.m
+    t = lambda k: torch.zeros(k, dtype=torch.float64, device=DEV)
+    ws = s.ert_workspace(sv)
+    with pytest.raises(h1w.H1wError) as ei:
+        h1w.h1w_gn_step(s.ctx, sv, t(sv.m), t(N), t(N), t(sv.n_e * N), t(sv.m * N), t(sv.m), t(3 * N + sv.m), ws,
+                        1e-10, 1e-8, 100, N)
+    assert ei.value.status == h1w.H1W_EINVAL
+    with pytest.raises(h1w.H1wError) as ei:   # no capacitance call yet
+        s.solve_direct(t(N))
+    assert ei.value.status == h1w.H1W_ESTATE
+    with pytest.raises(h1w.H1wError) as ei:   # unknown forward flag
+        h1w.h1w_forward(s.ctx, sv, t(N), t(sv.n_e * N), t(sv.m), ws, 1e-10, 100, N, flags=2)
+    assert ei.value.status == h1w.H1W_EINVAL
