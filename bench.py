@@ -373,6 +373,25 @@ def run_ert(args):
         fwd = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)]
         jac = [ev[2 * i + 1].elapsed_time(ev[2 * i + 2]) for i in range(args.steps)]
 
+        # the data term from the fields (no J stored: J^T r of h1w_adjoint, J p of h1w_ert_jvp)
+        # against the same products with the stored J (library FP64 GEMV), one pass each
+        r = torch.ones(sv.m, dtype=torch.float64, device=dev)
+        pv = torch.ones(N, dtype=torch.float64, device=dev)
+        fe = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        fe[0].record(stream)
+        JTr = S.adjoint(sv, ls, U, r=r, ws=ws)[0]
+        fe[1].record(stream)
+        S.jvp(sv, ls, U, pv, ws=ws)
+        fe[2].record(stream)
+        torch.mv(J.t(), r)
+        fe[3].record(stream)
+        torch.mv(J, pv)
+        fe[4].record(stream)
+        torch.cuda.synchronize()
+        fields_ms = {"JTr_from_fields": fe[0].elapsed_time(fe[1]), "Jp_from_fields": fe[1].elapsed_time(fe[2]),
+                     "JTr_stored_J_gemv": fe[2].elapsed_time(fe[3]), "Jp_stored_J_gemv": fe[3].elapsed_time(fe[4])}
+        del JTr
+
         # end to end through the public API: logsigma from pinned host memory, g back to it
         ls_host = torch.empty(N, dtype=torch.float64, pin_memory=True)
         ls_host.copy_(ls)
@@ -421,6 +440,7 @@ def run_ert(args):
                       "n": [n, n, n], "n_e": sv.n_e, "m": m, "l2": "inputs larger than L2 (fields "
                       "%.1f GB, J %.1f GB)" % (sv.n_e * N * 8 / 1e9, m * N * 8 / 1e9)},
            "forward_ms": float(np.median(fwd)), "jacobian_rows_ms": jac_ms, "pcg_iters": iters,
+           "data_term_ms": fields_ms,
            "rel_res_true": float(info.rel_res_true),
            "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "T FP32 inst/s",
                         "frac": ach / alu_peak, "traffic": NCU_BYTES_PER_J_ENTRY * m * N,

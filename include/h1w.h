@@ -277,7 +277,8 @@ typedef struct {
 
 /* Bytes of device workspace (256-byte aligned) that h1w_forward and h1w_adjoint
  * need for n_e electrodes and m measurements on this context's grid: about
- * (4 FP64 + 5 FP32) vectors per electrode plus the coefficients of every level.
+ * (4 FP64 + 5 FP32) vectors per electrode, the coefficients of every level and
+ * m N / 32 partial sums for h1w_ert_jvp.
  * 0 for invalid input or a context that is not H1W_FV_CELL. */
 size_t h1w_ert_workspace_size(const h1w_ctx* ctx, int32_t n_e, int32_t m);
 
@@ -305,6 +306,14 @@ h1w_status h1w_forward(h1w_ctx* ctx, const h1w_survey* survey, const double* log
  * fields are not touched). Synchronizes. */
 h1w_status h1w_adjoint(h1w_ctx* ctx, const h1w_survey* survey, const double* logsigma, const double* U,
                        const double* r, double* JTr, double* J, void* workspace, size_t ws_bytes);
+
+/* Jp (DEVICE, [m]) = J p for p (DEVICE, [N]), formed from the fields U of h1w_forward
+ * without storing J: each entry J_ic is formed from the face jumps of the pole fields,
+ * as in h1w_adjoint, and reduced over the cells in a fixed order. With the J^T r of
+ * h1w_adjoint it applies the Gauss-Newton operator's data term J^T J from n_e fields
+ * instead of m rows. Synchronizes. */
+h1w_status h1w_ert_jvp(h1w_ctx* ctx, const h1w_survey* survey, const double* logsigma, const double* U,
+                       const double* p, double* Jp, void* workspace, size_t ws_bytes);
 
 /* ---- Gauss-Newton step (Algorithm "Gauss-Newton with iterative solver") --------
  *

@@ -1240,6 +1240,15 @@ h1w_status h1w_adjoint(h1w_ctx* c, const h1w_survey* survey, const double* logsi
   return st == H1W_OK ? st : fail(c, st, err);
 }
 
+h1w_status h1w_ert_jvp(h1w_ctx* c, const h1w_survey* survey, const double* logsigma, const double* U,
+                       const double* p, double* Jp, void* workspace, size_t ws_bytes) {
+  if (!c) return h1w::set_global_error(H1W_EINVAL, "h1w_ert_jvp: NULL context");
+  if (c->disc != H1W_FV_CELL) return fail(c, H1W_EUNSUPPORTED, "h1w_ert_jvp: needs an H1W_FV_CELL grid");
+  std::string err;
+  const h1w_status st = h1w::ert_jvp(c->lev, c->nlev, c->stream, survey, logsigma, U, p, Jp, workspace, ws_bytes, err);
+  return st == H1W_OK ? st : fail(c, st, err);
+}
+
 h1w_status h1w_gn_step(h1w_ctx* c, const h1w_survey* survey, const double* g_obs, const double* m_ref,
                        double* mvec, double* U, double* J, double* g, double* scratch, void* ert_ws,
                        size_t ert_ws_bytes, double rtol_fwd, double rtol, int32_t maxit, uint32_t fwd_flags,

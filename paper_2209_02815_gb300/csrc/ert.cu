@@ -72,6 +72,7 @@ struct Layout {
   int* status;
   double *r64, *z64, *p64, *q64;
   double* partial;  // [2][n_e][kDotBlocks]
+  double* jvp;      // [m][blocks of the Jacobian kernel]: partial sums of J p
   double* scal;     // [kScal][n_e]
 };
 
@@ -111,6 +112,7 @@ size_t layout(Layout& W, char* base, const Level* lev, int nlev, int n_e, int m)
   W.p64 = B.take<double>(N * n_e);
   W.q64 = B.take<double>(N * n_e);
   W.partial = B.take<double>(2 * (size_t)n_e * kDotBlocks);
+  W.jvp = B.take<double>((size_t)m * (size_t)((N + kJacCells - 1) / kJacCells));
   W.scal = B.take<double>((size_t)kScal * n_e);
   return B.off + 256;
 }
@@ -552,7 +554,11 @@ __global__ void k_measure(const double* __restrict__ U, int64_t N, const int* __
 // FP64 and stored as double-floats, then the warps' partial sums of J^T r. The products
 // and sums of a row run in double-float arithmetic (about 48 bits) on the FP32 pipes, which
 // GB300 issues at 64 times its FP64 rate; only the scaling by -k_i is FP64.
-template <bool ROWS>
+// MODE kRows writes the rows of J, kJTr writes J^T r (r = rv), kJvp writes the per-block
+// partial sums of J p (p = rv, indexed by cell) to J[i * gridDim.x + block].
+enum { kRows = 0, kJTr = 1, kJvp = 2 };
+
+template <int MODE>
 __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const double* __restrict__ U, int ne,
                                                              const double* __restrict__ sig, unsigned dirichlet,
                                                              const int4* __restrict__ abmn, const double* __restrict__ kf,
@@ -618,6 +624,7 @@ __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const doub
   // (survey rows are ordered by source), so t_f = W_f (D_A - D_B) is formed once per
   // source and each row costs one difference, one product and one sum term per face.
   double acc_r = 0.0;
+  const double pc = (MODE == kJvp && p < N) ? rv[p] : 0.0;
   int la = -2, lb = -2;
   df t6[6];
   for (int i = warp; i < m; i += kJacWarps) {
@@ -648,13 +655,18 @@ __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const doub
     double sum = df_to_double(acc.get());
     if (!DM && DN) sum = -sum;
     const double val = -kf[i] * sum;
-    if (ROWS) {
+    if (MODE == kRows) {
       if (p < N) J[(int64_t)i * N + p] = val;
-    } else {
+    } else if (MODE == kJTr) {
       acc_r = fma(rv[i], val, acc_r);
+    } else {  // the warp's 32 cells of row i
+      double v = val * pc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (c == 0) J[(int64_t)i * gridDim.x + blockIdx.x] = v;
     }
   }
-  if (!ROWS) {
+  if (MODE == kJTr) {
     red[warp * kJacCells + c] = acc_r;
     __syncthreads();
     if (warp == 0 && p < N) {
@@ -663,6 +675,16 @@ __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const doub
       JTr[p] = s;
     }
   }
+}
+
+// Jp_i = sum over blocks of the partial sums of row i (one block per row, fixed order)
+__global__ void k_row_sums(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  __shared__ double red[kThreads / 32];
+  const double* row = partial + (int64_t)blockIdx.x * nb;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += row[b];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
 size_t jac_smem(int ne) { return sizeof(double) * ((size_t)ne * 6 * kJacCells + 6 * kJacCells + kJacWarps * kJacCells); }
@@ -931,18 +953,47 @@ h1w_status ert_adjoint(const Level* lev, int nl, cudaStream_t s, const h1w_surve
   const size_t smem = jac_smem(ne);
   const unsigned grid = (unsigned)((L0.N + kJacCells - 1) / kJacCells);
   if (J) {
-    cudaFuncSetAttribute(k_jacobian<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_jacobian<true><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.k, sv->m,
-                                                        nullptr, J, nullptr);
+    cudaFuncSetAttribute(k_jacobian<kRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobian<kRows><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.k, sv->m,
+                                                         nullptr, J, nullptr);
     note_launches(1);
   }
   if (JTr) {
-    cudaFuncSetAttribute(k_jacobian<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_jacobian<false><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.k, sv->m, r,
-                                                         nullptr, JTr);
+    cudaFuncSetAttribute(k_jacobian<kJTr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobian<kJTr><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.k, sv->m, r,
+                                                        nullptr, JTr);
     note_launches(1);
   }
   return check_cuda(s, err, "h1w_adjoint");
+}
+
+h1w_status ert_jvp(const Level* lev, int nl, cudaStream_t s, const h1w_survey* sv, const double* logsigma,
+                   const double* U, const double* pvec, double* Jp, void* ws, size_t ws_bytes, std::string& err) {
+  h1w_status st = validate_survey(lev, sv, err);
+  if (st != H1W_OK) return st;
+  if (!logsigma || !U || !pvec || (sv->m > 0 && !Jp) || !ws) {
+    err = "h1w_ert_jvp: NULL logsigma/U/p/Jp/workspace";
+    return H1W_EINVAL;
+  }
+  const int ne = sv->n_e;
+  Layout W;
+  if (layout(W, nullptr, lev, nl, ne, sv->m) > ws_bytes) {
+    err = "h1w_ert_jvp: workspace smaller than h1w_ert_workspace_size";
+    return H1W_EINVAL;
+  }
+  if (sv->m == 0) return H1W_OK;
+  layout(W, static_cast<char*>(ws), lev, nl, ne, sv->m);
+  upload_survey(W, sv, s);
+  const Level& L0 = lev[0];
+  k_exp<<<nblk(L0.N), kThreads, 0, s>>>(L0.N, logsigma, W.sig[0]);
+  const size_t smem = jac_smem(ne);
+  const unsigned grid = (unsigned)((L0.N + kJacCells - 1) / kJacCells);
+  cudaFuncSetAttribute(k_jacobian<kJvp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_jacobian<kJvp><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.k, sv->m, pvec,
+                                                      W.jvp, nullptr);
+  k_row_sums<<<sv->m, kThreads, 0, s>>>(W.jvp, (int)grid, Jp);
+  note_launches(3);
+  return check_cuda(s, err, "h1w_ert_jvp");
 }
 
 }  // namespace h1w

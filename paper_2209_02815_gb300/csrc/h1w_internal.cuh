@@ -219,6 +219,8 @@ size_t ert_workspace_bytes(const Level* lev, int nlev, int n_e, int m);
 h1w_status ert_forward(const Level* lev, int nlev, cudaStream_t s, const h1w_survey* sv, const double* logsigma,
                        double* U, double* g, void* ws, size_t ws_bytes, double rtol, int maxit, bool warm,
                        h1w_info* info, std::string& err);
+h1w_status ert_jvp(const Level* lev, int nlev, cudaStream_t s, const h1w_survey* sv, const double* logsigma,
+                   const double* U, const double* p, double* Jp, void* ws, size_t ws_bytes, std::string& err);
 h1w_status ert_adjoint(const Level* lev, int nlev, cudaStream_t s, const h1w_survey* sv, const double* logsigma,
                        const double* U, const double* r, double* JTr, double* J, void* ws, size_t ws_bytes,
                        std::string& err);

@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "h1w_ert_workspace_size": (SZ, [P, I32, I32]),
         "h1w_forward": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, SZ, D, I32, ctypes.c_uint32, IN]),
         "h1w_adjoint": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, SZ]),
+        "h1w_ert_jvp": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, SZ]),
         "h1w_gn_step": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, P, P, SZ, D, D, I32, ctypes.c_uint32,
                               ctypes.POINTER(GnInfo)]),
         "h1w_direct_workspace_size": (SZ, [P]),
@@ -521,6 +522,19 @@ class Solver:
             self._leave()
         self.m = survey.m
         return hist, g, J
+
+    def jvp(self, survey: Survey, logsigma, U, p, ws=None):
+        """J p from the fields U without storing J (h1w_ert_jvp)."""
+        ws = self.ert_workspace(survey) if ws is None else ws
+        Jp = torch.empty(survey.m, dtype=torch.float64, device=U.device)
+        self._enter(logsigma, U, p, Jp, ws)
+        try:
+            _check(load().h1w_ert_jvp(self.ctx, ctypes.byref(survey.c), _ptr(logsigma, self.N, "logsigma"),
+                                      _ptr(U, self.N * survey.n_e, "U"), _ptr(p, self.N, "p"),
+                                      _ptr(Jp, survey.m, "Jp"), ws.data_ptr(), ws.numel()), self.ctx)
+        finally:
+            self._leave()
+        return Jp
 
     def factors(self):
         m = self.m or 0

@@ -76,6 +76,11 @@ def test_forward_and_jacobian_match_oracle(n, h, dirichlet):
     # J^T r formed without J agrees with the stored rows of the same fields
     jtr_rows = Jg.T @ r
     assert np.abs(JTr.cpu().numpy() - jtr_rows).max() / np.abs(jtr_rows).max() < 1e-13
+    # and so does J p
+    pv = np.cos(np.arange(N) * 0.37)
+    Jp = s.jvp(sv, lst, U, torch.tensor(pv, device=DEV)).cpu().numpy()
+    assert np.abs(Jp - Jg @ pv).max() / np.abs(Jg @ pv).max() < 1e-12
+    assert np.abs(Jp - J0 @ pv).max() / np.abs(J0 @ pv).max() < 1e-8
 
 
 def test_jacobian_is_derivative_of_forward_on_gpu():
@@ -154,6 +159,10 @@ def test_full_size_properties(grid):
     assert float(torch.abs(rs + g).max() / torch.abs(g).max()) < 1e-9
     jr = J.T @ r
     assert float(torch.abs(JTr - jr).max() / torch.abs(jr).max()) < 1e-12
+    pv = torch.cos(torch.arange(n ** 3, device=DEV, dtype=torch.float64) * 0.37)
+    Jp = s.jvp(sv, ls, U, pv)
+    jp = J @ pv
+    assert float(torch.abs(Jp - jp).max() / torch.abs(jp).max()) < 1e-11
 
 
 def test_gn_steps_match_oracle():
