@@ -248,3 +248,39 @@ def test_gn_step_and_direct_argument_checks():
     with pytest.raises(h1w.H1wError) as ei:   # unknown forward flag
         h1w.h1w_forward(s.ctx, sv, t(N), t(sv.n_e * N), t(sv.m), ws, 1e-10, 100, N, flags=2)
     assert ei.value.status == h1w.H1W_EINVAL
+
+
+def test_max_electrodes():
+    """H1W_ERT_MAX_ELECTRODES = 128 electrodes: the Jacobian kernel stages 128 x 6 face
+    jumps for 32 cells (about 200 KB of shared memory per block). Fields, measurements,
+    J rows, J^T r and J p against the oracle; 129 electrodes are refused."""
+    n, h = (24, 20, 16), (1 / 24, 1 / 20, 1 / 16)
+    N = int(np.prod(n))
+    rng = np.random.default_rng(61)
+    ne = 128
+    cells = rng.choice(n[0] * n[1], size=ne, replace=False)
+    rows = []
+    for _ in range(300):
+        a, b, mm, nn = rng.choice(ne, size=4, replace=False)
+        rows.append((a, b if rng.random() < 0.5 else -1, mm, nn))
+    sv = h1w.Survey(cells, np.array(rows), rng.uniform(0.5, 2.0, 300), ALL_BUT_TOP)
+    s = _solver(n, h)
+    ls = _logsigma(n, 62)
+    lst = torch.tensor(ls, device=DEV)
+    g, U, info = s.forward(sv, lst, rtol=1e-13, maxit=300)
+    g0, U0 = oert.forward(n, h, ls, sv.cells, sv.abmn, sv.k, ALL_BUT_TOP)
+    assert np.abs(U.cpu().numpy() - U0).max() / np.abs(U0).max() < 1e-9
+    np.testing.assert_allclose(g.cpu().numpy(), g0, rtol=1e-9, atol=1e-9 * np.abs(g0).max())
+    r = np.sin(np.arange(sv.m))
+    JTr, J = s.adjoint(sv, lst, U, r=torch.tensor(r, device=DEV), rows=True)
+    J0 = oert.jacobian(n, h, ls, U0, sv.abmn, sv.k, ALL_BUT_TOP)
+    assert (np.abs(J.cpu().numpy() - J0).max(axis=1) / np.abs(J0).max(axis=1)).max() < 1e-8
+    assert np.abs(JTr.cpu().numpy() - J0.T @ r).max() / np.abs(J0.T @ r).max() < 1e-8
+    pv = np.cos(np.arange(N) * 0.11)
+    Jp = s.jvp(sv, lst, U, torch.tensor(pv, device=DEV)).cpu().numpy()
+    assert np.abs(Jp - J0 @ pv).max() / np.abs(J0 @ pv).max() < 1e-8
+    too_many = h1w.Survey(np.arange(129), [[0, -1, 1, 2]], [1.0], ALL_BUT_TOP)
+    assert h1w.h1w_ert_workspace_size(s.ctx, 129, 1) == 0
+    with pytest.raises(h1w.H1wError) as ei:
+        s.forward(too_many, lst, ws=torch.empty(1 << 20, dtype=torch.uint8, device=DEV))
+    assert ei.value.status == h1w.H1W_EINVAL
