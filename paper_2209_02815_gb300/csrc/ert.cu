@@ -63,6 +63,7 @@ struct Layout {
   int* cell;
   int4* abmn;
   double* k;
+  float2* nkdf;  // -k_i as double-floats (hi, lo)
   double* sig[kMaxLevels];
   double *tx64, *ty64, *tz64, *dg64;
   float *tx[kMaxLevels], *ty[kMaxLevels], *tz[kMaxLevels], *dg[kMaxLevels], *dinv[kMaxLevels];
@@ -84,6 +85,7 @@ size_t layout(Layout& W, char* base, const Level* lev, int nlev, int n_e, int m)
   W.cell = B.take<int>(n_e);
   W.abmn = B.take<int4>(m);
   W.k = B.take<double>(m);
+  W.nkdf = B.take<float2>(m);
   for (int l = 0; l < nlev; ++l) W.sig[l] = B.take<double>(lev[l].N);
   W.tx64 = B.take<double>(N);
   W.ty64 = B.take<double>(N);
@@ -554,6 +556,19 @@ __global__ void k_measure(const double* __restrict__ U, int64_t N, const int* __
 // FP64 and stored as double-floats, then the warps' partial sums of J^T r. The products
 // and sums of a row run in double-float arithmetic (about 48 bits) on the FP32 pipes, which
 // GB300 issues at 64 times its FP64 rate; only the scaling by -k_i is FP64.
+// A float as the equal double, by assembling the IEEE 754 bit fields with integer
+// instructions (a conversion instruction runs on the FP64 pipe, which GB300 issues at 1/64
+// of the FP32 rate). Zeros keep their sign; subnormal floats (below 1.2e-38) become zero;
+// infinities and NaNs keep their class.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u) return __hiloint2double(static_cast<int>(u & 0x80000000u), 0);
+  const unsigned e11 = (e == 0xFFu) ? 0x7FFu : e + (1023u - 127u);
+  const unsigned hi = (u & 0x80000000u) | (e11 << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
+}
+
 // MODE kRows writes the rows of J, kJTr writes J^T r (r = rv), kJvp writes the per-block
 // partial sums of J p (p = rv, indexed by cell) to J[i * gridDim.x + block].
 enum { kRows = 0, kJTr = 1, kJvp = 2 };
@@ -561,7 +576,7 @@ enum { kRows = 0, kJTr = 1, kJvp = 2 };
 template <int MODE>
 __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const double* __restrict__ U, int ne,
                                                              const double* __restrict__ sig, unsigned dirichlet,
-                                                             const int4* __restrict__ abmn, const double* __restrict__ kf,
+                                                             const int4* __restrict__ abmn, const float2* __restrict__ nkf,
                                                              int m, const double* __restrict__ rv, double* __restrict__ J,
                                                              double* __restrict__ JTr) {
   extern __shared__ double sm[];
@@ -652,9 +667,11 @@ __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const doub
 #pragma unroll
       for (int f = 0; f < 6; ++f) acc.add(df_mul(t6[f], D1[f * kJacCells]));
     }
-    double sum = df_to_double(acc.get());
-    if (!DM && DN) sum = -sum;
-    const double val = -kf[i] * sum;
+    df sum = acc.get();
+    if (!DM && DN) sum = df_neg(sum);
+    const float2 nk = nkf[i];
+    const df vd = df_mul(sum, df_make(nk.x, nk.y));  // -k_i * sum
+    const double val = f2d_bits(vd.hi) + f2d_bits(vd.lo);
     if (MODE == kRows) {
       if (p < N) J[(int64_t)i * N + p] = val;
     } else if (MODE == kJTr) {
@@ -777,6 +794,14 @@ h1w_status upload_survey(const Layout& W, const h1w_survey* sv, cudaStream_t s) 
   if (sv->m > 0) {
     cudaMemcpyAsync(W.abmn, sv->abmn, sizeof(int4) * sv->m, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(W.k, sv->k, sizeof(double) * sv->m, cudaMemcpyHostToDevice, s);
+    std::vector<float2> nk(sv->m);
+    for (int i = 0; i < sv->m; ++i) {
+      const double v = -sv->k[i];
+      nk[i].x = static_cast<float>(v);
+      nk[i].y = static_cast<float>(v - static_cast<double>(nk[i].x));
+    }
+    // pageable source: the copy has read it when the call returns
+    cudaMemcpyAsync(W.nkdf, nk.data(), sizeof(float2) * sv->m, cudaMemcpyHostToDevice, s);
   }
   return H1W_OK;
 }
@@ -954,13 +979,13 @@ h1w_status ert_adjoint(const Level* lev, int nl, cudaStream_t s, const h1w_surve
   const unsigned grid = (unsigned)((L0.N + kJacCells - 1) / kJacCells);
   if (J) {
     cudaFuncSetAttribute(k_jacobian<kRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_jacobian<kRows><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.k, sv->m,
+    k_jacobian<kRows><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.nkdf, sv->m,
                                                          nullptr, J, nullptr);
     note_launches(1);
   }
   if (JTr) {
     cudaFuncSetAttribute(k_jacobian<kJTr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_jacobian<kJTr><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.k, sv->m, r,
+    k_jacobian<kJTr><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.nkdf, sv->m, r,
                                                         nullptr, JTr);
     note_launches(1);
   }
@@ -989,7 +1014,7 @@ h1w_status ert_jvp(const Level* lev, int nl, cudaStream_t s, const h1w_survey* s
   const size_t smem = jac_smem(ne);
   const unsigned grid = (unsigned)((L0.N + kJacCells - 1) / kJacCells);
   cudaFuncSetAttribute(k_jacobian<kJvp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_jacobian<kJvp><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.k, sv->m, pvec,
+  k_jacobian<kJvp><<<grid, kJacWarps * 32, smem, s>>>(L0, U, ne, W.sig[0], sv->dirichlet, W.abmn, W.nkdf, sv->m, pvec,
                                                       W.jvp, nullptr);
   k_row_sums<<<sv->m, kThreads, 0, s>>>(W.jvp, (int)grid, Jp);
   note_launches(3);
