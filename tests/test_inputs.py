@@ -3,6 +3,7 @@ import math
 import os
 
 import numpy as np
+import pytest
 
 from paper_2209_02815_gb300 import inputs
 
@@ -55,3 +56,30 @@ def test_ert_problem_small():
     # on the truncated unit cube the magnitude is below 1/sigma_bg.
     s = pr.J.sum(axis=1)
     assert (s < 0).mean() > 0.9
+
+
+@pytest.mark.parametrize("n", [32, 128, 192])
+def test_ert_surveys_have_finite_geometric_factors(n):
+    """The line pair protocol gives C(32, 2) = 496 rows. The 8 x 8 dipole-dipole grid is
+    truncated to 1024 rows. The 6 x 8 grid pair protocol of the inversion workload skips
+    the rows whose M and N are equidistant from A (1/|AM| - 1/|AN| = 0) and keeps the first
+    1000 of the others. Every factor is finite, every electrode cell lies in the top layer,
+    and no row repeats an electrode."""
+    for cells, abmn, k, _ in (inputs.ert_survey(n), inputs.ert_survey(n, grid=(8, 8), m_rows=1024),
+                              inputs.gn_survey(n)):
+        assert np.all(np.isfinite(k)) and np.all(k != 0)
+        assert np.all((cells >= 0) & (cells < n * n))
+        for row in abmn:
+            used = [e for e in row if e >= 0]
+            assert len(used) == len(set(used))
+    assert len(inputs.ert_survey(n)[1]) == 496
+    assert len(inputs.ert_survey(n, grid=(8, 8), m_rows=1024)[1]) == 1024
+    assert len(inputs.gn_survey(n)[1]) == 1000
+
+
+def test_gn_truth_anomalies():
+    """Two Gaussian anomalies of peak factors 10 and 0.1 on a 0.01 S/m background."""
+    ls = inputs.gn_truth(64)
+    s = np.exp(ls)
+    assert abs(s.max() / 0.01 - 10.0) < 0.5 and abs(s.min() / 0.01 - 0.1) < 0.02
+    assert np.median(s) == pytest.approx(0.01, rel=1e-3)
