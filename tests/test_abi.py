@@ -55,3 +55,24 @@ def test_rhs_block_buffers_capped_at_m_max():
     o = h1w.h1w_default_options()
     o.rhs_block = 4
     assert 0 < h1w.h1w_workspace_size(g, 8, o) < sizes[8]
+
+
+def test_new_entry_points_reject_null_context_without_gpu():
+    """The ERT, Gauss-Newton and direct-solve entry points check their context on the
+    host; the options default to the Laplace-Woodbury preconditioner."""
+    from paper_2209_02815_gb300 import h1w
+    lib = h1w.load()
+    assert lib.h1w_ert_workspace_size(None, 4, 10) == 0
+    assert lib.h1w_direct_workspace_size(None) == 0
+    sv = h1w.Survey([0], [[0, -1, 0, -1]], [1.0], 0b101111)
+    assert lib.h1w_forward(None, ctypes.byref(sv.c), None, None, None, None, 0, 1e-10, 10, 0, None) == h1w.H1W_EINVAL
+    assert lib.h1w_adjoint(None, ctypes.byref(sv.c), None, None, None, None, None, None, 0) == h1w.H1W_EINVAL
+    assert lib.h1w_ert_jvp(None, ctypes.byref(sv.c), None, None, None, None, None, 0) == h1w.H1W_EINVAL
+    assert lib.h1w_solve_direct(None, None, None, None, 0) == h1w.H1W_EINVAL
+    assert lib.h1w_gn_step(None, ctypes.byref(sv.c), None, None, None, None, None, None, None, None, 0, 1e-10, 1e-8,
+                           10, 0, None) == h1w.H1W_EINVAL
+    assert h1w.h1w_default_options().precond == 0
+    bad = h1w.h1w_default_options()
+    bad.precond = 2
+    g = h1w.make_grid(h1w.H1W_FV_CELL, (32, 32, 32), (1 / 32,) * 3, 1e-3)
+    assert h1w.h1w_workspace_size(g, 8, bad) == 0
