@@ -313,3 +313,62 @@ def test_laplace_only_exact_inverse_terminates_within_m_plus_1(d):
     Ainv = np.linalg.inv(A)
     x, it, rel = wb.pcg(lambda v: Aop @ v, lambda v: Ainv @ v / alpha, b, 1e-10, 50)
     assert 1 < it <= J.shape[0] + 1 and rel <= 1e-10, it
+
+
+# --------------------------------------------------------------------------
+# Gauss-Newton right-hand side (Eq. 2.9 scaled by beta, with the mass term)
+# --------------------------------------------------------------------------
+
+def _gn_rhs_case(disc_kind):
+    if disc_kind == "q1":
+        n, h = (7, 6), (1 / 6, 1 / 5)
+    else:
+        n, h = (5, 4, 3), (0.2, 0.25, 1 / 3)
+    A = disc.regularization_operator(disc_kind, n, h)
+    N = A.shape[0]
+    rng = np.random.default_rng(31)
+    m = 5
+    J = rng.standard_normal((m, N))
+    dm = rng.standard_normal(N)
+    d = rng.standard_normal(m)
+    return A, J, dm, d, 0.37
+
+
+@pytest.mark.parametrize("disc_kind", ["q1", "fv"])
+def test_gn_rhs_is_minus_the_gradient_of_the_linearized_objective(disc_kind):
+    """b is minus the gradient at dm' = 0 of the quadratic model
+    Q(dm') = 1/2 ||d + J dm'||^2 + alpha/2 (dm + dm')^T (K + M) (dm + dm'):
+    central differences of Q (exact for a quadratic up to rounding) along random
+    directions v give -b . v. A sign slip or a dropped term in either part fails."""
+    A, J, dm, d, alpha = _gn_rhs_case(disc_kind)
+    b = wb.gn_rhs(A, alpha, dm, J, d)
+
+    def Q(step):
+        r = d + J @ step
+        u = dm + step
+        return 0.5 * float(r @ r) + 0.5 * alpha * float(u @ (A @ u))
+
+    rng = np.random.default_rng(32)
+    for _ in range(6):
+        v = rng.standard_normal(dm.size)
+        eps = 1e-3
+        fd = (Q(eps * v) - Q(-eps * v)) / (2 * eps)
+        assert abs(fd + float(b @ v)) <= 1e-9 * (abs(fd) + np.linalg.norm(b) * np.linalg.norm(v))
+
+
+@pytest.mark.parametrize("disc_kind", ["q1", "fv"])
+def test_gn_rhs_from_the_stacked_least_squares_problem(disc_kind):
+    """With K + M = R^T R (numpy Cholesky), the linearized step solves the stacked
+    least-squares problem min ||[J; sqrt(alpha) R] s - y||, y = -[d; sqrt(alpha) R dm];
+    its normal-equation right-hand side [J; sqrt(alpha) R]^T y is b."""
+    A, J, dm, d, alpha = _gn_rhs_case(disc_kind)
+    R = np.linalg.cholesky(A.toarray()).T
+    S = np.vstack([J, np.sqrt(alpha) * R])
+    y = -np.concatenate([d, np.sqrt(alpha) * (R @ dm)])
+    want = S.T @ y
+    b = wb.gn_rhs(A, alpha, dm, J, d)
+    assert np.abs(b - want).max() <= 1e-12 * np.abs(want).max()
+    # and the step it gives is the least-squares minimizer (QR)
+    step = np.linalg.solve(S.T @ S, b)
+    ls = np.linalg.lstsq(S, y, rcond=None)[0]
+    assert np.abs(step - ls).max() <= 1e-9 * np.abs(ls).max()
