@@ -81,6 +81,10 @@ typedef struct {
                             alpha^-1 [L^-1 - alpha^-1 H C^-1 H^T] (default); 1 = Laplace only,
                             alpha^-1 L^-1, the paper's variant without the capacitance matrix
                             (Sec. 3.2), for which h1w_capacitance skips lines H, C and chol */
+  int32_t pcg_mode;      /* h1w_pcg: 0 = the iteration driven from the device: the loop is a CUDA graph
+                            with a conditional while node, the scalars stay on the GPU and the host
+                            waits once per (re)start (default); 1 = a host loop that reads the residual
+                            norm back every iteration and times individual kernels (h1w_get_timings) */
 } h1w_options;
 
 typedef struct {
@@ -111,6 +115,10 @@ typedef struct {
   float t_vc_down_ms;           /* fused down-leg kernel of the finest level (line H, double-float cycle) */
   float t_vc_up_ms;             /* fused up-leg kernel of the finest level (line H, double-float cycle) */
   int32_t n_vc_down, n_vc_up;
+  float t_split_j_ms;           /* digit split of J before each GEMM panel (line C, tensor cores) */
+  float t_split_h_ms;           /* digit split of H before each GEMM panel (line C, tensor cores) */
+  float t_d2df_ms;              /* FP64 -> double-float conversion of J's row batches (line H) */
+  int32_t n_split_j, n_split_h, n_d2df, reserved2;
 } h1w_timings;
 
 typedef struct h1w_ctx h1w_ctx;
@@ -153,6 +161,28 @@ h1w_status h1w_capacitance(h1w_ctx* ctx, int32_t m, const double* J);
  * returns; the results equal those of h1w_capacitance on the same J.
  * Synchronizes. */
 h1w_status h1w_capacitance_from_host(h1w_ctx* ctx, int32_t m, const double* J_host, double* J_dev);
+
+/* Starts the row-batch copies of J_host (page-locked HOST, m x N) into J_dev (DEVICE)
+ * on the context's copy stream and returns at once, so that the copy of the next
+ * system's J runs while the current system is solved; the next
+ * h1w_capacitance_from_host(ctx, m, J_host, J_dev) with the same three arguments then
+ * waits only for the rows that have not yet arrived, batch by batch. The copies are
+ * ordered after the work already queued on the context's stream. J_dev must not be read
+ * by a later call before that capacitance (e.g. it must not be the J of the capacitance
+ * that the next h1w_pcg uses); J_host must stay valid and unchanged until that
+ * capacitance returns. At most two copy sets are pending at a time (double buffering):
+ * H1W_ESTATE otherwise, or when another pending copy targets J_dev. No counterpart in the
+ * paper (its data never leave the host). */
+h1w_status h1w_prefetch_J(h1w_ctx* ctx, int32_t m, const double* J_host, double* J_dev);
+
+/* Per-row-batch timeline of the last h1w_capacitance_from_host, in ms from the start of
+ * its line H (negative when a prefetched copy began earlier): copy_begin/end of the batch's
+ * rows on the copy stream, cycle_begin/end of its conversion and V-cycles on the
+ * context's stream (cycle_begin waits for copy_end). *nbatch receives the batch count;
+ * the arrays (any may be NULL) receive min(cap, *nbatch) entries; rows = the batch sizes. */
+h1w_status h1w_get_copy_profile(const h1w_ctx* ctx, int32_t cap, int32_t* nbatch, int32_t* rows,
+                                float* copy_begin_ms, float* copy_end_ms, float* cycle_begin_ms,
+                                float* cycle_end_ms);
 
 /* z = P^-1 r with P = alpha L-hat + J^T J, evaluated by the Woodbury formula
  * of Sec. 3.2: z = alpha^-1 [ L-hat^-1 r - alpha^-1 H C^-1 H^T r ].
@@ -201,6 +231,21 @@ h1w_status h1w_capacitance_factors(h1w_ctx* ctx, double* C, double* L);
 h1w_status h1w_solve_batch(h1w_ctx* const* ctxs, int32_t count, const int32_t* m, const double* const* J,
                            const double* const* b, double* const* x, double rtol, int32_t maxit,
                            int32_t threads, h1w_info* info, h1w_status* status);
+
+/* The same as h1w_solve_batch (lines H, C, chol and PCG for `count` independent systems,
+ * each with its own context on its own distinct stream, precond = 0), but as ONE CUDA
+ * graph: every system's capacitance and its device-driven PCG loop (a conditional while
+ * node, as pcg_mode = 0) are captured as parallel branches of a single graph, which is
+ * launched once, so the GPU schedules all systems' kernels together with no host thread
+ * and no host round trip per iteration. The graph is kept and replayed while the
+ * contexts, m, J, b, x, rtol and maxit are the same as in the previous call (it is
+ * captured again otherwise). A system whose recursive residual met rtol but whose true
+ * residual did not continues with h1w_pcg's restarts. Returns H1W_OK when every system
+ * converged, else the first failing status (that context's h1w_last_error has the
+ * reason). Synchronizes. No counterpart in the paper (it solves one system at a time). */
+h1w_status h1w_solve_batch_graph(h1w_ctx* const* ctxs, int32_t count, const int32_t* m, const double* const* J,
+                                 const double* const* b, double* const* x, double rtol, int32_t maxit,
+                                 h1w_info* info, h1w_status* status);
 
 /* Phase times and launch counts of the last h1w_capacitance / h1w_pcg. */
 h1w_status h1w_get_timings(const h1w_ctx* ctx, h1w_timings* out);
@@ -341,6 +386,36 @@ h1w_status h1w_gn_step(h1w_ctx* ctx, const h1w_survey* survey, const double* g_o
                        double* m, double* U, double* J, double* g, double* scratch, void* ert_ws,
                        size_t ert_ws_bytes, double rtol_fwd, double rtol, int32_t maxit, uint32_t fwd_flags,
                        h1w_gn_info* info);
+
+/* ---- Line chol on a caller's matrix, and failure-path testing -------------------
+ *
+ * h1w_cholesky: A = L L^T in place for a symmetric positive definite n x n matrix A
+ * (DEVICE, row-major, FP64), with the blocked kernels of line chol (Algorithm "MINRES
+ * with the Laplace-Woodbury preconditioner") that factor the capacitance matrix: on
+ * return the lower triangle holds L and the strict upper triangle is zero. Runs on the
+ * context's stream and synchronizes. H1W_ENOTSPD (with text) when a pivot is not
+ * positive, i.e. A is not numerically positive definite; A then holds a partial factor. */
+#define H1W_CHOLESKY_MAX_N 16384
+
+h1w_status h1w_cholesky(h1w_ctx* ctx, int32_t n, double* A);
+
+/* h1w_inject_stall: for testing the failure path of the bounded device waits, without a
+ * GPU fault. kind H1W_STALL_CAP_GEMM makes the copy warp of the tensor-core capacitance
+ * GEMM issue no copies, so that the waits of its MMA and epilogue warps run out and
+ * h1w_capacitance returns H1W_ETIMEOUT; H1W_STALL_PREC_SOLVE makes the first block of the
+ * cooperative C^-1 solve inside the preconditioner publish no result (m > 32 needed), so
+ * that the waits of the other blocks run out and h1w_pcg / h1w_apply_prec report
+ * H1W_ETIMEOUT (with maxit small, since PCG then iterates on a broken preconditioner).
+ * wait_limit_ns sets the limit of every bounded wait of this context (0: the default of
+ * one second; at most 60 s). H1W_STALL_NONE restores normal operation; the context stays
+ * usable after a timeout (h1w_capacitance must be called again, since a timed-out call
+ * leaves no valid capacitance). No counterpart in the paper. */
+enum { H1W_STALL_NONE = 0, H1W_STALL_CAP_GEMM = 1, H1W_STALL_PREC_SOLVE = 2 };
+
+h1w_status h1w_inject_stall(h1w_ctx* ctx, int32_t kind, int64_t wait_limit_ns);
+
+/* Changes h1w_options.pcg_mode of a live context (0 device-driven graph, 1 host loop). */
+h1w_status h1w_set_pcg_mode(h1w_ctx* ctx, int32_t mode);
 
 /* Text of the last error on this context (ctx = NULL: the last error of
  * h1w_setup on this thread). Never NULL. */

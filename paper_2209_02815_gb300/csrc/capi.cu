@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -36,6 +37,19 @@ struct Bump {
 
 struct LevelBufs {
   double *x, *b, *r, *da, *db;
+};
+
+// One set of row-batch copies of J from page-locked host memory into a device buffer
+// (h1w_capacitance_from_host, h1w_prefetch_J). The events are recorded on the copy stream
+// around each batch's copy; the capacitance that consumes the set waits on end[b] before
+// batch b's V-cycles.
+struct HostCopy {
+  const double* host = nullptr;
+  const double* dev = nullptr;
+  int m = 0;
+  bool active = false;
+  std::vector<int> edge;
+  std::vector<cudaEvent_t> beg, end;
 };
 
 }  // namespace
@@ -90,12 +104,34 @@ struct h1w_ctx {
   int num_sms = 152;     // SMs of the context's device
   int* trsv_flags = nullptr;  // per-block flags of the cooperative C^-1 solve
   int trsv_epoch = 0;
+  unsigned long long wait_ns = 1000000000ull;  // limit of every bounded device wait
+  int stall = H1W_STALL_NONE;                  // failure-path test injection (h1w_inject_stall)
+  // device-driven PCG: the loop as a CUDA graph with a conditional while node
+  bool capturing = false;       // launches are being captured: no per-kernel timing, no host reads
+  int* gflags = nullptr;        // flags of the cooperative C^-1 solve inside graphs
+  int* gepoch = nullptr;        // device epoch counter for them
+  double* gb = nullptr;         // right-hand side and solution of the single-system graph
+  double* gx = nullptr;
+  cudaStream_t body_stream = nullptr;  // captures the loop body
+  cudaStream_t cap_stream = nullptr;   // captures the graphs (the context's stream may be the legacy one)
+  cudaGraphExec_t pcg_exec = nullptr;  // cached single-system graph
+  int pcg_key_m = -1;
+  const double* pcg_key_J = nullptr;
+  int pcg_key_stall = 0;
+  unsigned long long pcg_key_wait = 0;
+  long long pcg_l_pre = 0, pcg_l_body = 0, pcg_l_post = 0;  // kernels per part of the graph
+  unsigned long long uid = 0;   // process-unique id (batch graph cache keys)
   cudaStream_t copy_stream = nullptr;   // host-to-device copies of h1w_capacitance_from_host
-  std::vector<cudaEvent_t> cev;          // one per row batch, plus one for ordering
+  HostCopy hcopy[2];                     // pending or running copies of J (at most two)
+  cudaEvent_t order_ev = nullptr;        // orders a copy after the work queued on the stream
+  std::vector<cudaEvent_t> cyc_beg, cyc_end;  // per row batch: its V-cycles start and end
+  // profile of the last h1w_capacitance_from_host, ms from the start of its line H
+  std::vector<int> prof_rows;
+  std::vector<float> prof_copy_beg, prof_copy_end, prof_cyc_beg, prof_cyc_end;
   cudaStream_t cycle_stream = nullptr;  // the preconditioner's V-cycle, beside its H^T r pass
   cudaEvent_t cycle_ev[2] = {};
-  float cat_ms[8];
-  int cat_n[8];
+  float cat_ms[16];
+  int cat_n[16];
   long long launches_cap, launches_pcg;
   std::string err;
 };
@@ -111,13 +147,15 @@ h1w_status h1w::set_global_error(h1w_status st, const std::string& msg) {
 
 namespace {
 
-enum { kCatGemm = 0, kCatJdot = 1, kCatOp = 2, kCatHdot = 3, kCatHupd = 4, kCatDown = 5, kCatUp = 6, kCatCount = 7 };
+enum { kCatGemm = 0, kCatJdot = 1, kCatOp = 2, kCatHdot = 3, kCatHupd = 4, kCatDown = 5, kCatUp = 6,
+       kCatSplitJ = 7, kCatSplitH = 8, kCatD2df = 9, kCatCount = 10 };
 
 void timed_begin(h1w_ctx* c) {
-  if (c->timing_on && c->have_ev && c->nk < h1w_ctx::kTimed) cudaEventRecord(c->kev[c->nk][0], c->stream);
+  if (c->timing_on && !c->capturing && c->have_ev && c->nk < h1w_ctx::kTimed)
+    cudaEventRecord(c->kev[c->nk][0], c->stream);
 }
 void timed_end(h1w_ctx* c, int cat) {
-  if (c->timing_on && c->have_ev && c->nk < h1w_ctx::kTimed) {
+  if (c->timing_on && !c->capturing && c->have_ev && c->nk < h1w_ctx::kTimed) {
     cudaEventRecord(c->kev[c->nk][1], c->stream);
     c->kcat[c->nk++] = cat;
   }
@@ -271,6 +309,7 @@ h1w_status validate(const h1w_grid* g, int32_t m_max, const h1w_options* o, std:
     if (o->mg_arith != 0 && o->mg_arith != 1) { why = "mg_arith must be 0 or 1"; return H1W_EINVAL; }
     if (o->mg_unfused != 0 && o->mg_unfused != 1) { why = "mg_unfused must be 0 or 1"; return H1W_EINVAL; }
     if (o->precond != 0 && o->precond != 1) { why = "precond must be 0 or 1"; return H1W_EINVAL; }
+    if (o->pcg_mode != 0 && o->pcg_mode != 1) { why = "pcg_mode must be 0 or 1"; return H1W_EINVAL; }
   }
   return H1W_OK;
 }
@@ -325,6 +364,7 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   double* cL = B.take<double>(Nc * Nc);
   int* dstatus = B.take<int>(4);
   int* tflags = B.take<int>(2 * ((m_max + 31) / 32 + 1));
+  int* gflags = B.take<int>(2 * ((m_max + 31) / 32 + 1) + 1);  // graph flags, then the epoch counter
   unsigned long long* dbits = B.take<unsigned long long>(4);
   const bool use_df = o.mg_arith == 0;
   // FP64 H: not needed when the cycle is double-float and C runs on the tensor cores
@@ -359,6 +399,8 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
                                           (int64_t)colsum_blocks(N0), (int64_t)dot_blocks(N0)});
   double* partial = B.take<double>(plen);
   double* scal = B.take<double>(16);
+  double* gb = B.take<double>(N0);
+  double* gx = B.take<double>(N0);
   if (c) {
     c->qdev = qdev;
     c->q1st = q1st;
@@ -372,6 +414,7 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
     c->r = r; c->z = z; c->z0 = z0; c->p = p; c->q = q;
     c->svec = svec; c->jz = jz; c->w = w; c->wtmp = wtmp;
     c->partial = partial; c->partial_len = plen; c->scal = scal;
+    c->gflags = gflags; c->gepoch = gflags + 2 * ((m_max + 31) / 32 + 1); c->gb = gb; c->gx = gx;
   }
   return B.off + 256;
 }
@@ -600,11 +643,20 @@ bool apply_prec_impl(h1w_ctx* c, const double* r, double* z, int rz_slot) {
     // y = C^-1 s by the two triangular solves: backward stable, so the Woodbury formula sees
     // C + dC with |dC| ~ eps |C|. A product with an explicitly formed C^-1 is not (each
     // column carries its own rounding), which for |C| ~ 1e10 breaks the preconditioner.
-    if (c->trsv_epoch == 0x7FFFFFFF) {  // flags hold epochs 1 .. 2^31 - 1
-      cudaMemsetAsync(c->trsv_flags, 0, sizeof(int) * 2 * ((c->m_max + 31) / 32 + 1), c->stream);
-      c->trsv_epoch = 0;
+    bool coop = false;
+    if (c->capturing) {  // replayed graphs: the epoch lives on the device and advances per solve
+      launch_bump(c->gepoch, c->stream);
+      coop = launch_chol_solve_coop(c->Lc, m, c->svec, c->gflags, 0, c->gepoch, c->dstatus, c->wait_ns,
+                                    c->stall == H1W_STALL_PREC_SOLVE ? 1 : 0, c->stream);
+    } else {
+      if (c->trsv_epoch == 0x7FFFFFFF) {  // flags hold epochs 1 .. 2^31 - 1
+        cudaMemsetAsync(c->trsv_flags, 0, sizeof(int) * 2 * ((c->m_max + 31) / 32 + 1), c->stream);
+        c->trsv_epoch = 0;
+      }
+      coop = launch_chol_solve_coop(c->Lc, m, c->svec, c->trsv_flags, ++c->trsv_epoch, nullptr, c->dstatus,
+                                    c->wait_ns, c->stall == H1W_STALL_PREC_SOLVE ? 1 : 0, c->stream);
     }
-    if (!launch_chol_solve_coop(c->Lc, m, c->svec, c->trsv_flags, ++c->trsv_epoch, c->dstatus, c->stream)) {
+    if (!coop) {
       launch_trsv_lower(c->Lc, m, c->svec, 1, c->stream);
       launch_trsv_upper_t(c->Lc, m, c->svec, 1, c->stream);
     }
@@ -644,6 +696,199 @@ double read_scalar(h1w_ctx* c, int slot) {
   return v;
 }
 
+// Enqueues on c->stream, which must be capturing into a graph, the whole PCG solve of
+// A x = b driven from the device: x = 0 and r = b (unless slot init is 0: a restart from
+// the true residual already in r), b.b and r.r, the loop as a conditional while node whose
+// body is one PCG iteration ending with the convergence test, and the FP64 true residual
+// r = b - A x with r.r in slot 11. Returns false when a graph call fails (text in c->err).
+bool capture_pcg(h1w_ctx* c, const double* b, double* x, bool clear_status) {
+  const int64_t N = c->lev[0].N;
+  const int m = c->m;
+  const cudaStream_t s = c->stream;
+  const long long l0 = g_kernel_launches.load();
+  // bounded waits of the C^-1 solves report in the status word (kept when the capacitance of
+  // the same graph has written to it)
+  if (clear_status) cudaMemsetAsync(c->dstatus, 0, sizeof(int), s);
+  launch_pcg_init(x, c->r, b, c->scal, N, s);
+  launch_dot_partial(b, b, N, c->partial, s);
+  launch_sum_to_scalar(c->partial, dot_blocks(N), c->scal + kSlotBB, s);
+  launch_dot_partial(c->r, c->r, N, c->partial, s);
+  launch_sum_to_scalar(c->partial, dot_blocks(N), c->scal + kSlotRR, s);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusActive) {
+    c->err = "pcg graph: the stream is not capturing";
+    return false;
+  }
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) {
+    c->err = "pcg graph: cudaGraphConditionalHandleCreate failed";
+    return false;
+  }
+  launch_pcg_start(c->scal, h, s);
+  if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess) {
+    c->err = "pcg graph: cudaStreamGetCaptureInfo failed";
+    return false;
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp) != cudaSuccess ||
+      cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess) {
+    c->err = "pcg graph: adding the conditional while node failed";
+    return false;
+  }
+  const long long l1 = g_kernel_launches.load();
+  // the body: one PCG iteration, captured on the body stream into the node's graph
+  if (!c->body_stream && cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    c->err = "pcg graph: cannot create the body stream";
+    return false;
+  }
+  if (cudaStreamBeginCaptureToGraph(c->body_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    c->err = "pcg graph: cudaStreamBeginCaptureToGraph failed";
+    return false;
+  }
+  c->stream = c->body_stream;
+  bool ok = apply_prec_impl(c, c->r, c->z, kSlotRZN);
+  if (ok) {
+    if (uses_df(c)) j_times_df(c, c->z, c->jz);
+    else j_times(c, c->J, c->z, c->jz);
+    launch_pcg_beta_dev(c->scal, c->stream);
+    launch_p_update_dev(c->p, c->z, c->w, c->jz, c->scal, N, m > 0 ? m : 0, c->stream);
+    apply_op_w(c, c->p, c->w, c->q, kSlotPQ, true);
+    launch_pcg_alpha_dev(c->scal, c->stream);
+    launch_xr_update(x, c->r, c->p, c->q, c->scal, N, c->partial, c->stream);
+    launch_sum_to_scalar(c->partial, colsum_blocks(N), c->scal + kSlotRR, c->stream);
+    launch_pcg_check(c->scal, h, c->stream);
+  }
+  c->stream = s;
+  cudaGraph_t body = nullptr;
+  const cudaError_t eb = cudaStreamEndCapture(c->body_stream, &body);
+  if (!ok || eb != cudaSuccess) {
+    c->err = !ok ? "pcg graph: multigrid kernel attribute failed"
+                 : std::string("pcg graph: capture of the loop body failed: ") + cudaGetErrorString(eb);
+    cudaGetLastError();
+    return false;
+  }
+  const long long l2 = g_kernel_launches.load();
+  // after the loop: the FP64 true residual with the caller's J
+  j_times(c, c->J, x, c->wtmp);
+  apply_op_w(c, x, c->wtmp, c->q, -1);
+  launch_true_residual(c->r, b, c->q, N, c->partial, s);
+  launch_sum_to_scalar(c->partial, colsum_blocks(N), c->scal + kSlotRRTrue, s);
+  const long long l3 = g_kernel_launches.load();
+  c->pcg_l_pre = l1 - l0;
+  c->pcg_l_body = l2 - l1;
+  c->pcg_l_post = l3 - l2;
+  return true;
+}
+
+// Builds (or reuses) the single-system graph of c: b from c->gb, x into c->gx.
+h1w_status pcg_graph_ready(h1w_ctx* c) {
+  if (c->pcg_exec && c->pcg_key_m == c->m && c->pcg_key_J == c->J && c->pcg_key_stall == c->stall &&
+      c->pcg_key_wait == c->wait_ns)
+    return H1W_OK;
+  if (c->pcg_exec) {
+    cudaGraphExecDestroy(c->pcg_exec);
+    c->pcg_exec = nullptr;
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pcg graph");
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(c, H1W_ECUDA, "pcg graph: cannot create the capture stream");
+  const cudaStream_t orig = c->stream;
+  c->stream = c->cap_stream;
+  c->capturing = true;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    c->capturing = false;
+    c->stream = orig;
+    return fail(c, H1W_ECUDA, "pcg graph: cudaStreamBeginCapture failed");
+  }
+  const bool ok = capture_pcg(c, c->gb, c->gx, true);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  c->capturing = false;
+  c->stream = orig;
+  if (!ok || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return fail(c, H1W_ECUDA, ok ? std::string("pcg graph: capture failed: ") + cudaGetErrorString(e) : c->err);
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&c->pcg_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    c->pcg_exec = nullptr;
+    cudaGetLastError();
+    return fail(c, H1W_ECUDA, std::string("pcg graph: instantiation failed: ") + cudaGetErrorString(ei));
+  }
+  c->pcg_key_m = c->m;
+  c->pcg_key_J = c->J;
+  c->pcg_key_stall = c->stall;
+  c->pcg_key_wait = c->wait_ns;
+  return H1W_OK;
+}
+
+// The preconditioner's second stream (double-float path with measurements): highest priority,
+// so that the cycle's small kernels are not queued behind the blocks of the pass beside them.
+bool ensure_cycle_stream(h1w_ctx* c) {
+  if (!(uses_df(c) && c->m > 0) || c->cycle_stream) return true;
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  bool made = cudaStreamCreateWithPriority(&c->cycle_stream, cudaStreamNonBlocking, hi) == cudaSuccess;
+  for (int e = 0; e < 2 && made; ++e)
+    made = cudaEventCreateWithFlags(&c->cycle_ev[e], cudaEventDisableTiming) == cudaSuccess;
+  return made;
+}
+
+// h1w_pcg with the loop driven from the device: one graph launch per (re)start, one host
+// read of the scalars after each.
+h1w_status pcg_graph_solve(h1w_ctx* c, const double* b, double* x, double rtol, int maxit, h1w_info* info) {
+  const int64_t N = c->lev[0].N;
+  const cudaStream_t s = c->stream;
+  h1w_status st = pcg_graph_ready(c);
+  if (st != H1W_OK) return st;
+  const long long l0 = g_kernel_launches.load();
+  if (c->have_ev) cudaEventRecord(c->ev[4], s);
+  cudaMemcpyAsync(c->gb, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  h1w_info inf{0, 0, 0.0, 0.0};
+  double sc[16] = {};
+  long long launched = 0;
+  for (int restart = 0; restart <= c->opt.max_restarts; ++restart) {
+    launch_pcg_set_scalars(c->scal, rtol, maxit, restart == 0 ? 1 : 0, s);
+    const int it0 = (int)sc[kSlotIt];
+    if (cudaGraphLaunch(c->pcg_exec, s) != cudaSuccess) return cuda_check(c, "pcg graph launch");
+    cudaMemcpyAsync(sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "pcg graph");
+    const int it = (int)sc[kSlotIt];
+    launched += c->pcg_l_pre + (long long)(it - it0) * c->pcg_l_body + c->pcg_l_post;
+    inf.iters = it;
+    const double bb = sc[kSlotBB];
+    inf.rel_res_true = bb > 0.0 ? std::sqrt(sc[kSlotRRTrue] / bb) : 0.0;
+    inf.rel_res_rec = bb > 0.0 ? std::sqrt(sc[kSlotRR] / bb) : 0.0;
+    if (inf.rel_res_true <= rtol || it >= maxit || !std::isfinite(inf.rel_res_true)) break;
+    ++inf.restarts;
+  }
+  cudaMemcpyAsync(x, c->gx, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  if (c->have_ev) cudaEventRecord(c->ev[5], s);
+  int dst = 0;
+  cudaMemcpyAsync(&dst, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "pcg graph");
+  c->launches_pcg = g_kernel_launches.load() - l0 + launched;
+  for (int k = kCatJdot; k <= kCatHupd; ++k) { c->cat_ms[k] = 0.f; c->cat_n[k] = 0; }
+  if (info) *info = inf;
+  st = cuda_check(c, "pcg graph");
+  if (st != H1W_OK) return st;
+  if (dst & kStatusTimeout) return fail(c, H1W_ETIMEOUT, "pcg: a bounded device wait ran out");
+  if (!(inf.rel_res_true <= rtol)) return fail(c, H1W_ENOTCONV, "PCG did not reach rtol within maxit");
+  return H1W_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -657,6 +902,7 @@ void h1w_default_options(h1w_options* opt) {
   opt->mg_arith = 0;
   opt->mg_unfused = 0;
   opt->precond = 0;
+  opt->pcg_mode = 0;
 }
 
 size_t h1w_workspace_size(const h1w_grid* grid, int32_t m_max, const h1w_options* opt) {
@@ -705,6 +951,11 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
   c->J = nullptr;
   layout(c, P, *grid, m_max, o, static_cast<char*>(workspace));
   cudaMemsetAsync(c->trsv_flags, 0, sizeof(int) * 2 * ((m_max + 31) / 32 + 1), c->stream);
+  cudaMemsetAsync(c->gflags, 0, sizeof(int) * (2 * ((m_max + 31) / 32 + 1) + 1), c->stream);
+  {
+    static std::atomic<unsigned long long> next_uid{1};
+    c->uid = next_uid.fetch_add(1);
+  }
   c->have_ev = true;
   for (int e = 0; e < 6; ++e)
     if (cudaEventCreate(&c->ev[e]) != cudaSuccess) c->have_ev = false;
@@ -713,7 +964,7 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
       if (cudaEventCreate(&c->kev[t][e]) != cudaSuccess) c->have_ev = false;
   c->nk = 0;
   c->timing_on = false;
-  for (int k = 0; k < 8; ++k) { c->cat_ms[k] = 0.f; c->cat_n[k] = 0; }
+  for (int k = 0; k < 16; ++k) { c->cat_ms[k] = 0.f; c->cat_n[k] = 0; }
   c->launches_cap = c->launches_pcg = 0;
 
   // level descriptors
@@ -847,11 +1098,96 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
 // conversion and V-cycles waiting only for that batch's copy.
 static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const double* J_host);
 
+// Row batches: rhs_block rows each. With J coming from the host the batches ramp up from
+// 16 rows by a factor of about 1.25 (rounded up to multiples of 8): the cycles start after
+// a short first copy, and while a batch runs the copy of the next, slightly larger one
+// completes (a cycle costs somewhat more per row than the copy of the row over the host
+// link), so the cycles rarely wait for data.
+static std::vector<int> batch_edges(const h1w_ctx* c, int m, bool from_host) {
+  const int nb = block_rhs(c->opt, c->m_max);
+  std::vector<int> edge{0};
+  for (int r0 = 0, bs = from_host ? std::min(nb, 16) : nb; r0 < m;) {
+    r0 = std::min(m, r0 + bs);
+    edge.push_back(r0);
+    if (from_host) bs = std::min(nb, (bs + bs / 4 + 7) / 8 * 8);
+  }
+  return edge;
+}
+
+static bool make_events(std::vector<cudaEvent_t>& v, size_t n) {
+  while (v.size() < n) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return false;
+    v.push_back(e);
+  }
+  return true;
+}
+
+// Queues the copies of J_host into J_dev on the copy stream, after the work already queued
+// on the context's stream (which may still read J_dev), one row batch at a time.
+static h1w_status issue_host_copies(h1w_ctx* c, HostCopy& h, int m, const double* J_host, const double* J_dev) {
+  const int64_t N = c->lev[0].N;
+  if (!c->copy_stream && cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create the copy stream");
+  if (!c->order_ev && cudaEventCreateWithFlags(&c->order_ev, cudaEventDisableTiming) != cudaSuccess)
+    return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create an event");
+  h.edge = batch_edges(c, m, true);
+  const int nbatch = (int)h.edge.size() - 1;
+  if (!make_events(h.beg, nbatch) || !make_events(h.end, nbatch))
+    return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create an event");
+  cudaEventRecord(c->order_ev, c->stream);
+  cudaStreamWaitEvent(c->copy_stream, c->order_ev, 0);
+  for (int bi = 0; bi < nbatch; ++bi) {
+    const int64_t r0 = h.edge[bi], nr = h.edge[bi + 1] - h.edge[bi];
+    cudaEventRecord(h.beg[bi], c->copy_stream);
+    cudaMemcpyAsync(const_cast<double*>(J_dev) + r0 * N, J_host + r0 * N, sizeof(double) * nr * N,
+                    cudaMemcpyHostToDevice, c->copy_stream);
+    cudaEventRecord(h.end[bi], c->copy_stream);
+  }
+  h.host = J_host;
+  h.dev = J_dev;
+  h.m = m;
+  h.active = true;
+  return cuda_check(c, "capacitance_from_host: copies");
+}
+
+// the pending copy set of (J_host, J_dev, m), or a new one queued now; null on failure
+static HostCopy* host_copies_for(h1w_ctx* c, int m, const double* J_host, const double* J_dev, h1w_status& st) {
+  st = H1W_OK;
+  for (HostCopy& h : c->hcopy)
+    if (h.active && h.host == J_host && h.dev == J_dev && h.m == m) return &h;
+  for (HostCopy& h : c->hcopy)
+    if (!h.active) {
+      st = issue_host_copies(c, h, m, J_host, J_dev);
+      return st == H1W_OK ? &h : nullptr;
+    }
+  st = fail(c, H1W_ESTATE, "capacitance_from_host: two other prefetches of J are pending");
+  return nullptr;
+}
+
 // every return waits for the copies of J_host, so that none outlives the call
 static h1w_status capacitance_impl(h1w_ctx* c, int32_t m, const double* J, const double* J_host) {
   const h1w_status st = capacitance_core(c, m, J, J_host);
-  if (J_host && c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  if (J_host) {
+    for (HostCopy& h : c->hcopy)
+      if (h.active && h.host == J_host && h.dev == J && h.m == m) {
+        if (!h.end.empty() && h.edge.size() > 1) cudaEventSynchronize(h.end[h.edge.size() - 2]);
+        h.active = false;
+      }
+  }
   return st;
+}
+
+// Host-side preparation of a capacitance that will be captured into a graph: the GEMM's tile
+// list for m rows, uploaded (a capture cannot copy from pageable host memory). Synchronizes.
+static h1w_status capacitance_prepare(h1w_ctx* c, int32_t m) {
+  if (m > 0 && c->opt.cap_gemm == 0 && c->opt.precond == 0) {
+    ozaki_tiles(m, c->oz_tiles_host);
+    cudaMemcpyAsync(c->oz.tiles, c->oz_tiles_host.data(), sizeof(int) * c->oz_tiles_host.size(),
+                    cudaMemcpyHostToDevice, c->stream);
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "capacitance_prepare");
+  return cuda_check(c, "capacitance_prepare");
 }
 
 static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const double* J_host) {
@@ -860,47 +1196,26 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
   c->J = J;
   const long long l0 = g_kernel_launches.load();
   if (m == 0) { c->launches_cap = 0; return H1W_OK; }
-  // row batches: rhs_block rows each. With J coming from the host the batches ramp up
-  // from 16 rows by a factor of about 1.25 (rounded up to multiples of 8): the cycles
-  // start after a short first copy, and while a batch runs the copy of the next, slightly
-  // larger one completes (a cycle costs somewhat more per row than the copy of the row
-  // over the host link), so the cycles rarely wait for data.
-  const int nb = block_rhs(c->opt, c->m_max);
-  std::vector<int> edge{0};
-  for (int r0 = 0, bs = J_host ? std::min(nb, 16) : nb; r0 < m;) {
-    r0 = std::min(m, r0 + bs);
-    edge.push_back(r0);
-    if (J_host) bs = std::min(nb, (bs + bs / 4 + 7) / 8 * 8);
-  }
-  const int nbatch = (int)edge.size() - 1;
+  HostCopy* hc = nullptr;
   if (J_host) {
-    if (!c->copy_stream && cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
-      return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create the copy stream");
-    while ((int)c->cev.size() < nbatch + 1) {
-      cudaEvent_t e;
-      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-        return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create an event");
-      c->cev.push_back(e);
-    }
-    // the copy may overwrite J only after work already queued on the context's stream
-    cudaEventRecord(c->cev[nbatch], c->stream);
-    cudaStreamWaitEvent(c->copy_stream, c->cev[nbatch], 0);
-    for (int bi = 0; bi < nbatch; ++bi) {
-      const int64_t r0 = edge[bi], nr = edge[bi + 1] - edge[bi];
-      cudaMemcpyAsync(const_cast<double*>(J) + r0 * N, J_host + r0 * N, sizeof(double) * nr * N,
-                      cudaMemcpyHostToDevice, c->copy_stream);
-      cudaEventRecord(c->cev[bi], c->copy_stream);
-    }
+    h1w_status st = H1W_OK;
+    hc = host_copies_for(c, m, J_host, J, st);
+    if (!hc) return st;
+    if (!make_events(c->cyc_beg, hc->edge.size()) || !make_events(c->cyc_end, hc->edge.size()))
+      return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create an event");
   }
-  if (c->have_ev) cudaEventRecord(c->ev[0], c->stream);
+  const std::vector<int> edge = hc ? hc->edge : batch_edges(c, m, false);
+  const int nbatch = (int)edge.size() - 1;
+  if (c->have_ev && !c->capturing) cudaEventRecord(c->ev[0], c->stream);
   if (c->opt.precond == 1) {  // Laplace-only preconditioner: J for the operator, no lines H, C, chol
     for (int bi = 0; bi < nbatch; ++bi) {
       const int64_t r0 = edge[bi], nr = edge[bi + 1] - edge[bi], o = r0 * N;
-      if (J_host) cudaStreamWaitEvent(c->stream, c->cev[bi], 0);
+      if (hc) cudaStreamWaitEvent(c->stream, hc->end[bi], 0);
       if (uses_df(c)) launch_d2df(nr * N, J + o, c->Jdf + o, c->stream);
     }
-    for (int k = 1; k < 4 && c->have_ev; ++k) cudaEventRecord(c->ev[k], c->stream);
+    for (int k = 1; k < 4 && c->have_ev && !c->capturing; ++k) cudaEventRecord(c->ev[k], c->stream);
     c->launches_cap = g_kernel_launches.load() - l0;
+    if (c->capturing) return cuda_check(c, "capacitance");
     const cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(c, H1W_ECUDA, std::string("capacitance: ") + cudaGetErrorString(e));
     return cuda_check(c, "capacitance");
@@ -913,26 +1228,43 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
   bool vc_ok = true;
   for (int bi = 0; bi < nbatch && vc_ok; ++bi) {
     const int64_t r0 = edge[bi], nr = edge[bi + 1] - edge[bi], o = r0 * N;
-    if (J_host) cudaStreamWaitEvent(c->stream, c->cev[bi], 0);
-    if (uses_df(c)) launch_d2df(nr * N, J + o, c->Jdf + o, c->stream);  // J for the cycle and the Krylov passes
+    if (hc) {
+      cudaStreamWaitEvent(c->stream, hc->end[bi], 0);
+      cudaEventRecord(c->cyc_beg[bi], c->stream);
+    }
+    if (uses_df(c)) {  // J for the cycle and the Krylov passes
+      timed_begin(c);
+      launch_d2df(nr * N, J + o, c->Jdf + o, c->stream);
+      timed_end(c, kCatD2df);
+    }
     vc_ok = vcycle_many(c, (int)nr, J + o, uses_df(c) ? c->Jdf + o : nullptr, h_df_only ? nullptr : c->H + o,
                         c->Hdf ? c->Hdf + o : nullptr);
+    if (hc) cudaEventRecord(c->cyc_end[bi], c->stream);
   }
   c->timing_on = c->time_vc = false;
   if (!vc_ok) return fail(c, H1W_ECUDA, "capacitance: multigrid kernel attribute failed");
-  if (c->have_ev) cudaEventRecord(c->ev[1], c->stream);
+  if (c->have_ev && !c->capturing) cudaEventRecord(c->ev[1], c->stream);
   cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
   int splits = 0;
   if (c->opt.cap_gemm == 0) {                                       // line C, tensor cores
     if (!ozaki_supported()) return fail(c, H1W_EUNSUPPORTED, "tensor-core capacitance GEMM needs sm_100-class GPU");
-    ozaki_tiles(m, c->oz_tiles_host);
-    cudaMemcpyAsync(c->oz.tiles, c->oz_tiles_host.data(), sizeof(int) * c->oz_tiles_host.size(),
-                    cudaMemcpyHostToDevice, c->stream);
+    if (!c->capturing) {  // a capture finds the tile list uploaded by capacitance_prepare
+      ozaki_tiles(m, c->oz_tiles_host);
+      cudaMemcpyAsync(c->oz.tiles, c->oz_tiles_host.data(), sizeof(int) * c->oz_tiles_host.size(),
+                      cudaMemcpyHostToDevice, c->stream);
+    }
     splits = ozaki_splits(m, c->oz.klen, c->num_sms);
+    c->oz.wait_ns = c->wait_ns;
+    c->oz.stall = c->stall == H1W_STALL_CAP_GEMM ? 1 : 0;
     c->timing_on = true;
     const bool ok = launch_ozaki_capacitance(
-        J, c->H, nullptr, h_df_only ? c->Hdf : nullptr, m, N, c->oz, splits, c->stream, [](void* p) { timed_begin(static_cast<h1w_ctx*>(p)); },
-        [](void* p) { timed_end(static_cast<h1w_ctx*>(p), kCatGemm); }, c);
+        J, c->H, nullptr, h_df_only ? c->Hdf : nullptr, m, N, c->oz, splits, c->stream,
+        [](void* p, int which, int begin) {
+          h1w_ctx* cx = static_cast<h1w_ctx*>(p);
+          if (begin) timed_begin(cx);
+          else timed_end(cx, which == kOzakiGemm ? kCatGemm : which == kOzakiSplitJ ? kCatSplitJ : kCatSplitH);
+        },
+        c);
     c->timing_on = false;
     if (!ok)
       return fail(c, H1W_ECUDA, "capacitance: tensor map encoding or kernel attribute failed");
@@ -944,17 +1276,39 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
     timed_end(c, kCatGemm);
     c->timing_on = false;
   }
-  if (c->have_ev) cudaEventRecord(c->ev[2], c->stream);
+  if (c->have_ev && !c->capturing) cudaEventRecord(c->ev[2], c->stream);
   launch_cap_finalize(c->gemm_partial, splits, m, c->grid.alpha, c->C, c->stream);
   cudaMemcpyAsync(c->Lc, c->C, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, c->stream);
   launch_chol(c->Lc, m, c->dstatus, c->stream);                    // line chol
-  if (c->have_ev) cudaEventRecord(c->ev[3], c->stream);
+  if (c->have_ev && !c->capturing) cudaEventRecord(c->ev[3], c->stream);
   c->launches_cap = g_kernel_launches.load() - l0;
+  if (c->capturing) return cuda_check(c, "capacitance");  // the status word is read after the graph ran
   int status = 0;
   cudaMemcpyAsync(&status, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail(c, H1W_ECUDA, std::string("capacitance: ") + cudaGetErrorString(e));
-  timed_collect(c, (1u << kCatGemm) | (1u << kCatDown) | (1u << kCatUp));
+  timed_collect(c, (1u << kCatGemm) | (1u << kCatDown) | (1u << kCatUp) | (1u << kCatSplitJ) | (1u << kCatSplitH) |
+                       (1u << kCatD2df));
+  if (hc && c->have_ev) {  // when each batch's copy began and ended, and its cycles began and ended
+    cudaEventSynchronize(hc->end[nbatch - 1]);
+    auto rel = [&](cudaEvent_t e) {
+      float ms = 0.f;
+      return cudaEventElapsedTime(&ms, c->ev[0], e) == cudaSuccess ? ms : 0.f;
+    };
+    c->prof_rows.assign(nbatch, 0);
+    c->prof_copy_beg.assign(nbatch, 0.f);
+    c->prof_copy_end.assign(nbatch, 0.f);
+    c->prof_cyc_beg.assign(nbatch, 0.f);
+    c->prof_cyc_end.assign(nbatch, 0.f);
+    for (int bi = 0; bi < nbatch; ++bi) {
+      c->prof_rows[bi] = edge[bi + 1] - edge[bi];
+      c->prof_copy_beg[bi] = rel(hc->beg[bi]);
+      c->prof_copy_end[bi] = rel(hc->end[bi]);
+      c->prof_cyc_beg[bi] = rel(c->cyc_beg[bi]);
+      c->prof_cyc_end[bi] = rel(c->cyc_end[bi]);
+    }
+    cudaGetLastError();
+  }
   h1w_status st = cuda_check(c, "capacitance");
   if (st != H1W_OK) return st;
   if (status & kStatusTimeout) {
@@ -980,6 +1334,33 @@ h1w_status h1w_capacitance_from_host(h1w_ctx* c, int32_t m, const double* J_host
   if (m < 0 || m > c->m_max) return fail(c, H1W_EINVAL, "m out of range [0, m_max]");
   if (m > 0 && (!J_host || !J_dev)) return fail(c, H1W_EINVAL, "J_host and J_dev must be non-NULL");
   return capacitance_impl(c, m, J_dev, m > 0 ? J_host : nullptr);
+}
+
+h1w_status h1w_prefetch_J(h1w_ctx* c, int32_t m, const double* J_host, double* J_dev) {
+  if (!c) return H1W_EINVAL;
+  if (m < 1 || m > c->m_max) return fail(c, H1W_EINVAL, "prefetch_J: m out of range [1, m_max]");
+  if (!J_host || !J_dev) return fail(c, H1W_EINVAL, "prefetch_J: J_host and J_dev must be non-NULL");
+  for (HostCopy& h : c->hcopy)
+    if (h.active && h.dev == J_dev && !(h.host == J_host && h.m == m))
+      return fail(c, H1W_ESTATE, "prefetch_J: another copy into J_dev is pending");
+  h1w_status st = H1W_OK;
+  host_copies_for(c, m, J_host, J_dev, st);
+  return st;
+}
+
+h1w_status h1w_get_copy_profile(const h1w_ctx* c, int32_t cap, int32_t* nbatch, int32_t* rows, float* copy_begin_ms,
+                                float* copy_end_ms, float* cycle_begin_ms, float* cycle_end_ms) {
+  if (!c || cap < 0) return H1W_EINVAL;
+  const int n = (int)c->prof_rows.size();
+  if (nbatch) *nbatch = n;
+  for (int i = 0; i < std::min(n, (int)cap); ++i) {
+    if (rows) rows[i] = c->prof_rows[i];
+    if (copy_begin_ms) copy_begin_ms[i] = c->prof_copy_beg[i];
+    if (copy_end_ms) copy_end_ms[i] = c->prof_copy_end[i];
+    if (cycle_begin_ms) cycle_begin_ms[i] = c->prof_cyc_beg[i];
+    if (cycle_end_ms) cycle_end_ms[i] = c->prof_cyc_end[i];
+  }
+  return H1W_OK;
 }
 
 h1w_status h1w_apply_prec(h1w_ctx* c, const double* r, double* z) {
@@ -1028,16 +1409,8 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
   const int m = c->m;
   cudaStream_t s = c->stream;
   enum { RZ = 0, PQ = 1, A = 2, RZN = 3, BETA = 4, RR = 5, BB = 6 };
-  if (uses_df(c) && m > 0 && !c->cycle_stream) {
-    // highest priority, so that the cycle's small kernels are not queued behind the blocks
-    // of the pass beside them
-    int lo = 0, hi = 0;
-    cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    bool made = cudaStreamCreateWithPriority(&c->cycle_stream, cudaStreamNonBlocking, hi) == cudaSuccess;
-    for (int e = 0; e < 2 && made; ++e)
-      made = cudaEventCreateWithFlags(&c->cycle_ev[e], cudaEventDisableTiming) == cudaSuccess;
-    if (!made) return fail(c, H1W_ECUDA, "pcg: cannot create the cycle stream or its events");
-  }
+  if (!ensure_cycle_stream(c)) return fail(c, H1W_ECUDA, "pcg: cannot create the cycle stream or its events");
+  if (c->opt.pcg_mode == 0) return pcg_graph_solve(c, b, x, rtol, maxit, info);
   const long long l0 = g_kernel_launches.load();
   if (c->have_ev) cudaEventRecord(c->ev[4], s);
   c->nk = 0;
@@ -1119,6 +1492,194 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
   return H1W_OK;
 }
 
+// ---- many systems in one graph ------------------------------------------------------
+
+namespace {
+
+struct BatchGraph {
+  std::vector<unsigned long long> key;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<long long> l_pre, l_body, l_post, l_cap;
+};
+std::mutex g_batch_mu;
+BatchGraph g_batch;                    // the last batch graph (replayed while its key matches)
+cudaStream_t g_batch_origin = nullptr;  // capture origin and launch stream
+int g_batch_dev = -1;
+
+unsigned long long bits_of(double v) {
+  unsigned long long u;
+  std::memcpy(&u, &v, sizeof(u));
+  return u;
+}
+
+}  // namespace
+
+h1w_status h1w_solve_batch_graph(h1w_ctx* const* ctxs, int32_t count, const int32_t* m, const double* const* J,
+                                 const double* const* b, double* const* x, double rtol, int32_t maxit,
+                                 h1w_info* info, h1w_status* status) {
+  if (count < 0 || (count > 0 && (!ctxs || !m || !J || !b || !x)))
+    return h1w::set_global_error(H1W_EINVAL, "h1w_solve_batch_graph: NULL arrays or negative count");
+  if (!(rtol > 0.0) || maxit < 0) return h1w::set_global_error(H1W_EINVAL, "h1w_solve_batch_graph: bad rtol/maxit");
+  for (int32_t i = 0; i < count; ++i) {
+    h1w_ctx* c = ctxs[i];
+    if (!c) return h1w::set_global_error(H1W_EINVAL, "h1w_solve_batch_graph: NULL context");
+    if (m[i] < 0 || m[i] > c->m_max || (m[i] > 0 && !J[i]) || !b[i] || !x[i] || b[i] == x[i])
+      return h1w::set_global_error(H1W_EINVAL, "h1w_solve_batch_graph: bad m, J, b or x of system " +
+                                                   std::to_string(i));
+    if (c->opt.precond != 0 && m[i] > 0)
+      return h1w::set_global_error(H1W_EUNSUPPORTED, "h1w_solve_batch_graph: needs precond = 0");
+    for (int32_t k = 0; k < i; ++k)
+      if (ctxs[k] == c) return h1w::set_global_error(H1W_EINVAL, "h1w_solve_batch_graph: contexts must be distinct");
+  }
+  if (count == 0) return H1W_OK;
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return h1w::set_global_error(H1W_ECUDA, "h1w_solve_batch_graph: no device");
+  std::vector<unsigned long long> key{(unsigned long long)count, bits_of(rtol), (unsigned long long)maxit,
+                                      (unsigned long long)dev};
+  for (int32_t i = 0; i < count; ++i) {
+    const h1w_ctx* c = ctxs[i];
+    key.insert(key.end(), {c->uid, (unsigned long long)m[i], (unsigned long long)(uintptr_t)J[i],
+                           (unsigned long long)(uintptr_t)b[i], (unsigned long long)(uintptr_t)x[i],
+                           (unsigned long long)c->stall, c->wait_ns});
+  }
+  for (int32_t i = 0; i < count; ++i) {  // host state of each system, as h1w_capacitance sets it
+    h1w_ctx* c = ctxs[i];
+    c->m = m[i];
+    c->J = J[i];
+    if (!ensure_cycle_stream(c)) return fail(c, H1W_ECUDA, "batch graph: cannot create the cycle stream");
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(c, H1W_ECUDA, "batch graph: cannot create the capture stream");
+  }
+  if (g_batch_dev != dev || !g_batch_origin) {
+    if (cudaStreamCreateWithFlags(&g_batch_origin, cudaStreamNonBlocking) != cudaSuccess)
+      return h1w::set_global_error(H1W_ECUDA, "h1w_solve_batch_graph: cannot create the origin stream");
+    g_batch_dev = dev;
+    if (g_batch.exec) cudaGraphExecDestroy(g_batch.exec);
+    g_batch = BatchGraph{};
+  }
+  if (!g_batch.exec || g_batch.key != key) {
+    if (g_batch.exec) cudaGraphExecDestroy(g_batch.exec);
+    g_batch = BatchGraph{};
+    for (int32_t i = 0; i < count; ++i) {
+      const h1w_status st = capacitance_prepare(ctxs[i], m[i]);
+      if (st != H1W_OK) return st;
+    }
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join(count, nullptr);
+    bool ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int32_t i = 0; i < count && ok; ++i)
+      ok = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess;
+    std::string why;
+    if (ok && cudaStreamBeginCapture(g_batch_origin, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      ok = false;
+      why = "cudaStreamBeginCapture failed";
+    }
+    if (ok) {
+      cudaEventRecord(fork, g_batch_origin);
+      g_batch.l_pre.assign(count, 0);
+      g_batch.l_body.assign(count, 0);
+      g_batch.l_post.assign(count, 0);
+      g_batch.l_cap.assign(count, 0);
+      for (int32_t i = 0; i < count && ok; ++i) {
+        h1w_ctx* c = ctxs[i];
+        const cudaStream_t orig = c->stream;
+        c->stream = c->cap_stream;
+        c->capturing = true;
+        cudaStreamWaitEvent(c->stream, fork, 0);
+        const long long l0 = g_kernel_launches.load();
+        if (capacitance_core(c, m[i], J[i], nullptr) != H1W_OK) {
+          ok = false;
+          why = c->err;
+        }
+        g_batch.l_cap[i] = g_kernel_launches.load() - l0;
+        if (ok) {
+          launch_pcg_set_scalars(c->scal, rtol, maxit, 1, c->stream);
+          ok = capture_pcg(c, b[i], x[i], m[i] == 0);
+          if (!ok) why = c->err;
+          g_batch.l_pre[i] = c->pcg_l_pre + 1;
+          g_batch.l_body[i] = c->pcg_l_body;
+          g_batch.l_post[i] = c->pcg_l_post;
+        }
+        cudaEventRecord(join[i], c->stream);
+        cudaStreamWaitEvent(g_batch_origin, join[i], 0);
+        c->capturing = false;
+        c->stream = orig;
+      }
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(g_batch_origin, &g);
+      if (ok && (e != cudaSuccess || !g)) {
+        ok = false;
+        why = std::string("capture failed: ") + cudaGetErrorString(e);
+      }
+      if (ok) {
+        const cudaError_t ei = cudaGraphInstantiate(&g_batch.exec, g, 0);
+        if (ei != cudaSuccess) {
+          ok = false;
+          g_batch.exec = nullptr;
+          why = std::string("instantiation failed: ") + cudaGetErrorString(ei);
+        }
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    for (int32_t i = 0; i < count; ++i) ctxs[i]->capturing = false;
+    if (fork) cudaEventDestroy(fork);
+    for (cudaEvent_t e : join)
+      if (e) cudaEventDestroy(e);
+    cudaGetLastError();
+    if (!ok) {
+      g_batch = BatchGraph{};
+      return h1w::set_global_error(H1W_ECUDA, "h1w_solve_batch_graph: " + why);
+    }
+    g_batch.key = key;
+  }
+  for (int32_t i = 0; i < count; ++i) {  // the graph starts after the work queued on each system's stream
+    if (!ctxs[i]->order_ev && cudaEventCreateWithFlags(&ctxs[i]->order_ev, cudaEventDisableTiming) != cudaSuccess)
+      return fail(ctxs[i], H1W_ECUDA, "batch graph: cannot create an event");
+    cudaEventRecord(ctxs[i]->order_ev, ctxs[i]->stream);
+    cudaStreamWaitEvent(g_batch_origin, ctxs[i]->order_ev, 0);
+  }
+  if (cudaGraphLaunch(g_batch.exec, g_batch_origin) != cudaSuccess || cudaStreamSynchronize(g_batch_origin) != cudaSuccess)
+    return h1w::set_global_error(H1W_ECUDA, std::string("h1w_solve_batch_graph: ") +
+                                                cudaGetErrorString(cudaGetLastError()));
+  h1w_status first = H1W_OK;
+  for (int32_t i = 0; i < count; ++i) {
+    h1w_ctx* c = ctxs[i];
+    double sc[16] = {};
+    int dst = 0;
+    cudaMemcpy(sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&dst, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost);
+    h1w_info inf{0, 0, 0.0, 0.0};
+    inf.iters = (int)sc[kSlotIt];
+    const double bb = sc[kSlotBB];
+    inf.rel_res_true = bb > 0.0 ? std::sqrt(sc[kSlotRRTrue] / bb) : 0.0;
+    inf.rel_res_rec = bb > 0.0 ? std::sqrt(sc[kSlotRR] / bb) : 0.0;
+    c->launches_cap = g_batch.l_cap[i];
+    c->launches_pcg = g_batch.l_pre[i] + (long long)inf.iters * g_batch.l_body[i] + g_batch.l_post[i];
+    h1w_status st = H1W_OK;
+    if (dst & kStatusNotSpd) {
+      c->m = -1;
+      st = fail(c, H1W_ENOTSPD, "capacitance matrix is not numerically positive definite");
+    } else if (dst & kStatusTimeout) {
+      st = fail(c, H1W_ETIMEOUT, "batch graph: a bounded device wait ran out");
+    } else if (!(inf.rel_res_true <= rtol) && inf.iters < maxit && std::isfinite(inf.rel_res_true)) {
+      // the recursive residual met rtol but the true one did not: continue this system with
+      // restarts from its true residual, as h1w_pcg does
+      st = h1w_pcg(c, b[i], x[i], rtol, maxit, &inf);
+    } else if (!(inf.rel_res_true <= rtol)) {
+      st = fail(c, H1W_ENOTCONV, "PCG did not reach rtol within maxit");
+    }
+    if (info) info[i] = inf;
+    if (status) status[i] = st;
+    if (first == H1W_OK && st != H1W_OK) first = st;
+  }
+  if (cudaGetLastError() != cudaSuccess)
+    return h1w::set_global_error(H1W_ECUDA, "h1w_solve_batch_graph: a CUDA call failed");
+  if (first != H1W_OK)
+    h1w::set_global_error(first, "h1w_solve_batch_graph: a system failed (see its context's last error)");
+  return first;
+}
+
 h1w_status h1w_capacitance_factors(h1w_ctx* c, double* C, double* L) {
   if (!c) return H1W_EINVAL;
   if (c->m < 0) return fail(c, H1W_ESTATE, "call h1w_capacitance first");
@@ -1162,6 +1723,12 @@ h1w_status h1w_get_timings(const h1w_ctx* c, h1w_timings* out) {
   t.t_vc_up_ms = c->cat_ms[kCatUp];
   t.n_vc_down = c->cat_n[kCatDown];
   t.n_vc_up = c->cat_n[kCatUp];
+  t.t_split_j_ms = c->cat_ms[kCatSplitJ];
+  t.t_split_h_ms = c->cat_ms[kCatSplitH];
+  t.t_d2df_ms = c->cat_ms[kCatD2df];
+  t.n_split_j = c->cat_n[kCatSplitJ];
+  t.n_split_h = c->cat_n[kCatSplitH];
+  t.n_d2df = c->cat_n[kCatD2df];
   *out = t;
   return H1W_OK;
 }
@@ -1300,19 +1867,66 @@ h1w_status h1w_gn_step(h1w_ctx* c, const h1w_survey* survey, const double* g_obs
   return H1W_OK;
 }
 
+h1w_status h1w_set_pcg_mode(h1w_ctx* c, int32_t mode) {
+  if (!c) return h1w::set_global_error(H1W_EINVAL, "h1w_set_pcg_mode: NULL context");
+  if (mode != 0 && mode != 1) return fail(c, H1W_EINVAL, "h1w_set_pcg_mode: mode must be 0 or 1");
+  c->opt.pcg_mode = mode;
+  return H1W_OK;
+}
+
+h1w_status h1w_inject_stall(h1w_ctx* c, int32_t kind, int64_t wait_limit_ns) {
+  if (!c) return h1w::set_global_error(H1W_EINVAL, "h1w_inject_stall: NULL context");
+  if (kind != H1W_STALL_NONE && kind != H1W_STALL_CAP_GEMM && kind != H1W_STALL_PREC_SOLVE)
+    return fail(c, H1W_EINVAL, "h1w_inject_stall: unknown kind");
+  if (wait_limit_ns < 0 || wait_limit_ns > 60000000000ll)
+    return fail(c, H1W_EINVAL, "h1w_inject_stall: wait_limit_ns out of range [0, 60 s]");
+  c->stall = kind;
+  c->wait_ns = wait_limit_ns > 0 ? (unsigned long long)wait_limit_ns : 1000000000ull;
+  return H1W_OK;
+}
+
+h1w_status h1w_cholesky(h1w_ctx* c, int32_t n, double* A) {
+  if (!c) return h1w::set_global_error(H1W_EINVAL, "h1w_cholesky: NULL context");
+  if (n < 1 || n > H1W_CHOLESKY_MAX_N) return fail(c, H1W_EINVAL, "h1w_cholesky: n out of range");
+  if (!A) return fail(c, H1W_EINVAL, "h1w_cholesky: A is NULL");
+  cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
+  launch_chol(A, n, c->dstatus, c->stream);
+  int status = 0;
+  cudaMemcpyAsync(&status, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  const cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, H1W_ECUDA, std::string("h1w_cholesky: ") + cudaGetErrorString(e));
+  const h1w_status st = cuda_check(c, "h1w_cholesky");
+  if (st != H1W_OK) return st;
+  if (status & kStatusNotSpd)
+    return fail(c, H1W_ENOTSPD, "h1w_cholesky: a pivot is not positive (the matrix is not numerically SPD)");
+  return H1W_OK;
+}
+
 void h1w_destroy(h1w_ctx* c) {
   if (!c) return;
   if (c->copy_stream) {
     cudaStreamSynchronize(c->copy_stream);
     cudaStreamDestroy(c->copy_stream);
   }
-  for (cudaEvent_t e : c->cev) cudaEventDestroy(e);
+  for (HostCopy& h : c->hcopy) {
+    for (cudaEvent_t e : h.beg) cudaEventDestroy(e);
+    for (cudaEvent_t e : h.end) cudaEventDestroy(e);
+  }
+  for (cudaEvent_t e : c->cyc_beg) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->cyc_end) cudaEventDestroy(e);
+  if (c->order_ev) cudaEventDestroy(c->order_ev);
   if (c->cycle_stream) {
     cudaStreamSynchronize(c->cycle_stream);
     cudaStreamDestroy(c->cycle_stream);
     for (int e = 0; e < 2; ++e)
       if (c->cycle_ev[e]) cudaEventDestroy(c->cycle_ev[e]);
   }
+  if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+  if (c->body_stream) {
+    cudaStreamSynchronize(c->body_stream);
+    cudaStreamDestroy(c->body_stream);
+  }
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->have_ev) {
     for (int e = 0; e < 6; ++e) cudaEventDestroy(c->ev[e]);
     for (int t = 0; t < h1w_ctx::kTimed; ++t)

@@ -476,7 +476,8 @@ __global__ void __launch_bounds__(512) k_trsv_upper_t(const double* __restrict__
 // D_p^-T (y_p - sum_{J>p} L_Jp^T z_J) and flag_b. Only the diagonal solves lie on the
 // critical path; the updates of different blocks run on different SMs (a single-block
 // solve is bound by the FP64 pipe of one SM). All CTAs must be resident: the launch is
-// cooperative. Every wait gives up after about a second, sets kStatusTimeout and returns.
+// cooperative. Every wait gives up after wait_ns (one second unless a test shortens it), sets
+// kStatusTimeout and returns.
 // The flags hold the epoch of the last solve, so they never need resetting.
 
 __device__ __forceinline__ uint64_t trsv_timer() {
@@ -488,15 +489,15 @@ __device__ __forceinline__ uint64_t trsv_timer() {
 // Wait until flag == epoch (bounded). Thread 0 polls and decides for the whole block, so
 // that every thread of the block returns the same answer; false on timeout (or when
 // another block already gave up).
-__device__ bool trsv_wait(const int* flag, int epoch, int* status, int* s_ok) {
+__device__ bool trsv_wait(const int* flag, int epoch, int* status, int* s_ok, uint64_t wait_ns) {
   if (threadIdx.x == 0) {
     const uint64_t t0 = trsv_timer();
     unsigned n = 0;
     int ok = 1;
     while (atomicAdd(const_cast<int*>(flag), 0) != epoch) {
-      // about a second, or 2^22 polls should the global timer not advance (a legitimate wait,
-      // for the blocks before this one, lasts well under a millisecond)
-      if ((++n & 63) == 0 && (trsv_timer() - t0 > 1000000000ull || n >= (1u << 22) ||
+      // wait_ns, or 2^22 polls should the global timer not advance (a legitimate wait, for
+      // the blocks before this one, lasts well under a millisecond)
+      if ((++n & 63) == 0 && (trsv_timer() - t0 > wait_ns || n >= (1u << 22) ||
                               (atomicAdd(status, 0) & kStatusTimeout))) {
         atomicOr(status, kStatusTimeout);
         ok = 0;
@@ -511,7 +512,12 @@ __device__ bool trsv_wait(const int* flag, int epoch, int* status, int* s_ok) {
 }
 
 __global__ void __launch_bounds__(256) k_chol_solve_coop(const double* __restrict__ L, int n, double* x,
-                                                        int* flag_f, int* flag_b, int epoch, int* status) {
+                                                        int* flag_f, int* flag_b, int epoch_arg,
+                                                        const int* epoch_ptr, int* status,
+                                                        unsigned long long wait_ns, int stall) {
+  // the epoch comes from the host, or (graph replays) from a device counter that a preceding
+  // kernel has advanced
+  const int epoch = epoch_ptr ? *epoch_ptr : epoch_arg;
   __shared__ double D[kNB][kNB + 1];
   __shared__ double acc[kNB];
   __shared__ int s_ok;
@@ -528,7 +534,7 @@ __global__ void __launch_bounds__(256) k_chol_solve_coop(const double* __restric
   {
     const int r = 4 * wid + (lane >> 3), t = lane & 7;
     for (int J = 0; J < p; ++J) {
-      if (!trsv_wait(flag_f + J, epoch, status, &s_ok)) return;
+      if (!trsv_wait(flag_f + J, epoch, status, &s_ok, wait_ns)) return;
       const int jb = J * kNB;
       double sacc = 0.0;
       if (r < nb) {
@@ -561,7 +567,7 @@ __global__ void __launch_bounds__(256) k_chol_solve_coop(const double* __restric
     __threadfence();  // the published values before the flag, from every writing lane
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && !(stall && p == 0)) {
     __threadfence();
     atomicExch(flag_f + p, epoch);
   }
@@ -569,7 +575,7 @@ __global__ void __launch_bounds__(256) k_chol_solve_coop(const double* __restric
   {
     const int r = 4 * wid + (lane & 3), t = lane >> 2;
     for (int J = nblk - 1; J > p; --J) {
-      if (!trsv_wait(flag_b + J, epoch, status, &s_ok)) return;
+      if (!trsv_wait(flag_b + J, epoch, status, &s_ok, wait_ns)) return;
       const int jb = J * kNB, jn = min(kNB, n - jb);
       double sacc = 0.0;
       if (r < nb) {
@@ -708,6 +714,87 @@ __global__ void k_sum_to_scalar(const double* __restrict__ partial, int n, doubl
 }
 
 __global__ void k_pcg_alpha(double* scal) { scal[2] = scal[0] / scal[1]; }
+
+// Device-driven PCG (the loop of h1w_pcg as a graph with a conditional while node). Slots
+// beyond the host-driven ones: 7 first, 8 iterations, 9 tol^2 = rtol^2 b.b, 10 maxit,
+// 11 true r.r, 12 init (start from x = 0), 13 rtol. The loop body is one PCG iteration
+// rotated so that it ends with the convergence test:
+//   z = P r; rz_new = r.z; beta (0 the first time); p = z + beta p; w = J p = J z + beta w;
+//   q = A p; a = rz / p.q; x += a p; r -= a q; rr = r.r; continue while rr > tol^2 and it < maxit.
+__global__ void k_pcg_set_scalars(double* scal, double rtol, int maxit, int init) {
+  scal[13] = rtol;
+  scal[10] = (double)maxit;
+  scal[12] = init ? 1.0 : 0.0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_pcg_init(double* __restrict__ x, double* __restrict__ r,
+                                                      const double* __restrict__ b, const double* __restrict__ scal,
+                                                      int64_t N) {
+  if (scal[12] == 0.0) return;  // a restart keeps x and the true residual in r
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) {
+    x[k] = 0.0;
+    r[k] = b[k];
+  }
+}
+
+__device__ __forceinline__ unsigned pcg_continue(const double* scal) {
+  const double rr = scal[5];
+  return (isfinite(rr) && rr > scal[9] && scal[8] < scal[10]) ? 1u : 0u;
+}
+
+// after b.b (slot 6) and r.r (slot 5) are formed: the tolerance, the counters, the condition
+__global__ void k_pcg_start(double* scal, cudaGraphConditionalHandle h) {
+  scal[9] = scal[13] * scal[13] * scal[6];
+  if (scal[12] != 0.0) scal[8] = 0.0;
+  scal[7] = 1.0;
+  cudaGraphSetConditional(h, pcg_continue(scal));
+}
+
+__global__ void k_pcg_beta_dev(double* scal) {
+  if (scal[7] != 0.0) {
+    scal[4] = 0.0;
+  } else {
+    scal[4] = scal[3] / scal[0];
+  }
+  scal[0] = scal[3];
+}
+
+__global__ void k_p_update_dev(double* __restrict__ p, const double* __restrict__ z, double* __restrict__ w,
+                               const double* __restrict__ jz, const double* __restrict__ scal, int64_t N, int m) {
+  const bool first = scal[7] != 0.0;
+  const double beta = scal[4];
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) p[k] = first ? z[k] : z[k] + beta * p[k];
+  if (k < m) w[k] = first ? jz[k] : jz[k] + beta * w[k];
+}
+
+__global__ void k_pcg_alpha_dev(double* scal) {
+  scal[2] = scal[0] / scal[1];
+  scal[7] = 0.0;
+}
+
+__global__ void k_pcg_check(double* scal, cudaGraphConditionalHandle h) {
+  scal[8] += 1.0;
+  cudaGraphSetConditional(h, pcg_continue(scal));
+}
+
+// r = b - q with partial sums of r.r per block
+__global__ void __launch_bounds__(kThreads) k_true_residual(double* __restrict__ r, const double* __restrict__ b,
+                                                           const double* __restrict__ q, int64_t N,
+                                                           double* __restrict__ partial) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double t = 0.0;
+  if (k < N) {
+    const double v = b[k] - q[k];
+    r[k] = v;
+    t = v * v;
+  }
+  t = block_sum(t);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void k_bump(int* counter) { *counter += 1; }
 
 __global__ void k_pcg_beta(double* scal) {
   scal[4] = scal[3] / scal[0];
@@ -882,8 +969,8 @@ void launch_trsv_upper_t(const double* L, int n, double* x, int nrhs, cudaStream
   note_launches(1);
 }
 
-bool launch_chol_solve_coop(const double* L, int n, double* x, int* flags, int epoch, int* status,
-                            cudaStream_t s) {
+bool launch_chol_solve_coop(const double* L, int n, double* x, int* flags, int epoch, const int* epoch_ptr,
+                            int* status, unsigned long long wait_ns, int stall, cudaStream_t s) {
   const int nblk = (n + kNB - 1) / kNB;
   int dev = 0, coop = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -894,9 +981,21 @@ bool launch_chol_solve_coop(const double* L, int n, double* x, int* flags, int e
     return false;
   int* flag_f = flags;
   int* flag_b = flags + nblk;
-  void* args[] = {(void*)&L, (void*)&n, (void*)&x, (void*)&flag_f, (void*)&flag_b, (void*)&epoch, (void*)&status};
-  if (cudaLaunchCooperativeKernel((const void*)k_chol_solve_coop, dim3(nblk), dim3(256), args, 0, s) != cudaSuccess)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblk);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_chol_solve_coop, L, n, x, flag_f, flag_b, epoch, epoch_ptr, status, wait_ns, stall) !=
+      cudaSuccess) {
+    cudaGetLastError();
     return false;
+  }
   note_launches(1);
   return true;
 }
@@ -950,6 +1049,47 @@ void launch_sum_to_scalar(const double* partial, int n, double* dst, cudaStream_
 }
 
 void launch_pcg_alpha(double* scal, cudaStream_t s) { k_pcg_alpha<<<1, 1, 0, s>>>(scal); }
+
+// ---- the PCG iteration driven from the device (graph replays, no host round trip) ----
+
+void launch_pcg_set_scalars(double* scal, double rtol, int maxit, int init, cudaStream_t s) {
+  k_pcg_set_scalars<<<1, 1, 0, s>>>(scal, rtol, maxit, init);
+  note_launches(1);
+}
+void launch_pcg_init(double* x, double* r, const double* b, const double* scal, int64_t N, cudaStream_t s) {
+  k_pcg_init<<<nblk(N), kThreads, 0, s>>>(x, r, b, scal, N);
+  note_launches(1);
+}
+void launch_pcg_start(double* scal, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_pcg_start<<<1, 1, 0, s>>>(scal, h);
+  note_launches(1);
+}
+void launch_pcg_beta_dev(double* scal, cudaStream_t s) {
+  k_pcg_beta_dev<<<1, 1, 0, s>>>(scal);
+  note_launches(1);
+}
+void launch_p_update_dev(double* p, const double* z, double* w, const double* jz, const double* scal, int64_t N,
+                         int m, cudaStream_t s) {
+  const int64_t n = N > m ? N : m;
+  k_p_update_dev<<<nblk(n), kThreads, 0, s>>>(p, z, w, jz, scal, N, m);
+  note_launches(1);
+}
+void launch_pcg_alpha_dev(double* scal, cudaStream_t s) {
+  k_pcg_alpha_dev<<<1, 1, 0, s>>>(scal);
+  note_launches(1);
+}
+void launch_pcg_check(double* scal, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_pcg_check<<<1, 1, 0, s>>>(scal, h);
+  note_launches(1);
+}
+void launch_true_residual(double* r, const double* b, const double* q, int64_t N, double* partial, cudaStream_t s) {
+  k_true_residual<<<nblk(N), kThreads, 0, s>>>(r, b, q, N, partial);
+  note_launches(1);
+}
+void launch_bump(int* counter, cudaStream_t s) {
+  k_bump<<<1, 1, 0, s>>>(counter);
+  note_launches(1);
+}
 void launch_pcg_beta(double* scal, cudaStream_t s) { k_pcg_beta<<<1, 1, 0, s>>>(scal); }
 
 void launch_xr_update(double* x, double* r, const double* p, const double* q, const double* scal,

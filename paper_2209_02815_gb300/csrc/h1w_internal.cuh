@@ -80,6 +80,8 @@ struct OzakiWork {
   double* partial;               // [splits][m][m]
   int* status;                   // device status word
   long long klen;                // K panel width (multiple of 2048)
+  unsigned long long wait_ns;    // limit of each bounded wait (0: one second)
+  int stall;                     // failure-path test: withhold the operand copies (see h1w_inject_stall)
 };
 long long ozaki_panel_width(long long N);
 long long ozaki_chunks(long long N);
@@ -90,10 +92,12 @@ int ozaki_splits(int m, long long kp, int sms);
 int ozaki_max_splits(int m);
 bool ozaki_supported();
 // Each operand as FP64 (J, H) or, when its double-float copy (Jdf, Hdf) is given, as that.
-// before/after (may be null) are called around each GEMM kernel launch with hook_arg.
+// hook (may be null) is called as hook(hook_arg, which, 1) before and hook(hook_arg, which, 0)
+// after each launch, which = kOzakiSplitJ, kOzakiSplitH (digit splits) or kOzakiGemm.
+enum { kOzakiGemm = 0, kOzakiSplitJ = 1, kOzakiSplitH = 2 };
 bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, const df* Hdf, int m, long long N,
-                              const OzakiWork& w, int splits, cudaStream_t s, void (*before)(void*),
-                              void (*after)(void*), void* hook_arg);
+                              const OzakiWork& w, int splits, cudaStream_t s, void (*hook)(void*, int, int),
+                              void* hook_arg);
 void ozaki_tiles(int m, std::vector<int>& out);
 
 // ---- kernel launchers (mg_kernels.cu) --------------------------------------
@@ -188,9 +192,13 @@ void launch_trsv_lower(const double* L, int n, double* x, int nrhs, cudaStream_t
 void launch_trsv_upper_t(const double* L, int n, double* x, int nrhs, cudaStream_t s);
 // x <- L^-T L^-1 x for one right-hand side in one cooperative launch of ceil(n / 32) CTAs.
 // flags: 2 ceil(n / 32) ints, zero before the first call; epoch > 0 and different from the
-// previous call's. False if the device cannot keep all CTAs resident (nothing launched).
-bool launch_chol_solve_coop(const double* L, int n, double* x, int* flags, int epoch, int* status,
-                            cudaStream_t s);
+// previous call's. Each wait gives up after wait_ns. stall (failure-path test): the first
+// block publishes no result, so the waits of the others run out. False if the device
+// cannot keep all CTAs resident (nothing launched).
+// epoch_ptr (may be null): a device counter holding the epoch instead of `epoch` (graph replays,
+// where a preceding launch_bump advances it).
+bool launch_chol_solve_coop(const double* L, int n, double* x, int* flags, int epoch, const int* epoch_ptr,
+                            int* status, unsigned long long wait_ns, int stall, cudaStream_t s);
 void launch_coarse_apply(const double* X, int n, int nrhs, const double* b, double* x,
                          cudaStream_t s);
 void launch_symmetrize_identity_solve(double* X, int n, cudaStream_t s);
@@ -203,6 +211,21 @@ void launch_cap_finalize(const double* partial, int splits, int m, double alpha,
 // Krylov scalar kernels: scal is a small device array (see ScalarSlot in capi.cu)
 void launch_sum_to_scalar(const double* partial, int n, double* dst, cudaStream_t s);
 void launch_pcg_alpha(double* scal, cudaStream_t s);
+// The PCG loop driven from the device (a graph with a conditional while node): scalar slots
+// 7 first, 8 iterations, 9 tol^2, 10 maxit, 11 true r.r, 12 init, 13 rtol (see dense_kernels.cu).
+enum : int { kSlotRZ = 0, kSlotPQ = 1, kSlotA = 2, kSlotRZN = 3, kSlotBeta = 4, kSlotRR = 5, kSlotBB = 6,
+             kSlotFirst = 7, kSlotIt = 8, kSlotTol2 = 9, kSlotMaxit = 10, kSlotRRTrue = 11, kSlotInit = 12,
+             kSlotRtol = 13 };
+void launch_pcg_set_scalars(double* scal, double rtol, int maxit, int init, cudaStream_t s);
+void launch_pcg_init(double* x, double* r, const double* b, const double* scal, int64_t N, cudaStream_t s);
+void launch_pcg_start(double* scal, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_pcg_beta_dev(double* scal, cudaStream_t s);
+void launch_p_update_dev(double* p, const double* z, double* w, const double* jz, const double* scal, int64_t N,
+                         int m, cudaStream_t s);
+void launch_pcg_alpha_dev(double* scal, cudaStream_t s);
+void launch_pcg_check(double* scal, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_true_residual(double* r, const double* b, const double* q, int64_t N, double* partial, cudaStream_t s);
+void launch_bump(int* counter, cudaStream_t s);
 void launch_pcg_beta(double* scal, cudaStream_t s);
 void launch_xr_update(double* x, double* r, const double* p, const double* q, const double* scal,
                       int64_t N, double* partial, cudaStream_t s);

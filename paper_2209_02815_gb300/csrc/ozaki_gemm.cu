@@ -92,15 +92,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false when the abort flag is set or about a second passes.
-__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait: false when the abort flag is set or wait_ns (normally one second) passes.
+__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, uint64_t wait_ns) {
   if (mbar_try(a, parity)) return true;
   const uint64_t t0 = gtimer();
   for (uint32_t n = 1;; ++n) {
     if (mbar_try(a, parity)) return true;
     if ((n & 255) == 0) {
       if (*abort_flag) return false;
-      if (gtimer() - t0 > kWaitNs || n >= kWaitPolls) return false;
+      if (gtimer() - t0 > wait_ns || n >= kWaitPolls) return false;
     }
   }
 }
@@ -157,6 +157,8 @@ struct OzakiArgs {
   long long kcta;       // K entries per CTA (multiple of kChunkK)
   long long klen;       // K extent of the digit tensors (multiple of kChunkK)
   long long kvalid;     // K entries of the panel holding data, rounded up to kChunkK (<= klen)
+  unsigned long long wait_ns;  // limit of each pipeline wait (one second unless a test shortens it)
+  int stall;            // failure-path test: the copy warp issues nothing, so every consumer's wait runs out
 };
 
 __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
@@ -197,11 +199,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) {
+    if (lane == 0 && !g.stall) {
       for (int it = 0; it < iters; ++it) {
         const int s = it & 1;
         const uint32_t ph = (it >> 1) & 1;
-        if (!mbar_wait(smem_u32(&bars[2 + s]), ph ^ 1, abort_flag)) {
+        if (!mbar_wait(smem_u32(&bars[2 + s]), ph ^ 1, abort_flag, g.wait_ns)) {
           *abort_flag = 1;
           break;
         }
@@ -233,12 +235,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
       int it = 0;
       bool ok = true;
       for (int c = 0; c < nchunks && ok; ++c) {
-        if (!mbar_wait(smem_u32(&bars[5]), (c & 1) ^ 1, abort_flag)) { ok = false; break; }
+        if (!mbar_wait(smem_u32(&bars[5]), (c & 1) ^ 1, abort_flag, g.wait_ns)) { ok = false; break; }
         tc_fence_after();
         for (int j = 0; j < kItersPerChunk; ++j, ++it) {
           const int s = it & 1;
           const uint32_t ph = (it >> 1) & 1;
-          if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(smem_u32(&bars[s]), ph, abort_flag, g.wait_ns)) { ok = false; break; }
           tc_fence_after();
           const uint32_t a0 = smem_u32(smem + s * kStageBytes);
           const uint64_t adesc0 = desc_sw64(a0);
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
       // lane 0 waits; the warp follows its result so that the .sync.aligned
       // TMEM loads below stay warp-uniform
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(smem_u32(&bars[4]), c & 1, abort_flag) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(smem_u32(&bars[4]), c & 1, abort_flag, g.wait_ns) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) { if (lane == 0) *abort_flag = 1; break; }
       __syncwarp();
@@ -576,8 +578,8 @@ bool ozaki_supported() {
 // comes as FP64 (J, H) or, when its double-float copy (Jdf, Hdf) is given, as that.
 // Returns false when the kernel attribute cannot be set.
 bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, const df* Hdf, int m, long long N,
-                              const OzakiWork& w, int splits, cudaStream_t s, void (*before)(void*),
-                              void (*after)(void*), void* hook_arg) {
+                              const OzakiWork& w, int splits, cudaStream_t s, void (*hook)(void*, int, int),
+                              void* hook_arg) {
   const long long kp = w.klen;
   const long long nch = (N + kChunkK - 1) / kChunkK;
   int* eA = w.expo;
@@ -597,10 +599,14 @@ bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, c
     uint16_t* dA = static_cast<uint16_t*>(w.digitsA);
     uint16_t* dB = static_cast<uint16_t*>(w.digitsB);
     const dim3 ga(rowsA / kSplitRows, gx), gb(rowsB / kSplitRows, gx);
+    if (hook) hook(hook_arg, kOzakiSplitJ, 1);
     if (Jdf) k_split_digits<df><<<ga, kSplitThreads, 0, s>>>(Jdf, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
     else k_split_digits<double><<<ga, kSplitThreads, 0, s>>>(J, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
+    if (hook) hook(hook_arg, kOzakiSplitJ, 0);
+    if (hook) hook(hook_arg, kOzakiSplitH, 1);
     if (Hdf) k_split_digits<df><<<gb, kSplitThreads, 0, s>>>(Hdf, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
     else k_split_digits<double><<<gb, kSplitThreads, 0, s>>>(H, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
+    if (hook) hook(hook_arg, kOzakiSplitH, 0);
     OzakiArgs a;
     a.dA = dA;
     a.dB = dB;
@@ -615,9 +621,11 @@ bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, c
     a.kcta = kcta;
     a.klen = kp;
     a.kvalid = (kw + kChunkK - 1) / kChunkK * kChunkK;
-    if (before) before(hook_arg);
+    a.wait_ns = w.wait_ns ? w.wait_ns : kWaitNs;
+    a.stall = w.stall;
+    if (hook) hook(hook_arg, kOzakiGemm, 1);
     k_ozaki_gemm<<<dim3(tiles, splits), kGemmThreads, kSmemBytes, s>>>(a);
-    if (after) after(hook_arg);
+    if (hook) hook(hook_arg, kOzakiGemm, 0);
     note_launches(3);
   }
   return true;

@@ -20,6 +20,7 @@ from . import build as _build
 H1W_OK, H1W_EINVAL, H1W_ENOMEM, H1W_ECUDA, H1W_ENOTCONV = 0, 1, 2, 3, 4
 H1W_ENOTSPD, H1W_ETIMEOUT, H1W_EUNSUPPORTED, H1W_ESTATE = 5, 6, 7, 8
 H1W_Q1_VERTEX, H1W_FV_CELL = 1, 2
+H1W_STALL_NONE, H1W_STALL_CAP_GEMM, H1W_STALL_PREC_SOLVE = 0, 1, 2
 
 _STATUS_NAMES = {0: "H1W_OK", 1: "H1W_EINVAL", 2: "H1W_ENOMEM", 3: "H1W_ECUDA", 4: "H1W_ENOTCONV",
                  5: "H1W_ENOTSPD", 6: "H1W_ETIMEOUT", 7: "H1W_EUNSUPPORTED", 8: "H1W_ESTATE"}
@@ -39,7 +40,8 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int32), ("rhs_block", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("cap_gemm", ctypes.c_int32),
-                ("mg_arith", ctypes.c_int32), ("mg_unfused", ctypes.c_int32), ("precond", ctypes.c_int32)]
+                ("mg_arith", ctypes.c_int32), ("mg_unfused", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("pcg_mode", ctypes.c_int32)]
 
 
 class Timings(ctypes.Structure):
@@ -50,7 +52,9 @@ class Timings(ctypes.Structure):
                 ("t_hupd_ms", ctypes.c_float), ("n_gemm_kernel", ctypes.c_int32), ("n_jdot", ctypes.c_int32),
                 ("n_op", ctypes.c_int32), ("n_hdot", ctypes.c_int32), ("n_hupd", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("t_vc_down_ms", ctypes.c_float), ("t_vc_up_ms", ctypes.c_float),
-                ("n_vc_down", ctypes.c_int32), ("n_vc_up", ctypes.c_int32)]
+                ("n_vc_down", ctypes.c_int32), ("n_vc_up", ctypes.c_int32), ("t_split_j_ms", ctypes.c_float),
+                ("t_split_h_ms", ctypes.c_float), ("t_d2df_ms", ctypes.c_float), ("n_split_j", ctypes.c_int32),
+                ("n_split_h", ctypes.c_int32), ("n_d2df", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -102,6 +106,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "h1w_apply_op_static": (I32, [G, I32, P, P, P, P]),
         "h1w_solve_batch": (I32, [ctypes.POINTER(P), I32, ctypes.POINTER(I32), ctypes.POINTER(P),
                                   ctypes.POINTER(P), ctypes.POINTER(P), D, I32, I32, IN, ctypes.POINTER(I32)]),
+        "h1w_solve_batch_graph": (I32, [ctypes.POINTER(P), I32, ctypes.POINTER(I32), ctypes.POINTER(P),
+                                        ctypes.POINTER(P), ctypes.POINTER(P), D, I32, IN, ctypes.POINTER(I32)]),
         "h1w_ert_workspace_size": (SZ, [P, I32, I32]),
         "h1w_forward": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, SZ, D, I32, ctypes.c_uint32, IN]),
         "h1w_adjoint": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, SZ]),
@@ -110,6 +116,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                               ctypes.POINTER(GnInfo)]),
         "h1w_direct_workspace_size": (SZ, [P]),
         "h1w_solve_direct": (I32, [P, P, P, P, SZ]),
+        "h1w_cholesky": (I32, [P, I32, P]),
+        "h1w_prefetch_J": (I32, [P, I32, P, P]),
+        "h1w_get_copy_profile": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                       ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                       ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+        "h1w_inject_stall": (I32, [P, I32, ctypes.c_int64]),
+        "h1w_set_pcg_mode": (I32, [P, I32]),
         "h1w_last_error": (ctypes.c_char_p, [P]),
         "h1w_destroy": (None, [P]),
     }
@@ -196,9 +209,10 @@ def h1w_capacitance_from_host(ctx, m: int, J_host: torch.Tensor, J_dev: torch.Te
                                             _ptr(J_dev, m * N, "J_dev") if m > 0 else None), ctx)
 
 
-def solve_batch(solvers, Js, bs, xs, rtol: float, maxit: int = 500, threads: int = 8):
-    """Capacitance + PCG for several Solver objects at once (h1w_solve_batch). Each
-    solver must have been created on its own stream. Returns (list of Info, list of
+def solve_batch(solvers, Js, bs, xs, rtol: float, maxit: int = 500, threads: int = 8, graph: bool = False):
+    """Capacitance + PCG for several Solver objects at once: h1w_solve_batch (a pool of host
+    threads) or, with graph=True, h1w_solve_batch_graph (all systems in one CUDA graph).
+    Each solver must have been created on its own stream. Returns (list of Info, list of
     status codes); raises H1wError when a system failed."""
     n = len(solvers)
     P = ctypes.c_void_p
@@ -215,7 +229,10 @@ def solve_batch(solvers, Js, bs, xs, rtol: float, maxit: int = 500, threads: int
         s.m = int(J.shape[0]) if J is not None else 0
         s._enter(J, b, x)
     try:
-        st = load().h1w_solve_batch(ctxs, n, ms, Jp, bp, xp, float(rtol), int(maxit), int(threads), infos, sts)
+        if graph:
+            st = load().h1w_solve_batch_graph(ctxs, n, ms, Jp, bp, xp, float(rtol), int(maxit), infos, sts)
+        else:
+            st = load().h1w_solve_batch(ctxs, n, ms, Jp, bp, xp, float(rtol), int(maxit), int(threads), infos, sts)
     finally:
         for s in solvers:
             s._leave()
@@ -347,6 +364,18 @@ def h1w_gn_step(ctx, survey: Survey, g_obs: torch.Tensor, m_ref: torch.Tensor, m
     return info
 
 
+def h1w_cholesky(ctx, A: torch.Tensor) -> None:
+    """A = L L^T in place (A: n x n FP64 CUDA tensor, row-major), line chol's kernels."""
+    n = int(A.shape[0])
+    if A.dim() != 2 or A.shape[1] != n:
+        raise ValueError("A must be square")
+    _check(load().h1w_cholesky(ctx, n, _ptr(A, n * n, "A")), ctx)
+
+
+def h1w_inject_stall(ctx, kind: int, wait_limit_ns: int = 0) -> None:
+    _check(load().h1w_inject_stall(ctx, int(kind), int(wait_limit_ns)), ctx)
+
+
 def h1w_destroy(ctx) -> None:
     if ctx:
         load().h1w_destroy(ctx)
@@ -410,6 +439,26 @@ class Solver:
         h1w_capacitance_from_host(self.ctx, m, J_host, J_dev, self.N)
         self._leave()
         self.m = m
+
+    def prefetch_J(self, J_host: torch.Tensor, J_dev: torch.Tensor) -> None:
+        """Starts copying J_host (pinned) into J_dev for a later capacitance_from_host with the
+        same pair (h1w_prefetch_J); the caller keeps both alive until then."""
+        m = int(J_host.shape[0])
+        if J_host.is_cuda or not J_host.is_pinned() or J_host.dtype != torch.float64 or not J_host.is_contiguous():
+            raise ValueError("J_host must be a pinned, contiguous float64 CPU tensor")
+        self._enter(J_dev)
+        _check(load().h1w_prefetch_J(self.ctx, m, J_host.data_ptr(), _ptr(J_dev, m * self.N, "J_dev")), self.ctx)
+        self._leave()
+
+    def copy_profile(self, cap: int = 256):
+        """Per-batch timeline of the last capacitance_from_host (h1w_get_copy_profile): a list of
+        dicts with rows, copy_begin, copy_end, cycle_begin, cycle_end in ms from line H's start."""
+        n = ctypes.c_int32()
+        rows = (ctypes.c_int32 * cap)()
+        arr = [(ctypes.c_float * cap)() for _ in range(4)]
+        _check(load().h1w_get_copy_profile(self.ctx, cap, ctypes.byref(n), rows, *arr), self.ctx)
+        keys = ("copy_begin", "copy_end", "cycle_begin", "cycle_end")
+        return [dict(rows=int(rows[i]), **{k: float(a[i]) for k, a in zip(keys, arr)}) for i in range(min(n.value, cap))]
 
     def apply_prec(self, r, z=None):
         z = torch.empty_like(r) if z is None else z
@@ -544,6 +593,22 @@ class Solver:
         h1w_capacitance_factors(self.ctx, C, L, m)
         self._leave()
         return C, L
+
+    def cholesky(self, A):
+        """Factors A in place on the context's stream (h1w_cholesky); returns A."""
+        self._enter(A)
+        try:
+            h1w_cholesky(self.ctx, A)
+        finally:
+            self._leave()
+        return A
+
+    def set_pcg_mode(self, mode: int) -> None:
+        """0: the PCG loop driven from the device (CUDA graph); 1: the host loop."""
+        _check(load().h1w_set_pcg_mode(self.ctx, int(mode)), self.ctx)
+
+    def inject_stall(self, kind: int, wait_limit_ns: int = 0) -> None:
+        h1w_inject_stall(self.ctx, kind, wait_limit_ns)
 
     def timings(self) -> Timings:
         return h1w_get_timings(self.ctx)

@@ -354,6 +354,56 @@ def test_capacitance_from_host_equals_device_path(rhs_block):
     assert torch.equal(Ca, Cb) and torch.equal(La, Lb)
 
 
+def test_prefetched_capacitance_from_host_equals_device_path():
+    """Double-buffered prefetch (h1w_prefetch_J) of the next system's J during the current
+    solve: three systems in a row, each capacitance bit-identical to the device entry point,
+    the solutions equal, and the per-batch copy profile is ordered (each batch's cycles
+    start after its copy ended)."""
+    d, n, h = _fv((24, 24, 24))
+    N = int(np.prod(n))
+    m = 70
+    rng = np.random.default_rng(43)
+    Jhs = [torch.as_tensor(rng.standard_normal((m, N)) / np.sqrt(N)).pin_memory() for _ in range(3)]
+    b = _t(rng.standard_normal(N))
+    ref = _gpu(d, n, h, 1e-2, m)
+    S = _gpu(d, n, h, 1e-2, m)
+    bufs = [torch.empty((m, N), dtype=torch.float64, device=DEV) for _ in range(2)]
+    S.prefetch_J(Jhs[0], bufs[0])
+    for k in range(3):
+        if k + 1 < 3:
+            S.prefetch_J(Jhs[k + 1], bufs[(k + 1) % 2])
+        S.capacitance_from_host(Jhs[k], bufs[k % 2])
+        prof = S.copy_profile()
+        assert sum(p["rows"] for p in prof) == m
+        for p in prof:
+            assert p["copy_end"] >= p["copy_begin"]
+            assert p["cycle_begin"] >= p["copy_end"] - 1e-3
+        C, L = S.factors()
+        x, _ = S.pcg(b, 1e-12, 200)
+        ref.capacitance(Jhs[k].to(DEV))
+        Cr, Lr = ref.factors()
+        xr, _ = ref.pcg(b, 1e-12, 200)
+        assert torch.equal(bufs[k % 2], Jhs[k].to(DEV))
+        assert torch.equal(C, Cr) and torch.equal(L, Lr)
+        assert torch.equal(x, xr)
+
+
+def test_prefetch_rejects_a_third_pending_copy():
+    d, n, h = _fv((16, 8, 12))
+    N = int(np.prod(n))
+    m = 9
+    S = _gpu(d, n, h, 1e-2, m)
+    Jh = torch.zeros((m, N), dtype=torch.float64).pin_memory()
+    bufs = [torch.empty((m, N), dtype=torch.float64, device=DEV) for _ in range(3)]
+    S.prefetch_J(Jh, bufs[0])
+    S.prefetch_J(Jh, bufs[1])
+    with pytest.raises(h1w.H1wError) as ei:
+        S.prefetch_J(Jh, bufs[2])
+    assert ei.value.status == h1w.H1W_ESTATE
+    S.capacitance_from_host(Jh, bufs[0])
+    S.capacitance_from_host(Jh, bufs[1])
+
+
 def test_solve_batch_matches_individual_solves():
     """Systems of different grids, discretizations and measurement counts
     (including m = 0), solved together by h1w_solve_batch on their own streams,
