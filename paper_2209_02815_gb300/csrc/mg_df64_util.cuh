@@ -18,10 +18,20 @@ __device__ __forceinline__ df dzero() { return df_make(0.f, 0.f); }
 // Cascaded summation of double-floats: the high parts are added with TwoSum,
 // their rounding errors and the low parts are collected in one float, and the
 // result is renormalized once. For the handful of terms summed here the
-// error stays near 2^-46 of the largest term.
+// error stays near 2^-46 of the largest term. The first term is taken as it is
+// (s = hi, e = lo): adding it to an empty sum by TwoSum gives the same two floats
+// (up to the sign of a zero) for 8 instructions that IEEE rules keep the compiler
+// from removing. Where the adds are unrolled, `first` is known at compile time.
 struct dsum {
   float s = 0.f, e = 0.f;
+  bool first = true;
   __device__ __forceinline__ void add(df v) {
+    if (first) {
+      s = v.hi;
+      e = v.lo;
+      first = false;
+      return;
+    }
     const df t = two_sum(s, v.hi);
     s = t.hi;
     e = __fadd_rn(e, __fadd_rn(t.lo, v.lo));
