@@ -36,6 +36,7 @@ N_SIDE = 128
 N_E = 32
 ALPHA = 1e-3
 RTOL = 1e-8
+ACC_RTOL = 1e-11   # the FP64 form's tolerance for the accuracy comparison (near its attainable floor)
 MAXIT = 1000
 METRIC = "GN linear solves/s at rel-res 1e-8"
 # FP32 instructions per fine cell of the fused double-float legs (isotropic 7-point operator;
@@ -57,9 +58,10 @@ HBM_BYTES_UP = 25.0
 # ncu DRAM read + write bytes per fine cell and right-hand side of the finest up leg, from one
 # capture of the 64^3 case with 128 right-hand sides (the kernel build these figures belong to
 # is named by NCU_TRAFFIC_BUILD; traffic is reported only while it matches FUSED_BUILD)
-NCU_BYTES_PER_CELL_RHS = {"k_post_fused": (599.294464e6 + 242.928896e6) / (262144 * 128)}
-NCU_TRAFFIC_BUILD = "df-legs-v1"
-FUSED_BUILD = "df-legs-v2"
+NCU_BYTES_PER_CELL_RHS = {"k_post_fused": (599.148544e6 + 242.237184e6) / (262144 * 128),
+                          "k_pre_fused": (285.612544e6 + 255.360512e6) / (262144 * 128)}
+NCU_TRAFFIC_BUILD = "df-legs-v3"
+FUSED_BUILD = "df-legs-v3"
 DTYPE_MIXED = "mixed(df48+bf16-digit, fp64 outer)"
 
 
@@ -97,6 +99,13 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of the ERT step: a batch of this many independent 2D Q1 systems "
                          "(sides 128..1024, m 8..256, alpha log-uniform 1e-4..1e-1) solved by h1w_solve_batch")
+    ap.add_argument("--batch-mode", default="graph", choices=["graph", "threads"],
+                    help="--batch: one CUDA graph for all systems (h1w_solve_batch_graph) or a pool of host "
+                         "threads (h1w_solve_batch)")
+    ap.add_argument("--no-autotune", action="store_true", help="--batch: default rhs_block for every instance")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="after timing: the solution's error against the plain FP64 GPU form solved to 1e-12 "
+                         "(frees the mixed workspace first; for the largest sizes)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip the oracle's FP64 residual of the timed solution (rank 0)")
@@ -276,24 +285,37 @@ def run_batch(args):
     dev = torch.device("cuda", local)
     descs = inputs.batch_instances(args.batch)
     solvers, Js, bs, xs = [], [], [], []
+    tuned = {}
+    t_tune = time.perf_counter()
     for dsc in descs:
         n = dsc["n"]
         J, b = inputs.batch_instance_data(dsc, device=dev)
+        g = h1w.make_grid(h1w.H1W_Q1_VERTEX, (n, n), (1.0 / (n - 1),) * 2, dsc["alpha"])
+        opt = None
+        if not args.no_autotune:
+            # rhs_block of line H's batched V-cycle per instance shape (cached per side and m)
+            opt, ms_rhs = h1w.h1w_autotune(g, dsc["m"], device=dev)
+            tuned["%dx%d m=%d" % (n, n, dsc["m"])] = {"rhs_block": int(opt.rhs_block),
+                                                       "vcycle_ms_per_rhs": ms_rhs}
         solvers.append(h1w.Solver(h1w.H1W_Q1_VERTEX, (n, n), (1.0 / (n - 1),) * 2, dsc["alpha"], dsc["m"],
-                                  device=dev, stream=torch.cuda.Stream(dev)))
+                                  device=dev, stream=torch.cuda.Stream(dev), opt=opt))
         Js.append(J)
         bs.append(b)
         xs.append(torch.empty_like(b))
     torch.cuda.synchronize()
+    t_tune = time.perf_counter() - t_tune
+    graph = args.batch_mode == "graph"
     for _ in range(args.warmup):
-        infos, _ = h1w.solve_batch(solvers, Js, bs, xs, RTOL, MAXIT)
+        infos, _ = h1w.solve_batch(solvers, Js, bs, xs, RTOL, MAXIT, graph=graph)
     barrier(world)
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
     t0 = time.perf_counter()
+    launches = 0
     for _ in range(args.steps):
-        infos, _ = h1w.solve_batch(solvers, Js, bs, xs, RTOL, MAXIT)
+        infos, _ = h1w.solve_batch(solvers, Js, bs, xs, RTOL, MAXIT, graph=graph)
+        launches += sum(int(S_.timings().launches_capacitance + S_.timings().launches_pcg) for S_ in solvers)
     torch.cuda.synchronize()
     dt = allmax(world, (time.perf_counter() - t0) * 1e3)
     clocks = clk.stop()
@@ -302,13 +324,16 @@ def run_batch(args):
            "warmup": args.warmup, "ms_per_step": dt / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": DTYPE_MIXED, "data": "synthetic",
            "config": {"workload": "%d independent 2D Q1 systems per step (sides 128-1024, m 8-256, "
-                                  "alpha log-uniform 1e-4..1e-1), h1w_solve_batch" % len(descs),
+                                  "alpha log-uniform 1e-4..1e-1), %s" %
+                                  (len(descs), "h1w_solve_batch_graph (one CUDA graph)" if graph else
+                                   "h1w_solve_batch (host thread pool)"),
                       "dof_total": int(sum(d["n"] ** 2 for d in descs)),
                       "J_entries": int(sum(d["n"] ** 2 * d["m"] for d in descs)),
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "pcg_iters": [int(i.iters) for i in infos], "max_rel_res_true": max(float(i.rel_res_true) for i in infos),
            "clocks": clocks, "timing": "host wall clock around whole batches (each call synchronizes)",
-           "impl": "ours"}
+           "gpu_launches": launches, "autotune": tuned or None,
+           "setup_and_autotune_s": t_tune, "impl": "ours"}
     if rank == 0:
         print(json.dumps(out))
 
@@ -681,10 +706,17 @@ def run_ours(args):
                 if pipelined:
                     S.prefetch_J(J_host, bufs[0])
                 for k_ in range(steps):
-                    if pipelined and k_ + 1 < steps:
-                        S.prefetch_J(J_host, bufs[(k_ + 1) % 2])
-                    b_dev.copy_(b_host, non_blocking=True)
+                    # where b's small copy goes matters: behind the next step's J on the copy
+                    # engine it would wait for all of J, and issued on the solver's stream just
+                    # before h1w_capacitance_from_host it held line H back until every row of J
+                    # had arrived (measured); so b goes before the prefetch, or after line H
+                    if pipelined:
+                        b_dev.copy_(b_host, non_blocking=True)
+                        if k_ + 1 < steps:
+                            S.prefetch_J(J_host, bufs[(k_ + 1) % 2])
                     S.capacitance_from_host(J_host, bufs[k_ % 2] if pipelined else J_dev)
+                    if not pipelined:
+                        b_dev.copy_(b_host, non_blocking=True)
                     waits.append(copy_waits())
                     S.pcg(b_dev, RTOL, MAXIT, x=x)
                     x_host.copy_(x, non_blocking=True)
@@ -725,28 +757,52 @@ def run_ours(args):
         # the plain FP64 GPU form of the same step (FP64 V-cycle and Krylov passes, FP64
         # CUDA-core capacitance GEMM), same inputs, for comparison with the headline
         fp64_form = None
-        if args.fp64_form_steps > 0 and args.arith == "mixed":
+        accuracy = None
+        x64_keep = None
+        if (args.fp64_form_steps > 0 or args.accuracy) and args.arith == "mixed":
             o64 = h1w.h1w_default_options()
             o64.cap_gemm = 1
             o64.mg_arith = 1
+            if args.accuracy:   # both workspaces do not fit at the largest sizes
+                x_tight, i_tight = S.pcg(b, ACC_RTOL, 4 * MAXIT, x=torch.empty_like(x), raise_on_notconv=False)
+                S.close()
+                del S
+                torch.cuda.synchronize()
+                torch.cuda.empty_cache()
             S64 = h1w.Solver(h1w.H1W_FV_CELL, (n, n, n), (1.0 / n,) * 3, ALPHA, m, device=dev, stream=stream,
                              opt=o64)
             S64.capacitance(J)                      # untimed warm-up solve
             S64.pcg(b, RTOL, MAXIT, x=x)
+            if args.accuracy:
+                # the timed mixed-precision solution against the plain FP64 form solved to 1e-12
+                x64, i64 = S64.pcg(b, ACC_RTOL, 4 * MAXIT, x=torch.empty_like(x), raise_on_notconv=False)
+                dx = x_timed - x64
+                accuracy = {"rel_err_vs_fp64_form": float(torch.linalg.norm(dx) / torch.linalg.norm(x64)),
+                            "max_abs_err_over_max_abs": float(dx.abs().max() / x64.abs().max()),
+                            "fp64_form_rtol": ACC_RTOL, "fp64_form_iters": int(i64.iters),
+                            "fp64_form_rel_res_true": float(i64.rel_res_true),
+                            "mixed_rtol": RTOL, "bound": 1e-7,
+                            "mixed_at_fp64_form_rtol": {
+                                "rel_err_vs_fp64_form": float(torch.linalg.norm(x_tight - x64) / torch.linalg.norm(x64)),
+                                "max_abs_err_over_max_abs": float((x_tight - x64).abs().max() / x64.abs().max()),
+                                "iters": int(i_tight.iters), "restarts": int(i_tight.restarts),
+                                "rel_res_true": float(i_tight.rel_res_true)}}
+                x64_keep = x64
             torch.cuda.synchronize()
-            g0 = torch.cuda.Event(enable_timing=True)
-            g1 = torch.cuda.Event(enable_timing=True)
-            g0.record(stream)
-            for _ in range(args.fp64_form_steps):
-                S64.capacitance(J)
-                _, inf64 = S64.pcg(b, RTOL, MAXIT, x=x)
-            g1.record(stream)
-            torch.cuda.synchronize()
-            gms = allmax(world, g0.elapsed_time(g1))
-            fp64_form = {"value": world * args.fp64_form_steps / (gms / 1e3), "unit": "solves/s",
-                         "ms_per_step": gms / args.fp64_form_steps, "steps": args.fp64_form_steps,
-                         "pcg_iters": int(inf64.iters), "rel_res_true": float(inf64.rel_res_true),
-                         "options": "cap_gemm=1 (FP64 CUDA-core GEMM), mg_arith=1 (FP64 V-cycle and passes)"}
+            if args.fp64_form_steps > 0:
+                g0 = torch.cuda.Event(enable_timing=True)
+                g1 = torch.cuda.Event(enable_timing=True)
+                g0.record(stream)
+                for _ in range(args.fp64_form_steps):
+                    S64.capacitance(J)
+                    _, inf64 = S64.pcg(b, RTOL, MAXIT, x=x)
+                g1.record(stream)
+                torch.cuda.synchronize()
+                gms = allmax(world, g0.elapsed_time(g1))
+                fp64_form = {"value": world * args.fp64_form_steps / (gms / 1e3), "unit": "solves/s",
+                             "ms_per_step": gms / args.fp64_form_steps, "steps": args.fp64_form_steps,
+                             "pcg_iters": int(inf64.iters), "rel_res_true": float(inf64.rel_res_true),
+                             "options": "cap_gemm=1 (FP64 CUDA-core GEMM), mg_arith=1 (FP64 V-cycle and passes)"}
             del S64
 
     value = world * args.steps / (ms_max / 1e3)
@@ -829,9 +885,10 @@ def run_ours(args):
     # (dram__bytes_read.sum + dram__bytes_write.sum of the finest up leg), scaled by the cells x
     # right-hand sides of an average launch here: reads equal the algorithmic x, b and
     # coarse-vector bytes there, so traffic grows in proportion
-    if roofline and dom.startswith("k_post_fused") and n_up and NCU_TRAFFIC_BUILD == FUSED_BUILD:
-        roofline["traffic"] = NCU_BYTES_PER_CELL_RHS["k_post_fused"] * float(m) * N * args.steps / n_up
-        roofline["traffic_note"] = "ncu 64^3 x 128 RHS capture, scaled by cell-RHS per launch"
+    for key_, n_key in (("k_post_fused", "vc_up"), ("k_pre_fused", "vc_down")):
+        if roofline and dom.startswith(key_) and kern[n_key][1] and NCU_TRAFFIC_BUILD == FUSED_BUILD:
+            roofline["traffic"] = NCU_BYTES_PER_CELL_RHS[key_] * float(m) * N * args.steps / kern[n_key][1]
+            roofline["traffic_note"] = "ncu 64^3 x 128 RHS capture, scaled by cell-RHS per launch"
     if roofline:
         roofline["peak_note"] = "of measured (MEASURED_PEAKS.json)" if peaks else "of fallback"
     # independent check of the timed solution: the oracle's FP64 operator (C, CSR K + M,
@@ -849,6 +906,9 @@ def run_ours(args):
         res = b_np - op.apply(x_np)
         oracle_check = {"rel_res_true_oracle": float(np.linalg.norm(res) / np.linalg.norm(b_np)),
                         "rel_res_true_gpu": float(rel_true), "seconds": time.perf_counter() - t0_,
+                        "fp64_form_1e-12_rel_res_true_oracle": (
+                            float(np.linalg.norm(b_np - op.apply(x64_keep.cpu().numpy())) / np.linalg.norm(b_np))
+                            if accuracy else None),
                         "note": "||b - A x||/||b|| of the last timed solution, A applied by the oracle "
                                 "(CSR K + M and FP64 J on the host)"}
     out = {
@@ -871,7 +931,7 @@ def run_ours(args):
                   {"everything": "f64 (plain FP64 form: FP64 cycle and passes, CUDA-core C)"}),
         "pcg_loop": "device-driven (CUDA graph with a conditional while node)" if args.pcg_mode == 0 else "host loop",
         "roofline": roofline, "kernels": table, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
-        "fp64_form": fp64_form, "oracle_check": oracle_check,
+        "fp64_form": fp64_form, "accuracy": accuracy, "oracle_check": oracle_check,
         "impl": "ours",
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.cpu_full_solve:

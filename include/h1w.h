@@ -247,6 +247,21 @@ h1w_status h1w_solve_batch_graph(h1w_ctx* const* ctxs, int32_t count, const int3
                                  const double* const* b, double* const* x, double rtol, int32_t maxit,
                                  h1w_info* info, h1w_status* status);
 
+/* Autotuner of the batched V-cycle: for this grid and m measurements, sets up a context
+ * for each candidate rhs_block (8 .. 256, at most m; every other option from `base`, which
+ * may be NULL for the defaults), times one batch of V-cycles on the device with CUDA
+ * events (line H's cycle, double-float path), and writes `base` with the smallest
+ * rhs_block whose time per right-hand side is within 5 % of the fastest (the cycle's
+ * buffers grow with the block) to *out; *ms_per_rhs (may be NULL) gets its time. The
+ * result is cached in the process per (discretization, grid, m, smoother), so later calls
+ * return at once. The workspace (DEVICE, 256-byte aligned, h1w_autotune_workspace_size
+ * bytes) is scratch for the candidate contexts; stream as in h1w_setup. Paths without a
+ * batched double-float cycle (m = 0, mg_arith = 1, precond = 1) return `base` untimed.
+ * Synchronizes. No counterpart in the paper. */
+size_t h1w_autotune_workspace_size(const h1w_grid* grid, int32_t m, const h1w_options* base);
+h1w_status h1w_autotune(const h1w_grid* grid, int32_t m, const h1w_options* base, void* workspace, size_t ws_bytes,
+                        void* stream, h1w_options* out, float* ms_per_rhs);
+
 /* Phase times and launch counts of the last h1w_capacitance / h1w_pcg. */
 h1w_status h1w_get_timings(const h1w_ctx* ctx, h1w_timings* out);
 

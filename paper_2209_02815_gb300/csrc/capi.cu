@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -1678,6 +1680,120 @@ h1w_status h1w_solve_batch_graph(h1w_ctx* const* ctxs, int32_t count, const int3
   if (first != H1W_OK)
     h1w::set_global_error(first, "h1w_solve_batch_graph: a system failed (see its context's last error)");
   return first;
+}
+
+// ---- autotuner: right-hand sides per batched V-cycle --------------------------------
+
+namespace {
+
+constexpr int kTuneCandidates[] = {8, 16, 32, 64, 128, 256};
+
+struct TuneKey {
+  int disc, n0, n1, n2, m, cheb, unfused;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(disc, n0, n1, n2, m, cheb, unfused) < std::tie(o.disc, o.n0, o.n1, o.n2, o.m, o.cheb, o.unfused);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, float>> g_tune_cache;
+
+// distinct effective block sizes: a context never batches more than m rows
+std::vector<int> tune_candidates(int m) {
+  std::vector<int> out;
+  for (int rb : kTuneCandidates) {
+    const int eff = std::min(rb, std::max(m, 1));
+    if (out.empty() || out.back() != eff) out.push_back(eff);
+  }
+  return out;
+}
+
+}  // namespace
+
+size_t h1w_autotune_workspace_size(const h1w_grid* grid, int32_t m, const h1w_options* base) {
+  h1w_options o;
+  h1w_default_options(&o);
+  if (base) o = *base;
+  size_t need = 0;
+  for (int rb : tune_candidates(m)) {
+    o.rhs_block = rb;
+    const size_t s = h1w_workspace_size(grid, m, &o);
+    if (s == 0) return 0;
+    need = std::max(need, s);
+  }
+  return need;
+}
+
+h1w_status h1w_autotune(const h1w_grid* grid, int32_t m, const h1w_options* base, void* workspace, size_t ws_bytes,
+                        void* stream, h1w_options* out, float* ms_per_rhs) {
+  if (!grid || !out) return h1w::set_global_error(H1W_EINVAL, "h1w_autotune: grid and out must be non-NULL");
+  h1w_options o;
+  h1w_default_options(&o);
+  if (base) o = *base;
+  *out = o;
+  if (ms_per_rhs) *ms_per_rhs = 0.f;
+  if (m <= 0 || o.mg_arith != 0 || o.precond != 0) return H1W_OK;  // nothing to tune on these paths
+  const TuneKey key{grid->disc, grid->n[0], grid->n[1], grid->n[2], m, o.cheb_degree, o.mg_unfused};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      out->rhs_block = it->second.first;
+      if (ms_per_rhs) *ms_per_rhs = it->second.second;
+      return H1W_OK;
+    }
+  }
+  const size_t need = h1w_autotune_workspace_size(grid, m, &o);
+  if (need == 0) return h1w::set_global_error(H1W_EINVAL, "h1w_autotune: invalid grid or options");
+  if (!workspace || ws_bytes < need)
+    return h1w::set_global_error(H1W_ENOMEM, "h1w_autotune: workspace too small: need " + std::to_string(need));
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return h1w::set_global_error(H1W_ECUDA, "h1w_autotune: cannot create events");
+  std::vector<std::pair<int, float>> timed_rb;
+  h1w_status st = H1W_OK;
+  for (int rb : tune_candidates(m)) {
+    h1w_options oc = o;
+    oc.rhs_block = rb;
+    h1w_ctx* c = nullptr;
+    st = h1w_setup(grid, m, &oc, workspace, ws_bytes, stream, &c);
+    if (st != H1W_OK) break;
+    const int nr = std::min(rb, m);
+    // any finite values will do: the cycle's cost does not depend on them
+    launch_fill(reinterpret_cast<double*>(c->Jdf), 1e-3, (int64_t)nr * c->lev[0].N, c->stream);
+    bool ok = vcycle_many(c, nr, nullptr, c->Jdf, nullptr, c->Hdf);  // warm-up (kernel attributes)
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 2 && ok; ++r) ok = vcycle_many(c, nr, nullptr, c->Jdf, nullptr, c->Hdf);
+    cudaEventRecord(e1, c->stream);
+    float ms = 0.f;
+    const bool timed = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    h1w_destroy(c);
+    if (!ok || !timed) {
+      st = h1w::set_global_error(H1W_ECUDA, "h1w_autotune: timing the batched V-cycle failed");
+      break;
+    }
+    timed_rb.push_back({rb, ms / (2.0f * nr)});
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != H1W_OK) return st;
+  // the smallest block within 5 % of the fastest: the V-cycle buffers grow with the block
+  float fastest = timed_rb[0].second;
+  for (const auto& t : timed_rb) fastest = std::min(fastest, t.second);
+  int best = timed_rb.back().first;
+  float best_ms = timed_rb.back().second;
+  for (const auto& t : timed_rb)
+    if (t.second <= 1.05f * fastest) {
+      best = t.first;
+      best_ms = t.second;
+      break;
+    }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = {best, best_ms};
+  }
+  out->rhs_block = best;
+  if (ms_per_rhs) *ms_per_rhs = best_ms;
+  return H1W_OK;
 }
 
 h1w_status h1w_capacitance_factors(h1w_ctx* c, double* C, double* L) {

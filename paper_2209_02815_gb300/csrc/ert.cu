@@ -558,8 +558,10 @@ __global__ void k_measure(const double* __restrict__ U, int64_t N, const int* __
 // GB300 issues at 64 times its FP64 rate; only the scaling by -k_i is FP64.
 // A float as the equal double, by assembling the IEEE 754 bit fields with integer
 // instructions (a conversion instruction runs on the FP64 pipe, which GB300 issues at 1/64
-// of the FP32 rate). Zeros keep their sign; subnormal floats (below 1.2e-38) become zero;
-// infinities and NaNs keep their class.
+// of the FP32 rate). Zeros keep their sign; subnormal floats (below 2^-126, about 1.2e-38)
+// become zero; infinities and NaNs keep their class. In J = -k_i (hi + lo) this drops lo
+// only when |lo| < 2^-126, i.e. |hi| below about 2^-102 (2e-31): such an entry keeps
+// its hi part, and its absolute error stays below |k_i| 2^-126.
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xFFu;

@@ -30,6 +30,7 @@
 // instead of exchanging it. Only b, x and the coarse vectors go through HBM.
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "df64.cuh"
 #include "h1w_internal.cuh"
@@ -77,8 +78,8 @@ constexpr int kP1 = (kA1 + kThr - 1) / kThr;
 constexpr int kTab = 27;
 
 constexpr int kRX = kH1 * kTX;                                  // fine rows of tile + 1 x coarse columns
-constexpr size_t kPreSmem = sizeof(df) * (3 * kA3 + 3 * kA1 + 3 * kA2 + kA1 + 3 * kTab + 1 + kRX + 2 * kTX);
-constexpr size_t kPostSmem = sizeof(df) * (4 * kA2 + 3 * kA2 + kAX + 3 * kA1 + 2 * kA1 + 4 * kTab);
+constexpr size_t kPreSmem = sizeof(df) * (3 * kA3 + 3 * kA1 + 3 * kA2 + kA1 + 3 * kTab + 1 + kRX + 2 * kTX);  // see k_pre_fused
+constexpr size_t kPostSmem = sizeof(df) * (4 * kA2 + 3 * kA2 + kAX + 4 * kA1 + 2 * kA1 + 4 * kTab);  // see k_post_fused
 
 __device__ __forceinline__ bool in_xy(const Level& L, int i, int j) {
   return i >= 0 && i < L.nx && j >= 0 && j < L.ny;
@@ -166,7 +167,8 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L,
   df* xx = x + (int64_t)blockIdx.z * L.N;
   df* cc = bc + (int64_t)blockIdx.z * Lc.N;
   const int u_beg = Z0 - 3, u_end = Z1 + 2;
-#define SLOT(p) (((p) - u_beg) % 3)
+  // ring slots of planes u, u - 1, u - 2 (rotated once per plane instead of a modulo per access)
+  int sl0 = 0, sl1 = 2, sl2 = 1;
 
   // element descriptors, the same on every plane
   int d3[kP3], r3[kP3], d2[kP2], d1[kP1];
@@ -223,8 +225,8 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L,
     const int t = u - u_beg;
     // step 1, plane u: g = D^-1 b over tile + 3; b kept over tile + 1
     {
-      df* Go = Gp + SLOT(u) * kA3;
-      df* Bo = Bp + SLOT(u) * kA1;
+      df* Go = Gp + sl0 * kA3;
+      df* Bo = Bp + sl0 * kA1;
       const bool uin = (u >= 0 && u < L.nz);
       const int cz = 9 * ((u > 0) + (u < L.nz - 1));
 #pragma unroll
@@ -241,10 +243,10 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L,
     // step 2, plane v = u - 1: x = beta g + gam_c N_T(g) over tile + 2
     if (t >= 2) {
       const int v = u - 1;
-      const df* G0 = Gp + SLOT(v - 1) * kA3;
-      const df* G1 = Gp + SLOT(v) * kA3;
-      const df* G2 = Gp + SLOT(v + 1) * kA3;
-      df* Xo = Xp + SLOT(v) * kA2;
+      const df* G0 = Gp + sl2 * kA3;
+      const df* G1 = Gp + sl1 * kA3;
+      const df* G2 = Gp + sl0 * kA3;
+      df* Xo = Xp + sl1 * kA2;
       const bool vin = (v >= 0 && v < L.nz);
       const bool vout = (v >= Z0 && v < Z1);
       const int cz = 9 * ((v > 0) + (v < L.nz - 1));
@@ -269,10 +271,10 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L,
     // step 3, plane w = u - 2: residual b + N_T(x) - d_c x over tile + 1, then P^T
     if (t >= 4) {
       const int w = u - 2;
-      const df* X0 = Xp + SLOT(w - 1) * kA2;
-      const df* X1 = Xp + SLOT(w) * kA2;
-      const df* X2 = Xp + SLOT(w + 1) * kA2;
-      const df* B1 = Bp + SLOT(w) * kA1;
+      const df* X0 = Xp + sl0 * kA2;  // plane w - 1 = u - 3 shares the slot of u
+      const df* X1 = Xp + sl2 * kA2;
+      const df* X2 = Xp + sl1 * kA2;
+      const df* B1 = Bp + sl2 * kA1;
       const bool win = (w >= 0 && w < L.nz);
       const int cz = 9 * ((w > 0) + (w < L.nz - 1));
 #pragma unroll
@@ -341,23 +343,31 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_PRE_MINB) k_pre_fused(Level L,
         }
       }
     }
+    const int s_old = sl2;  // the slot of u - 2 takes plane u + 1
+    sl2 = sl1;
+    sl1 = sl0;
+    sl0 = s_old;
   }
-#undef SLOT
 }
 
 // Up leg. Grid: (xy tiles, z segments of segZ fine planes (even), right-hand sides).
-// y and y64 (either may be null) must not overlap x, xc or b.
+// y and y64 (either may be null) must not overlap x, xc or b. The march over the planes
+// is unrolled by four (the x' and d0 rings hold four planes, r0 two), so those ring slots
+// are compile-time constants; the coarse ring (three interpolated coarse planes) is
+// indexed at run time.
 template <bool ISO, typename TB>
 __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level L, Level Lc, FusedCoef F, const df* __restrict__ x,
                                                      const df* __restrict__ xc, const TB* __restrict__ b,
                                                      df* __restrict__ y, double* __restrict__ y64, int segZ) {
   extern __shared__ df sm[];
-  df* Xp = sm;               // x' over tile + 2, 4 planes
-  df* Pp = Xp + 4 * kA2;     // coarse planes interpolated along x and y, over tile + 2, 3 planes
-  df* Px = Pp + 3 * kA2;     // one coarse plane interpolated along x: kHC coarse rows x kW2 fine columns
-  df* Dp = Px + kAX;         // d0 over tile + 1, 3 planes
-  df* Rp = Dp + 3 * kA1;     // r0 over tile + 1, 2 planes
-  df* td = Rp + 2 * kA1;     // d, del, eta, kap by class
+  // layout (in df): x' over tile + 2, 4 planes; coarse planes interpolated along x and y over
+  // tile + 2, 3 planes; one coarse plane interpolated along x (kHC coarse rows x kW2 fine
+  // columns); d0 over tile + 1, 4 planes; r0 over tile + 1, 2 planes; d, del, eta, kap by class
+  constexpr int oX = 0, oP = oX + 4 * kA2, oPx = oP + 3 * kA2, oD = oPx + kAX, oR = oD + 4 * kA1;
+  constexpr int oTd = oR + 2 * kA1;
+  df* Pp = sm + oP;
+  df* Px = sm + oPx;
+  df* td = sm + oTd;
   df* tdel = td + kTab;
   df* teta = tdel + kTab;
   df* tkap = teta + kTab;
@@ -378,10 +388,8 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
   const df* xx = x + off;
   const TB* bb = b + off;
   const df* cx = xc + (int64_t)blockIdx.z * Lc.N;
-  const int u_beg = Z0 - 2, u_end = Z1 + 1;
+  const int u_beg = Z0 - 2, u_end = Z1 + 1;  // u_beg is even (segZ is even)
   const int Kb = (u_beg >> 1) - 1;  // first coarse plane the block reads
-#define SLOT3(p) (((p) - u_beg) % 3)
-#define SLOT4(p) (((p) - u_beg) & 3)
 #define CSLOT(K) (((K) - Kb) % 3)
 
   constexpr int kPI = kFX * kFY / kThr;  // tile cells per thread in step 3
@@ -413,24 +421,44 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
   // coarse cell and 1/4 on the next one towards the fine cell; clamping that neighbour
   // to the grid gives the boundary rule (all weight on the parent) without a branch.
   // Entries for fine cells outside the domain are computed from clamped indices too and
-  // never used: step 1 zeroes them.
+  // never used: step 1 zeroes them. The source offsets are the same on every plane.
+  constexpr int kRXp = (kAX + kThr - 1) / kThr;
+  int ix0[kRXp], ix1[kRXp], iy0[kP2], iy1[kP2];
+#pragma unroll
+  for (int r = 0; r < kRXp; ++r) {
+    const int e = tid + r * kThr;
+    const int jl = e / kW2, fl = e - jl * kW2;
+    const int gJ = min(max(C0y - 2 + jl, 0), Lc.ny - 1), gx = F0x - 2 + fl;
+    const int I0 = gx >> 1, I1 = (gx & 1) ? I0 + 1 : I0 - 1;
+    ix0[r] = gJ * Lc.nx + min(max(I0, 0), Lc.nx - 1);
+    ix1[r] = gJ * Lc.nx + min(max(I1, 0), Lc.nx - 1);
+  }
+#pragma unroll
+  for (int q = 0; q < kP2; ++q) {
+    const int e = tid + q * kThr;
+    const int ey = e / kW2, lx = e - ey * kW2;
+    const int gy = F0y - 2 + ey;
+    const int J0 = gy >> 1, J1 = (gy & 1) ? J0 + 1 : J0 - 1;
+    iy0[q] = (min(max(J0, 0), Lc.ny - 1) - (C0y - 2)) * kW2 + lx;
+    iy1[q] = (min(max(J1, 0), Lc.ny - 1) - (C0y - 2)) * kW2 + lx;
+  }
   auto interp_x = [&](int K) {
     const bool kin = (K >= 0 && K < Lc.nz);
-    for (int e = tid; e < kAX; e += kThr) {
-      const int jl = e / kW2, fl = e - jl * kW2;
-      const int gJ = min(max(C0y - 2 + jl, 0), Lc.ny - 1), gx = F0x - 2 + fl;
-      const int I0 = gx >> 1, I1 = (gx & 1) ? I0 + 1 : I0 - 1;
-      const int c0 = min(max(I0, 0), Lc.nx - 1), c1 = min(max(I1, 0), Lc.nx - 1);
-      df v = dzero();
-      if (kin) {
-        const df* row = cx + K * plc + (int64_t)gJ * Lc.nx;
-        const df a = row[c0], b1 = row[c1];
-        dsum s;
-        s.add(df_mul_f(a, 0.75f));
-        s.add(df_make(b1.hi * 0.25f, b1.lo * 0.25f));
-        v = s.get();
+    const df* plane_c = cx + (kin ? K : 0) * plc;
+#pragma unroll
+    for (int r = 0; r < kRXp; ++r) {
+      const int e = tid + r * kThr;
+      if ((r + 1) * kThr <= kAX || e < kAX) {
+        df v = dzero();
+        if (kin) {
+          const df a = plane_c[ix0[r]], b1 = plane_c[ix1[r]];
+          dsum s;
+          s.add(df_mul_f(a, 0.75f));
+          s.add(df_make(b1.hi * 0.25f, b1.lo * 0.25f));
+          v = s.get();
+        }
+        Px[e] = v;
       }
-      Px[e] = v;
     }
   };
   auto interp_y = [&](int K) {
@@ -438,12 +466,8 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
 #pragma unroll
     for (int q = 0; q < kP2; ++q) {
       const int e = tid + q * kThr;
-      if (e < kA2) {
-        const int ey = e / kW2, lx = e - ey * kW2;
-        const int gy = F0y - 2 + ey;
-        const int J0 = gy >> 1, J1 = (gy & 1) ? J0 + 1 : J0 - 1;
-        const int r0 = min(max(J0, 0), Lc.ny - 1) - (C0y - 2), r1 = min(max(J1, 0), Lc.ny - 1) - (C0y - 2);
-        const df a = Px[r0 * kW2 + lx], b1 = Px[r1 * kW2 + lx];
+      if ((q + 1) * kThr <= kA2 || e < kA2) {
+        const df a = Px[iy0[q]], b1 = Px[iy1[q]];
         dsum s;
         s.add(df_mul_f(a, 0.75f));
         s.add(df_make(b1.hi * 0.25f, b1.lo * 0.25f));
@@ -474,11 +498,14 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
   fetch_x(u_beg);
   fetch_b(u_beg + 1);  // the first plane step 2 works on
 
-  for (int u = u_beg; u <= u_end; ++u) {
-    const int t = u - u_beg;
+  // one plane of the march: u = u_beg + t with t = 4 j + k; the x' and d0 slot of plane
+  // u - i is (k - i) mod 4, the r0 slot (k - i) mod 2
+  auto plane = [&](auto kc, int t) {
+    constexpr int k = decltype(kc)::value;
+    constexpr int x0 = k, x1 = (k + 3) & 3, x2 = (k + 2) & 3, x3 = (k + 1) & 3;  // u, u-1, u-2, u-3
+    const int u = u_beg + t;
     // step 1, plane u: x' = x + P xc over tile + 2
     {
-      df* Xo = Xp + SLOT4(u) * kA2;
       const bool uin = (u >= 0 && u < L.nz);
       int fz[2] = {Kb, Kb};
       float wz[2] = {0.f, 0.f};
@@ -488,7 +515,7 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
 #pragma unroll
       for (int q = 0; q < kP2; ++q) {
         const int e = tid + q * kThr;
-        if (e < kA2) {
+        if ((q + 1) * kThr <= kA2 || e < kA2) {
           df v = dzero();
           if (uin && d2[q] >= 0) {
             dsum s;
@@ -497,12 +524,12 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
             if (nz_ > 1) s.add(scale_w(P1[e], wz[1]));
             v = s.get();
           }
-          Xo[e] = v;
+          sm[oX + x0 * kA2 + e] = v;
         }
       }
       if (u < u_end) fetch_x(u + 1);
       // at u = 2K - 1 the planes K - 1 and K are in use; interpolate K + 1 for u = 2K + 1
-      if ((u & 1) && u < u_end) {
+      if ((k & 1) && u < u_end) {
         interp_x(((u + 1) >> 1) + 1);
         __syncthreads();
         interp_y(((u + 1) >> 1) + 1);
@@ -512,17 +539,15 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
     // step 2, plane v = u - 1: r0 = b + N_T(x') - d_c x', d0 = del_c r0 over tile + 1
     if (t >= 2) {
       const int v = u - 1;
-      const df* X0 = Xp + SLOT4(v - 1) * kA2;
-      const df* X1 = Xp + SLOT4(v) * kA2;
-      const df* X2 = Xp + SLOT4(v + 1) * kA2;
-      df* Ro = Rp + ((v - u_beg) & 1) * kA1;
-      df* Do = Dp + SLOT3(v) * kA1;
+      const df* X0 = sm + oX + x2 * kA2;
+      const df* X1 = sm + oX + x1 * kA2;
+      const df* X2 = sm + oX + x0 * kA2;
       const bool vin = (v >= 0 && v < L.nz);
       const int cz = 9 * ((v > 0) + (v < L.nz - 1));
 #pragma unroll
       for (int q = 0; q < kP1; ++q) {
         const int e = tid + q * kThr;
-        if (e < kA1) {
+        if ((q + 1) * kThr <= kA1 || e < kA1) {
           df rv = dzero(), dv = dzero();
           if (vin && d1[q] >= 0) {
             const int c = desc_cls(d1[q]) + cz;
@@ -534,8 +559,8 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
             rv = s.get();
             dv = df_mul(tdel[c], rv);
           }
-          Ro[e] = rv;
-          Do[e] = dv;
+          sm[oR + ((k + 1) & 1) * kA1 + e] = rv;
+          sm[oD + x1 * kA1 + e] = dv;
         }
       }
       if (v < Z1) fetch_b(v + 1);
@@ -544,11 +569,11 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
     // step 3, plane w = u - 2 (in [Z0, Z1)): y = x' + eta_c r0 + kap_c N_T(d0) on the tile
     if (t >= 4) {
       const int w = u - 2;
-      const df* D0 = Dp + SLOT3(w - 1) * kA1;
-      const df* D1 = Dp + SLOT3(w) * kA1;
-      const df* D2 = Dp + SLOT3(w + 1) * kA1;
-      const df* R1 = Rp + ((w - u_beg) & 1) * kA1;
-      const df* X1 = Xp + SLOT4(w) * kA2;
+      const df* D0 = sm + oD + x3 * kA1;
+      const df* D1 = sm + oD + x2 * kA1;
+      const df* D2 = sm + oD + x1 * kA1;
+      const df* R1 = sm + oR + (k & 1) * kA1;
+      const df* X1 = sm + oX + x2 * kA2;
       const int cz = 9 * ((w > 0) + (w < L.nz - 1));
 #pragma unroll
       for (int q = 0; q < kPI; ++q) {
@@ -566,9 +591,17 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
         }
       }
     }
+  };
+  const int T = u_end - u_beg;
+  for (int t = 0; t <= T; t += 4) {
+    plane(std::integral_constant<int, 0>{}, t);
+    if (t + 1 > T) break;
+    plane(std::integral_constant<int, 1>{}, t + 1);
+    if (t + 2 > T) break;
+    plane(std::integral_constant<int, 2>{}, t + 2);
+    if (t + 3 > T) break;
+    plane(std::integral_constant<int, 3>{}, t + 3);
   }
-#undef SLOT3
-#undef SLOT4
 #undef CSLOT
 }
 

@@ -108,6 +108,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                   ctypes.POINTER(P), ctypes.POINTER(P), D, I32, I32, IN, ctypes.POINTER(I32)]),
         "h1w_solve_batch_graph": (I32, [ctypes.POINTER(P), I32, ctypes.POINTER(I32), ctypes.POINTER(P),
                                         ctypes.POINTER(P), ctypes.POINTER(P), D, I32, IN, ctypes.POINTER(I32)]),
+        "h1w_autotune_workspace_size": (SZ, [G, I32, O]),
+        "h1w_autotune": (I32, [G, I32, O, P, SZ, P, O, ctypes.POINTER(ctypes.c_float)]),
         "h1w_ert_workspace_size": (SZ, [P, I32, I32]),
         "h1w_forward": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, SZ, D, I32, ctypes.c_uint32, IN]),
         "h1w_adjoint": (I32, [P, ctypes.POINTER(SurveyC), P, P, P, P, P, P, SZ]),
@@ -209,6 +211,23 @@ def h1w_capacitance_from_host(ctx, m: int, J_host: torch.Tensor, J_dev: torch.Te
                                             _ptr(J_dev, m * N, "J_dev") if m > 0 else None), ctx)
 
 
+def h1w_autotune(grid: Grid, m: int, base: Options | None = None, device="cuda",
+                 stream: torch.cuda.Stream | None = None):
+    """Options with the fastest rhs_block for this grid and m (h1w_autotune; cached per
+    process) and the V-cycle time per right-hand side in ms."""
+    size = int(load().h1w_autotune_workspace_size(ctypes.byref(grid), int(m),
+                                                  ctypes.byref(base) if base is not None else None))
+    if size == 0:
+        raise H1wError(H1W_EINVAL, "invalid grid/options for h1w_autotune")
+    ws = torch.empty(size, dtype=torch.uint8, device=device)
+    s = (stream or torch.cuda.current_stream(ws.device)).cuda_stream
+    out = Options()
+    ms = ctypes.c_float()
+    _check(load().h1w_autotune(ctypes.byref(grid), int(m), ctypes.byref(base) if base is not None else None,
+                               ws.data_ptr(), ws.numel(), s, ctypes.byref(out), ctypes.byref(ms)), None)
+    return out, float(ms.value)
+
+
 def solve_batch(solvers, Js, bs, xs, rtol: float, maxit: int = 500, threads: int = 8, graph: bool = False):
     """Capacitance + PCG for several Solver objects at once: h1w_solve_batch (a pool of host
     threads) or, with graph=True, h1w_solve_batch_graph (all systems in one CUDA graph).
@@ -287,10 +306,16 @@ def h1w_get_timings(ctx) -> Timings:
 
 def h1w_apply_op_static(grid: Grid, m: int, J: torch.Tensor | None, p: torch.Tensor, q: torch.Tensor,
                         N: int, stream: torch.cuda.Stream | None = None) -> None:
-    """Workspace-free operator apply (scratch in a fixed device array)."""
-    s = (stream or torch.cuda.current_stream(p.device)).cuda_stream
-    _check(load().h1w_apply_op_static(ctypes.byref(grid), int(m), _ptr(J, m * N, "J") if m > 0 else None,
-                                      _ptr(p, N, "p"), _ptr(q, N, "q"), s), None)
+    """Workspace-free operator apply (scratch in a fixed device array). The library takes the
+    scratch address and launches on the current device, so the call runs with p's device
+    current; J, p and q must all be on it."""
+    for t, nm in ((J, "J"), (q, "q")):
+        if t is not None and t.device != p.device:
+            raise ValueError(f"{nm} is on {t.device}, p on {p.device}")
+    with torch.cuda.device(p.device):
+        s = (stream or torch.cuda.current_stream(p.device)).cuda_stream
+        _check(load().h1w_apply_op_static(ctypes.byref(grid), int(m), _ptr(J, m * N, "J") if m > 0 else None,
+                                          _ptr(p, N, "p"), _ptr(q, N, "q"), s), None)
 
 
 class Survey:

@@ -123,3 +123,30 @@ def test_batch_shaped_instances_against_oracle(side, m, alpha):
     xf = xf.cpu().numpy()
     assert np.linalg.norm(xn - xf) <= 1e-7 * np.linalg.norm(xf)
     assert np.abs(xn - xf).max() <= 1e-7 * np.abs(xf).max()
+
+
+def test_autotune_picks_a_block_and_caches_it():
+    """h1w_autotune times line H's batched cycle for each candidate rhs_block and returns
+    one of them; the second call comes from the cache; the tuned context solves to the
+    same bits as the default one (each right-hand side's cycle does not depend on the batch)."""
+    import time
+    n, m, alpha = (96, 80), 40, 1e-2
+    h = tuple(1.0 / (v - 1) for v in n)
+    g = h1w.make_grid(h1w.H1W_Q1_VERTEX, n, h, alpha)
+    opt, ms = h1w.h1w_autotune(g, m, device=DEV)
+    assert opt.rhs_block in (8, 16, 32, 40) and ms > 0.0
+    t0 = time.perf_counter()
+    opt2, ms2 = h1w.h1w_autotune(g, m, device=DEV)
+    assert time.perf_counter() - t0 < 0.5
+    assert opt2.rhs_block == opt.rhs_block and ms2 == ms
+    N = n[0] * n[1]
+    rng = np.random.default_rng(74)
+    J = torch.as_tensor(rng.standard_normal((m, N)) / np.sqrt(N), device=DEV)
+    b = torch.as_tensor(rng.standard_normal(N), device=DEV)
+    T = h1w.Solver(h1w.H1W_Q1_VERTEX, n, h, alpha, m, device=DEV, opt=opt)
+    D = _solver("q1", n, alpha, m)
+    T.capacitance(J)
+    D.capacitance(J)
+    xt, _ = T.pcg(b, 1e-10)
+    xd, _ = D.pcg(b, 1e-10)
+    assert torch.equal(xt, xd)

@@ -504,10 +504,14 @@ def test_dipole_grid_solution_error_vs_oracle(cap_gemm, mg_arith):
     S.capacitance(_t(pr.J))
     x, info = S.pcg(_t(b_ref), 1e-12, 400)
     assert info.rel_res_true <= 1e-12
-    err = _rel(x.cpu().numpy(), x_ref)
+    xn = x.cpu().numpy()
+    err = _rel(xn, x_ref)
+    err_max = float(np.abs(xn - x_ref).max() / np.abs(x_ref).max())
     print(f"dipole grid 32^3 m=60 ({'mixed' if cap_gemm == 0 else 'fp64'}): iters {info.iters}, "
-          f"restarts {info.restarts}, rel error vs oracle {err:.2e}")
+          f"restarts {info.restarts}, rel error vs oracle {err:.2e}, max entry error {err_max:.2e}")
     assert err <= 1e-7
+    # entry by entry too: a localised error (e.g. at a tile edge) could hide under the norm
+    assert err_max <= 1e-7
 
 
 def test_ert_64cube_m496_converges_like_fp64_form():

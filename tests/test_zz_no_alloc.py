@@ -24,25 +24,35 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("disc,n,h", [
-    (h1w.H1W_FV_CELL, (40, 24, 20), (1 / 40, 1 / 24, 1 / 20)),
-    (h1w.H1W_Q1_VERTEX, (130, 67), (1 / 129, 1 / 66)),
+@pytest.mark.parametrize("disc,n,h,m", [
+    (h1w.H1W_FV_CELL, (40, 24, 20), (1 / 40, 1 / 24, 1 / 20), 37),
+    (h1w.H1W_FV_CELL, (32, 32, 32), (1 / 32,) * 3, 37),      # isotropic: the equal-T stencil branch
+    (h1w.H1W_FV_CELL, (24, 16, 20), (1 / 24, 1 / 16, 1 / 20), 0),
+    (h1w.H1W_Q1_VERTEX, (130, 67), (1 / 129, 1 / 66), 37),
+    (h1w.H1W_Q1_VERTEX, (64, 64), (1 / 63,) * 2, 0),
 ])
-def test_static_apply_matches_workspace_apply_twice(disc, n, h):
-    alpha, m = 3e-3, 37
-    S = h1w.Solver(disc, n, h, alpha, m, device=DEV)
+def test_static_apply_matches_workspace_apply_twice(disc, n, h, m):
+    alpha = 3e-3
+    S = h1w.Solver(disc, n, h, alpha, max(m, 1), device=DEV)
     g = torch.Generator(device=DEV).manual_seed(7)
-    J = torch.randn(m, S.N, dtype=torch.float64, device=DEV, generator=g) / S.N ** 0.5
+    J = torch.randn(m, S.N, dtype=torch.float64, device=DEV, generator=g) / S.N ** 0.5 if m else None
     S.capacitance(J)
     grid = h1w.make_grid(disc, n, h, alpha)
+    ps = [torch.randn(S.N, dtype=torch.float64, device=DEV, generator=g) for _ in range(2)]
+    qs = [torch.full_like(ps[0], float("nan")) for _ in range(2)]
+    refs = [S.apply_op(p) for p in ps]
+    torch.cuda.synchronize()
     for call in range(2):
-        p = torch.randn(S.N, dtype=torch.float64, device=DEV, generator=g)
-        q_ref = S.apply_op(p)
-        q = torch.full_like(p, float("nan"))
-        h1w.h1w_apply_op_static(grid, m, J, p, q, S.N)
+        if call == 1:  # the entry point allocates nothing: device memory is the same after the call
+            free0 = torch.cuda.mem_get_info()[0]
+            alloc0 = torch.cuda.memory_allocated()
+        h1w.h1w_apply_op_static(grid, m, J, ps[call], qs[call], S.N)
         torch.cuda.synchronize()
-        assert torch.isfinite(q).all(), f"call {call}"
-        assert _rel(q, q_ref) <= RTOL, f"call {call}"
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_allocated() == alloc0
+        assert torch.isfinite(qs[call]).all(), f"call {call}"
+        assert _rel(qs[call], refs[call]) <= RTOL, f"call {call}"
 
 
 def test_static_apply_rejects_sizes_beyond_scratch():
