@@ -252,9 +252,11 @@ def oracle_sample(J_host, logsigma, m_ref, d, n, budget_s: float, iters_fallback
     t0 = time.perf_counter()
     s = J_host @ v
     t_jpass = time.perf_counter() - t0                 # one pass over an m x N matrix
-    k = min(m, 64)
+    # GEMM sample k x N x k (line C is m x N x m); a 256-row block runs at close to the
+    # full product's BLAS efficiency (a 64-row one ran 11x slower per flop on the box)
+    k = min(m, 256)
     t0 = time.perf_counter()
-    _ = J_host[:k] @ J_host[:k].T                       # GEMM sample: k x N x k
+    _ = J_host[:k] @ J_host[:k].T
     t_g = time.perf_counter() - t0
     t_gemm = t_g * (m / k) ** 2
     path = os.path.join(ROOT, "oracle", "reference_run.json")
@@ -951,8 +953,8 @@ def run_ours(args):
                                "unit": "solves/s", "cores": s["threads"], "kind": "oracle",
                                "sample": ("oracle phases timed on bounded samples and extrapolated: "
                                           f"{s['vcycles_timed']} scipy V-cycles (x m), "
-                                          f"{s['applies_timed']} operator applies, one 64-row GEMM "
-                                          "(scaled by (m/64)^2), iterations from the oracle's full "
+                                          f"{s['applies_timed']} operator applies, one 256-row GEMM "
+                                          "(scaled by (m/256)^2), iterations from the oracle's full "
                                           "solve of this workload"), "detail": s}
     if rank == 0:
         print(json.dumps(out))
@@ -998,7 +1000,7 @@ def run_reference(args):
            "impl": "reference",
            "cpu_baseline": {"value": value, "unit": "solves/s", "kind": "oracle", "cores": last["threads"],
                             "sample": "EXTRAPOLATED: each step times the oracle's phases on bounded "
-                                      "samples (scipy V-cycles, C operator applies, a 64-row GEMM) and "
+                                      "samples (scipy V-cycles, C operator applies, a 256-row GEMM) and "
                                       "extrapolates them to one full solve with the oracle's own "
                                       "iteration count; ms_per_step is the sample's wall time",
                             "detail": last},

@@ -10,6 +10,8 @@
 // kernels (mg_kernels.cu) and the oracle apply: 7-point FV operator, degree-k
 // Chebyshev-Jacobi smoothing, cell-centred trilinear transfer with R = P^T,
 // dense coarsest solve (kept in FP64).
+#include <cstdint>
+
 #include "df64.cuh"
 #include "h1w_internal.cuh"
 #include "mg_df64_util.cuh"
@@ -183,7 +185,20 @@ __global__ void k_coarse_apply_df(const double* __restrict__ X, int n, const df*
   if (lane == 0) x[(int64_t)blockIdx.y * n + row] = df_from_double(s);
 }
 
+// two entries per thread with 16-byte loads and stores (both arrays 16-byte aligned: the
+// callers pass workspace slices and row batches of even length); an odd tail is done singly
 __global__ void k_d2df(int64_t n, const double* __restrict__ src, df* __restrict__ dst) {
+  const int64_t p = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (p + 1 < n) {
+    const double2 v = *reinterpret_cast<const double2*>(src + p);
+    const df a = df_from_double_fast(v.x), b = df_from_double_fast(v.y);
+    *reinterpret_cast<float4*>(dst + p) = make_float4(a.hi, a.lo, b.hi, b.lo);
+  } else if (p < n) {
+    dst[p] = df_from_double_fast(src[p]);
+  }
+}
+
+__global__ void k_d2df_1(int64_t n, const double* __restrict__ src, df* __restrict__ dst) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p < n) dst[p] = df_from_double_fast(src[p]);
 }
@@ -254,7 +269,13 @@ void launch_coarse_apply_df(const double* X, int n, int nrhs, const df* b, df* x
 }
 
 void launch_d2df(int64_t n, const double* src, df* dst, cudaStream_t s) {
-  k_d2df<<<nblk(n), kThreads, 0, s>>>(n, src, dst);
+  // the paired loads need 16-byte alignment; otherwise fall back to the single-entry form
+  if ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) {
+    k_d2df_1<<<nblk(n), kThreads, 0, s>>>(n, src, dst);
+    note_launches(1);
+    return;
+  }
+  k_d2df<<<nblk((n + 1) / 2), kThreads, 0, s>>>(n, src, dst);
   note_launches(1);
 }
 

@@ -442,24 +442,40 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
     iy0[q] = (min(max(J0, 0), Lc.ny - 1) - (C0y - 2)) * kW2 + lx;
     iy1[q] = (min(max(J1, 0), Lc.ny - 1) - (C0y - 2)) * kW2 + lx;
   }
-  auto interp_x = [&](int K) {
-    const bool kin = (K >= 0 && K < Lc.nz);
-    const df* plane_c = cx + (kin ? K : 0) * plc;
+  // the coarse values of the next plane to interpolate are loaded a plane ahead into
+  // registers (ca, cb), so that their L2 latency hides behind a plane of smoothing
+  df ca[kRXp], cb[kRXp];
+  bool ck = false;  // the loaded plane is inside the coarse grid
+  auto interp_x_load = [&](int K) {
+    ck = (K >= 0 && K < Lc.nz);
+    const df* plane_c = cx + (ck ? K : 0) * plc;
+#pragma unroll
+    for (int r = 0; r < kRXp; ++r) {
+      const int e = tid + r * kThr;
+      const bool in = ck && ((r + 1) * kThr <= kAX || e < kAX);
+      ca[r] = in ? plane_c[ix0[r]] : dzero();
+      cb[r] = in ? plane_c[ix1[r]] : dzero();
+    }
+  };
+  auto interp_x_store = [&]() {
 #pragma unroll
     for (int r = 0; r < kRXp; ++r) {
       const int e = tid + r * kThr;
       if ((r + 1) * kThr <= kAX || e < kAX) {
         df v = dzero();
-        if (kin) {
-          const df a = plane_c[ix0[r]], b1 = plane_c[ix1[r]];
+        if (ck) {
           dsum s;
-          s.add(df_mul_f(a, 0.75f));
-          s.add(df_make(b1.hi * 0.25f, b1.lo * 0.25f));
+          s.add(df_mul_f(ca[r], 0.75f));
+          s.add(df_make(cb[r].hi * 0.25f, cb[r].lo * 0.25f));
           v = s.get();
         }
         Px[e] = v;
       }
     }
+  };
+  auto interp_x = [&](int K) {
+    interp_x_load(K);
+    interp_x_store();
   };
   auto interp_y = [&](int K) {
     df* dst = Pp + CSLOT(K) * kA2;
@@ -529,11 +545,13 @@ __global__ void __launch_bounds__(kThr, H1W_FUSED_POST_MINB) k_post_fused(Level 
       }
       if (u < u_end) fetch_x(u + 1);
       // at u = 2K - 1 the planes K - 1 and K are in use; interpolate K + 1 for u = 2K + 1
+      // (its coarse values were loaded at plane u - 1)
       if ((k & 1) && u < u_end) {
-        interp_x(((u + 1) >> 1) + 1);
+        interp_x_store();
         __syncthreads();
         interp_y(((u + 1) >> 1) + 1);
       }
+      if (!(k & 1) && u + 1 < u_end) interp_x_load(((u + 2) >> 1) + 1);
     }
     __syncthreads();
     // step 2, plane v = u - 1: r0 = b + N_T(x') - d_c x', d0 = del_c r0 over tile + 1
