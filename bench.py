@@ -335,6 +335,9 @@ def run_batch(args):
            "pcg_iters": [int(i.iters) for i in infos], "max_rel_res_true": max(float(i.rel_res_true) for i in infos),
            "clocks": clocks, "timing": "host wall clock around whole batches (each call synchronizes)",
            "gpu_launches": launches, "autotune": tuned or None,
+           "phases_ms_sum_over_systems": ({k_: round(sum(float(getattr(S_.timings(), k_)) for S_ in solvers), 2)
+                                           for k_ in ("t_H_ms", "t_C_ms", "t_chol_ms", "t_pcg_ms")}
+                                          if not graph else None),
            "setup_and_autotune_s": t_tune, "impl": "ours"}
     if rank == 0:
         print(json.dumps(out))

@@ -245,6 +245,30 @@ void q1_coarse_1d(const std::vector<double>& q, int nf, int nc, std::vector<doub
   }
 }
 
+// The longest index range around the middle of a 1D Q1 factor set q = [Kd, Ko, Md, Mo, Dd, Do]
+// (n entries each) on which every vertex's entries (diagonal, and the couplings to both
+// neighbours) equal the middle vertex's bit for bit; the end vertices are never included
+// (they lack a neighbour). Empty (lo > hi) when n < 3.
+void q1_uniform_range(const std::vector<double>& q, int n, int& lo, int& hi) {
+  lo = 1;
+  hi = 0;
+  if (n < 3) return;
+  auto same = [&](int i, int r) {
+    for (int t = 0; t < 3; ++t) {
+      const double* d = q.data() + (2 * t) * n;
+      const double* o = q.data() + (2 * t + 1) * n;
+      if (std::memcmp(&d[i], &d[r], sizeof(double)) || std::memcmp(&o[i], &o[r], sizeof(double)) ||
+          std::memcmp(&o[i - 1], &o[r - 1], sizeof(double)))
+        return false;
+    }
+    return true;
+  };
+  const int r = n / 2;
+  lo = hi = r;
+  while (lo - 1 >= 1 && same(lo - 1, r)) --lo;
+  while (hi + 1 <= n - 2 && same(hi + 1, r)) ++hi;
+}
+
 struct Plan {
   int nlev = 0;
   int n[kMaxLevels][3];
@@ -1011,6 +1035,18 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
         stoff += 10 * L.N;
         launch_q1_stencil_df(L, st, c->stream);
         L.q1st = st;
+        // the vertices whose 1D factor entries equal those of the middle vertex have the
+        // middle vertex's stencil: the kernels take it from the Level instead of the table
+        int lo[2], hi[2];
+        for (int a = 0; a < 2; ++a) q1_uniform_range(c->qhost[l][a], a == 0 ? L.nx : L.ny, lo[a], hi[a]);
+        L.q1_ilo = lo[0]; L.q1_ihi = hi[0]; L.q1_jlo = lo[1]; L.q1_jhi = hi[1];
+        for (int k = 0; k < 10; ++k) L.q1c[k] = df_make(0.f, 0.f);
+        if (lo[0] <= hi[0] && lo[1] <= hi[1]) {
+          const int64_t pm = (int64_t)((lo[1] + hi[1]) / 2) * L.nx + (lo[0] + hi[0]) / 2;
+          for (int k = 0; k < 10; ++k)
+            cudaMemcpyAsync(&L.q1c[k], st + (int64_t)k * L.N + pm, sizeof(df), cudaMemcpyDeviceToHost, c->stream);
+          if (cudaStreamSynchronize(c->stream) != cudaSuccess) { L.q1_ilo = 1; L.q1_ihi = 0; }
+        }
       }
     }
   }

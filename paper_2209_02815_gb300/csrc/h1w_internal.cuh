@@ -30,6 +30,10 @@ struct Level {
   const double* qx;              // Q1 x-axis coefficients [6][nx] (device)
   const double* qy;              // Q1 y-axis coefficients [6][ny] (device)
   const df* q1st;                // Q1 double-float cycle: per-vertex stencil [9][N] and 1/diag [N] (device)
+  // Q1: the box of vertices [q1_ilo, q1_ihi] x [q1_jlo, q1_jhi] whose stencil and 1/diag equal
+  // q1c (the table's entries there, read back at setup); empty when ilo > ihi
+  int q1_ilo, q1_ihi, q1_jlo, q1_jhi;
+  df q1c[10];
   double lam;                    // upper bound of spec(D^-1 A) (Gershgorin)
   int cx, cy, cz;                // axis coarsened towards the next level
   int iso;                       // FV with Tx == Ty == Tz

@@ -48,64 +48,127 @@ __global__ void k_q1_stencil_df(Level L, df* __restrict__ st) {
   st[9 * L.N + p] = df_from_double(1.0 / c00);
 }
 
-// (A u)_p; coefficients of neighbours outside the grid are zero and skipped
-__device__ __forceinline__ df q1_apply_df(const Level& L, const df* __restrict__ u, int i, int j, int64_t p) {
+// Launch geometry of the vertex kernels: 64 x 4 vertices per block (no index division),
+// grid z over the right-hand sides, kRpt of them per thread (the stencil coefficients of a
+// vertex are loaded once and applied to each).
+constexpr int kBX = 64, kBY = 4;
+constexpr int kRpt = 2;
+
+// (A u)_p for kRpt right-hand sides u[k] (offsets off[k] from u); coefficients of neighbours
+// outside the grid are zero and skipped; nk right-hand sides are present (1 or kRpt)
+// vertex (i, j) lies in the box whose stencil is the constant L.q1c
+__device__ __forceinline__ bool q1_uniform(const Level& L, int i, int j) {
+  return i >= L.q1_ilo && i <= L.q1_ihi && j >= L.q1_jlo && j <= L.q1_jhi;
+}
+
+__device__ __forceinline__ void q1_apply_df(const Level& L, const df* __restrict__ u, const int64_t* off, int nk,
+                                            int i, int j, int64_t p, df* out) {
   const df* st = L.q1st;
-  dsum s;
+  dsum s[kRpt];
+  if (q1_uniform(L, i, j)) {  // every neighbour exists; the coefficients are the box's (same values)
 #pragma unroll
-  for (int b = -1; b <= 1; ++b) {
-    if (j + b < 0 || j + b >= L.ny) continue;
+    for (int b = -1; b <= 1; ++b)
 #pragma unroll
-    for (int a = -1; a <= 1; ++a) {
-      if (i + a < 0 || i + a >= L.nx) continue;
-      s.add(df_mul(st[(int64_t)(3 * (b + 1) + (a + 1)) * L.N + p], u[p + (int64_t)b * L.nx + a]));
+      for (int a = -1; a <= 1; ++a) {
+        const df c = L.q1c[3 * (b + 1) + (a + 1)];
+        const int64_t q = p + (int64_t)b * L.nx + a;
+#pragma unroll
+        for (int k = 0; k < kRpt; ++k)
+          if (k < nk) s[k].add(df_mul(c, u[off[k] + q]));
+      }
+  } else {
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) {
+      if (j + b < 0 || j + b >= L.ny) continue;
+#pragma unroll
+      for (int a = -1; a <= 1; ++a) {
+        if (i + a < 0 || i + a >= L.nx) continue;
+        const df c = st[(int64_t)(3 * (b + 1) + (a + 1)) * L.N + p];
+        const int64_t q = p + (int64_t)b * L.nx + a;
+#pragma unroll
+        for (int k = 0; k < kRpt; ++k)
+          if (k < nk) s[k].add(df_mul(c, u[off[k] + q]));
+      }
     }
   }
-  return s.get();
+#pragma unroll
+  for (int k = 0; k < kRpt; ++k) out[k] = s[k].get();
+}
+
+__device__ __forceinline__ df q1_dinv(const Level& L, int i, int j, int64_t p) {
+  return q1_uniform(L, i, j) ? L.q1c[9] : L.q1st[9 * L.N + p];
 }
 
 struct Vtx {
-  int i, j;
-  int64_t p, off;
+  int i, j, nk;
+  int64_t p, off[kRpt];
 };
-__device__ __forceinline__ bool vtx_of(const Level& L, Vtx& v) {
-  v.p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v.p >= L.N) return false;
-  v.i = (int)(v.p % L.nx);
-  v.j = (int)(v.p / L.nx);
-  v.off = (int64_t)blockIdx.y * L.N;
+// vertex of this thread on level L and its right-hand sides (blockIdx.z * kRpt + k < nrhs)
+__device__ __forceinline__ bool vtx_of(const Level& L, int nrhs, Vtx& v) {
+  v.i = (int)(blockIdx.x * kBX + threadIdx.x);
+  v.j = (int)(blockIdx.y * kBY + threadIdx.y);
+  if (v.i >= L.nx || v.j >= L.ny) return false;
+  v.p = (int64_t)v.j * L.nx + v.i;
+  const int r0 = (int)blockIdx.z * kRpt;
+  v.nk = min(kRpt, nrhs - r0);
+#pragma unroll
+  for (int k = 0; k < kRpt; ++k) v.off[k] = (int64_t)(r0 + (k < v.nk ? k : 0)) * L.N;
   return true;
 }
 
-__global__ void k_q1_cheb_first_df(Level L, const df* __restrict__ b, df* __restrict__ x, df* __restrict__ r,
-                                   df* __restrict__ d, int zero_x, df inv_theta) {
+__global__ void __launch_bounds__(kBX * kBY) k_q1_cheb_first_df(Level L, int nrhs, const df* __restrict__ b,
+                                                              df* __restrict__ x, df* __restrict__ r,
+                                                              df* __restrict__ d, int zero_x, df inv_theta) {
   Vtx v;
-  if (!vtx_of(L, v)) return;
-  df rv = b[v.off + v.p];
-  if (!zero_x) rv = df_sub(rv, q1_apply_df(L, x + v.off, v.i, v.j, v.p));
-  const df dv = df_mul(df_mul(rv, L.q1st[9 * L.N + v.p]), inv_theta);
-  r[v.off + v.p] = rv;
-  d[v.off + v.p] = dv;
-  if (zero_x) x[v.off + v.p] = dv;  // otherwise x is read by neighbours; the next step adds d
+  if (!vtx_of(L, nrhs, v)) return;
+  df ax[kRpt];
+  if (!zero_x) q1_apply_df(L, x, v.off, v.nk, v.i, v.j, v.p, ax);
+  const df dinv = q1_dinv(L, v.i, v.j, v.p);
+#pragma unroll
+  for (int k = 0; k < kRpt; ++k) {
+    if (k >= v.nk) break;
+    const int64_t o = v.off[k] + v.p;
+    df rv = b[o];
+    if (!zero_x) rv = df_sub(rv, ax[k]);
+    const df dv = df_mul(df_mul(rv, dinv), inv_theta);
+    r[o] = rv;
+    d[o] = dv;
+    if (zero_x) x[o] = dv;  // otherwise x is read by neighbours; the next step adds d
+  }
 }
 
-__global__ void k_q1_cheb_step_df(Level L, df* __restrict__ r, const df* __restrict__ d_old,
-                                  df* __restrict__ d_new, df* __restrict__ x, df c1, df c2, int add_old) {
+__global__ void __launch_bounds__(kBX * kBY) k_q1_cheb_step_df(Level L, int nrhs, df* __restrict__ r,
+                                                             const df* __restrict__ d_old, df* __restrict__ d_new,
+                                                             df* __restrict__ x, df c1, df c2, int add_old) {
   Vtx v;
-  if (!vtx_of(L, v)) return;
-  const int64_t o = v.off + v.p;
-  const df dold = d_old[o];
-  const df rv = df_sub(r[o], q1_apply_df(L, d_old + v.off, v.i, v.j, v.p));
-  const df dv = df_add(df_mul(c1, dold), df_mul(c2, df_mul(rv, L.q1st[9 * L.N + v.p])));
-  r[o] = rv;
-  d_new[o] = dv;
-  x[o] = df_add(x[o], add_old ? df_add(dold, dv) : dv);
+  if (!vtx_of(L, nrhs, v)) return;
+  df ad[kRpt];
+  q1_apply_df(L, d_old, v.off, v.nk, v.i, v.j, v.p, ad);
+  const df dinv = q1_dinv(L, v.i, v.j, v.p);
+#pragma unroll
+  for (int k = 0; k < kRpt; ++k) {
+    if (k >= v.nk) break;
+    const int64_t o = v.off[k] + v.p;
+    const df dold = d_old[o];
+    const df rv = df_sub(r[o], ad[k]);
+    const df dv = df_add(df_mul(c1, dold), df_mul(c2, df_mul(rv, dinv)));
+    r[o] = rv;
+    d_new[o] = dv;
+    x[o] = df_add(x[o], add_old ? df_add(dold, dv) : dv);
+  }
 }
 
-__global__ void k_q1_residual_df(Level L, const df* __restrict__ b, const df* __restrict__ x, df* __restrict__ r) {
+__global__ void __launch_bounds__(kBX * kBY) k_q1_residual_df(Level L, int nrhs, const df* __restrict__ b,
+                                                            const df* __restrict__ x, df* __restrict__ r) {
   Vtx v;
-  if (!vtx_of(L, v)) return;
-  r[v.off + v.p] = df_sub(b[v.off + v.p], q1_apply_df(L, x + v.off, v.i, v.j, v.p));
+  if (!vtx_of(L, nrhs, v)) return;
+  df ax[kRpt];
+  q1_apply_df(L, x, v.off, v.nk, v.i, v.j, v.p, ax);
+#pragma unroll
+  for (int k = 0; k < kRpt; ++k) {
+    if (k >= v.nk) break;
+    r[v.off[k] + v.p] = df_sub(b[v.off[k] + v.p], ax[k]);
+  }
 }
 
 // 1D Q1 transfers: a fine vertex is a coarse vertex iff it is even or the last one
@@ -134,11 +197,12 @@ __device__ __forceinline__ df halve(df v, float w) {  // w is 1 or 1/2: exact
   return w == 1.f ? v : df_make(v.hi * 0.5f, v.lo * 0.5f);
 }
 
-__global__ void k_q1_restrict_df(Level Lf, Level Lc, const df* __restrict__ rf, df* __restrict__ bc) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= Lc.N) return;
-  const int I = (int)(p % Lc.nx), J = (int)(p / Lc.nx);
-  const df* r = rf + (int64_t)blockIdx.y * Lf.N;
+__global__ void __launch_bounds__(kBX * kBY) k_q1_restrict_df(Level Lf, Level Lc, const df* __restrict__ rf,
+                                                            df* __restrict__ bc) {
+  const int I = (int)(blockIdx.x * kBX + threadIdx.x), J = (int)(blockIdx.y * kBY + threadIdx.y);
+  if (I >= Lc.nx || J >= Lc.ny) return;
+  const int64_t p = (int64_t)J * Lc.nx + I;
+  const df* r = rf + (int64_t)blockIdx.z * Lf.N;
   int fx[3], fy[3];
   float wx[3], wy[3];
   const int nx_ = q1_rst(I, Lf.nx, Lf.cx, fx, wx);
@@ -150,17 +214,19 @@ __global__ void k_q1_restrict_df(Level Lf, Level Lc, const df* __restrict__ rf, 
     for (int a = 0; a < nx_; ++a) sx.add(halve(row[fx[a]], wx[a]));
     acc.add(halve(sx.get(), wy[b]));
   }
-  bc[(int64_t)blockIdx.y * Lc.N + p] = acc.get();
+  bc[(int64_t)blockIdx.z * Lc.N + p] = acc.get();
 }
 
-__global__ void k_q1_prolong_add_df(Level Lf, Level Lc, const df* __restrict__ xc, df* __restrict__ xf) {
-  Vtx v;
-  if (!vtx_of(Lf, v)) return;
-  const df* c = xc + (int64_t)blockIdx.y * Lc.N;
+__global__ void __launch_bounds__(kBX * kBY) k_q1_prolong_add_df(Level Lf, Level Lc, const df* __restrict__ xc,
+                                                               df* __restrict__ xf) {
+  const int i = (int)(blockIdx.x * kBX + threadIdx.x), j = (int)(blockIdx.y * kBY + threadIdx.y);
+  if (i >= Lf.nx || j >= Lf.ny) return;
+  const int64_t p = (int64_t)j * Lf.nx + i;
+  const df* c = xc + (int64_t)blockIdx.z * Lc.N;
   int fx[2], fy[2];
   float wx[2], wy[2];
-  const int nx_ = q1_prl(v.i, Lf.nx, Lc.nx, Lf.cx, fx, wx);
-  const int ny_ = q1_prl(v.j, Lf.ny, Lc.ny, Lf.cy, fy, wy);
+  const int nx_ = q1_prl(i, Lf.nx, Lc.nx, Lf.cx, fx, wx);
+  const int ny_ = q1_prl(j, Lf.ny, Lc.ny, Lf.cy, fy, wy);
   dsum acc;
   for (int b = 0; b < ny_; ++b) {
     const df* row = c + (int64_t)fy[b] * Lc.nx;
@@ -168,11 +234,16 @@ __global__ void k_q1_prolong_add_df(Level Lf, Level Lc, const df* __restrict__ x
     for (int a = 0; a < nx_; ++a) sx.add(halve(row[fx[a]], wx[a]));
     acc.add(halve(sx.get(), wy[b]));
   }
-  const int64_t o = v.off + v.p;
+  const int64_t o = (int64_t)blockIdx.z * Lf.N + p;
   xf[o] = df_add(xf[o], acc.get());
 }
 
 inline dim3 grid_of(int64_t n, int nrhs) { return dim3((unsigned)((n + kThreads - 1) / kThreads), (unsigned)nrhs); }
+// the vertex kernels: 64 x 4 vertices per block, z = groups of `per` right-hand sides
+inline dim3 grid2(const Level& L, int nrhs, int per) {
+  return dim3((unsigned)((L.nx + kBX - 1) / kBX), (unsigned)((L.ny + kBY - 1) / kBY), (unsigned)((nrhs + per - 1) / per));
+}
+const dim3 kBlock2(kBX, kBY);
 
 }  // namespace
 
@@ -182,24 +253,24 @@ void launch_q1_stencil_df(const Level& L, df* st, cudaStream_t s) {
 }
 void launch_q1_cheb_first_df(const Level& L, int nrhs, const df* b, df* x, df* r, df* d, bool zero_x, df inv_theta,
                              cudaStream_t s) {
-  k_q1_cheb_first_df<<<grid_of(L.N, nrhs), kThreads, 0, s>>>(L, b, x, r, d, zero_x ? 1 : 0, inv_theta);
+  k_q1_cheb_first_df<<<grid2(L, nrhs, kRpt), kBlock2, 0, s>>>(L, nrhs, b, x, r, d, zero_x ? 1 : 0, inv_theta);
   note_launches(1);
 }
 void launch_q1_cheb_step_df(const Level& L, int nrhs, df* r, const df* d_old, df* d_new, df* x, df c1, df c2,
                             bool add_old, cudaStream_t s) {
-  k_q1_cheb_step_df<<<grid_of(L.N, nrhs), kThreads, 0, s>>>(L, r, d_old, d_new, x, c1, c2, add_old ? 1 : 0);
+  k_q1_cheb_step_df<<<grid2(L, nrhs, kRpt), kBlock2, 0, s>>>(L, nrhs, r, d_old, d_new, x, c1, c2, add_old ? 1 : 0);
   note_launches(1);
 }
 void launch_q1_residual_df(const Level& L, int nrhs, const df* b, const df* x, df* r, cudaStream_t s) {
-  k_q1_residual_df<<<grid_of(L.N, nrhs), kThreads, 0, s>>>(L, b, x, r);
+  k_q1_residual_df<<<grid2(L, nrhs, kRpt), kBlock2, 0, s>>>(L, nrhs, b, x, r);
   note_launches(1);
 }
 void launch_q1_restrict_df(const Level& Lf, const Level& Lc, int nrhs, const df* rf, df* bc, cudaStream_t s) {
-  k_q1_restrict_df<<<grid_of(Lc.N, nrhs), kThreads, 0, s>>>(Lf, Lc, rf, bc);
+  k_q1_restrict_df<<<grid2(Lc, nrhs, 1), kBlock2, 0, s>>>(Lf, Lc, rf, bc);
   note_launches(1);
 }
 void launch_q1_prolong_add_df(const Level& Lf, const Level& Lc, int nrhs, const df* xc, df* xf, cudaStream_t s) {
-  k_q1_prolong_add_df<<<grid_of(Lf.N, nrhs), kThreads, 0, s>>>(Lf, Lc, xc, xf);
+  k_q1_prolong_add_df<<<grid2(Lf, nrhs, 1), kBlock2, 0, s>>>(Lf, Lc, xc, xf);
   note_launches(1);
 }
 
