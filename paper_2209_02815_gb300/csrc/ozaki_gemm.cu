@@ -475,17 +475,36 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_digits(const XS* __rest
   constexpr bool kDf = std::is_same<XS, df>::value;
   XS x[8];
   int best = 0;
+  // the thread's 8 entries are 64 contiguous bytes: four 16-byte loads when they all lie in
+  // the panel and the row start is 16-byte aligned (N even), else entry by entry
+  const bool whole = row < m && kc + 8 <= kw && (N & 1) == 0 &&
+                     (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  if (whole) {
+    const float4* src = reinterpret_cast<const float4*>(X + row * N + k0 + kc);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float4 f = src[v];
+      if constexpr (kDf) {
+        x[2 * v] = df_make(f.x, f.y);
+        x[2 * v + 1] = df_make(f.z, f.w);
+      } else {
+        x[2 * v] = __hiloint2double(__float_as_int(f.y), __float_as_int(f.x));
+        x[2 * v + 1] = __hiloint2double(__float_as_int(f.w), __float_as_int(f.z));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const long long k = kc + t;
+      if constexpr (kDf) x[t] = (k < kw && row < m) ? X[row * N + k0 + k] : df_make(0.f, 0.f);
+      else x[t] = (k < kw && row < m) ? X[row * N + k0 + k] : 0.0;
+    }
+  }
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
-    const long long k = kc + t;
     int ex;
-    if constexpr (kDf) {
-      x[t] = (k < kw && row < m) ? X[row * N + k0 + k] : df_make(0.f, 0.f);
-      ex = static_cast<int>((__float_as_uint(x[t].hi) >> 23) & 0xFF);
-    } else {
-      x[t] = (k < kw && row < m) ? X[row * N + k0 + k] : 0.0;
-      ex = static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x[t])) >> 52) & 0x7FF);
-    }
+    if constexpr (kDf) ex = static_cast<int>((__float_as_uint(x[t].hi) >> 23) & 0xFF);
+    else ex = static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x[t])) >> 52) & 0x7FF);
     best = ex > best ? ex : best;
   }
   // max over the row's lanes of this warp (its chunks and stages), then over the warps
