@@ -258,42 +258,61 @@ __global__ void k_apply64(Level L, const double* tx, const double* ty, const dou
 // The FP32 cycle kernels take one field per thread (grid y = field): the blocks in flight
 // then work on the same field, whose neighbouring planes stay in L2, where a loop over the
 // fields inside each thread spread the working set over all of them.
-__global__ void k_cheb_first32(Level L, Coef32 C, const float* __restrict__ b, float* __restrict__ x,
+// The FP32 cycle's kernels take kFpt fields per thread (grid y = groups of fields): a cell's
+// stencil coefficients and its index arithmetic serve all of them.
+constexpr int kFpt = 4;
+
+__global__ void k_cheb_first32(Level L, Coef32 C, int ne, const float* __restrict__ b, float* __restrict__ x,
                                float* __restrict__ r, float* __restrict__ d, int zero_x, float inv_theta) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
   const float di = C.dinv[p] * inv_theta;
-  const int64_t o = (int64_t)blockIdx.y * L.N;
-  float rv = b[o + p];
-  if (!zero_x) rv -= stencil_apply(S, x + o, p);
-  r[o + p] = rv;
-  d[o + p] = di * rv;
-  if (zero_x) x[o + p] = di * rv;
+#pragma unroll
+  for (int f = 0; f < kFpt; ++f) {
+    const int e = (int)blockIdx.y * kFpt + f;
+    if (e >= ne) break;
+    const int64_t o = (int64_t)e * L.N;
+    float rv = b[o + p];
+    if (!zero_x) rv -= stencil_apply(S, x + o, p);
+    r[o + p] = rv;
+    d[o + p] = di * rv;
+    if (zero_x) x[o + p] = di * rv;
+  }
 }
 
-__global__ void k_cheb_step32(Level L, Coef32 C, float* __restrict__ r, const float* __restrict__ dold,
+__global__ void k_cheb_step32(Level L, Coef32 C, int ne, float* __restrict__ r, const float* __restrict__ dold,
                               float* __restrict__ dnew, float* __restrict__ x, float c1, float c2, int add_old) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
   const float di = C.dinv[p];
-  const int64_t o = (int64_t)blockIdx.y * L.N;
-  const float d0 = dold[o + p];
-  const float rv = r[o + p] - stencil_apply(S, dold + o, p);
-  const float dv = c1 * d0 + c2 * di * rv;
-  r[o + p] = rv;
-  dnew[o + p] = dv;
-  x[o + p] += add_old ? d0 + dv : dv;
+#pragma unroll
+  for (int f = 0; f < kFpt; ++f) {
+    const int e = (int)blockIdx.y * kFpt + f;
+    if (e >= ne) break;
+    const int64_t o = (int64_t)e * L.N;
+    const float d0 = dold[o + p];
+    const float rv = r[o + p] - stencil_apply(S, dold + o, p);
+    const float dv = c1 * d0 + c2 * di * rv;
+    r[o + p] = rv;
+    dnew[o + p] = dv;
+    x[o + p] += add_old ? d0 + dv : dv;
+  }
 }
 
-__global__ void k_resid32(Level L, Coef32 C, const float* __restrict__ b, const float* __restrict__ x,
+__global__ void k_resid32(Level L, Coef32 C, int ne, const float* __restrict__ b, const float* __restrict__ x,
                           float* __restrict__ r) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
-  const int64_t o = (int64_t)blockIdx.y * L.N;
-  r[o + p] = b[o + p] - stencil_apply(S, x + o, p);
+#pragma unroll
+  for (int f = 0; f < kFpt; ++f) {
+    const int e = (int)blockIdx.y * kFpt + f;
+    if (e >= ne) break;
+    const int64_t o = (int64_t)e * L.N;
+    r[o + p] = b[o + p] - stencil_apply(S, x + o, p);
+  }
 }
 
 // Cell-centred trilinear transfer weights of one axis (2:1 agglomeration), as in the
@@ -329,7 +348,7 @@ __device__ __forceinline__ void prl_1d(int i, int nc, int coarsened, int f[2], f
 }
 
 // grid: (coarse cells / 256, fields)
-__global__ void k_restrict32(Level Lf, Level Lc, const float* __restrict__ rf, float* __restrict__ bc) {
+__global__ void k_restrict32(Level Lf, Level Lc, int ne, const float* __restrict__ rf, float* __restrict__ bc) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= Lc.N) return;
   int I, J, K;
@@ -339,21 +358,25 @@ __global__ void k_restrict32(Level Lf, Level Lc, const float* __restrict__ rf, f
   rst_1d(I, Lc.nx, Lf.cx, fx, wx);
   rst_1d(J, Lc.ny, Lf.cy, fy, wy);
   rst_1d(K, Lc.nz, Lf.cz, fz, wz);
-  const float* r = rf + (int64_t)blockIdx.y * Lf.N;
-  float acc = 0.f;
+  {  // one field per thread here: the restriction is bound by the latency of its 64 loads
+    const int e = (int)blockIdx.y;
+    if (e >= ne) return;
+    const float* r = rf + (int64_t)e * Lf.N;
+    float acc = 0.f;
 #pragma unroll
-  for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < 4; ++c)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const float* row = r + ((int64_t)fz[c] * Lf.ny + fy[b]) * Lf.nx;
-      const float s = wx[0] * row[fx[0]] + wx[1] * row[fx[1]] + wx[2] * row[fx[2]] + wx[3] * row[fx[3]];
-      acc += wy[b] * wz[c] * s;
-    }
-  bc[(int64_t)blockIdx.y * Lc.N + p] = acc;
+      for (int b = 0; b < 4; ++b) {
+        const float* row = r + ((int64_t)fz[c] * Lf.ny + fy[b]) * Lf.nx;
+        const float s = wx[0] * row[fx[0]] + wx[1] * row[fx[1]] + wx[2] * row[fx[2]] + wx[3] * row[fx[3]];
+        acc += wy[b] * wz[c] * s;
+      }
+    bc[(int64_t)e * Lc.N + p] = acc;
+  }
 }
 
 // grid: (fine cells / 256, fields)
-__global__ void k_prolong_add32(Level Lf, Level Lc, const float* __restrict__ xc, float* __restrict__ xf) {
+__global__ void k_prolong_add32(Level Lf, Level Lc, int ne, const float* __restrict__ xc, float* __restrict__ xf) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= Lf.N) return;
   int i, j, k;
@@ -363,16 +386,21 @@ __global__ void k_prolong_add32(Level Lf, Level Lc, const float* __restrict__ xc
   prl_1d(i, Lc.nx, Lf.cx, fx, wx);
   prl_1d(j, Lc.ny, Lf.cy, fy, wy);
   prl_1d(k, Lc.nz, Lf.cz, fz, wz);
-  const float* c = xc + (int64_t)blockIdx.y * Lc.N;
-  float acc = 0.f;
 #pragma unroll
-  for (int cc = 0; cc < 2; ++cc)
+  for (int f = 0; f < kFpt; ++f) {
+    const int e = (int)blockIdx.y * kFpt + f;
+    if (e >= ne) break;
+    const float* c = xc + (int64_t)e * Lc.N;
+    float acc = 0.f;
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const float* row = c + ((int64_t)fz[cc] * Lc.ny + fy[b]) * Lc.nx;
-      acc += wy[b] * wz[cc] * (wx[0] * row[fx[0]] + wx[1] * row[fx[1]]);
-    }
-  xf[(int64_t)blockIdx.y * Lf.N + p] += acc;
+    for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const float* row = c + ((int64_t)fz[cc] * Lc.ny + fy[b]) * Lc.nx;
+        acc += wy[b] * wz[cc] * (wx[0] * row[fx[0]] + wx[1] * row[fx[1]]);
+      }
+    xf[(int64_t)e * Lf.N + p] += acc;
+  }
 }
 
 // x_e = X b_e on the coarsest level (X: dense inverse, n x n, FP32)
@@ -728,9 +756,9 @@ void smooth32(const Layout& W, const Level* lev, int l, int ne, const Cheb& K, c
               cudaStream_t s) {
   const Level& L = lev[l];
   const Coef32 C = coef_of(W, l);
-  const dim3 grid(nblk(L.N), ne);
-  k_cheb_first32<<<grid, kThreads, 0, s>>>(L, C, b, x, W.r[l], W.da[l], zero_x ? 1 : 0, K.inv_theta);
-  k_cheb_step32<<<grid, kThreads, 0, s>>>(L, C, W.r[l], W.da[l], W.db[l], x, K.c1, K.c2, zero_x ? 0 : 1);
+  const dim3 grid(nblk(L.N), (ne + kFpt - 1) / kFpt);
+  k_cheb_first32<<<grid, kThreads, 0, s>>>(L, C, ne, b, x, W.r[l], W.da[l], zero_x ? 1 : 0, K.inv_theta);
+  k_cheb_step32<<<grid, kThreads, 0, s>>>(L, C, ne, W.r[l], W.da[l], W.db[l], x, K.c1, K.c2, zero_x ? 0 : 1);
   note_launches(2);
 }
 
@@ -739,8 +767,9 @@ void vcycle32(const Layout& W, const Level* lev, int nl, int ne, cudaStream_t s)
   const Cheb K = cheb_coefs();
   for (int l = 0; l < nl - 1; ++l) {
     smooth32(W, lev, l, ne, K, W.b[l], W.x[l], true, s);
-    k_resid32<<<dim3(nblk(lev[l].N), ne), kThreads, 0, s>>>(lev[l], coef_of(W, l), W.b[l], W.x[l], W.r[l]);
-    k_restrict32<<<dim3(nblk(lev[l + 1].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], W.r[l], W.b[l + 1]);
+    const unsigned ng = (unsigned)((ne + kFpt - 1) / kFpt);
+    k_resid32<<<dim3(nblk(lev[l].N), ng), kThreads, 0, s>>>(lev[l], coef_of(W, l), ne, W.b[l], W.x[l], W.r[l]);
+    k_restrict32<<<dim3(nblk(lev[l + 1].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
     note_launches(2);
   }
   const int nc = (int)lev[nl - 1].N;
@@ -748,7 +777,8 @@ void vcycle32(const Layout& W, const Level* lev, int nl, int ne, cudaStream_t s)
                                                                                                   W.x[nl - 1]);
   note_launches(1);
   for (int l = nl - 2; l >= 0; --l) {
-    k_prolong_add32<<<dim3(nblk(lev[l].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], W.x[l + 1], W.x[l]);
+    k_prolong_add32<<<dim3(nblk(lev[l].N), (ne + kFpt - 1) / kFpt), kThreads, 0, s>>>(lev[l], lev[l + 1], ne,
+                                                                                    W.x[l + 1], W.x[l]);
     note_launches(1);
     smooth32(W, lev, l, ne, K, W.b[l], W.x[l], false, s);
   }
