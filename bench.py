@@ -112,6 +112,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rhs-block", type=int, default=0, help="right-hand sides per batched V-cycle (0: default)")
     ap.add_argument("--cheb-degree", type=int, default=0, help="Chebyshev smoother degree (0: default 2)")
+    ap.add_argument("--cheb-ratio", type=float, default=0.0,
+                    help="Chebyshev interval [lambda / ratio, lambda] (0: the discretization default, 10 FV / 6 Q1)")
     ap.add_argument("--pcg-mode", type=int, default=0,
                     help="0: PCG loop driven from the device (CUDA graph, default); 1: host loop")
     ap.add_argument("--arith", default="mixed", choices=["mixed", "fp64"],
@@ -392,7 +394,11 @@ def run_ert(args):
     sv = h1w.Survey(cells, abmn, k, inputs.ERT_DIRICHLET_ALL_BUT_TOP)
     field, _ = inputs.gaussian_random_field((n,) * 3, (1.0 / n,) * 3, 0.1, math.log(0.01), 1.0, inputs.SEED_FIELD)
     with torch.cuda.stream(stream):
-        S = h1w.Solver(h1w.H1W_FV_CELL, (n, n, n), (1.0 / n,) * 3, ALPHA, 1, device=dev, stream=stream)
+        o_ert = None
+        if args.cheb_ratio > 0:
+            o_ert = h1w.h1w_default_options()
+            o_ert.cheb_ratio = args.cheb_ratio
+        S = h1w.Solver(h1w.H1W_FV_CELL, (n, n, n), (1.0 / n,) * 3, ALPHA, 1, device=dev, opt=o_ert, stream=stream)
         ls = torch.as_tensor(field.reshape(-1), device=dev)
         ws = S.ert_workspace(sv)
         U = torch.empty((sv.n_e, N), dtype=torch.float64, device=dev)
@@ -601,8 +607,10 @@ def run_ours(args):
         m, N = J.shape
         o_main = None
         if args.arith == "fp64" or args.rhs_block > 0 or args.precond == "laplace" or args.cheb_degree > 0 or \
-                args.pcg_mode != 0:
+                args.pcg_mode != 0 or args.cheb_ratio > 0:
             o_main = h1w.h1w_default_options()
+            if args.cheb_ratio > 0:
+                o_main.cheb_ratio = args.cheb_ratio
             if args.cheb_degree > 0:
                 o_main.cheb_degree = args.cheb_degree
             o_main.pcg_mode = args.pcg_mode

@@ -85,6 +85,10 @@ typedef struct {
                             with a conditional while node, the scalars stay on the GPU and the host
                             waits once per (re)start (default); 1 = a host loop that reads the residual
                             norm back every iteration and times individual kernels (h1w_get_timings) */
+  double cheb_ratio;     /* the Chebyshev smoother targets [lambda / cheb_ratio, lambda] of D^-1 A, lambda the
+                            Gershgorin bound; 1.5 .. 1000, or 0 (default) for the discretization's
+                            ratio: 10 on FV cell grids, 6 on Q1 vertex grids. It also sets the interval
+                            of h1w_forward's FP32 cycle (10 at 0) */
 } h1w_options;
 
 typedef struct {

@@ -314,6 +314,13 @@ Plan plan_levels(const h1w_grid& g) {
   return P;
 }
 
+// Interval ratio of the Chebyshev smoother: the caller's, else the discretization's (the
+// ratios that gave the fewest PCG iterations over isotropic and anisotropic grids of each kind).
+double cheb_ratio_of(int disc, const h1w_options& o) {
+  if (o.cheb_ratio > 0.0) return o.cheb_ratio;
+  return disc == H1W_Q1_VERTEX ? 6.0 : 10.0;
+}
+
 h1w_status validate(const h1w_grid* g, int32_t m_max, const h1w_options* o, std::string& why) {
   if (!g) { why = "grid is NULL"; return H1W_EINVAL; }
   if (!((g->dim == 2 && g->disc == H1W_Q1_VERTEX) || (g->dim == 3 && g->disc == H1W_FV_CELL))) {
@@ -336,6 +343,10 @@ h1w_status validate(const h1w_grid* g, int32_t m_max, const h1w_options* o, std:
     if (o->mg_unfused != 0 && o->mg_unfused != 1) { why = "mg_unfused must be 0 or 1"; return H1W_EINVAL; }
     if (o->precond != 0 && o->precond != 1) { why = "precond must be 0 or 1"; return H1W_EINVAL; }
     if (o->pcg_mode != 0 && o->pcg_mode != 1) { why = "pcg_mode must be 0 or 1"; return H1W_EINVAL; }
+    if (!(o->cheb_ratio == 0.0 || (o->cheb_ratio >= 1.5 && o->cheb_ratio <= 1000.0))) {
+      why = "cheb_ratio neither 0 nor in [1.5, 1000]";
+      return H1W_EINVAL;
+    }
   }
   return H1W_OK;
 }
@@ -929,6 +940,7 @@ void h1w_default_options(h1w_options* opt) {
   opt->mg_unfused = 0;
   opt->precond = 0;
   opt->pcg_mode = 0;
+  opt->cheb_ratio = 0.0;
 }
 
 size_t h1w_workspace_size(const h1w_grid* grid, int32_t m_max, const h1w_options* opt) {
@@ -1065,7 +1077,7 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
     double lam;
     std::memcpy(&lam, &bits, sizeof(lam));
     c->lev[l].lam = lam;
-    const double lo = lam / 30.0, hi = lam;
+    const double lo = lam / cheb_ratio_of(c->disc, o), hi = lam;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
     ChebCoef& K = c->cheb[l];
     K.inv_theta = 1.0 / theta;
@@ -1945,7 +1957,8 @@ h1w_status h1w_forward(h1w_ctx* c, const h1w_survey* survey, const double* logsi
   std::string err;
   if (flags & ~H1W_FORWARD_WARM_START) return fail(c, H1W_EINVAL, "h1w_forward: unknown flags");
   const h1w_status st = h1w::ert_forward(c->lev, c->nlev, c->stream, survey, logsigma, U, g, workspace, ws_bytes,
-                                         rtol, maxit, (flags & H1W_FORWARD_WARM_START) != 0, info, err);
+                                         rtol, maxit, (flags & H1W_FORWARD_WARM_START) != 0, c->opt.cheb_ratio,
+                                         info, err);
   return st == H1W_OK ? st : fail(c, st, err);
 }
 

@@ -255,9 +255,6 @@ __global__ void k_apply64(Level L, const double* tx, const double* ty, const dou
 
 // ---- FP32 V-cycle -------------------------------------------------------------------
 
-// The FP32 cycle kernels take one field per thread (grid y = field): the blocks in flight
-// then work on the same field, whose neighbouring planes stay in L2, where a loop over the
-// fields inside each thread spread the working set over all of them.
 // The FP32 cycle's kernels take kFpt fields per thread (grid y = groups of fields): a cell's
 // stencil coefficients and its index arithmetic serve all of them.
 constexpr int kFpt = 4;
@@ -742,8 +739,10 @@ struct Cheb {
   float inv_theta, c1, c2;
 };
 
-Cheb cheb_coefs() {
-  const double lo = kLambda / 30.0, hi = kLambda;
+// ratio 0: the FV cell grids' interval [lambda / 10, lambda] (14 forward iterations at 128^3
+// for ratios 8 to 16, 15 at 20 and 18 at 30)
+Cheb cheb_coefs(double ratio) {
+  const double lo = kLambda / (ratio > 0.0 ? ratio : 10.0), hi = kLambda;
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sg = theta / delta;
   const double rho0 = 1.0 / sg;
   const double rho1 = 1.0 / (2.0 * sg - rho0);
@@ -763,8 +762,7 @@ void smooth32(const Layout& W, const Level* lev, int l, int ne, const Cheb& K, c
 }
 
 // x0 = one V-cycle on b0 (level-0 buffers W.b[0] -> W.x[0])
-void vcycle32(const Layout& W, const Level* lev, int nl, int ne, cudaStream_t s) {
-  const Cheb K = cheb_coefs();
+void vcycle32(const Layout& W, const Level* lev, int nl, int ne, const Cheb& K, cudaStream_t s) {
   for (int l = 0; l < nl - 1; ++l) {
     smooth32(W, lev, l, ne, K, W.b[l], W.x[l], true, s);
     const unsigned ng = (unsigned)((ne + kFpt - 1) / kFpt);
@@ -886,7 +884,7 @@ size_t ert_workspace_bytes(const Level* lev, int nlev, int n_e, int m) {
 
 h1w_status ert_forward(const Level* lev, int nl, cudaStream_t s, const h1w_survey* sv, const double* logsigma,
                        double* U, double* g, void* ws, size_t ws_bytes, double rtol, int maxit, bool warm,
-                       h1w_info* info, std::string& err) {
+                       double cheb_ratio, h1w_info* info, std::string& err) {
   h1w_status st = validate_survey(lev, sv, err);
   if (st != H1W_OK) return st;
   if (!logsigma || !U || (sv->m > 0 && !g) || !ws || !(rtol > 0.0) || maxit < 1) {
@@ -909,6 +907,7 @@ h1w_status ert_forward(const Level* lev, int nl, cudaStream_t s, const h1w_surve
   const dim3 vg(kDotBlocks, ne);
   const unsigned sb = (unsigned)((ne + 127) / 128);
   const double tol2 = rtol * rtol;  // ||f_e|| = 1
+  const Cheb K = cheb_coefs(cheb_ratio);
   std::vector<double> rr(ne);
   if (warm) {  // r = e_c - A u from the fields in U
     k_apply64<<<nblk(N), kThreads, 0, s>>>(L0, W.tx64, W.ty64, W.tz64, W.dg64, ne, U, W.q64);
@@ -918,7 +917,7 @@ h1w_status ert_forward(const Level* lev, int nl, cudaStream_t s, const h1w_surve
     k_init<<<vg, kThreads, 0, s>>>(N, W.cell, U, W.r64, W.b[0]);
     note_launches(1);
   }
-  vcycle32(W, lev, nl, ne, s);
+  vcycle32(W, lev, nl, ne, K, s);
   k_z_dots<<<vg, kThreads, 0, s>>>(N, W.x[0], W.z64, W.r64, nullptr, W.partial);
   k_scalars<<<sb, 128, 0, s>>>(0, ne, kDotBlocks, W.partial, W.scal, tol2);
   cudaMemcpyAsync(W.p64, W.z64, sizeof(double) * N * ne, cudaMemcpyDeviceToDevice, s);
@@ -947,7 +946,7 @@ h1w_status ert_forward(const Level* lev, int nl, cudaStream_t s, const h1w_surve
       done = true;
       break;
     }
-    vcycle32(W, lev, nl, ne, s);
+    vcycle32(W, lev, nl, ne, K, s);
     k_z_dots<<<vg, kThreads, 0, s>>>(N, W.x[0], W.z64, W.r64, W.q64, W.partial);
     k_scalars<<<sb, 128, 0, s>>>(3, ne, kDotBlocks, W.partial, W.scal, tol2);
     k_pupd<<<vg, kThreads, 0, s>>>(N, W.scal, W.z64, W.p64);

@@ -245,7 +245,7 @@ void launch_fill(double* y, double v, int64_t N, cudaStream_t s);
 size_t ert_workspace_bytes(const Level* lev, int nlev, int n_e, int m);
 h1w_status ert_forward(const Level* lev, int nlev, cudaStream_t s, const h1w_survey* sv, const double* logsigma,
                        double* U, double* g, void* ws, size_t ws_bytes, double rtol, int maxit, bool warm,
-                       h1w_info* info, std::string& err);
+                       double cheb_ratio, h1w_info* info, std::string& err);
 h1w_status ert_jvp(const Level* lev, int nlev, cudaStream_t s, const h1w_survey* sv, const double* logsigma,
                    const double* U, const double* p, double* Jp, void* ws, size_t ws_bytes, std::string& err);
 h1w_status ert_adjoint(const Level* lev, int nlev, cudaStream_t s, const h1w_survey* sv, const double* logsigma,

@@ -189,11 +189,16 @@ def test_gn_steps_match_oracle():
         hist, g, _ = s.gn_inversion(sv, torch.tensor(g_obs, device=DEV), torch.tensor(m_ref, device=DEV), m_dev, 1,
                                     rtol_fwd=1e-13, rtol=1e-12)
         dm, g0, _ = ogn.gn_step(n, h, alpha, m_host, m_ref, cells, abmn, k, ALL_BUT_TOP, g_obs)
-        np.testing.assert_allclose(g.cpu().numpy(), g0, rtol=1e-9)
+        # the second step's data follow the first update, on which the GPU's PCG (rtol 1e-12)
+        # and the oracle's dense solve agree to cond * rtol: small entries are compared
+        # against the largest datum
+        np.testing.assert_allclose(g.cpu().numpy(), g0, rtol=1e-9, atol=1e-9 * np.abs(g0).max())
         m_host = m_host + dm
         err = np.abs(m_dev.cpu().numpy() - m_host).max() / np.abs(dm).max()
         assert err < 1e-7, (step, err)
-        assert hist[0].misfit == pytest.approx(np.linalg.norm(g0 - g_obs), rel=1e-9)
+        # the misfit is that of the returned data (which the line above compares with the oracle's)
+        assert hist[0].misfit == pytest.approx(np.linalg.norm(g.cpu().numpy() - g_obs), rel=1e-11)
+        assert abs(hist[0].misfit - np.linalg.norm(g0 - g_obs)) <= 1.01 * np.linalg.norm(g.cpu().numpy() - g0)
 
 
 def test_gn_inversion_reduces_misfit():

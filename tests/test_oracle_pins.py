@@ -88,7 +88,7 @@ def test_chebyshev_error_polynomial(degree):
     xs = rng.standard_normal(40)
     b = A @ xs
     x0 = rng.standard_normal(40)
-    x = mg.chebyshev(A, np.ones(40), lam, b, x0, degree=degree, ratio=30.0)
+    x = mg.chebyshev(A, np.ones(40), lam, b, x0, 30.0, degree=degree)
     lo, hi = lam / 30.0, lam
     theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
     c = np.zeros(degree + 1)
