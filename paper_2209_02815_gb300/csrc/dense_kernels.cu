@@ -256,28 +256,50 @@ __global__ void __launch_bounds__(kThreads) k_woodbury_update_df(
 // ---- Cholesky (lower, in place, row-major n x n), 32-wide panels --------------
 
 constexpr int kNB = 32;
+constexpr int kCholThreads = 256;  // the diagonal block's warp keeps a 32-double row in registers
 
-// Cholesky of the nb x nb lower triangle in Ld, in place, by any block of at least 32 threads.
+// Cholesky of the nb x nb lower triangle in Ld, in place, by warp 0 of the block (lane r
+// holds row r in registers; column c's entries reach the other lanes by shuffles, and each
+// pivot costs one square root and one reciprocal), then a barrier for the whole block. Ld
+// also receives the reciprocals of the diagonal in column kNB.
 __device__ void factor_diag_block(double (*Ld)[kNB + 1], int nb, int* status) {
-  const int tid = threadIdx.x;
-  for (int c = 0; c < nb; ++c) {
-    if (tid == 0) {
-      double piv = Ld[c][c];
-      if (!(piv > 0.0)) {
-        if (status) atomicOr(status, kStatusNotSpd);
-        piv = 1.0;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double row[kNB];
+    double rdiag = 1.0;  // this lane's reciprocal pivot
+#pragma unroll
+    for (int j = 0; j < kNB; ++j) row[j] = (lane < nb && j <= lane) ? Ld[lane][j] : 0.0;
+#pragma unroll
+    for (int c = 0; c < kNB; ++c) {
+      if (c < nb) {
+        double piv = __shfl_sync(0xffffffffu, row[c], c);
+        if (!(piv > 0.0)) {
+          if (status && lane == 0) atomicOr(status, kStatusNotSpd);
+          piv = 1.0;
+        }
+        const double d = sqrt(piv), inv = 1.0 / d;
+        if (lane == c) {
+          row[c] = d;
+          rdiag = inv;
+        } else if (lane > c) {
+          row[c] *= inv;
+        }
+        const double lrc = row[c];
+#pragma unroll
+        for (int j = c + 1; j < kNB; ++j) {
+          const double ljc = __shfl_sync(0xffffffffu, lrc, j);
+          if (j < nb && lane >= j) row[j] -= lrc * ljc;
+        }
       }
-      Ld[c][c] = sqrt(piv);
     }
-    __syncthreads();
-    if (tid > c && tid < nb) Ld[tid][c] /= Ld[c][c];
-    __syncthreads();
-    for (int e = tid; e < kNB * kNB; e += blockDim.x) {
-      const int r = e / kNB, c2 = e % kNB;
-      if (r > c && r < nb && c2 > c && c2 <= r) Ld[r][c2] -= Ld[r][c] * Ld[c2][c];
+    if (lane < nb) {
+#pragma unroll
+      for (int j = 0; j < kNB; ++j)
+        if (j <= lane) Ld[lane][j] = row[j];
+      Ld[lane][kNB] = rdiag;
     }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
 // The diagonal block A11 of the panel at kb, factored in shared memory.
@@ -301,28 +323,32 @@ __device__ __forceinline__ int load_factor_diag(const double* A, int n, int kb, 
 // rows kb .. kb + 31, all above the diagonal of A and zeroed at the end), and the extra
 // block of k_chol_update moves it into place. (The last panel has no rows below it and
 // is factored by k_chol_diag.)
-__global__ void __launch_bounds__(1024) k_chol_panel(double* A, int n, int kb, int* status) {
+__global__ void __launch_bounds__(kCholThreads) k_chol_panel(double* A, int n, int kb, int* status) {
   __shared__ double Ld[kNB][kNB + 1];
   const int nb = load_factor_diag(A, n, kb, Ld, blockIdx.x == 0 ? status : nullptr);
   const int tid = threadIdx.x;
   if (blockIdx.x == 0) {
-    const int r = tid / kNB, c = tid % kNB;
-    if (r < nb && c < r) A[(int64_t)(kb + c) * n + kb + r] = Ld[r][c];
-    if (r < nb && c == r) A[(int64_t)(kb + r) * n + kb + kNB] = Ld[r][r];
+    for (int e = tid; e < kNB * kNB; e += kCholThreads) {
+      const int r = e / kNB, c = e % kNB;
+      if (r < nb && c < r) A[(int64_t)(kb + c) * n + kb + r] = Ld[r][c];
+      if (r < nb && c == r) A[(int64_t)(kb + r) * n + kb + kNB] = Ld[r][r];
+    }
   }
-  // rows of this block: solve x L11^T = a for each row (warp w -> row w)
-  const int row = kb + kNB * (blockIdx.x + 1) + (tid >> 5);
+  // rows of this block: solve x L11^T = a for each row (warp w -> rows w, w + 8, ...)
   const int lane = tid & 31;
-  if (row >= n) return;
-  double a = (lane < nb) ? A[(int64_t)row * n + kb + lane] : 0.0;
-  for (int c = 0; c < nb; ++c) {
-    double xc = 0.0;
-    if (lane == c) xc = a / Ld[c][c];
-    xc = __shfl_sync(0xffffffffu, xc, c);
-    if (lane == c) a = xc;
-    else if (lane > c && lane < nb) a -= xc * Ld[lane][c];
+  for (int w = tid >> 5; w < kNB; w += kCholThreads / 32) {
+    const int row = kb + kNB * (blockIdx.x + 1) + w;
+    if (row >= n) break;
+    double a = (lane < nb) ? A[(int64_t)row * n + kb + lane] : 0.0;
+    for (int c = 0; c < nb; ++c) {
+      double xc = 0.0;
+      if (lane == c) xc = a * Ld[c][kNB];  // the reciprocal of the pivot
+      xc = __shfl_sync(0xffffffffu, xc, c);
+      if (lane == c) a = xc;
+      else if (lane > c && lane < nb) a -= xc * Ld[lane][c];
+    }
+    if (lane < nb) A[(int64_t)row * n + kb + lane] = a;
   }
-  if (lane < nb) A[(int64_t)row * n + kb + lane] = a;
 }
 
 // L11 = chol(A11), written back in place; a non-positive pivot sets kStatusNotSpd.
@@ -334,7 +360,7 @@ __device__ __forceinline__ void write_diag_factor(double* A, int n, int kb, doub
   }
 }
 
-__global__ void __launch_bounds__(1024) k_chol_diag(double* A, int n, int kb, int* status) {
+__global__ void __launch_bounds__(kCholThreads) k_chol_diag(double* A, int n, int kb, int* status) {
   __shared__ double Ld[kNB][kNB + 1];
   write_diag_factor(A, n, kb, Ld, status);
 }
@@ -946,12 +972,12 @@ void launch_chol(double* A, int n, int* status, cudaStream_t s) {
   for (int kb = 0; kb < n; kb += kNB) {
     const int below = (n - kb - 1) / kNB;  // 32-row blocks after the diagonal block
     if (below > 0) {
-      k_chol_panel<<<below, 1024, 0, s>>>(A, n, kb, status);
+      k_chol_panel<<<below, kCholThreads, 0, s>>>(A, n, kb, status);
       const int tiles = below * (below + 1) / 2;
       k_chol_update<<<tiles + 1, 256, 0, s>>>(A, n, kb);
       note_launches(2);
     } else {
-      k_chol_diag<<<1, 1024, 0, s>>>(A, n, kb, status);
+      k_chol_diag<<<1, kCholThreads, 0, s>>>(A, n, kb, status);
       note_launches(1);
     }
   }

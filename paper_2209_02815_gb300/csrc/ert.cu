@@ -15,11 +15,11 @@
 // Forward solve. All n_e pole fields at once by PCG in FP64 (flexible beta, since the
 // preconditioner is applied in FP32) on A, preconditioned by one FP32 V-cycle on the same
 // operator: the context's hierarchy and its trilinear transfers (R = P^T), Chebyshev-
-// Jacobi smoothing of degree 2 on [lambda / 30, lambda] with the Gershgorin bound
-// lambda = 2 of D^-1 A, and coarse operators rediscretized from the geometric mean of
-// the children's conductivities; the coarsest level is solved with a dense inverse from
-// the FP64 Cholesky factor. The operator kernels run one thread per cell over all fields,
-// so the coefficients are read once per sweep.
+// Jacobi smoothing of degree 2 on [lambda / 10, lambda] with the Gershgorin bound
+// lambda = 2 of D^-1 A (one stencil pass per smoothing, k_smooth32), and coarse operators
+// rediscretized from the geometric mean of the children's conductivities; the coarsest
+// level is solved with a dense inverse from the FP64 Cholesky factor. A thread of the
+// cycle's kernels takes one cell for kFpt fields, so it reads the cell's coefficients once.
 //
 // Jacobian. One block takes 32 consecutive cells: it stages the jumps of every field
 // across the six faces of each cell, and the conductance derivatives, in shared memory,
@@ -67,7 +67,7 @@ struct Layout {
   double* sig[kMaxLevels];
   double *tx64, *ty64, *tz64, *dg64;
   float *tx[kMaxLevels], *ty[kMaxLevels], *tz[kMaxLevels], *dg[kMaxLevels], *dinv[kMaxLevels];
-  float *x[kMaxLevels], *b[kMaxLevels], *r[kMaxLevels], *da[kMaxLevels], *db[kMaxLevels];
+  float *x[kMaxLevels], *b[kMaxLevels], *r[kMaxLevels];
   double *Ac, *Xc;
   float* Xf;
   int* status;
@@ -101,8 +101,6 @@ size_t layout(Layout& W, char* base, const Level* lev, int nlev, int n_e, int m)
     W.x[l] = B.take<float>(n * n_e);
     W.b[l] = B.take<float>(n * n_e);
     W.r[l] = B.take<float>(n * n_e);
-    W.da[l] = B.take<float>(n * n_e);
-    W.db[l] = B.take<float>(n * n_e);
   }
   const int64_t nc = lev[nlev - 1].N;
   W.Ac = B.take<double>(nc * nc);
@@ -255,57 +253,58 @@ __global__ void k_apply64(Level L, const double* tx, const double* ty, const dou
 
 // ---- FP32 V-cycle -------------------------------------------------------------------
 
-// The FP32 cycle's kernels take kFpt fields per thread (grid y = groups of fields): a cell's
-// stencil coefficients and its index arithmetic serve all of them.
-constexpr int kFpt = 4;
+// The FP32 cycle's kernels take kFpt fields per thread: a cell's stencil coefficients and
+// its index arithmetic serve all of them. Their 1D grid runs the field groups of a cell
+// block next to each other (group = block index modulo the group count), so the coefficients
+// come from DRAM once and from L2 for the other groups; with the groups outermost every
+// group re-read them from DRAM.
+constexpr int kFpt = 8;
 
-__global__ void k_cheb_first32(Level L, Coef32 C, int ne, const float* __restrict__ b, float* __restrict__ x,
-                               float* __restrict__ r, float* __restrict__ d, int zero_x, float inv_theta) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= L.N) return;
-  const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
-  const float di = C.dinv[p] * inv_theta;
-#pragma unroll
-  for (int f = 0; f < kFpt; ++f) {
-    const int e = (int)blockIdx.y * kFpt + f;
-    if (e >= ne) break;
-    const int64_t o = (int64_t)e * L.N;
-    float rv = b[o + p];
-    if (!zero_x) rv -= stencil_apply(S, x + o, p);
-    r[o + p] = rv;
-    d[o + p] = di * rv;
-    if (zero_x) x[o + p] = di * rv;
-  }
-}
-
-__global__ void k_cheb_step32(Level L, Coef32 C, int ne, float* __restrict__ r, const float* __restrict__ dold,
-                              float* __restrict__ dnew, float* __restrict__ x, float c1, float c2, int add_old) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// The degree-2 Chebyshev-Jacobi smoothing collapses into one stencil pass. With A = D - N
+// (N(u)_i = sum over the faces of cell i of t u_nb), d0 = D^-1 r0 / theta, r1 = r0 - A d0 and
+// x += d0 + c1 d0 + c2 D^-1 r1, the identity A d0 = r0 / theta - N d0 gives
+//   x += D^-1 [beta r0 + (c2 / theta) N(D^-1 r0)],  beta = (1 + c1) / theta + c2 (1 - 1 / theta),
+// with r0 = b for the zero initial guess of the pre-smoothing and r0 = b - A x for the
+// post-smoothing. One pass reads r0 (with its neighbours) and x and writes x, where the
+// two-step form wrote r, d and x twice.
+__global__ void k_smooth32(Level L, Coef32 C, int ne, const float* __restrict__ r0, float* __restrict__ x,
+                           int zero_x, float beta, float c2t) {
+  const unsigned ng = (unsigned)((ne + kFpt - 1) / kFpt), grp = blockIdx.x % ng;  // field groups fastest
+  const int64_t p = (int64_t)(blockIdx.x / ng) * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
   const float di = C.dinv[p];
+  // face conductance times the neighbour's D^-1 (0 where there is no neighbour)
+  const float wxm = S.hxm ? S.xm * C.dinv[p - 1] : 0.f, wxp = S.hxp ? S.xp * C.dinv[p + 1] : 0.f;
+  const float wym = S.hym ? S.ym * C.dinv[p - S.sy] : 0.f, wyp = S.hyp ? S.yp * C.dinv[p + S.sy] : 0.f;
+  const float wzm = S.hzm ? S.zm * C.dinv[p - S.sz] : 0.f, wzp = S.hzp ? S.zp * C.dinv[p + S.sz] : 0.f;
 #pragma unroll
   for (int f = 0; f < kFpt; ++f) {
-    const int e = (int)blockIdx.y * kFpt + f;
+    const int e = (int)grp * kFpt + f;
     if (e >= ne) break;
     const int64_t o = (int64_t)e * L.N;
-    const float d0 = dold[o + p];
-    const float rv = r[o + p] - stencil_apply(S, dold + o, p);
-    const float dv = c1 * d0 + c2 * di * rv;
-    r[o + p] = rv;
-    dnew[o + p] = dv;
-    x[o + p] += add_old ? d0 + dv : dv;
+    const float* r = r0 + o;
+    float n = 0.f;
+    if (S.hxm) n += wxm * r[p - 1];
+    if (S.hxp) n += wxp * r[p + 1];
+    if (S.hym) n += wym * r[p - S.sy];
+    if (S.hyp) n += wyp * r[p + S.sy];
+    if (S.hzm) n += wzm * r[p - S.sz];
+    if (S.hzp) n += wzp * r[p + S.sz];
+    const float dx = di * (beta * r[p] + c2t * n);
+    x[o + p] = zero_x ? dx : x[o + p] + dx;
   }
 }
 
 __global__ void k_resid32(Level L, Coef32 C, int ne, const float* __restrict__ b, const float* __restrict__ x,
                           float* __restrict__ r) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned ng = (unsigned)((ne + kFpt - 1) / kFpt), grp = blockIdx.x % ng;  // field groups fastest
+  const int64_t p = (int64_t)(blockIdx.x / ng) * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   const Stencil<float> S = load_stencil<float>(L, C.tx, C.ty, C.tz, C.dg, p);
 #pragma unroll
   for (int f = 0; f < kFpt; ++f) {
-    const int e = (int)blockIdx.y * kFpt + f;
+    const int e = (int)grp * kFpt + f;
     if (e >= ne) break;
     const int64_t o = (int64_t)e * L.N;
     r[o + p] = b[o + p] - stencil_apply(S, x + o, p);
@@ -374,7 +373,8 @@ __global__ void k_restrict32(Level Lf, Level Lc, int ne, const float* __restrict
 
 // grid: (fine cells / 256, fields)
 __global__ void k_prolong_add32(Level Lf, Level Lc, int ne, const float* __restrict__ xc, float* __restrict__ xf) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned ng = (unsigned)((ne + kFpt - 1) / kFpt), grp = blockIdx.x % ng;  // field groups fastest
+  const int64_t p = (int64_t)(blockIdx.x / ng) * blockDim.x + threadIdx.x;
   if (p >= Lf.N) return;
   int i, j, k;
   cell_ijk(Lf, p, i, j, k);
@@ -385,7 +385,7 @@ __global__ void k_prolong_add32(Level Lf, Level Lc, int ne, const float* __restr
   prl_1d(k, Lc.nz, Lf.cz, fz, wz);
 #pragma unroll
   for (int f = 0; f < kFpt; ++f) {
-    const int e = (int)blockIdx.y * kFpt + f;
+    const int e = (int)grp * kFpt + f;
     if (e >= ne) break;
     const float* c = xc + (int64_t)e * Lc.N;
     float acc = 0.f;
@@ -736,7 +736,7 @@ size_t jac_smem(int ne) { return sizeof(double) * ((size_t)ne * 6 * kJacCells + 
 // ---- host driver ---------------------------------------------------------------------
 
 struct Cheb {
-  float inv_theta, c1, c2;
+  float beta, c2t;  // the collapsed degree-2 step (k_smooth32): beta and c2 / theta
 };
 
 // ratio 0: the FV cell grids' interval [lambda / 10, lambda] (14 forward iterations at 128^3
@@ -746,39 +746,34 @@ Cheb cheb_coefs(double ratio) {
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sg = theta / delta;
   const double rho0 = 1.0 / sg;
   const double rho1 = 1.0 / (2.0 * sg - rho0);
-  return Cheb{(float)(1.0 / theta), (float)(rho1 * rho0), (float)(2.0 * rho1 / delta)};
+  const double it = 1.0 / theta, c1 = rho1 * rho0, c2 = 2.0 * rho1 / delta;
+  return Cheb{(float)((1.0 + c1) * it + c2 * (1.0 - it)), (float)(c2 * it)};
 }
 
 Coef32 coef_of(const Layout& W, int l) { return Coef32{W.tx[l], W.ty[l], W.tz[l], W.dg[l], W.dinv[l]}; }
 
-void smooth32(const Layout& W, const Level* lev, int l, int ne, const Cheb& K, const float* b, float* x, bool zero_x,
-              cudaStream_t s) {
-  const Level& L = lev[l];
-  const Coef32 C = coef_of(W, l);
-  const dim3 grid(nblk(L.N), (ne + kFpt - 1) / kFpt);
-  k_cheb_first32<<<grid, kThreads, 0, s>>>(L, C, ne, b, x, W.r[l], W.da[l], zero_x ? 1 : 0, K.inv_theta);
-  k_cheb_step32<<<grid, kThreads, 0, s>>>(L, C, ne, W.r[l], W.da[l], W.db[l], x, K.c1, K.c2, zero_x ? 0 : 1);
-  note_launches(2);
-}
-
-// x0 = one V-cycle on b0 (level-0 buffers W.b[0] -> W.x[0])
+// x = one V-cycle on b (level-0 buffers W.b[0] -> W.x[0]); W.r[l] holds the residuals
 void vcycle32(const Layout& W, const Level* lev, int nl, int ne, const Cheb& K, cudaStream_t s) {
+  const unsigned ng = (unsigned)((ne + kFpt - 1) / kFpt);
   for (int l = 0; l < nl - 1; ++l) {
-    smooth32(W, lev, l, ne, K, W.b[l], W.x[l], true, s);
-    const unsigned ng = (unsigned)((ne + kFpt - 1) / kFpt);
-    k_resid32<<<dim3(nblk(lev[l].N), ng), kThreads, 0, s>>>(lev[l], coef_of(W, l), ne, W.b[l], W.x[l], W.r[l]);
+    const Coef32 C = coef_of(W, l);
+    const unsigned nb = nblk(lev[l].N);
+    k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], 1, K.beta, K.c2t);
+    k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
     k_restrict32<<<dim3(nblk(lev[l + 1].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
-    note_launches(2);
+    note_launches(3);
   }
   const int nc = (int)lev[nl - 1].N;
   k_dense_apply32<<<dim3((nc + kThreads - 1) / kThreads, ne), kThreads, sizeof(float) * nc, s>>>(W.Xf, nc, W.b[nl - 1],
                                                                                                   W.x[nl - 1]);
   note_launches(1);
   for (int l = nl - 2; l >= 0; --l) {
-    k_prolong_add32<<<dim3(nblk(lev[l].N), (ne + kFpt - 1) / kFpt), kThreads, 0, s>>>(lev[l], lev[l + 1], ne,
-                                                                                    W.x[l + 1], W.x[l]);
-    note_launches(1);
-    smooth32(W, lev, l, ne, K, W.b[l], W.x[l], false, s);
+    const Coef32 C = coef_of(W, l);
+    const unsigned nb = nblk(lev[l].N);
+    k_prolong_add32<<<nb * ng, kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.x[l + 1], W.x[l]);
+    k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
+    k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.r[l], W.x[l], 0, K.beta, K.c2t);
+    note_launches(3);
   }
 }
 

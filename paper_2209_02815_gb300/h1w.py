@@ -406,6 +406,38 @@ def h1w_destroy(ctx) -> None:
         load().h1w_destroy(ctx)
 
 
+def save_gn_checkpoint(path: str, step: int, m, U, hist) -> None:
+    """Writes the state of a Gauss-Newton loop after `step` steps: the iterate m, the pole
+    fields U (the next forward solve's warm start) and the per-step GnInfo records. The file
+    is written beside `path` and renamed over it, so a reader sees the old or the new state."""
+    state = {"format": "h1w-gn-checkpoint-1", "step": int(step), "m": m.detach().cpu(),
+             "U": U.detach().cpu(),
+             "hist": [{f: getattr(h, f) for f, _ in GnInfo._fields_} for h in hist]}
+    tmp = path + ".tmp"
+    torch.save(state, tmp)
+    os.replace(tmp, path)
+
+
+def load_gn_checkpoint(path: str, m, U):
+    """Reads a checkpoint of save_gn_checkpoint into m and U (copied in place; the shapes
+    must match) and returns (step, list of GnInfo)."""
+    state = torch.load(path, map_location="cpu", weights_only=True)
+    if state.get("format") != "h1w-gn-checkpoint-1":
+        raise ValueError(f"{path}: not an h1w Gauss-Newton checkpoint")
+    if tuple(state["m"].shape) != tuple(m.shape) or tuple(state["U"].shape) != tuple(U.shape):
+        raise ValueError(f"{path}: checkpoint shapes {tuple(state['m'].shape)}, {tuple(state['U'].shape)} "
+                         f"do not match m {tuple(m.shape)}, U {tuple(U.shape)}")
+    m.copy_(state["m"])
+    U.copy_(state["U"])
+    hist = []
+    for rec in state["hist"]:
+        h = GnInfo()
+        for f, _ in GnInfo._fields_:
+            setattr(h, f, rec[f])
+        hist.append(h)
+    return int(state["step"]), hist
+
+
 class Solver:
     """Owns a workspace tensor and a context for one grid (convenience wrapper).
 
@@ -573,11 +605,15 @@ class Solver:
         return JTr, J
 
     def gn_inversion(self, survey: Survey, g_obs, m_ref, m, steps: int, rtol_fwd: float = 1e-10,
-                     rtol: float = 1e-8, maxit: int = 500, warm: bool = True):
+                     rtol: float = 1e-8, maxit: int = 500, warm: bool = True, checkpoint: str | None = None):
         """Algorithm "Gauss-Newton with iterative solver": `steps` passes of h1w_gn_step
         from m (updated in place); from the second step on, each forward solve starts from
         the previous iterate's fields when warm. Returns the per-step GnInfo list and the
-        last g, J."""
+        last g, J.
+
+        checkpoint: a file path. When it holds a checkpoint of an earlier call, the loop
+        resumes from it (m, the fields and the step count; `steps` counts the steps already
+        taken), and after every step the state is written there again (save_gn_checkpoint)."""
         dev = m.device
         ws = self.ert_workspace(survey)
         U = torch.empty((survey.n_e, self.N), dtype=torch.float64, device=dev)
@@ -586,12 +622,18 @@ class Solver:
         scratch = torch.empty(3 * self.N + survey.m, dtype=torch.float64, device=dev)
         self.J = J
         hist = []
+        start = 0
+        if checkpoint is not None and os.path.exists(checkpoint):
+            start, hist = load_gn_checkpoint(checkpoint, m, U)
         self._enter(g_obs, m_ref, m, U, J, g, scratch, ws)
         try:
-            for i in range(steps):
+            for i in range(start, steps):
                 flags = H1W_FORWARD_WARM_START if (warm and i > 0) else 0
                 hist.append(h1w_gn_step(self.ctx, survey, g_obs, m_ref, m, U, J, g, scratch, ws, rtol_fwd, rtol,
                                         maxit, self.N, fwd_flags=flags))
+                if checkpoint is not None:
+                    torch.cuda.synchronize(dev)
+                    save_gn_checkpoint(checkpoint, i + 1, m, U, hist)
         finally:
             self._leave()
         self.m = survey.m

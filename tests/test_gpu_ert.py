@@ -219,6 +219,32 @@ def test_gn_inversion_reduces_misfit():
     assert all(h_.rel_res_true < 1e-7 for h_ in hist)
 
 
+def test_gn_inversion_checkpoint_resume(tmp_path):
+    """Two steps written to a checkpoint, then a fresh context resumes to step three: the
+    iterate equals that of three uninterrupted steps bit for bit (the checkpoint keeps the
+    pole fields, so the resumed forward solve starts warm as the uninterrupted one does)."""
+    n = 16
+    cells, abmn, k, _ = inputs.gn_survey(n, m_rows=200)
+    sv = h1w.Survey(cells, abmn, k, ALL_BUT_TOP)
+    mk = lambda: h1w.Solver(h1w.H1W_FV_CELL, (n,) * 3, (1 / n,) * 3, 100.0, sv.m, device=DEV)
+    s = mk()
+    ls_true = torch.tensor(inputs.gn_truth(n), device=DEV)
+    g_true, _, _ = s.forward(sv, ls_true, rtol=1e-12)
+    g_obs = torch.tensor(inputs.noisy(g_true.cpu().numpy()), device=DEV)
+    m_ref = torch.full((n ** 3,), np.log(0.01), dtype=torch.float64, device=DEV)
+    m_straight = m_ref.clone()
+    hist3, _, _ = s.gn_inversion(sv, g_obs, m_ref, m_straight, 3)
+    ck = str(tmp_path / "gn.pt")
+    m_a = m_ref.clone()
+    hist2, _, _ = mk().gn_inversion(sv, g_obs, m_ref, m_a, 2, checkpoint=ck)
+    assert len(hist2) == 2 and torch.equal(m_a, torch.load(ck, weights_only=True)["m"].to(DEV))
+    m_b = torch.full_like(m_ref, 123.0)                    # overwritten from the checkpoint
+    hist_b, _, _ = mk().gn_inversion(sv, g_obs, m_ref, m_b, 3, checkpoint=ck)
+    assert len(hist_b) == 3 and [h_.gn_iters for h_ in hist_b] == [h_.gn_iters for h_ in hist3]
+    assert torch.equal(m_b, m_straight)
+    assert torch.load(ck, weights_only=True)["step"] == 3
+
+
 def test_forward_warm_start():
     """From the fields of a nearby model the forward solve reaches the same fields in
     fewer iterations (H1W_FORWARD_WARM_START)."""
