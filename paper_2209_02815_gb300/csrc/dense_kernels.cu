@@ -257,6 +257,7 @@ __global__ void __launch_bounds__(kThreads) k_woodbury_update_df(
 
 constexpr int kNB = 32;
 constexpr int kCholThreads = 256;  // the diagonal block's warp keeps a 32-double row in registers
+constexpr int kCholRows = kCholThreads / 32;  // panel rows per block of k_chol_panel
 
 // Cholesky of the nb x nb lower triangle in Ld, in place, by warp 0 of the block (lane r
 // holds row r in registers; column c's entries reach the other lanes by shuffles, and each
@@ -277,7 +278,7 @@ __device__ void factor_diag_block(double (*Ld)[kNB + 1], int nb, int* status) {
           if (status && lane == 0) atomicOr(status, kStatusNotSpd);
           piv = 1.0;
         }
-        const double d = sqrt(piv), inv = 1.0 / d;
+        const double inv = rsqrt(piv), d = piv * inv;
         if (lane == c) {
           row[c] = d;
           rdiag = inv;
@@ -315,8 +316,9 @@ __device__ __forceinline__ int load_factor_diag(const double* A, int n, int kb, 
   return nb;
 }
 
-// L21: one block per 32-row block below the panel (grid.x = their number, blockDim = 1024).
-// Each block factors A11 again from A and solves its rows against it. A11 must still be
+// L21: one block per kCholRows rows below the panel, one warp per row. Each block factors
+// A11 again from A (the factorization is a latency chain of one warp, so repeating it in
+// every block costs no time) and solves its rows against it. A11 must still be
 // unfactored in A while any of these blocks may start (the blocks of a launch need not
 // run together), so block 0 parks L11 where no block of this launch reads (its strict
 // lower part transposed into the upper triangle of A11, its diagonal in column kb + 32 of
@@ -334,11 +336,11 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_panel(double* A, int n, i
       if (r < nb && c == r) A[(int64_t)(kb + r) * n + kb + kNB] = Ld[r][r];
     }
   }
-  // rows of this block: solve x L11^T = a for each row (warp w -> rows w, w + 8, ...)
+  // rows of this block: solve x L11^T = a for each row (one row per warp)
   const int lane = tid & 31;
-  for (int w = tid >> 5; w < kNB; w += kCholThreads / 32) {
-    const int row = kb + kNB * (blockIdx.x + 1) + w;
-    if (row >= n) break;
+  {
+    const int row = kb + kNB + blockIdx.x * kCholRows + (tid >> 5);
+    if (row >= n) return;
     double a = (lane < nb) ? A[(int64_t)row * n + kb + lane] : 0.0;
     for (int c = 0; c < nb; ++c) {
       double xc = 0.0;
@@ -972,7 +974,8 @@ void launch_chol(double* A, int n, int* status, cudaStream_t s) {
   for (int kb = 0; kb < n; kb += kNB) {
     const int below = (n - kb - 1) / kNB;  // 32-row blocks after the diagonal block
     if (below > 0) {
-      k_chol_panel<<<below, kCholThreads, 0, s>>>(A, n, kb, status);
+      const int rows = n - kb - kNB;
+      k_chol_panel<<<(rows + kCholRows - 1) / kCholRows, kCholThreads, 0, s>>>(A, n, kb, status);
       const int tiles = below * (below + 1) / 2;
       k_chol_update<<<tiles + 1, 256, 0, s>>>(A, n, kb);
       note_launches(2);

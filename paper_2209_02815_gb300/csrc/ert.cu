@@ -27,6 +27,7 @@
 // same kernel accumulates J^T r without storing J.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -371,6 +372,62 @@ __global__ void k_restrict32(Level Lf, Level Lc, int ne, const float* __restrict
   }
 }
 
+// The restriction on a level whose x axis is coarsened: a thread takes the coarse pair
+// (2t, 2t + 1) of one row, whose x footprints are fine cells 4t - 1 .. 4t + 2 and
+// 4t + 1 .. 4t + 4, and reads each fine row segment once: 4t .. 4t + 3 as two 8-byte loads
+// (fine rows have an even length, so 4t is 8-byte aligned), 4t - 1 and 4t + 4 alone where
+// they exist. Half the load instructions of one coarse cell per thread. Grid: (pairs / 256,
+// fields); every other coarse quantity as in k_restrict32.
+__global__ void k_restrict32_pairs(Level Lf, Level Lc, int ne, const float* __restrict__ rf,
+                                   float* __restrict__ bc) {
+  const int nx2 = (Lc.nx + 1) >> 1;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t npair = (int64_t)nx2 * Lc.ny * Lc.nz;
+  if (q >= npair) return;
+  const unsigned u = (unsigned)q;
+  const unsigned row = u / (unsigned)nx2;
+  const int t = (int)(u - row * (unsigned)nx2);
+  const int K = (int)(row / (unsigned)Lc.ny), J = (int)(row - (unsigned)K * Lc.ny);
+  const int e = (int)blockIdx.y;
+  if (e >= ne) return;
+  const int I0 = 2 * t, I1 = I0 + 1;
+  const bool has1 = I1 < Lc.nx;
+  // x weights of the two coarse cells at fine offsets -1 .. 4 from 4t (0 where not used)
+  float a[6], b[6];
+  {
+    const bool lo0 = I0 >= 1, hi0 = I0 + 1 < Lc.nx;
+    a[0] = lo0 ? 0.25f : 0.f; a[1] = lo0 ? 0.75f : 1.f; a[2] = hi0 ? 0.75f : 1.f; a[3] = hi0 ? 0.25f : 0.f;
+    a[4] = 0.f; a[5] = 0.f;
+    const bool hi1 = I1 + 1 < Lc.nx;
+    b[0] = 0.f; b[1] = 0.f;
+    b[2] = has1 ? 0.25f : 0.f; b[3] = has1 ? 0.75f : 0.f;
+    b[4] = has1 ? (hi1 ? 0.75f : 1.f) : 0.f; b[5] = (has1 && hi1) ? 0.25f : 0.f;
+  }
+  int fy[4], fz[4];
+  float wy[4], wz[4];
+  rst_1d(J, Lc.ny, Lf.cy, fy, wy);
+  rst_1d(K, Lc.nz, Lf.cz, fz, wz);
+  const int x0 = 4 * t;
+  const bool left = x0 >= 1, right = x0 + 4 < Lf.nx, mid2 = x0 + 2 < Lf.nx;
+  const float* r = rf + (int64_t)e * Lf.N;
+  float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) {
+      const float* rw = r + ((int64_t)fz[c] * Lf.ny + fy[bb]) * Lf.nx + x0;
+      const float2 m0 = *reinterpret_cast<const float2*>(rw);
+      const float2 m1 = mid2 ? *reinterpret_cast<const float2*>(rw + 2) : make_float2(0.f, 0.f);
+      const float vl = left ? rw[-1] : 0.f, vr = right ? rw[4] : 0.f;
+      const float w = wy[bb] * wz[c];
+      acc0 += w * (a[0] * vl + a[1] * m0.x + a[2] * m0.y + a[3] * m1.x);
+      acc1 += w * (b[2] * m0.y + b[3] * m1.x + b[4] * m1.y + b[5] * vr);
+    }
+  float* out = bc + (int64_t)e * Lc.N + ((int64_t)K * Lc.ny + J) * Lc.nx + I0;
+  out[0] = acc0;
+  if (has1) out[1] = acc1;
+}
+
 // grid: (fine cells / 256, fields)
 __global__ void k_prolong_add32(Level Lf, Level Lc, int ne, const float* __restrict__ xc, float* __restrict__ xf) {
   const unsigned ng = (unsigned)((ne + kFpt - 1) / kFpt), grp = blockIdx.x % ng;  // field groups fastest
@@ -397,6 +454,53 @@ __global__ void k_prolong_add32(Level Lf, Level Lc, int ne, const float* __restr
         acc += wy[b] * wz[cc] * (wx[0] * row[fx[0]] + wx[1] * row[fx[1]]);
       }
     xf[(int64_t)e * Lf.N + p] += acc;
+  }
+}
+
+// The prolongation on a level whose x axis is coarsened: a thread takes the fine pair
+// (2I, 2I + 1) of one row, the two children of coarse cell I, which read coarse cells I - 1,
+// I and I + 1 of each coarse row (three loads for two fine cells instead of four) and are
+// read and written as one 8-byte pair. Same arithmetic, in the same order, as
+// k_prolong_add32; the field groups of a pair block are adjacent in the 1D grid.
+__global__ void k_prolong_add32_pairs(Level Lf, Level Lc, int ne, const float* __restrict__ xc,
+                                      float* __restrict__ xf) {
+  const unsigned ng = (unsigned)((ne + kFpt - 1) / kFpt), grp = blockIdx.x % ng;
+  const int64_t q = (int64_t)(blockIdx.x / ng) * blockDim.x + threadIdx.x;
+  const int64_t npair = (int64_t)Lc.nx * Lf.ny * Lf.nz;
+  if (q >= npair) return;
+  const unsigned u = (unsigned)q;
+  const unsigned row = u / (unsigned)Lc.nx;
+  const int I = (int)(u - row * (unsigned)Lc.nx);
+  const int k = (int)(row / (unsigned)Lf.ny), j = (int)(row - (unsigned)k * Lf.ny);
+  int fy[2], fz[2];
+  float wy[2], wz[2];
+  prl_1d(j, Lc.ny, Lf.cy, fy, wy);
+  prl_1d(k, Lc.nz, Lf.cz, fz, wz);
+  const bool hl = I >= 1, hr = I + 1 < Lc.nx;
+  const float a0 = hl ? 0.75f : 1.f, a1 = hl ? 0.25f : 0.f;  // fine 2I: the parent and its left neighbour
+  const float b0 = hr ? 0.75f : 1.f, b1 = hr ? 0.25f : 0.f;  // fine 2I + 1: the parent and its right one
+  const int Il = hl ? I - 1 : I, Ir = hr ? I + 1 : I;
+  const int64_t pf = ((int64_t)k * Lf.ny + j) * Lf.nx + 2 * I;
+#pragma unroll
+  for (int f = 0; f < kFpt; ++f) {
+    const int e = (int)grp * kFpt + f;
+    if (e >= ne) break;
+    const float* c = xc + (int64_t)e * Lc.N;
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const float* rw = c + ((int64_t)fz[cc] * Lc.ny + fy[b]) * Lc.nx;
+        const float vm = rw[I];
+        s0 += wy[b] * wz[cc] * (a0 * vm + a1 * rw[Il]);
+        s1 += wy[b] * wz[cc] * (b0 * vm + b1 * rw[Ir]);
+      }
+    float2* xp = reinterpret_cast<float2*>(xf + (int64_t)e * Lf.N + pf);
+    float2 v = *xp;
+    v.x += s0;
+    v.y += s1;
+    *xp = v;
   }
 }
 
@@ -760,7 +864,12 @@ void vcycle32(const Layout& W, const Level* lev, int nl, int ne, const Cheb& K, 
     const unsigned nb = nblk(lev[l].N);
     k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], 1, K.beta, K.c2t);
     k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
-    k_restrict32<<<dim3(nblk(lev[l + 1].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
+    if (lev[l].cx && (reinterpret_cast<uintptr_t>(W.r[l]) & 7) == 0) {  // 8-byte loads need an aligned workspace
+      const int64_t npair = (int64_t)((lev[l + 1].nx + 1) / 2) * lev[l + 1].ny * lev[l + 1].nz;
+      k_restrict32_pairs<<<dim3(nblk(npair), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
+    } else {
+      k_restrict32<<<dim3(nblk(lev[l + 1].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
+    }
     note_launches(3);
   }
   const int nc = (int)lev[nl - 1].N;
@@ -770,7 +879,12 @@ void vcycle32(const Layout& W, const Level* lev, int nl, int ne, const Cheb& K, 
   for (int l = nl - 2; l >= 0; --l) {
     const Coef32 C = coef_of(W, l);
     const unsigned nb = nblk(lev[l].N);
-    k_prolong_add32<<<nb * ng, kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.x[l + 1], W.x[l]);
+    if (lev[l].cx && (reinterpret_cast<uintptr_t>(W.x[l]) & 7) == 0) {  // 8-byte pairs need an aligned workspace
+      const int64_t npair = (int64_t)lev[l + 1].nx * lev[l].ny * lev[l].nz;
+      k_prolong_add32_pairs<<<nblk(npair) * ng, kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.x[l + 1], W.x[l]);
+    } else {
+      k_prolong_add32<<<nb * ng, kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.x[l + 1], W.x[l]);
+    }
     k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
     k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.r[l], W.x[l], 0, K.beta, K.c2t);
     note_launches(3);
