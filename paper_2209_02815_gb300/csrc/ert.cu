@@ -583,15 +583,47 @@ __global__ void k_dots(int64_t N, const double* __restrict__ a, const double* __
 }
 
 // z = (double) z32; partials r . z and z . q
-__global__ void k_z_dots(int64_t N, const float* __restrict__ z32, double* __restrict__ z, const double* __restrict__ r,
+// A float as the equal double, by assembling the IEEE 754 bit fields with integer
+// instructions (a conversion instruction runs on the FP64 pipe, which GB300 issues at 1/64
+// of the FP32 rate). Zeros keep their sign; subnormal floats (below 2^-126, about 1.2e-38)
+// become zero; infinities and NaNs keep their class. In J = -k_i (hi + lo) this drops lo
+// only when |lo| < 2^-126, i.e. |hi| below about 2^-102 (2e-31): such an entry keeps
+// its hi part, and its absolute error stays below |k_i| 2^-126.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u) return __hiloint2double(static_cast<int>(u & 0x80000000u), 0);
+  const unsigned e11 = (e == 0xFFu) ? 0x7FFu : e + (1023u - 127u);
+  const unsigned hi = (u & 0x80000000u) | (e11 << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
+}
+
+// A double as a float by its bit fields, rounding toward zero: the FP32 cycle's input needs
+// no correct rounding, and this keeps the conversion off the FP64 pipe. Magnitudes below the
+// float normal range become zero, above it infinity; NaNs stay NaNs.
+__device__ __forceinline__ float d2f_trunc(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = static_cast<int>((hi >> 20) & 0x7FFu);
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // the top 23 significand bits
+  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+  const int ef = e - 1023 + 127;
+  if (ef <= 0) return __uint_as_float(sign);
+  if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | (static_cast<unsigned>(ef) << 23) | m);
+}
+
+// The preconditioned residual z stays in the cycle's FP32 output; the PCG kernels widen it
+// to FP64 where they read it, by f2d_bits (no FP64-pipe conversion, no FP64 copy of z).
+__global__ void k_z_dots(int64_t N, const float* __restrict__ z32, const double* __restrict__ r,
                          const double* __restrict__ q, double* __restrict__ partial) {
   __shared__ double red[kThreads / 32];
   const int e = blockIdx.y, ne = gridDim.y;
   double s0 = 0.0, s1 = 0.0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = e * N + p;
-    const double zv = (double)z32[o];
-    z[o] = zv;
+    const double zv = f2d_bits(z32[o]);
     s0 += r[o] * zv;
     if (q) s1 += zv * q[o];
   }
@@ -603,7 +635,7 @@ __global__ void k_z_dots(int64_t N, const float* __restrict__ z32, double* __res
   }
 }
 
-// x += alpha p; r -= alpha q; b32 = (float) r; partial r . r
+// x += alpha p; r -= alpha q; b32 = r in FP32 (truncated); partial r . r
 __global__ void k_xr(int64_t N, const double* __restrict__ scal, double* __restrict__ x, double* __restrict__ r,
                      const double* __restrict__ p_, const double* __restrict__ q, float* __restrict__ b32,
                      double* __restrict__ partial) {
@@ -616,20 +648,22 @@ __global__ void k_xr(int64_t N, const double* __restrict__ scal, double* __restr
     x[o] += a * p_[o];
     const double rv = r[o] - a * q[o];
     r[o] = rv;
-    b32[o] = (float)rv;
+    b32[o] = d2f_trunc(rv);
     s0 += rv * rv;
   }
   s0 = block_sum(s0, red);
   if (threadIdx.x == 0) partial[(int64_t)e * gridDim.x + blockIdx.x] = s0;
 }
 
-// p = z + beta p
-__global__ void k_pupd(int64_t N, const double* __restrict__ scal, const double* __restrict__ z, double* __restrict__ p_) {
+// p = z + beta p (first: p = z)
+__global__ void k_pupd(int64_t N, const double* __restrict__ scal, const float* __restrict__ z32,
+                       double* __restrict__ p_, int first) {
   const int e = blockIdx.y, ne = gridDim.y;
-  const double be = scal[kBeta * ne + e];
+  const double be = first ? 0.0 : scal[kBeta * ne + e];
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = e * N + p;
-    p_[o] = z[o] + be * p_[o];
+    const double zv = f2d_bits(z32[o]);
+    p_[o] = first ? zv : zv + be * p_[o];
   }
 }
 
@@ -685,20 +719,6 @@ __global__ void k_measure(const double* __restrict__ U, int64_t N, const int* __
 // FP64 and stored as double-floats, then the warps' partial sums of J^T r. The products
 // and sums of a row run in double-float arithmetic (about 48 bits) on the FP32 pipes, which
 // GB300 issues at 64 times its FP64 rate; only the scaling by -k_i is FP64.
-// A float as the equal double, by assembling the IEEE 754 bit fields with integer
-// instructions (a conversion instruction runs on the FP64 pipe, which GB300 issues at 1/64
-// of the FP32 rate). Zeros keep their sign; subnormal floats (below 2^-126, about 1.2e-38)
-// become zero; infinities and NaNs keep their class. In J = -k_i (hi + lo) this drops lo
-// only when |lo| < 2^-126, i.e. |hi| below about 2^-102 (2e-31): such an entry keeps
-// its hi part, and its absolute error stays below |k_i| 2^-126.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xFFu;
-  if (e == 0u) return __hiloint2double(static_cast<int>(u & 0x80000000u), 0);
-  const unsigned e11 = (e == 0xFFu) ? 0x7FFu : e + (1023u - 127u);
-  const unsigned hi = (u & 0x80000000u) | (e11 << 20) | ((u & 0x7FFFFFu) >> 3);
-  return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
-}
 
 // MODE kRows writes the rows of J, kJTr writes J^T r (r = rv), kJvp writes the per-block
 // partial sums of J p (p = rv, indexed by cell) to J[i * gridDim.x + block].
@@ -1027,10 +1047,10 @@ h1w_status ert_forward(const Level* lev, int nl, cudaStream_t s, const h1w_surve
     note_launches(1);
   }
   vcycle32(W, lev, nl, ne, K, s);
-  k_z_dots<<<vg, kThreads, 0, s>>>(N, W.x[0], W.z64, W.r64, nullptr, W.partial);
+  k_z_dots<<<vg, kThreads, 0, s>>>(N, W.x[0], W.r64, nullptr, W.partial);
   k_scalars<<<sb, 128, 0, s>>>(0, ne, kDotBlocks, W.partial, W.scal, tol2);
-  cudaMemcpyAsync(W.p64, W.z64, sizeof(double) * N * ne, cudaMemcpyDeviceToDevice, s);
-  note_launches(2);
+  k_pupd<<<vg, kThreads, 0, s>>>(N, W.scal, W.x[0], W.p64, 1);
+  note_launches(3);
   int it = 0;
   bool done = false;
   double worst = 1.0;
@@ -1056,9 +1076,9 @@ h1w_status ert_forward(const Level* lev, int nl, cudaStream_t s, const h1w_surve
       break;
     }
     vcycle32(W, lev, nl, ne, K, s);
-    k_z_dots<<<vg, kThreads, 0, s>>>(N, W.x[0], W.z64, W.r64, W.q64, W.partial);
+    k_z_dots<<<vg, kThreads, 0, s>>>(N, W.x[0], W.r64, W.q64, W.partial);
     k_scalars<<<sb, 128, 0, s>>>(3, ne, kDotBlocks, W.partial, W.scal, tol2);
-    k_pupd<<<vg, kThreads, 0, s>>>(N, W.scal, W.z64, W.p64);
+    k_pupd<<<vg, kThreads, 0, s>>>(N, W.scal, W.x[0], W.p64, 0);
     note_launches(3);
   }
   if (sv->m > 0) {
