@@ -835,7 +835,7 @@ def run_ours(args):
     tiles = sum(max(0, (m + 63) // 64 - 2 * I) for I in range((m + 127) // 128))
     kp = min(((N + 2047) // 2048) * 2048, 262144)
     panels = (N + kp - 1) // kp
-    gemm_flops_launch = tiles * 36 * 2.0 * 128 * 64 * kp        # digit-pair products per panel launch
+    gemm_flops_launch = tiles * 28 * 2.0 * 128 * 64 * kp        # digit-pair products per panel launch
     table = {}
     def rate(name, total_ms, n, per_launch, unit, bound, peak, note):
         if n == 0 or total_ms <= 0:
@@ -882,13 +882,13 @@ def run_ours(args):
     rate("k_woodbury_update_df (z update)", kern["hupd"][0], kern["hupd"][1], mat + 32.0 * N, "GB/s", "hbm", hbm,
          "bytes of H, z0, r and z per pass")
     # operand preparation of line C and line H: per panel, the split of J (FP64 in) and of H
-    # (double-float in) writes eight BF16 digits (16 bytes) per entry plus one exponent per
-    # 1024-entry chunk; the conversion of J to double-floats reads 8 and writes 8 bytes per entry
+    # (double-float in) writes seven BF16 digits (14 bytes) per entry plus one exponent per
+    # 512-entry chunk; the conversion of J to double-floats reads 8 and writes 8 bytes per entry
     kw_avg = float(N) / panels
-    rate("k_split_digits<double> (J digits)", kern["split_j"][0], kern["split_j"][1], 24.0 * m * kw_avg, "GB/s",
-         "hbm", hbm, "8 bytes of J in, 16 bytes of digits out per entry of one K panel")
-    rate("k_split_digits<df> (H digits)", kern["split_h"][0], kern["split_h"][1], 24.0 * m * kw_avg, "GB/s",
-         "hbm", hbm, "8 bytes of H (double-float) in, 16 bytes of digits out per entry of one K panel")
+    rate("k_split_digits<double> (J digits)", kern["split_j"][0], kern["split_j"][1], 22.0 * m * kw_avg, "GB/s",
+         "hbm", hbm, "8 bytes of J in, 14 bytes of digits out per entry of one K panel")
+    rate("k_split_digits<df> (H digits)", kern["split_h"][0], kern["split_h"][1], 22.0 * m * kw_avg, "GB/s",
+         "hbm", hbm, "8 bytes of H (double-float) in, 14 bytes of digits out per entry of one K panel")
     if kern["d2df"][1]:
         rate("k_d2df (J to double-floats, line H)", kern["d2df"][0], kern["d2df"][1],
              16.0 * m * N * args.steps / kern["d2df"][1], "GB/s", "hbm", hbm,

@@ -417,8 +417,8 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   const long long kp = ozaki_panel_width(N0);
   OzakiWork ow{};
   if (oz) {
-    ow.digitsA = B.take<uint16_t>((size_t)8 * ((m_max + 127) / 128 * 128) * kp);
-    ow.digitsB = B.take<uint16_t>((size_t)8 * ((m_max + 63) / 64 * 64) * kp);
+    ow.digitsA = B.take<uint16_t>((size_t)ozaki_digit_slices() * ((m_max + 127) / 128 * 128) * kp);
+    ow.digitsB = B.take<uint16_t>((size_t)ozaki_digit_slices() * ((m_max + 63) / 64 * 64) * kp);
     ow.expo = B.take<int>(2 * (size_t)m_max * ozaki_chunks(N0));
     ow.tiles = B.take<int>(2 * (size_t)ozaki_num_tiles(m_max));
     ow.klen = kp;
@@ -1317,7 +1317,8 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
         c);
     c->timing_on = false;
     if (!ok)
-      return fail(c, H1W_ECUDA, "capacitance: tensor map encoding or kernel attribute failed");
+      return fail(c, H1W_ECUDA, std::string("capacitance: tensor-core GEMM not launched: ") +
+                                    cudaGetErrorString(cudaGetLastError()));
   } else {                                                          // line C, FP64 CUDA cores
     splits = cap_gemm_splits(m, N);
     c->timing_on = true;

@@ -89,6 +89,7 @@ struct OzakiWork {
 };
 long long ozaki_panel_width(long long N);
 long long ozaki_chunks(long long N);
+int ozaki_digit_slices();  // BF16 digit slices per operand entry
 int ozaki_num_tiles(int m);
 constexpr int kMaxSms = 256;  // SM counts above this are treated as this many
 // K splits per panel for a GPU with sms SMs; never above ozaki_max_splits(m)

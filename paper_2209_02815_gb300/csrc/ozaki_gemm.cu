@@ -10,31 +10,32 @@
 // "digits" and multiplied digit by digit on the tensor cores, with every
 // FP32 accumulation kept exact:
 //
-//  * Chunk scaling: for each row i of J (or H) and each chunk c of 1024
+//  * Chunk scaling: for each row i of J (or H) and each chunk c of 512
 //    consecutive K entries an exponent e_ic with max_{k in c} |x_ik| < 2^e_ic.
-//    Each entry becomes the integer Y = round(x 2^(47 - e_ic)), |Y| <= 2^47,
-//    written in balanced base 64 as eight digits Y = sum_p d_p 64^(7-p),
-//    d_p in [-32, 32]; each digit is exact in BF16. Scaling per chunk rather
+//    Each entry becomes the integer Y = round(x 2^(48 - e_ic)), |Y| <= 2^48,
+//    written in balanced base 128 as seven digits Y = sum_p d_p 128^(6-p),
+//    d_1..d_6 in [-64, 63], |d_0| <= 65; each digit is exact in BF16. Scaling per chunk rather
 //    than per row keeps the error of the dropped digit pairs proportional to
 //    the chunk's own maxima, which matters for sensitivity rows that peak
 //    sharply near the electrodes (a 100-fold smaller error in C there).
-//  * Digit products d_p d'_q (|.| <= 2^10) of the same level l = p + q are
+//  * Digit products d_p d'_q (|.| <= 65 * 64) of the same level l = p + q are
 //    summed into one FP32 TMEM accumulator (64 columns per level); pairs with
-//    p + q > 7 (weight below 2^-48) are dropped, leaving 36 pairs in 8 levels,
-//    issued as 12 MMAs per 16-wide K step (digit p of J against a stack of
+//    p + q > 6 (weight below 2^-49) are dropped, leaving 28 pairs in 7 levels,
+//    issued as 10 MMAs per 16-wide K step (digit p of J against a stack of
 //    consecutive digits of H lands on consecutive levels). Over a chunk of
-//    1024 K entries a level sum is an integer below 8 * 1024 * 2^10 = 2^23,
-//    so the FP32 accumulation is exact.
-//  * After every chunk the epilogue warps read the 8 level sums from TMEM,
-//    combine them exactly in 64-bit integers as T_hi = sum_{l<4} S_l 64^(3-l)
-//    and T_lo = sum_{l>=4} S_l 64^(7-l), and add
-//    2^(e_ic + f_jc - 52) (2^24 T_hi + T_lo) to FP64 accumulators.
+//    512 K entries a level sum is an integer below 512 (2 * 65 * 64 + 5 * 64^2)
+//    < 2^24, so the FP32 accumulation is exact. (Base 64, eight digits and
+//    1024-entry chunks take 36 pairs for the same 48 bits.)
+//  * After every chunk the epilogue warps read the 7 level sums from TMEM,
+//    combine them as T_hi = sum_{l<4} S_l 128^(3-l) (exactly, 64-bit integers)
+//    and T_lo = sum_{l>=4} S_l 128^(6-l) (FP32, |T_lo| < 2^38), and add
+//    2^(e_ic + f_jc - 54) (2^21 T_hi + T_lo) to FP64 accumulators.
 //
 // Kernel layout: one CTA per (128 x 64 output tile, K range); warp 0 moves
-// all eight digit slices of both operands per 32-wide K stage with two bulk
+// all seven digit slices of both operands per 32-wide K stage with two bulk
 // copies (the digits are stored pre-swizzled in the stage's shared-memory
-// image; 64-byte swizzle, double buffered), warp 1 owns TMEM (512 columns = 8
-// levels x 64) and issues tcgen05.mma, warps 2..9 drain TMEM. Every
+// image; 64-byte swizzle, double buffered), warp 1 owns TMEM (512 columns, of
+// which 7 levels x 64 are used) and issues tcgen05.mma, warps 2..17 drain TMEM. Every
 // mbarrier wait is bounded (about one second); on expiry the CTA records
 // status bit kStatusTimeout, drains what it started and returns.
 #include <cuda_bf16.h>
@@ -48,19 +49,21 @@
 namespace h1w {
 namespace {
 
-constexpr int kSlices = 8;
+constexpr int kSlices = 7;
+constexpr int kLevels = 7;                 // digit-pair levels kept: p + q <= 6
 constexpr int kTileM = 128;                // rows of J per tile (TMEM lanes)
 constexpr int kTileN = 64;                 // rows of H per tile (columns per level)
 constexpr int kKt = 32;                    // K per stage: 64-byte rows
-constexpr int kChunkK = 1024;              // K per exact accumulation chunk
+constexpr int kChunkK = 512;               // K per exact accumulation chunk
 constexpr int kItersPerChunk = kChunkK / kKt;
-constexpr int kABytes = kSlices * kTileM * kKt * 2;   // 65536
-constexpr int kBBytes = kSlices * kTileN * kKt * 2;   // 32768
-constexpr int kStageBytes = kABytes + kBBytes;        // 98304
+constexpr int kABytes = kSlices * kTileM * kKt * 2;   // 57344
+constexpr int kBBytes = kSlices * kTileN * kKt * 2;   // 28672
+constexpr int kStageBytes = kABytes + kBBytes;        // 86016 (a multiple of 1024)
 constexpr int kStages = 2;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 128;
-constexpr int kGemmThreads = 320;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;              // 4 lane quadrants x 4 quarters of the 64 columns
+constexpr int kEpiCols = kTileN / 4;       // columns per epilogue thread
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // one second per wait
 // and at most this many polls per wait, should the global timer not advance (a legitimate
 // wait, for one copy or one MMA, lasts microseconds)
@@ -131,14 +134,12 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -161,6 +162,7 @@ struct OzakiArgs {
   int stall;            // failure-path test: the copy warp issues nothing, so every consumer's wait runs out
 };
 
+// 18 warps: four or five per SM sub-partition (16K registers each) cap a thread at 96 registers
 __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -227,11 +229,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
 #pragma unroll
       for (int nq = 1; nq <= 4; ++nq)
         idesc[nq] = (1u << 4) | (1u << 7) | (1u << 10) | (((nq * kTileN) >> 3) << 17) | ((kTileM >> 4) << 24);
-      // (p, q0, nq) covering every pair p + q <= 7 once, N <= 256 per MMA
-      constexpr int kMmas = 12;
-      constexpr int kP[kMmas] = {0, 0, 1, 1, 2, 2, 3, 3, 4, 5, 6, 7};
-      constexpr int kQ0[kMmas] = {0, 4, 0, 4, 0, 4, 0, 4, 0, 0, 0, 0};
-      constexpr int kNq[kMmas] = {4, 4, 4, 3, 4, 2, 4, 1, 4, 3, 2, 1};
+      // (p, q0, nq) covering every pair p + q <= 6 once, N <= 256 per MMA
+      constexpr int kMmas = 10;
+      constexpr int kP[kMmas] = {0, 0, 1, 1, 2, 2, 3, 4, 5, 6};
+      constexpr int kQ0[kMmas] = {0, 4, 0, 4, 0, 4, 0, 0, 0, 0};
+      constexpr int kNq[kMmas] = {4, 3, 4, 2, 4, 1, 4, 3, 2, 1};
       int it = 0;
       bool ok = true;
       for (int c = 0; c < nchunks && ok; ++c) {
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
               // descriptor start addresses are in 16-byte units
               const uint64_t ad = adesc0 + static_cast<uint64_t>((kP[u] * kTileM * kKt * 2 + ks * 32) >> 4);
               const uint64_t bd = bdesc0 + static_cast<uint64_t>((kQ0[u] * kTileN * kKt * 2 + ks * 32) >> 4);
-              // the first MMA of a chunk (p = 0, both halves) overwrites all 512 columns
+              // the first MMAs of a chunk (p = 0, both halves) overwrite all 7 levels
               const uint32_t acc = (j == 0 && ks == 0 && kP[u] == 0) ? 0u : 1u;
               mma_bf16(tmem + static_cast<uint32_t>((kP[u] + kQ0[u]) * kTileN), ad, bd, idesc[kNq[u]], acc);
             }
@@ -266,15 +268,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
       if (!ok) *abort_flag = 1;
     }
   } else {
-    // epilogue: warps 2..9; lane quadrant = warp % 4, column half = (warp - 2) / 4
-    const int quad = warp & 3, half = (warp - 2) >> 2;
-    double acc[32];
+    // epilogue: warps 2 .. 2 + kEpiWarps - 1; lane quadrant = warp % 4 (the TMEM lanes a warp
+    // may read), column quarter = (warp - 2) / 4. All seven level sums of a chunk are read
+    // before TMEM is handed back, and the FP64 work of the chunk comes after, so the next
+    // chunk's MMAs wait only for the TMEM loads: the FP64 pipe (1/64 of the FP32 rate) would
+    // otherwise stall the tensor cores for several microseconds per chunk.
+    const int quad = warp & 3, quarter = (warp - 2) >> 2;
+    double acc[kEpiCols];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+    for (int j = 0; j < kEpiCols; ++j) acc[j] = 0.0;
     const int row = row0 + 32 * quad + lane;
-    const int colb = col0 + half * 32;
+    const int colb = col0 + quarter * kEpiCols;
+    const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * quad) << 16) + quarter * kEpiCols;
     for (int c = 0; c < nchunks; ++c) {
-      // per-chunk scale factors 2^(e_row + f_col - 52) for this thread's 32 columns
+      // per-chunk scale factors 2^(e_row + f_col - 54) for this thread's columns
       const long long gch = g.chunk0 + kbeg / kChunkK + c;
       const int er = (row < g.m) ? g.eA[gch * g.m + row] : -100000;
       // lane 0 waits; the warp follows its result so that the .sync.aligned
@@ -285,44 +292,53 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
       if (!ok) { if (lane == 0) *abort_flag = 1; break; }
       __syncwarp();
       tc_fence_after();
+      // levels 0..3 exactly in 64-bit integers: |T_hi| < 2^24 * 128^3 * 1.01 < 2^46
+      long long Thi[kEpiCols];
+#pragma unroll
+      for (int j = 0; j < kEpiCols; ++j) Thi[j] = 0;
 #pragma unroll 1
-      for (int grp = 0; grp < 2; ++grp) {
-        // levels 4 grp .. 4 grp + 3 combined exactly: |T| < 2^23 * 64^3 * 1.02 < 2^42
-        long long T[32];
+      for (int lev = 0; lev < 4; ++lev) {
+        uint32_t v[kEpiCols];
+        tmem_ld16(tbase + lev * kTileN, v);
+        tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) T[j] = 0;
+        for (int j = 0; j < kEpiCols; ++j)
+          Thi[j] = Thi[j] * 128 + static_cast<long long>(__float2int_rn(__uint_as_float(v[j])));
+      }
+      // levels 4..6 in FP32: |T_lo| < 2^38, so its rounding (below 2^15 units of the last
+      // level) stays under the rounding of the digit split itself
+      float Tlo[kEpiCols];
+#pragma unroll
+      for (int j = 0; j < kEpiCols; ++j) Tlo[j] = 0.f;
 #pragma unroll 1
-        for (int lev = 4 * grp; lev < 4 * grp + 4; ++lev) {
-          uint32_t v[32];
-          tmem_ld32(tmem + (static_cast<uint32_t>(32 * quad) << 16) + lev * kTileN + half * 32, v);
-          tmem_wait_ld();
+      for (int lev = 4; lev < kLevels; ++lev) {
+        uint32_t v[kEpiCols];
+        tmem_ld16(tbase + lev * kTileN, v);
+        tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) T[j] = T[j] * 64 + static_cast<long long>(__float2int_rn(__uint_as_float(v[j])));
-        }
-        if (grp == 1) {
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(&bars[5]));  // TMEM may be overwritten now
-        }
-        // the upper group carries the weight 64^4 = 2^24
-        const int wexp = grp == 0 ? 24 : 0;
+        for (int j = 0; j < kEpiCols; ++j) Tlo[j] = fmaf(Tlo[j], 128.f, __uint_as_float(v[j]));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars[5]));  // TMEM may be overwritten now
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = colb + j;
-          const int ec = (col < g.m) ? g.eB[gch * g.m + col] : -100000;
-          const int k2 = er + ec - 52 + wexp;
-          // 2^k2 from its bit pattern (0 below the normal range; such chunks are negligible)
-          const double scale = (k2 >= -1022 && k2 <= 1023)
-                                   ? __longlong_as_double(static_cast<long long>(k2 + 1023) << 52)
-                                   : 0.0;
-          acc[j] = fma(static_cast<double>(T[j]), scale, acc[j]);
-        }
+      for (int j = 0; j < kEpiCols; ++j) {
+        const int col = colb + j;
+        const int ec = (col < g.m) ? g.eB[gch * g.m + col] : -100000;
+        const int k2 = er + ec - 54;
+        // 2^k2 from its bit pattern (0 below the normal range; such chunks are negligible)
+        const double scale = (k2 >= -1022 && k2 <= 1023)
+                                 ? __longlong_as_double(static_cast<long long>(k2 + 1023) << 52)
+                                 : 0.0;
+        // 2^21 T_hi + T_lo (the upper group carries the weight 128^3 = 2^21)
+        const double val = fma(static_cast<double>(Thi[j]), 2097152.0, static_cast<double>(Tlo[j]));
+        acc[j] = fma(val, scale, acc[j]);
       }
     }
     if (!*abort_flag && row < g.m) {
       double* dst = g.partial + static_cast<long long>(blockIdx.y) * g.m * g.m + static_cast<long long>(row) * g.m;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < kEpiCols; ++j) {
         const int col = colb + j;
         if (col < g.m) dst[col] = g.accumulate ? dst[col] + acc[j] : acc[j];
       }
@@ -359,56 +375,56 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
 // ---- operand split ---------------------------------------------------------------
 
 __device__ __forceinline__ long long digits_source(double x, int echunk) {
-  // Y = round(|x| 2^(47 - e)) with the sign of x (integer arithmetic on the bits)
+  // Y = round(|x| 2^(48 - e)) with the sign of x (integer arithmetic on the bits)
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   const int ex = static_cast<int>((b >> 52) & 0x7FF);
   const long long M = static_cast<long long>((b & 0xFFFFFFFFFFFFFull) | (ex ? (1ull << 52) : 0ull));
-  const int sh = 1028 + echunk - (ex ? ex : 1);
+  const int sh = 1027 + echunk - (ex ? ex : 1);
   long long Y = 0;
   if (M != 0 && sh >= 1 && sh <= 54) Y = (M + (1ll << (sh - 1))) >> sh;
   return (b >> 63) ? -Y : Y;
 }
 
-// The same for one FP32 part of a double-float: |v| < 2^e, so the shift is at least -23
-// and |Y| <= 2^47 (integer arithmetic on the bits).
+// The same for one FP32 part of a double-float: |v| < 2^e, so the shift is at least -24
+// and |Y| <= 2^48 (integer arithmetic on the bits).
 __device__ __forceinline__ long long digits_source_f32(float v, int echunk) {
   const unsigned b = __float_as_uint(v);
   const int ex = static_cast<int>((b >> 23) & 0xFF);
   const long long M = static_cast<long long>((b & 0x7FFFFFu) | (ex ? 0x800000u : 0u));
-  const int sh = 103 + echunk - (ex ? ex : 1);
+  const int sh = 102 + echunk - (ex ? ex : 1);
   long long Y = 0;
   if (M != 0 && sh <= 24) Y = sh >= 1 ? (M + (1ll << (sh - 1))) >> sh : M << (-sh);
   return (b >> 31) ? -Y : Y;
 }
 
-// Balanced base-64 digits Y = sum_p d_p 64^(7 - p), d_1..d_7 in [-32, 31], |Y| <= 2^47.
-// The low four digits are fixed by Y modulo 2^24: their value is the representative of
-// Y mod 2^24 in [-32 S, 31 S], S = 1 + 64 + 64^2 + 64^3 (a window of exactly 2^24 values),
-// so Y splits once into that low part and an exact high part, and each is taken apart
-// in 32-bit arithmetic; the digits are those of the digit-by-digit recurrence.
+// Balanced base-128 digits Y = sum_p d_p 128^(6 - p), d_1..d_6 in [-64, 63], |Y| <= 2^48
+// (so |d_0| <= 65). The low three digits are fixed by Y modulo 2^21: their value is the
+// representative of Y mod 2^21 in [-64 S, 63 S], S = 1 + 128 + 128^2 (a window of exactly
+// 2^21 values), so Y splits once into that low part and an exact high part, and each is
+// taken apart in 32-bit arithmetic; the digits are those of the digit-by-digit recurrence.
 __device__ __forceinline__ void balanced_digits(long long Y, int (&d)[kSlices]) {
-  constexpr int kS32 = 32 * (1 + 64 + 4096 + 262144);
-  const int lo = static_cast<int>((Y + kS32) & 0xFFFFFF) - kS32;
-  int hi = static_cast<int>((Y - lo) >> 24);
+  constexpr int kS64 = 64 * (1 + 128 + 16384);
+  const int lo = static_cast<int>((Y + kS64) & 0x1FFFFF) - kS64;
+  int hi = static_cast<int>((Y - lo) >> 21);
   int y = lo;
 #pragma unroll
-  for (int p = 7; p >= 4; --p) {
-    const int r = ((y + 32) & 63) - 32;
+  for (int p = 6; p >= 4; --p) {
+    const int r = ((y + 64) & 127) - 64;
     d[p] = r;
-    y = (y - r) >> 6;
+    y = (y - r) >> 7;
   }
 #pragma unroll
   for (int p = 3; p >= 1; --p) {
-    const int r = ((hi + 32) & 63) - 32;
+    const int r = ((hi + 64) & 127) - 64;
     d[p] = r;
-    hi = (hi - r) >> 6;
+    hi = (hi - r) >> 7;
   }
   d[0] = hi;
 }
 
 // Two small integers (|d| < 2^22) as a packed pair of BF16 values, exactly: adding d to
 // the bit pattern of 1.5 * 2^23 and subtracting 1.5 * 2^23 gives float(d); a value of at
-// most 6 significant bits leaves the low 16 bits of the float zero, so its upper half is
+// most 8 significant bits leaves the low 16 bits of the float zero, so its upper half is
 // the BF16 encoding.
 __device__ __forceinline__ uint32_t pack_bf16x2(int d0, int d1) {
   const float f0 = __fsub_rn(__int_as_float(0x4B400000 + d0), 12582912.0f);
@@ -416,7 +432,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(int d0, int d1) {
   return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
 }
 
-// Eight balanced base-64 digits of each of 8 consecutive K entries, written as one 16-byte
+// Seven balanced base-128 digits of each of 8 consecutive K entries, written as one 16-byte
 // chunk per digit slice into the stage-tiled, pre-swizzled layout the GEMM copies from:
 // [row block][K block of kKt][slice][row in block][kKt], 16-byte chunk c of a row stored at
 // c ^ ((row >> 1) & 3) (64-byte swizzle).
@@ -444,19 +460,19 @@ __device__ __forceinline__ void store_digits(long long (&Y)[8], int row, long lo
 }
 
 // Split of one K panel [k0, k0 + kw) of X (m rows of N) into digits. A block of
-// 128 kSplitRows threads covers kSplitRows consecutive rows and one chunk of 1024 K
+// 64 kSplitRows threads covers kSplitRows consecutive rows and one chunk of 512 K
 // entries. A warp takes 8 / kSplitRows K stages of 32 entries; in a stage, lane =
 // 4 (row in the group) + 16-byte chunk, so each warp reads row segments of 256 bytes and
 // writes kSplitRows consecutive rows (64 kSplitRows bytes) of a stage image per digit
 // slice. Per row it finds the chunk exponent e with max |x| < 2^e (-100000 for an
 // all-zero chunk), stores it at e[(chunk0 + blockIdx.y) m + row] and writes the digits of
-// x 2^(47 - e). Grid: (rows rounded up to R / kSplitRows, klen / 1024), rows fastest, so
+// x 2^(48 - e). Grid: (rows rounded up to R / kSplitRows, klen / 512), rows fastest, so
 // that blocks running together fill neighbouring rows of the same stage images. XS is double
 // (FP64) or df (double-float, value hi + lo: the exponent comes from the high parts, since
 // |hi + lo| <= |hi| (1 + 2^-24) stays within the digit range, and each part is scaled on
-// its own, so the value is represented to within 2^(e - 47)).
+// its own, so the value is represented to within 2^(e - 48)).
 constexpr int kSplitRows = 1;
-constexpr int kSplitThreads = 128 * kSplitRows;
+constexpr int kSplitThreads = kChunkK / 8 * kSplitRows;  // 8 entries per thread
 
 template <typename XS>
 __global__ void __launch_bounds__(kSplitThreads) k_split_digits(const XS* __restrict__ X, int m, long long N,
@@ -595,7 +611,7 @@ bool ozaki_supported() {
 
 // C partials (FP64, [splits][m][m], upper tiles) of J H^T via the digit split. Each operand
 // comes as FP64 (J, H) or, when its double-float copy (Jdf, Hdf) is given, as that.
-// Returns false when the kernel attribute cannot be set.
+// Returns false when the kernel attribute cannot be set or the GEMM launch is refused.
 bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, const df* Hdf, int m, long long N,
                               const OzakiWork& w, int splits, cudaStream_t s, void (*hook)(void*, int, int),
                               void* hook_arg) {
@@ -644,6 +660,7 @@ bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, c
     a.stall = w.stall;
     if (hook) hook(hook_arg, kOzakiGemm, 1);
     k_ozaki_gemm<<<dim3(tiles, splits), kGemmThreads, kSmemBytes, s>>>(a);
+    if (cudaPeekAtLastError() != cudaSuccess) return false;  // a launch the GPU refused (resources)
     if (hook) hook(hook_arg, kOzakiGemm, 0);
     note_launches(3);
   }
@@ -651,5 +668,6 @@ bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, c
 }
 
 long long ozaki_chunks(long long N) { return (N + kChunkK - 1) / kChunkK; }
+int ozaki_digit_slices() { return kSlices; }
 
 }  // namespace h1w
