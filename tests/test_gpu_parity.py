@@ -157,8 +157,9 @@ def test_apply_op_and_rhs_parity(case):
 @pytest.mark.parametrize("cap_gemm", [0, 1], ids=["tensor", "fp64"])
 def test_capacitance_and_prec_parity(case, m, cap_gemm):
     """C, its Cholesky factor and the preconditioner, with line C on the tensor
-    cores (42-bit digit split: error below 2^-42 of the row maxima, i.e. a few
-    1e-12 of ||C|| for these Gaussian rows) or on the FP64 CUDA cores."""
+    cores (49-bit digit split per 512-entry chunk: error below about 2^-48 of the
+    chunk maxima, i.e. far below 1e-11 of ||C|| for these Gaussian rows) or on the
+    FP64 CUDA cores."""
     d, n, h = case
     H = mg.build_hierarchy(d, n, h)
     N = H.N
@@ -298,7 +299,7 @@ def test_status_codes():
 def test_tensor_capacitance_matches_fp64(n, m):
     """Line C on the tensor cores against the FP64 CUDA-core GEMM on the same
     GPU-built H (more than one 262144-wide K panel, up to four, ragged tiles): the
-    digit split keeps 42 bits of every row, so C agrees to ~1e-11 of ||C||."""
+    digit split keeps 49 bits of every chunk of a row, so C agrees to ~1e-11 of ||C||."""
     h = tuple(1.0 / v for v in n)
     N = int(np.prod(n))
     rng = np.random.default_rng(41)
@@ -317,8 +318,9 @@ def test_tensor_capacitance_on_peaked_ert_rows():
     """ERT sensitivity rows peak sharply at the electrodes and C reaches ~1e9.
     The preconditioner stays within a few percent of the exact one only if
     the absolute error of C is far below 1; the chunk-scaled digit split keeps
-    ||C_tensor - C_fp64||_2 of order 1e-3 here (an exact CPU emulation of the
-    split gives 1.6e-3 at 64^3), checked against 2e-2."""
+    ||C_tensor - C_fp64||_2 of order 1e-3 or less here (an exact CPU emulation of
+    the base-64 split gave 1.6e-3 at 64^3; the base-128 one is more accurate),
+    checked against 2e-2."""
     n = 48
     pr = inputs.ert_problem(n, n_e_line=32, alpha=1e-3, device=DEV)
     Cs = []
