@@ -260,6 +260,7 @@ __global__ void k_apply64(Level L, const double* tx, const double* ty, const dou
 // come from DRAM once and from L2 for the other groups; with the groups outermost every
 // group re-read them from DRAM.
 constexpr int kFpt = 8;
+constexpr int kErtCycles = 1;  // V-cycles per application of the forward's preconditioner
 
 // The degree-2 Chebyshev-Jacobi smoothing collapses into one stencil pass. With A = D - N
 // (N(u)_i = sum over the faces of cell i of t u_nb), d0 = D^-1 r0 / theta, r1 = r0 - A d0 and
@@ -786,14 +787,17 @@ __global__ void __launch_bounds__(kJacWarps * 32) k_jacobian(Level L, const doub
   df w6[6];
 #pragma unroll
   for (int f = 0; f < 6; ++f) w6[f] = Wf[f * kJacCells + c];
-  // The measurements of a warp mostly share their source (A, B) with the previous one
-  // (survey rows are ordered by source), so t_f = W_f (D_A - D_B) is formed once per
-  // source and each row costs one difference, one product and one sum term per face.
+  // A warp takes a contiguous range of measurements. Survey rows are ordered by source
+  // (A, B), so consecutive rows of a warp share it: t_f = W_f (D_A - D_B) is formed once per
+  // source and warp, and each row costs one difference, one product and one sum term per
+  // face. (Dealt out round-robin, each warp met a new source every other row.)
   double acc_r = 0.0;
   const double pc = (MODE == kJvp && p < N) ? rv[p] : 0.0;
   int la = -2, lb = -2;
   df t6[6];
-  for (int i = warp; i < m; i += kJacWarps) {
+  const int per = (m + kJacWarps - 1) / kJacWarps;
+  const int i_end = min(m, (warp + 1) * per);
+  for (int i = warp * per; i < i_end; ++i) {
     const int4 q = abmn[i];
     if (q.x != la || q.y != lb) {  // warp-uniform
       la = q.x;
@@ -879,10 +883,18 @@ Coef32 coef_of(const Layout& W, int l) { return Coef32{W.tx[l], W.ty[l], W.tz[l]
 // x = one V-cycle on b (level-0 buffers W.b[0] -> W.x[0]); W.r[l] holds the residuals
 void vcycle32(const Layout& W, const Level* lev, int nl, int ne, const Cheb& K, cudaStream_t s) {
   const unsigned ng = (unsigned)((ne + kFpt - 1) / kFpt);
+  for (int cyc = 0; cyc < kErtCycles; ++cyc) {
   for (int l = 0; l < nl - 1; ++l) {
     const Coef32 C = coef_of(W, l);
     const unsigned nb = nblk(lev[l].N);
-    k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], 1, K.beta, K.c2t);
+    if (l == 0 && cyc > 0) {  // a further cycle starts from the current x: smooth the residual
+      k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
+      k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.r[l], W.x[l], 0, K.beta, K.c2t);
+      note_launches(2);
+    } else {
+      k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], 1, K.beta, K.c2t);
+      note_launches(1);
+    }
     k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
     if (lev[l].cx && (reinterpret_cast<uintptr_t>(W.r[l]) & 7) == 0) {  // 8-byte loads need an aligned workspace
       const int64_t npair = (int64_t)((lev[l + 1].nx + 1) / 2) * lev[l + 1].ny * lev[l + 1].nz;
@@ -890,7 +902,7 @@ void vcycle32(const Layout& W, const Level* lev, int nl, int ne, const Cheb& K, 
     } else {
       k_restrict32<<<dim3(nblk(lev[l + 1].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
     }
-    note_launches(3);
+    note_launches(2);
   }
   const int nc = (int)lev[nl - 1].N;
   k_dense_apply32<<<dim3((nc + kThreads - 1) / kThreads, ne), kThreads, sizeof(float) * nc, s>>>(W.Xf, nc, W.b[nl - 1],
@@ -908,6 +920,7 @@ void vcycle32(const Layout& W, const Level* lev, int nl, int ne, const Cheb& K, 
     k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
     k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.r[l], W.x[l], 0, K.beta, K.c2t);
     note_launches(3);
+  }
   }
 }
 
