@@ -260,7 +260,10 @@ __global__ void k_apply64(Level L, const double* tx, const double* ty, const dou
 // come from DRAM once and from L2 for the other groups; with the groups outermost every
 // group re-read them from DRAM.
 constexpr int kFpt = 8;
-constexpr int kErtCycles = 1;  // V-cycles per application of the forward's preconditioner
+// V-cycles per application of the forward's preconditioner: the FP32 cycle costs less than
+// an outer FP64 iteration (the operator runs on the FP64 pipe), so two cycles pay: 14 -> 9
+// iterations and 54.6 -> 51.9 ms per forward at 128^3 with 32 fields (three: 7, 53.3 ms)
+constexpr int kErtCycles = 2;
 
 // The degree-2 Chebyshev-Jacobi smoothing collapses into one stencil pass. With A = D - N
 // (N(u)_i = sum over the faces of cell i of t u_nb), d0 = D^-1 r0 / theta, r1 = r0 - A d0 and
@@ -880,47 +883,48 @@ Cheb cheb_coefs(double ratio) {
 
 Coef32 coef_of(const Layout& W, int l) { return Coef32{W.tx[l], W.ty[l], W.tz[l], W.dg[l], W.dinv[l]}; }
 
-// x = one V-cycle on b (level-0 buffers W.b[0] -> W.x[0]); W.r[l] holds the residuals
+// x = kErtCycles V-cycles on b (level-0 buffers W.b[0] -> W.x[0]; a further cycle starts from the
+// previous x); W.r[l] holds the residuals
 void vcycle32(const Layout& W, const Level* lev, int nl, int ne, const Cheb& K, cudaStream_t s) {
   const unsigned ng = (unsigned)((ne + kFpt - 1) / kFpt);
   for (int cyc = 0; cyc < kErtCycles; ++cyc) {
-  for (int l = 0; l < nl - 1; ++l) {
-    const Coef32 C = coef_of(W, l);
-    const unsigned nb = nblk(lev[l].N);
-    if (l == 0 && cyc > 0) {  // a further cycle starts from the current x: smooth the residual
+    for (int l = 0; l < nl - 1; ++l) {
+      const Coef32 C = coef_of(W, l);
+      const unsigned nb = nblk(lev[l].N);
+      if (l == 0 && cyc > 0) {  // a further cycle starts from the current x: smooth the residual
+        k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
+        k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.r[l], W.x[l], 0, K.beta, K.c2t);
+        note_launches(2);
+      } else {
+        k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], 1, K.beta, K.c2t);
+        note_launches(1);
+      }
+      k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
+      if (lev[l].cx && (reinterpret_cast<uintptr_t>(W.r[l]) & 7) == 0) {  // 8-byte loads need an aligned workspace
+        const int64_t npair = (int64_t)((lev[l + 1].nx + 1) / 2) * lev[l + 1].ny * lev[l + 1].nz;
+        k_restrict32_pairs<<<dim3(nblk(npair), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
+      } else {
+        k_restrict32<<<dim3(nblk(lev[l + 1].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
+      }
+      note_launches(2);
+    }
+    const int nc = (int)lev[nl - 1].N;
+    k_dense_apply32<<<dim3((nc + kThreads - 1) / kThreads, ne), kThreads, sizeof(float) * nc, s>>>(W.Xf, nc, W.b[nl - 1],
+                                                                                                    W.x[nl - 1]);
+    note_launches(1);
+    for (int l = nl - 2; l >= 0; --l) {
+      const Coef32 C = coef_of(W, l);
+      const unsigned nb = nblk(lev[l].N);
+      if (lev[l].cx && (reinterpret_cast<uintptr_t>(W.x[l]) & 7) == 0) {  // 8-byte pairs need an aligned workspace
+        const int64_t npair = (int64_t)lev[l + 1].nx * lev[l].ny * lev[l].nz;
+        k_prolong_add32_pairs<<<nblk(npair) * ng, kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.x[l + 1], W.x[l]);
+      } else {
+        k_prolong_add32<<<nb * ng, kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.x[l + 1], W.x[l]);
+      }
       k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
       k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.r[l], W.x[l], 0, K.beta, K.c2t);
-      note_launches(2);
-    } else {
-      k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], 1, K.beta, K.c2t);
-      note_launches(1);
+      note_launches(3);
     }
-    k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
-    if (lev[l].cx && (reinterpret_cast<uintptr_t>(W.r[l]) & 7) == 0) {  // 8-byte loads need an aligned workspace
-      const int64_t npair = (int64_t)((lev[l + 1].nx + 1) / 2) * lev[l + 1].ny * lev[l + 1].nz;
-      k_restrict32_pairs<<<dim3(nblk(npair), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
-    } else {
-      k_restrict32<<<dim3(nblk(lev[l + 1].N), ne), kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.r[l], W.b[l + 1]);
-    }
-    note_launches(2);
-  }
-  const int nc = (int)lev[nl - 1].N;
-  k_dense_apply32<<<dim3((nc + kThreads - 1) / kThreads, ne), kThreads, sizeof(float) * nc, s>>>(W.Xf, nc, W.b[nl - 1],
-                                                                                                  W.x[nl - 1]);
-  note_launches(1);
-  for (int l = nl - 2; l >= 0; --l) {
-    const Coef32 C = coef_of(W, l);
-    const unsigned nb = nblk(lev[l].N);
-    if (lev[l].cx && (reinterpret_cast<uintptr_t>(W.x[l]) & 7) == 0) {  // 8-byte pairs need an aligned workspace
-      const int64_t npair = (int64_t)lev[l + 1].nx * lev[l].ny * lev[l].nz;
-      k_prolong_add32_pairs<<<nblk(npair) * ng, kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.x[l + 1], W.x[l]);
-    } else {
-      k_prolong_add32<<<nb * ng, kThreads, 0, s>>>(lev[l], lev[l + 1], ne, W.x[l + 1], W.x[l]);
-    }
-    k_resid32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.b[l], W.x[l], W.r[l]);
-    k_smooth32<<<nb * ng, kThreads, 0, s>>>(lev[l], C, ne, W.r[l], W.x[l], 0, K.beta, K.c2t);
-    note_launches(3);
-  }
   }
 }
 
