@@ -508,6 +508,11 @@ void smooth_df(h1w_ctx* c, int l, int nrhs, const df* b, df* x, bool zero_x) {
   df* da = dfp(c->buf[l].da);
   df* db = dfp(c->buf[l].db);
   const bool q1 = c->disc == H1W_Q1_VERTEX;
+  if (q1 && c->opt.cheb_degree == 2) {  // the two steps in one pass (after the residual, from a nonzero x)
+    if (!zero_x) launch_q1_residual_df(L, nrhs, b, x, r, c->stream);
+    launch_q1_smooth_df(L, nrhs, zero_x ? b : r, x, zero_x, K.beta_df, K.c2t_df, c->stream);
+    return;
+  }
   if (q1) launch_q1_cheb_first_df(L, nrhs, b, x, r, da, zero_x, K.inv_theta_df, c->stream);
   else launch_cheb_first_df(L, nrhs, b, x, r, da, zero_x, K.inv_theta_df, c->stream);
   bool pending = !zero_x;
@@ -1059,6 +1064,8 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
             cudaMemcpyAsync(&L.q1c[k], st + (int64_t)k * L.N + pm, sizeof(df), cudaMemcpyDeviceToHost, c->stream);
           if (cudaStreamSynchronize(c->stream) != cudaSuccess) { L.q1_ilo = 1; L.q1_ihi = 0; }
         }
+        const double dinv_box = (double)L.q1c[9].hi + (double)L.q1c[9].lo;
+        for (int k = 0; k < 9; ++k) L.q1w[k] = df_host(((double)L.q1c[k].hi + (double)L.q1c[k].lo) * dinv_box);
       }
     }
   }
@@ -1090,6 +1097,10 @@ h1w_status h1w_setup(const h1w_grid* grid, int32_t m_max, const h1w_options* opt
       K.c1_df[j] = df_host(K.c1[j]);
       K.c2_df[j] = df_host(K.c2[j]);
       rho_prev = rho;
+    }
+    if (o.cheb_degree == 2) {
+      K.beta_df = df_host(K.inv_theta * (1.0 + K.c1[1]) + K.c2[1] * (1.0 - K.inv_theta));
+      K.c2t_df = df_host(K.c2[1] * K.inv_theta);
     }
     if (c->disc == H1W_FV_CELL && o.cheb_degree == 2) {   // constants of the fused smoothing legs
       const Level& L = c->lev[l];

@@ -34,6 +34,7 @@ struct Level {
   // q1c (the table's entries there, read back at setup); empty when ilo > ihi
   int q1_ilo, q1_ihi, q1_jlo, q1_jhi;
   df q1c[10];
+  df q1w[9];                     // q1c[k] q1c[9]: a coupling times the box's inverse diagonal
   double lam;                    // upper bound of spec(D^-1 A) (Gershgorin)
   int cx, cy, cz;                // axis coarsened towards the next level
   int iso;                       // FV with Tx == Ty == Tz
@@ -63,6 +64,8 @@ struct ChebCoef {
   double c1[8];       // rho_j rho_{j-1} for step j (1-based; index 0 unused)
   double c2[8];       // 2 rho_j / delta
   df inv_theta_df, c1_df[8], c2_df[8];  // the same as double-floats
+  // degree 2 collapsed into one pass: x += D^-1 [beta r0 + c2t N(D^-1 r0)], A = D - N
+  df beta_df, c2t_df;
 };
 
 // Kernels launched by this library in this process (every launcher adds its count).
@@ -150,6 +153,8 @@ void launch_q1_cheb_first_df(const Level& L, int nrhs, const df* b, df* x, df* r
                              cudaStream_t s);
 void launch_q1_cheb_step_df(const Level& L, int nrhs, df* r, const df* d_old, df* d_new, df* x, df c1, df c2,
                             bool add_old, cudaStream_t s);
+void launch_q1_smooth_df(const Level& L, int nrhs, const df* r0, df* x, bool zero_x, df beta, df c2t,
+                         cudaStream_t s);
 void launch_q1_residual_df(const Level& L, int nrhs, const df* b, const df* x, df* r, cudaStream_t s);
 void launch_q1_restrict_df(const Level& Lf, const Level& Lc, int nrhs, const df* rf, df* bc, cudaStream_t s);
 void launch_q1_prolong_add_df(const Level& Lf, const Level& Lc, int nrhs, const df* xc, df* xf, cudaStream_t s);

@@ -158,6 +158,56 @@ __global__ void __launch_bounds__(kBX * kBY) k_q1_cheb_step_df(Level L, int nrhs
   }
 }
 
+// Degree-2 Chebyshev smoothing in one pass: with A = D - N (N the off-diagonal couplings
+// negated), the two steps from x0 give x0 + D^-1 [beta r0 + c2t N(D^-1 r0)], r0 = b - A x0
+// (r0 = b from a zero guess), by the identity A (D^-1 r0 / theta) = r0 / theta - N D^-1 r0.
+// The sum runs over c_nb dinv_nb r0_nb; vertices whose whole neighbourhood lies in the
+// uniform box take c_nb dinv_nb from the level's constants (q1w).
+__global__ void __launch_bounds__(kBX * kBY) k_q1_smooth_df(Level L, int nrhs, const df* __restrict__ r0,
+                                                          df* __restrict__ x, int zero_x, df beta, df c2t) {
+  Vtx v;
+  if (!vtx_of(L, nrhs, v)) return;
+  dsum s[kRpt];
+  const bool inner = v.i > L.q1_ilo && v.i < L.q1_ihi && v.j > L.q1_jlo && v.j < L.q1_jhi;
+  if (inner) {
+#pragma unroll
+    for (int b = -1; b <= 1; ++b)
+#pragma unroll
+      for (int a = -1; a <= 1; ++a) {
+        if (a == 0 && b == 0) continue;
+        const df w = L.q1w[3 * (b + 1) + (a + 1)];
+        const int64_t q = v.p + (int64_t)b * L.nx + a;
+#pragma unroll
+        for (int k = 0; k < kRpt; ++k)
+          if (k < v.nk) s[k].add(df_mul(w, r0[v.off[k] + q]));
+      }
+  } else {
+    const df* st = L.q1st;
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) {
+      if (v.j + b < 0 || v.j + b >= L.ny) continue;
+#pragma unroll
+      for (int a = -1; a <= 1; ++a) {
+        if ((a == 0 && b == 0) || v.i + a < 0 || v.i + a >= L.nx) continue;
+        const int64_t q = v.p + (int64_t)b * L.nx + a;
+        const df w = df_mul(st[(int64_t)(3 * (b + 1) + (a + 1)) * L.N + v.p], q1_dinv(L, v.i + a, v.j + b, q));
+#pragma unroll
+        for (int k = 0; k < kRpt; ++k)
+          if (k < v.nk) s[k].add(df_mul(w, r0[v.off[k] + q]));
+      }
+    }
+  }
+  const df dinv = q1_dinv(L, v.i, v.j, v.p);
+#pragma unroll
+  for (int k = 0; k < kRpt; ++k) {
+    if (k >= v.nk) break;
+    const int64_t o = v.off[k] + v.p;
+    // N(D^-1 r0) = -(the sum above)
+    const df val = df_mul(dinv, df_sub(df_mul(beta, r0[o]), df_mul(c2t, s[k].get())));
+    x[o] = zero_x ? val : df_add(x[o], val);
+  }
+}
+
 __global__ void __launch_bounds__(kBX * kBY) k_q1_residual_df(Level L, int nrhs, const df* __restrict__ b,
                                                             const df* __restrict__ x, df* __restrict__ r) {
   Vtx v;
@@ -259,6 +309,11 @@ void launch_q1_cheb_first_df(const Level& L, int nrhs, const df* b, df* x, df* r
 void launch_q1_cheb_step_df(const Level& L, int nrhs, df* r, const df* d_old, df* d_new, df* x, df c1, df c2,
                             bool add_old, cudaStream_t s) {
   k_q1_cheb_step_df<<<grid2(L, nrhs, kRpt), kBlock2, 0, s>>>(L, nrhs, r, d_old, d_new, x, c1, c2, add_old ? 1 : 0);
+  note_launches(1);
+}
+void launch_q1_smooth_df(const Level& L, int nrhs, const df* r0, df* x, bool zero_x, df beta, df c2t,
+                         cudaStream_t s) {
+  k_q1_smooth_df<<<grid2(L, nrhs, kRpt), kBlock2, 0, s>>>(L, nrhs, r0, x, zero_x ? 1 : 0, beta, c2t);
   note_launches(1);
 }
 void launch_q1_residual_df(const Level& L, int nrhs, const df* b, const df* x, df* r, cudaStream_t s) {
