@@ -51,6 +51,7 @@ namespace {
 
 constexpr int kSlices = 7;
 constexpr int kLevels = 7;                 // digit-pair levels kept: p + q <= 6
+static_assert(kLevels == 7, "the epilogue reads levels 0..3 and 4..6");
 constexpr int kTileM = 128;                // rows of J per tile (TMEM lanes)
 constexpr int kTileN = 64;                 // rows of H per tile (columns per level)
 constexpr int kKt = 32;                    // K per stage: 64-byte rows
@@ -296,27 +297,30 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_ozaki_gemm(OzakiArgs g) {
       long long Thi[kEpiCols];
 #pragma unroll
       for (int j = 0; j < kEpiCols; ++j) Thi[j] = 0;
+      // two TMEM loads in flight per wait (each wait is a round trip while the tensor cores idle)
 #pragma unroll 1
-      for (int lev = 0; lev < 4; ++lev) {
-        uint32_t v[kEpiCols];
-        tmem_ld16(tbase + lev * kTileN, v);
+      for (int lev = 0; lev < 4; lev += 2) {
+        uint32_t v0[kEpiCols], v1[kEpiCols];
+        tmem_ld16(tbase + lev * kTileN, v0);
+        tmem_ld16(tbase + (lev + 1) * kTileN, v1);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < kEpiCols; ++j)
-          Thi[j] = Thi[j] * 128 + static_cast<long long>(__float2int_rn(__uint_as_float(v[j])));
+          Thi[j] = (Thi[j] * 128 + static_cast<long long>(__float2int_rn(__uint_as_float(v0[j])))) * 128 +
+                   static_cast<long long>(__float2int_rn(__uint_as_float(v1[j])));
       }
       // levels 4..6 in FP32: |T_lo| < 2^38, so its rounding (below 2^15 units of the last
       // level) stays under the rounding of the digit split itself
       float Tlo[kEpiCols];
-#pragma unroll
-      for (int j = 0; j < kEpiCols; ++j) Tlo[j] = 0.f;
-#pragma unroll 1
-      for (int lev = 4; lev < kLevels; ++lev) {
-        uint32_t v[kEpiCols];
-        tmem_ld16(tbase + lev * kTileN, v);
+      {
+        uint32_t v4[kEpiCols], v5[kEpiCols], v6[kEpiCols];
+        tmem_ld16(tbase + 4 * kTileN, v4);
+        tmem_ld16(tbase + 5 * kTileN, v5);
+        tmem_ld16(tbase + 6 * kTileN, v6);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < kEpiCols; ++j) Tlo[j] = fmaf(Tlo[j], 128.f, __uint_as_float(v[j]));
+        for (int j = 0; j < kEpiCols; ++j)
+          Tlo[j] = fmaf(fmaf(__uint_as_float(v4[j]), 128.f, __uint_as_float(v5[j])), 128.f, __uint_as_float(v6[j]));
       }
       tc_fence_before();
       __syncwarp();
