@@ -718,6 +718,7 @@ def run_ours(args):
                 ev[0].record(stream)
                 bufs = (J_dev, J_dev2)
                 if pipelined:
+                    b_dev.copy_(b_host, non_blocking=True)   # the first step's b, ahead of its J
                     S.prefetch_J(J_host, bufs[0])
                 for k_ in range(steps):
                     # where b's small copy goes matters: behind the next step's J on the copy
@@ -725,7 +726,8 @@ def run_ours(args):
                     # before h1w_capacitance_from_host it held line H back until every row of J
                     # had arrived (measured); so b goes before the prefetch, or after line H
                     if pipelined:
-                        b_dev.copy_(b_host, non_blocking=True)
+                        if k_ > 0:
+                            b_dev.copy_(b_host, non_blocking=True)
                         if k_ + 1 < steps:
                             S.prefetch_J(J_host, bufs[(k_ + 1) % 2])
                     S.capacitance_from_host(J_host, bufs[k_ % 2] if pipelined else J_dev)
