@@ -349,7 +349,7 @@ size_t h1w_ert_workspace_size(const h1w_ctx* ctx, int32_t n_e, int32_t m);
 /* Pole fields and measurements for the log-conductivity logsigma (N, DEVICE).
  * U (DEVICE, [n_e][N], caller-owned) receives the fields u_e, g (DEVICE, [m])
  * the measurements. The fields are solved together by PCG in FP64 to
- * ||e_c - A u_e||_2 <= rtol (unit sources), preconditioned by one FP32 V-cycle
+ * ||e_c - A u_e||_2 <= rtol (unit sources), preconditioned by two FP32 V-cycles
  * on the same operator over the context's hierarchy, from u_e = 0 or, with
  * H1W_FORWARD_WARM_START, from the fields already in U (e.g. those of the previous
  * Gauss-Newton iterate). The survey's host arrays

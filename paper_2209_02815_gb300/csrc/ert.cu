@@ -13,8 +13,8 @@
 // of d(conductance)/dm_c times the jumps of v and w across the face.
 //
 // Forward solve. All n_e pole fields at once by PCG in FP64 (flexible beta, since the
-// preconditioner is applied in FP32) on A, preconditioned by one FP32 V-cycle on the same
-// operator: the context's hierarchy and its trilinear transfers (R = P^T), Chebyshev-
+// preconditioner is applied in FP32) on A, preconditioned by two FP32 V-cycles on the same
+// operator (the second from the first's result; kErtCycles): the context's hierarchy and its trilinear transfers (R = P^T), Chebyshev-
 // Jacobi smoothing of degree 2 on [lambda / 10, lambda] with the Gershgorin bound
 // lambda = 2 of D^-1 A (one stencil pass per smoothing, k_smooth32), and coarse operators
 // rediscretized from the geometric mean of the children's conductivities; the coarsest
