@@ -48,6 +48,7 @@ CASES = [
     ((24, 16, 12), (0.05, 0.06, 0.08), 0b110000),             # anisotropic, Dirichlet top and bottom
     ((9, 7, 5), (0.1, 0.1, 0.1), 0b000001),                   # one level (dense solve), one Dirichlet face
     ((32, 32, 32), (1 / 32,) * 3, ALL_BUT_TOP),               # three levels
+    ((21, 16, 12), (1 / 21, 1 / 16, 1 / 12), ALL_BUT_TOP),    # odd x: x not coarsened (one-cell transfers)
 ]
 
 
