@@ -685,7 +685,6 @@ def run_ours(args):
             b_host.copy_(b)
             x_host = torch.empty_like(b_host).pin_memory()
             J_dev = torch.empty_like(J)
-            b_dev = torch.empty_like(b)
             # the plain host-to-device copy rate of J, for reference
             c0 = torch.cuda.Event(enable_timing=True)
             c1 = torch.cuda.Event(enable_timing=True)
@@ -697,45 +696,42 @@ def run_ours(args):
             J_dev2 = torch.empty_like(J)
 
             def copy_waits():
-                # time line H's stream waited for rows of J, and the host-link rate of each batch
+                # time line H's stream waited for rows of J, and the host-link rate of the step's
+                # whole copy of J (first batch's start to last batch's end; the copy runs without
+                # gaps, so this is the link's rate)
                 prof = S.copy_profile()
-                wait, prev, rates = 0.0, 0.0, []
+                wait, prev = 0.0, 0.0
                 for pb in prof:
                     wait += max(0.0, pb["cycle_begin"] - prev)
                     prev = pb["cycle_end"]
-                    dt_ = pb["copy_end"] - pb["copy_begin"]
+                rate = None
+                if prof:
+                    dt_ = prof[-1]["copy_end"] - prof[0]["copy_begin"]
                     if dt_ > 0:
-                        rates.append(pb["rows"] * N * 8 / (dt_ / 1e3) / 1e9)
-                return wait, (min(rates) if rates else None), (statistics.median(rates) if rates else None)
+                        rate = sum(pb["rows"] for pb in prof) * N * 8 / (dt_ / 1e3) / 1e9
+                return wait, rate
 
             def e2e_run(steps, pipelined):
                 # one step: b in, J in (row batches, overlapped with line H), solve, x out. Pipelined:
-                # the copy of the next step's J into the other device buffer starts before this
-                # step's capacitance (h1w_prefetch_J), so it overlaps this step's solve as well
+                # the copy of the next step's J into the other device buffer (h1w_prefetch_J) starts
+                # once this step's capacitance has returned, so it runs beside this step's PCG and
+                # is done, or nearly, when the next step's line H needs its rows. The first step's
+                # J is copied by its own capacitance call, batch by batch under line H.
                 ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
                 waits = []
                 phases_k = []
                 ev[0].record(stream)
                 bufs = (J_dev, J_dev2)
-                if pipelined:
-                    b_dev.copy_(b_host, non_blocking=True)   # the first step's b, ahead of its J
-                    S.prefetch_J(J_host, bufs[0])
                 for k_ in range(steps):
-                    # where b's small copy goes matters: behind the next step's J on the copy
-                    # engine it would wait for all of J, and issued on the solver's stream just
-                    # before h1w_capacitance_from_host it held line H back until every row of J
-                    # had arrived (measured); so b goes before the prefetch, or after line H
-                    if pipelined:
-                        if k_ > 0:
-                            b_dev.copy_(b_host, non_blocking=True)
-                        if k_ + 1 < steps:
-                            S.prefetch_J(J_host, bufs[(k_ + 1) % 2])
+                    # b and x go through h1w_pcg_host, which reads and writes the pinned host
+                    # vectors with kernels: a host copy queued on the solver's stream while a
+                    # copy of J ran on the copy stream held the stream's next work back until
+                    # all of J had arrived (measured, about 40 ms per step)
                     S.capacitance_from_host(J_host, bufs[k_ % 2] if pipelined else J_dev)
-                    if not pipelined:
-                        b_dev.copy_(b_host, non_blocking=True)
+                    if pipelined and k_ + 1 < steps:
+                        S.prefetch_J(J_host, bufs[(k_ + 1) % 2])
                     waits.append(copy_waits())
-                    S.pcg(b_dev, RTOL, MAXIT, x=x)
-                    x_host.copy_(x, non_blocking=True)
+                    S.pcg_host(b_host, x_host, RTOL, MAXIT)
                     ev[k_ + 1].record(stream)
                     t_ = S.timings()
                     phases_k.append([round(float(getattr(t_, p_)), 2) for p_ in phase])
@@ -749,8 +745,7 @@ def run_ours(args):
                         "step_ms": step_ms,
                         "lineH_copy_wait_ms": [w[0] for w in waits],
                         "phases_ms_per_step (H, C, chol, pcg)": phases_k,
-                        "link_gb_per_s_min_batch": [w[1] for w in waits],
-                        "link_gb_per_s_median_batch": [w[2] for w in waits]}
+                        "link_gb_per_s": [w[1] for w in waits]}
 
             e2e_run(1, False)  # untimed: the first call creates the copy stream and its events
             e2e_run(2, True)
@@ -760,12 +755,12 @@ def run_ours(args):
             e2e = e2e_run(args.e2e_steps, True)
             e2e.update({"h2d_bytes_per_step": int(J.numel() * 8 + b.numel() * 8),
                         "d2h_bytes_per_step": int(x.numel() * 8), "h2d_copy_gb_per_s": h2d_gbs,
-                        "api": "Solver.prefetch_J + capacitance_from_host + pcg (h1w_prefetch_J, "
-                               "h1w_capacitance_from_host, h1w_pcg), J double-buffered on the device",
+                        "api": "Solver.capacitance_from_host + prefetch_J + pcg_host (h1w_capacitance_from_host, "
+                               "h1w_prefetch_J of the next J, h1w_pcg_host), J double-buffered on the device",
                         "unpipelined": {k_: te0[k_] for k_ in ("value", "median_value", "median_step_ms",
                                                               "min_step_ms", "max_step_ms", "step_ms",
                                                               "lineH_copy_wait_ms",
-                                                              "link_gb_per_s_median_batch")},
+                                                              "link_gb_per_s")},
                         "last_step_phases_ms": {k_: float(getattr(te, k_)) for k_ in phase}})
             del J_dev2
             del J_host, J_dev

@@ -83,8 +83,10 @@ typedef struct {
                             (Sec. 3.2), for which h1w_capacitance skips lines H, C and chol */
   int32_t pcg_mode;      /* h1w_pcg: 0 = the iteration driven from the device: the loop is a CUDA graph
                             with a conditional while node, the scalars stay on the GPU and the host
-                            waits once per (re)start (default); 1 = a host loop that reads the residual
-                            norm back every iteration and times individual kernels (h1w_get_timings) */
+                            waits once per (re)start (default; the context keeps the graphs of the two
+                            J addresses used last, so alternating between two device copies of J
+                            captures each once); 1 = a host loop that reads the residual norm back
+                            every iteration and times individual kernels (h1w_get_timings) */
   double cheb_ratio;     /* the Chebyshev smoother targets [lambda / cheb_ratio, lambda] of D^-1 A, lambda the
                             Gershgorin bound; 1.5 .. 1000, or 0 (default) for the discretization's
                             ratio: 10 on FV cell grids, 6 on Q1 vertex grids. It also sets the interval
@@ -217,6 +219,15 @@ h1w_status h1w_gn_rhs(h1w_ctx* ctx, const double* dm, const double* d, double* b
  * H1W_ENOTCONV when maxit is reached first (x holds the last iterate). */
 h1w_status h1w_pcg(h1w_ctx* ctx, const double* b, double* x, double rtol, int32_t maxit,
                    h1w_info* info);
+
+/* h1w_pcg with b and x in page-locked HOST memory (cudaHostAlloc'ed or registered, N
+ * entries each): b is read and x written by kernels through the device's view of that
+ * memory, so the solve queues no copy-engine work on the context's stream. (A host copy
+ * queued there behind a large h1w_prefetch_J copy made the stream's following work wait
+ * for all of that copy.) The solve runs on the context's own buffers. H1W_EINVAL if either
+ * pointer is not page-locked host memory the device can address. Synchronizes. */
+h1w_status h1w_pcg_host(h1w_ctx* ctx, const double* b_host, double* x_host, double rtol, int32_t maxit,
+                        h1w_info* info);
 
 /* Copies the capacitance matrix C and its lower Cholesky factor L (m x m,
  * row-major, DEVICE) into caller buffers (either may be NULL). */

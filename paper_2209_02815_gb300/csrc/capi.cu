@@ -50,6 +50,7 @@ struct HostCopy {
   const double* dev = nullptr;
   int m = 0;
   bool active = false;
+  bool prefetched = false;   // issued by h1w_prefetch_J, ahead of the capacitance that consumes it
   std::vector<int> edge;
   std::vector<cudaEvent_t> beg, end;
 };
@@ -87,6 +88,7 @@ struct h1w_ctx {
   int64_t gemm_partial_len;
   OzakiWork oz;                  // tensor-core capacitance buffers (cap_gemm = 0)
   std::vector<int> oz_tiles_host;
+  int oz_tiles_m = -1;           // m of the tile list on the device
   // Krylov vectors
   double *r, *z, *z0, *p, *q;
   double *svec, *jz, *w, *wtmp;
@@ -116,12 +118,20 @@ struct h1w_ctx {
   double* gx = nullptr;
   cudaStream_t body_stream = nullptr;  // captures the loop body
   cudaStream_t cap_stream = nullptr;   // captures the graphs (the context's stream may be the legacy one)
-  cudaGraphExec_t pcg_exec = nullptr;  // cached single-system graph
-  int pcg_key_m = -1;
-  const double* pcg_key_J = nullptr;
-  int pcg_key_stall = 0;
-  unsigned long long pcg_key_wait = 0;
-  long long pcg_l_pre = 0, pcg_l_body = 0, pcg_l_post = 0;  // kernels per part of the graph
+  // cached single-system graphs: two, so that a caller alternating between two device copies
+  // of J (double-buffered host copies) finds both; the true residual bakes J's address in
+  struct PcgGraph {
+    cudaGraphExec_t exec = nullptr;
+    int m = -1;
+    const double* J = nullptr;
+    int stall = 0;
+    unsigned long long wait = 0;
+    long long l_pre = 0, l_body = 0, l_post = 0;
+    unsigned long long used = 0;  // last use, for replacing the older one
+  } pcg_g[2];
+  int pcg_cur = 0;              // the entry pcg_graph_ready chose
+  unsigned long long pcg_clock = 0;
+  long long pcg_l_pre = 0, pcg_l_body = 0, pcg_l_post = 0;  // kernels per part of the last captured graph
   unsigned long long uid = 0;   // process-unique id (batch graph cache keys)
   cudaStream_t copy_stream = nullptr;   // host-to-device copies of h1w_capacitance_from_host
   HostCopy hcopy[2];                     // pending or running copies of J (at most two)
@@ -834,12 +844,20 @@ bool capture_pcg(h1w_ctx* c, const double* b, double* x, bool clear_status) {
 
 // Builds (or reuses) the single-system graph of c: b from c->gb, x into c->gx.
 h1w_status pcg_graph_ready(h1w_ctx* c) {
-  if (c->pcg_exec && c->pcg_key_m == c->m && c->pcg_key_J == c->J && c->pcg_key_stall == c->stall &&
-      c->pcg_key_wait == c->wait_ns)
-    return H1W_OK;
-  if (c->pcg_exec) {
-    cudaGraphExecDestroy(c->pcg_exec);
-    c->pcg_exec = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    h1w_ctx::PcgGraph& e = c->pcg_g[i];
+    if (e.exec && e.m == c->m && e.J == c->J && e.stall == c->stall && e.wait == c->wait_ns) {
+      e.used = ++c->pcg_clock;
+      c->pcg_cur = i;
+      return H1W_OK;
+    }
+  }
+  // replace an empty entry, else the one used longest ago
+  const int slot = !c->pcg_g[0].exec ? 0 : !c->pcg_g[1].exec ? 1 : (c->pcg_g[0].used <= c->pcg_g[1].used ? 0 : 1);
+  h1w_ctx::PcgGraph& G = c->pcg_g[slot];
+  if (G.exec) {
+    cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
   }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pcg graph");
   if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -862,17 +880,22 @@ h1w_status pcg_graph_ready(h1w_ctx* c) {
     cudaGetLastError();
     return fail(c, H1W_ECUDA, ok ? std::string("pcg graph: capture failed: ") + cudaGetErrorString(e) : c->err);
   }
-  const cudaError_t ei = cudaGraphInstantiate(&c->pcg_exec, g, 0);
+  const cudaError_t ei = cudaGraphInstantiate(&G.exec, g, 0);
   cudaGraphDestroy(g);
   if (ei != cudaSuccess) {
-    c->pcg_exec = nullptr;
+    G.exec = nullptr;
     cudaGetLastError();
     return fail(c, H1W_ECUDA, std::string("pcg graph: instantiation failed: ") + cudaGetErrorString(ei));
   }
-  c->pcg_key_m = c->m;
-  c->pcg_key_J = c->J;
-  c->pcg_key_stall = c->stall;
-  c->pcg_key_wait = c->wait_ns;
+  G.m = c->m;
+  G.J = c->J;
+  G.stall = c->stall;
+  G.wait = c->wait_ns;
+  G.l_pre = c->pcg_l_pre;
+  G.l_body = c->pcg_l_body;
+  G.l_post = c->pcg_l_post;
+  G.used = ++c->pcg_clock;
+  c->pcg_cur = slot;
   return H1W_OK;
 }
 
@@ -895,20 +918,21 @@ h1w_status pcg_graph_solve(h1w_ctx* c, const double* b, double* x, double rtol, 
   const cudaStream_t s = c->stream;
   h1w_status st = pcg_graph_ready(c);
   if (st != H1W_OK) return st;
+  const h1w_ctx::PcgGraph& G = c->pcg_g[c->pcg_cur];
   const long long l0 = g_kernel_launches.load();
   if (c->have_ev) cudaEventRecord(c->ev[4], s);
-  cudaMemcpyAsync(c->gb, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  h1w::launch_copy(c->gb, b, (int64_t)N, s);
   h1w_info inf{0, 0, 0.0, 0.0};
   double sc[16] = {};
   long long launched = 0;
   for (int restart = 0; restart <= c->opt.max_restarts; ++restart) {
     launch_pcg_set_scalars(c->scal, rtol, maxit, restart == 0 ? 1 : 0, s);
     const int it0 = (int)sc[kSlotIt];
-    if (cudaGraphLaunch(c->pcg_exec, s) != cudaSuccess) return cuda_check(c, "pcg graph launch");
+    if (cudaGraphLaunch(G.exec, s) != cudaSuccess) return cuda_check(c, "pcg graph launch");
     cudaMemcpyAsync(sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "pcg graph");
     const int it = (int)sc[kSlotIt];
-    launched += c->pcg_l_pre + (long long)(it - it0) * c->pcg_l_body + c->pcg_l_post;
+    launched += G.l_pre + (long long)(it - it0) * G.l_body + G.l_post;
     inf.iters = it;
     const double bb = sc[kSlotBB];
     inf.rel_res_true = bb > 0.0 ? std::sqrt(sc[kSlotRRTrue] / bb) : 0.0;
@@ -916,7 +940,7 @@ h1w_status pcg_graph_solve(h1w_ctx* c, const double* b, double* x, double rtol, 
     if (inf.rel_res_true <= rtol || it >= maxit || !std::isfinite(inf.rel_res_true)) break;
     ++inf.restarts;
   }
-  cudaMemcpyAsync(x, c->gx, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  h1w::launch_copy(x, c->gx, (int64_t)N, s);
   if (c->have_ev) cudaEventRecord(c->ev[5], s);
   int dst = 0;
   cudaMemcpyAsync(&dst, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -1194,6 +1218,13 @@ static h1w_status issue_host_copies(h1w_ctx* c, HostCopy& h, int m, const double
     return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create an event");
   h.edge = batch_edges(c, m, true);
   const int nbatch = (int)h.edge.size() - 1;
+  // fresh events for every copy set: re-recording the events that the context's stream waited
+  // on when this set's previous copies were consumed held that stream back until the new
+  // copies had finished (measured: the next step's work waited about one copy of J)
+  for (cudaEvent_t e : h.beg) cudaEventDestroy(e);
+  for (cudaEvent_t e : h.end) cudaEventDestroy(e);
+  h.beg.clear();
+  h.end.clear();
   if (!make_events(h.beg, nbatch) || !make_events(h.end, nbatch))
     return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create an event");
   cudaEventRecord(c->order_ev, c->stream);
@@ -1209,6 +1240,7 @@ static h1w_status issue_host_copies(h1w_ctx* c, HostCopy& h, int m, const double
   h.dev = J_dev;
   h.m = m;
   h.active = true;
+  h.prefetched = false;
   return cuda_check(c, "capacitance_from_host: copies");
 }
 
@@ -1239,14 +1271,21 @@ static h1w_status capacitance_impl(h1w_ctx* c, int32_t m, const double* J, const
   return st;
 }
 
+// The GEMM's tile list for m rows, uploaded only when m differs from the last upload: a copy
+// from host memory on the context's stream would queue on a copy engine behind a pending
+// prefetch of J.
+static void upload_tiles(h1w_ctx* c, int m) {
+  if (c->oz_tiles_m == m) return;
+  ozaki_tiles(m, c->oz_tiles_host);
+  cudaMemcpyAsync(c->oz.tiles, c->oz_tiles_host.data(), sizeof(int) * c->oz_tiles_host.size(),
+                  cudaMemcpyHostToDevice, c->stream);
+  c->oz_tiles_m = m;
+}
+
 // Host-side preparation of a capacitance that will be captured into a graph: the GEMM's tile
 // list for m rows, uploaded (a capture cannot copy from pageable host memory). Synchronizes.
 static h1w_status capacitance_prepare(h1w_ctx* c, int32_t m) {
-  if (m > 0 && c->opt.cap_gemm == 0 && c->opt.precond == 0) {
-    ozaki_tiles(m, c->oz_tiles_host);
-    cudaMemcpyAsync(c->oz.tiles, c->oz_tiles_host.data(), sizeof(int) * c->oz_tiles_host.size(),
-                    cudaMemcpyHostToDevice, c->stream);
-  }
+  if (m > 0 && c->opt.cap_gemm == 0 && c->opt.precond == 0) upload_tiles(c, m);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "capacitance_prepare");
   return cuda_check(c, "capacitance_prepare");
 }
@@ -1262,16 +1301,32 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
     h1w_status st = H1W_OK;
     hc = host_copies_for(c, m, J_host, J, st);
     if (!hc) return st;
-    if (!make_events(c->cyc_beg, hc->edge.size()) || !make_events(c->cyc_end, hc->edge.size()))
+  }
+  // V-cycle batches: the copy batches when this call issued the copies (they grow from 16
+  // rows, so the cycles start early and follow the copy), else the standard rhs_block
+  // batches, each waiting for the copy batch that holds its last row (a prefetched copy is
+  // usually complete, and small batches would only cost cycle efficiency)
+  const bool own = hc && !hc->prefetched;
+  const std::vector<int> edge = own ? hc->edge : batch_edges(c, m, false);
+  const int nbatch = (int)edge.size() - 1;
+  std::vector<int> cov_first, cov_last;   // per V-cycle batch: copy batches of its first and last rows
+  if (hc) {
+    const int ncb = (int)hc->edge.size() - 1;
+    for (int bi = 0, j = 0; bi < nbatch; ++bi) {
+      while (j < ncb - 1 && hc->edge[j + 1] <= edge[bi]) ++j;
+      cov_first.push_back(j);
+      int k = j;
+      while (k < ncb - 1 && hc->edge[k + 1] < edge[bi + 1]) ++k;
+      cov_last.push_back(k);
+    }
+    if (!make_events(c->cyc_beg, nbatch) || !make_events(c->cyc_end, nbatch))
       return fail(c, H1W_ECUDA, "capacitance_from_host: cannot create an event");
   }
-  const std::vector<int> edge = hc ? hc->edge : batch_edges(c, m, false);
-  const int nbatch = (int)edge.size() - 1;
   if (c->have_ev && !c->capturing) cudaEventRecord(c->ev[0], c->stream);
   if (c->opt.precond == 1) {  // Laplace-only preconditioner: J for the operator, no lines H, C, chol
     for (int bi = 0; bi < nbatch; ++bi) {
       const int64_t r0 = edge[bi], nr = edge[bi + 1] - edge[bi], o = r0 * N;
-      if (hc) cudaStreamWaitEvent(c->stream, hc->end[bi], 0);
+      if (hc) cudaStreamWaitEvent(c->stream, hc->end[cov_last[bi]], 0);
       if (uses_df(c)) launch_d2df(nr * N, J + o, c->Jdf + o, c->stream);
     }
     for (int k = 1; k < 4 && c->have_ev && !c->capturing; ++k) cudaEventRecord(c->ev[k], c->stream);
@@ -1290,7 +1345,7 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
   for (int bi = 0; bi < nbatch && vc_ok; ++bi) {
     const int64_t r0 = edge[bi], nr = edge[bi + 1] - edge[bi], o = r0 * N;
     if (hc) {
-      cudaStreamWaitEvent(c->stream, hc->end[bi], 0);
+      cudaStreamWaitEvent(c->stream, hc->end[cov_last[bi]], 0);
       cudaEventRecord(c->cyc_beg[bi], c->stream);
     }
     if (uses_df(c)) {  // J for the cycle and the Krylov passes
@@ -1309,11 +1364,7 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
   int splits = 0;
   if (c->opt.cap_gemm == 0) {                                       // line C, tensor cores
     if (!ozaki_supported()) return fail(c, H1W_EUNSUPPORTED, "tensor-core capacitance GEMM needs sm_100-class GPU");
-    if (!c->capturing) {  // a capture finds the tile list uploaded by capacitance_prepare
-      ozaki_tiles(m, c->oz_tiles_host);
-      cudaMemcpyAsync(c->oz.tiles, c->oz_tiles_host.data(), sizeof(int) * c->oz_tiles_host.size(),
-                      cudaMemcpyHostToDevice, c->stream);
-    }
+    if (!c->capturing) upload_tiles(c, m);  // a capture finds the list uploaded by capacitance_prepare
     splits = ozaki_splits(m, c->oz.klen, c->num_sms);
     c->oz.wait_ns = c->wait_ns;
     c->oz.stall = c->stall == H1W_STALL_CAP_GEMM ? 1 : 0;
@@ -1340,7 +1391,7 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
   }
   if (c->have_ev && !c->capturing) cudaEventRecord(c->ev[2], c->stream);
   launch_cap_finalize(c->gemm_partial, splits, m, c->grid.alpha, c->C, c->stream);
-  cudaMemcpyAsync(c->Lc, c->C, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, c->stream);
+  h1w::launch_copy(c->Lc, c->C, (int64_t)m * m, c->stream);
   launch_chol(c->Lc, m, c->dstatus, c->stream);                    // line chol
   if (c->have_ev && !c->capturing) cudaEventRecord(c->ev[3], c->stream);
   c->launches_cap = g_kernel_launches.load() - l0;
@@ -1352,7 +1403,7 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
   timed_collect(c, (1u << kCatGemm) | (1u << kCatDown) | (1u << kCatUp) | (1u << kCatSplitJ) | (1u << kCatSplitH) |
                        (1u << kCatD2df));
   if (hc && c->have_ev) {  // when each batch's copy began and ended, and its cycles began and ended
-    cudaEventSynchronize(hc->end[nbatch - 1]);
+    cudaEventSynchronize(hc->end[hc->edge.size() - 2]);
     auto rel = [&](cudaEvent_t e) {
       float ms = 0.f;
       return cudaEventElapsedTime(&ms, c->ev[0], e) == cudaSuccess ? ms : 0.f;
@@ -1364,8 +1415,8 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
     c->prof_cyc_end.assign(nbatch, 0.f);
     for (int bi = 0; bi < nbatch; ++bi) {
       c->prof_rows[bi] = edge[bi + 1] - edge[bi];
-      c->prof_copy_beg[bi] = rel(hc->beg[bi]);
-      c->prof_copy_end[bi] = rel(hc->end[bi]);
+      c->prof_copy_beg[bi] = rel(hc->beg[cov_first[bi]]);
+      c->prof_copy_end[bi] = rel(hc->end[cov_last[bi]]);
       c->prof_cyc_beg[bi] = rel(c->cyc_beg[bi]);
       c->prof_cyc_end[bi] = rel(c->cyc_end[bi]);
     }
@@ -1398,6 +1449,36 @@ h1w_status h1w_capacitance_from_host(h1w_ctx* c, int32_t m, const double* J_host
   return capacitance_impl(c, m, J_dev, m > 0 ? J_host : nullptr);
 }
 
+// The device's address of page-locked host memory, or null when p is not such memory.
+static const double* host_view(const void* p) {
+  cudaPointerAttributes a{};
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return static_cast<const double*>(a.devicePointer);
+}
+
+h1w_status h1w_pcg_host(h1w_ctx* c, const double* b_host, double* x_host, double rtol, int32_t maxit,
+                        h1w_info* info) {
+  if (!c) return H1W_EINVAL;
+  if (!b_host || !x_host || b_host == x_host)
+    return fail(c, H1W_EINVAL, "pcg_host: b_host and x_host must be distinct non-NULL pointers");
+  const double* bd = host_view(b_host);
+  double* xd = const_cast<double*>(host_view(x_host));
+  if (!bd || !xd) return fail(c, H1W_EINVAL, "pcg_host: b_host and x_host must be page-locked host memory");
+  const int64_t N = c->lev[0].N;
+  if (c->m < 0) return fail(c, H1W_ESTATE, "call h1w_capacitance first");
+  h1w::launch_copy(c->gb, bd, N, c->stream);   // b in, read by a kernel
+  const h1w_status st = h1w_pcg(c, c->gb, c->gx, rtol, maxit, info);
+  if (st != H1W_OK && st != H1W_ENOTCONV) return st;
+  h1w::launch_copy(xd, c->gx, N, c->stream);   // x out (also the last iterate on ENOTCONV)
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pcg_host");
+  const h1w_status sc = cuda_check(c, "pcg_host");
+  return sc != H1W_OK ? sc : st;
+}
+
 h1w_status h1w_prefetch_J(h1w_ctx* c, int32_t m, const double* J_host, double* J_dev) {
   if (!c) return H1W_EINVAL;
   if (m < 1 || m > c->m_max) return fail(c, H1W_EINVAL, "prefetch_J: m out of range [1, m_max]");
@@ -1406,7 +1487,8 @@ h1w_status h1w_prefetch_J(h1w_ctx* c, int32_t m, const double* J_host, double* J
     if (h.active && h.dev == J_dev && !(h.host == J_host && h.m == m))
       return fail(c, H1W_ESTATE, "prefetch_J: another copy into J_dev is pending");
   h1w_status st = H1W_OK;
-  host_copies_for(c, m, J_host, J_dev, st);
+  HostCopy* h = host_copies_for(c, m, J_host, J_dev, st);
+  if (h) h->prefetched = true;
   return st;
 }
 
@@ -1492,7 +1574,7 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
     c->launches_pcg = g_kernel_launches.load() - l0;
     return cuda_check(c, "pcg");
   }
-  cudaMemcpyAsync(c->r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  h1w::launch_copy(c->r, b, (int64_t)N, s);
   double rr = bnorm * bnorm;
   const double tol = rtol * bnorm;
   int it = 0;
@@ -1522,7 +1604,7 @@ h1w_status h1w_pcg(h1w_ctx* c, const double* b, double* x, double rtol, int32_t 
     // true residual r = b - A x
     j_times(c, c->J, x, c->wtmp);
     apply_op_w(c, x, c->wtmp, c->q, -1);
-    cudaMemcpyAsync(c->r, c->q, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+    h1w::launch_copy(c->r, c->q, (int64_t)N, s);
     launch_axpby(c->r, 1.0, b, -1.0, N, s);
     launch_dot_partial(c->r, c->r, N, c->partial, s);
     launch_sum_to_scalar(c->partial, dot_blocks(N), c->scal + RR, s);
@@ -1861,8 +1943,8 @@ h1w_status h1w_capacitance_factors(h1w_ctx* c, double* C, double* L) {
   if (c->m < 0) return fail(c, H1W_ESTATE, "call h1w_capacitance first");
   if (c->opt.precond == 1) return fail(c, H1W_ESTATE, "precond = 1 forms no capacitance matrix");
   const size_t bytes = sizeof(double) * c->m * c->m;
-  if (C && bytes) cudaMemcpyAsync(C, c->C, bytes, cudaMemcpyDeviceToDevice, c->stream);
-  if (L && bytes) cudaMemcpyAsync(L, c->Lc, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (C && bytes) h1w::launch_copy(C, c->C, (int64_t)c->m * c->m, c->stream);
+  if (L && bytes) h1w::launch_copy(L, c->Lc, (int64_t)c->m * c->m, c->stream);
   return cuda_check(c, "capacitance_factors");
 }
 
@@ -1943,7 +2025,7 @@ h1w_status h1w_solve_direct(h1w_ctx* c, const double* b, double* x, void* worksp
   launch_dense_gn(A, n, c->grid.alpha, c->J, c->m, c->stream);       // alpha (K + M) + J^T J
   cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
   launch_chol(A, n, c->dstatus, c->stream);
-  if (x != b) cudaMemcpyAsync(x, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+  if (x != b) h1w::launch_copy(x, b, (int64_t)n, c->stream);
   launch_trsv_lower(A, n, x, 1, c->stream);
   launch_trsv_upper_t(A, n, x, 1, c->stream);
   int status = 0;
@@ -2012,9 +2094,9 @@ h1w_status h1w_gn_step(h1w_ctx* c, const h1w_survey* survey, const double* g_obs
   if (st != H1W_OK) return st;
   st = h1w_adjoint(c, survey, mvec, U, nullptr, nullptr, J, ert_ws, ert_ws_bytes);
   if (st != H1W_OK) return st;
-  cudaMemcpyAsync(d, g, sizeof(double) * m, cudaMemcpyDeviceToDevice, c->stream);
+  h1w::launch_copy(d, g, (int64_t)m, c->stream);
   h1w::launch_axpby(d, -1.0, g_obs, 1.0, m, c->stream);
-  cudaMemcpyAsync(dmr, mvec, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream);
+  h1w::launch_copy(dmr, mvec, (int64_t)N, c->stream);
   h1w::launch_axpby(dmr, -1.0, m_ref, 1.0, N, c->stream);
   std::vector<double> dh(m);
   cudaMemcpyAsync(dh.data(), d, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream);
@@ -2098,7 +2180,8 @@ void h1w_destroy(h1w_ctx* c) {
     for (int e = 0; e < 2; ++e)
       if (c->cycle_ev[e]) cudaEventDestroy(c->cycle_ev[e]);
   }
-  if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+  for (h1w_ctx::PcgGraph& e : c->pcg_g)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
   if (c->body_stream) {
     cudaStreamSynchronize(c->body_stream);
     cudaStreamDestroy(c->body_stream);

@@ -878,6 +878,11 @@ __global__ void k_fill(double* y, double v, int64_t N) {
   if (k < N) y[k] = v;
 }
 
+__global__ void k_copy(double* __restrict__ y, const double* __restrict__ x, int64_t N) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) y[k] = x[k];
+}
+
 inline unsigned nblk(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -1152,6 +1157,14 @@ void launch_dot_partial(const double* a, const double* b, int64_t N, double* par
 
 void launch_fill(double* y, double v, int64_t N, cudaStream_t s) {
   k_fill<<<nblk(N), kThreads, 0, s>>>(y, v, N);
+  note_launches(1);
+}
+
+// A device-to-device copy as a kernel: a cudaMemcpyAsync between device buffers goes to a copy
+// engine, where it queues behind host-to-device copies of J issued earlier on another stream.
+void launch_copy(double* y, const double* x, int64_t N, cudaStream_t s) {
+  if (N <= 0) return;
+  k_copy<<<nblk(N), kThreads, 0, s>>>(y, x, N);
   note_launches(1);
 }
 

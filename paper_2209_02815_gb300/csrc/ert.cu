@@ -1107,7 +1107,7 @@ h1w_status ert_forward(const Level* lev, int nl, cudaStream_t s, const h1w_surve
     k_apply64<<<nblk(N), kThreads, 0, s>>>(L0, W.tx64, W.ty64, W.tz64, W.dg64, ne, U, W.q64);
     k_init<<<vg, kThreads, 0, s>>>(N, W.cell, W.z64, W.r64, W.b[0]);
     note_launches(2);
-    cudaMemcpyAsync(W.p64, W.q64, sizeof(double) * N * ne, cudaMemcpyDeviceToDevice, s);
+    launch_copy(W.p64, W.q64, (int64_t)N * ne, s);
     launch_axpby(W.p64, 1.0, W.r64, -1.0, N * ne, s);  // p = r - q
     k_dots<<<vg, kThreads, 0, s>>>(N, W.p64, W.p64, nullptr, nullptr, W.partial);
     k_scalars<<<sb, 128, 0, s>>>(2, ne, kDotBlocks, W.partial, W.scal, 0.0);

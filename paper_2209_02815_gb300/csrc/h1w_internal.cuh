@@ -246,6 +246,7 @@ void launch_dot_partial(const double* a, const double* b, int64_t N, double* par
                         cudaStream_t s);
 int dot_blocks(int64_t N);
 void launch_fill(double* y, double v, int64_t N, cudaStream_t s);
+void launch_copy(double* y, const double* x, int64_t N, cudaStream_t s);
 
 // ---- ERT forward model and Jacobian (ert.cu), on a context's FV hierarchy ----------
 size_t ert_workspace_bytes(const Level* lev, int nlev, int n_e, int m);

@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "h1w_vcycle": (I32, [P, I32, P, P]),
         "h1w_gn_rhs": (I32, [P, P, P, P]),
         "h1w_pcg": (I32, [P, P, P, D, I32, IN]),
+        "h1w_pcg_host": (I32, [P, P, P, D, I32, IN]),
         "h1w_capacitance_factors": (I32, [P, P, P]),
         "h1w_level_info": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "h1w_get_timings": (I32, [P, ctypes.POINTER(Timings)]),
@@ -281,6 +282,27 @@ def h1w_pcg(ctx, b: torch.Tensor, x: torch.Tensor, rtol: float, maxit: int, N: i
             raise_on_notconv: bool = True) -> Info:
     info = Info()
     st = load().h1w_pcg(ctx, _ptr(b, N, "b"), _ptr(x, N, "x"), float(rtol), int(maxit), ctypes.byref(info))
+    if st == H1W_ENOTCONV and not raise_on_notconv:
+        return info
+    _check(st, ctx)
+    return info
+
+
+def _host_ptr(t: torch.Tensor, n: int, name: str) -> int:
+    if t.is_cuda or not t.is_pinned():
+        raise ValueError(f"{name} must be a pinned CPU tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous float64")
+    if t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} entries, needs {n}")
+    return t.data_ptr()
+
+
+def h1w_pcg_host(ctx, b_host: torch.Tensor, x_host: torch.Tensor, rtol: float, maxit: int, N: int,
+                 raise_on_notconv: bool = True) -> Info:
+    info = Info()
+    st = load().h1w_pcg_host(ctx, _host_ptr(b_host, N, "b_host"), _host_ptr(x_host, N, "x_host"), float(rtol),
+                             int(maxit), ctypes.byref(info))
     if st == H1W_ENOTCONV and not raise_on_notconv:
         return info
     _check(st, ctx)
@@ -554,6 +576,15 @@ class Solver:
         finally:
             self._leave()
         return x, info
+
+    def pcg_host(self, b_host, x_host, rtol: float, maxit: int = 500, raise_on_notconv=True):
+        """h1w_pcg_host: b_host in and x_host out (pinned CPU tensors), read and written by kernels."""
+        self._enter()
+        try:
+            info = h1w_pcg_host(self.ctx, b_host, x_host, rtol, maxit, self.N, raise_on_notconv)
+        finally:
+            self._leave()
+        return info
 
     def solve_direct(self, b, x=None):
         """x = (alpha (K + M) + J^T J)^-1 b by a dense Cholesky factorization (small grids;

@@ -390,6 +390,37 @@ def test_prefetched_capacitance_from_host_equals_device_path():
         assert torch.equal(x, xr)
 
 
+@pytest.mark.parametrize("pcg_mode", [0, 1])
+def test_pcg_host_equals_device_pcg(pcg_mode):
+    """h1w_pcg_host (b read from, x written to pinned host memory by kernels) gives bit for bit
+    the solution and iteration count of h1w_pcg on device vectors, in both loop forms, with the
+    next system's J prefetched beside it; pageable host memory is refused with H1W_EINVAL."""
+    d, n, h = _fv((24, 16, 20))
+    N = int(np.prod(n))
+    m = 33
+    rng = np.random.default_rng(44)
+    Jh = torch.as_tensor(rng.standard_normal((m, N)) / np.sqrt(N)).pin_memory()
+    b = _t(rng.standard_normal(N))
+    S = _gpu(d, n, h, 1e-2, m, pcg_mode=pcg_mode)
+    bufs = [torch.empty((m, N), dtype=torch.float64, device=DEV) for _ in range(2)]
+    S.capacitance_from_host(Jh, bufs[0])
+    xd, infod = S.pcg(b, 1e-11, 300)
+    xd = xd.clone()
+    b_host = b.cpu().pin_memory()
+    x_host = torch.full((N,), float("nan"), dtype=torch.float64).pin_memory()
+    S.prefetch_J(Jh, bufs[1])
+    info = S.pcg_host(b_host, x_host, 1e-11, 300)
+    assert info.iters == infod.iters and info.rel_res_true == infod.rel_res_true
+    assert torch.equal(x_host, xd.cpu())
+    S.capacitance_from_host(Jh, bufs[1])
+    info2 = S.pcg_host(b_host, x_host, 1e-11, 300)
+    assert info2.iters == infod.iters and torch.equal(x_host, xd.cpu())
+    pageable = torch.zeros(N, dtype=torch.float64)
+    st = h1w.load().h1w_pcg_host(S.ctx, pageable.data_ptr(), x_host.data_ptr(), 1e-11, 300, None)
+    assert st == h1w.H1W_EINVAL
+    assert "page-locked" in h1w.h1w_last_error(S.ctx)
+
+
 def test_prefetch_rejects_a_third_pending_copy():
     d, n, h = _fv((16, 8, 12))
     N = int(np.prod(n))
