@@ -171,18 +171,40 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// x[r] = X b[r] with the FP64 dense inverse of the coarsest operator; one warp per (row, rhs)
-__global__ void k_coarse_apply_df(const double* __restrict__ X, int n, const df* __restrict__ b,
-                                  df* __restrict__ x) {
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
+// x[r] = X b[r] with the FP64 dense inverse of the coarsest operator (n <= kCoarseLimit).
+// A block takes kCoarseRows rows (kCoarseRowsPerWarp per warp) of one right-hand side and
+// converts that right-hand side to FP64 once, in shared memory, so that the FP64 pipe does
+// one FMA per product (a conversion per product took three more FP64 operations). Each row
+// keeps lane-strided partial sums over j and one warp reduction, in the same order as one
+// warp per row would.
+constexpr int kCoarseRowsPerWarp = 4;
+constexpr int kCoarseRows = 8 * kCoarseRowsPerWarp;  // 256 threads
+
+__global__ void __launch_bounds__(256) k_coarse_apply_df(const double* __restrict__ X, int n,
+                                                         const df* __restrict__ b, df* __restrict__ x) {
+  __shared__ double bs[kCoarseLimit];
   const df* br = b + (int64_t)blockIdx.y * n;
-  const double* xr = X + (int64_t)row * n;
-  double s = 0.0;
-  for (int j = lane; j < n; j += 32) s += xr[j] * df_to_double(br[j]);
-  s = warp_sum(s);
-  if (lane == 0) x[(int64_t)blockIdx.y * n + row] = df_from_double(s);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) bs[j] = df_to_double(br[j]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * kCoarseRows + (threadIdx.x >> 5) * kCoarseRowsPerWarp;
+  if (row0 >= n) return;
+  const double* xr[kCoarseRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kCoarseRowsPerWarp; ++r) xr[r] = X + (int64_t)min(row0 + r, n - 1) * n;
+  double s[kCoarseRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kCoarseRowsPerWarp; ++r) s[r] = 0.0;
+  for (int j = lane; j < n; j += 32) {
+    const double bj = bs[j];
+#pragma unroll
+    for (int r = 0; r < kCoarseRowsPerWarp; ++r) s[r] = fma(xr[r][j], bj, s[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < kCoarseRowsPerWarp; ++r) {
+    const double t = warp_sum(s[r]);
+    if (lane == 0 && row0 + r < n) x[(int64_t)blockIdx.y * n + row0 + r] = df_from_double(t);
+  }
 }
 
 // two entries per thread with 16-byte loads and stores (both arrays 16-byte aligned: the
@@ -264,7 +286,7 @@ void launch_prolong_add_df(const Level& Lf, const Level& Lc, int nrhs, const df*
 }
 
 void launch_coarse_apply_df(const double* X, int n, int nrhs, const df* b, df* x, cudaStream_t s) {
-  k_coarse_apply_df<<<dim3((unsigned)((n + 7) / 8), nrhs), 256, 0, s>>>(X, n, b, x);
+  k_coarse_apply_df<<<dim3((unsigned)((n + kCoarseRows - 1) / kCoarseRows), nrhs), 256, 0, s>>>(X, n, b, x);
   note_launches(1);
 }
 
