@@ -356,19 +356,21 @@ def test_capacitance_from_host_equals_device_path(rhs_block):
     assert torch.equal(Ca, Cb) and torch.equal(La, Lb)
 
 
-def test_prefetched_capacitance_from_host_equals_device_path():
+@pytest.mark.parametrize("rhs_block", [128, 20])
+def test_prefetched_capacitance_from_host_equals_device_path(rhs_block):
     """Double-buffered prefetch (h1w_prefetch_J) of the next system's J during the current
     solve: three systems in a row, each capacitance bit-identical to the device entry point,
     the solutions equal, and the per-batch copy profile is ordered (each batch's cycles
-    start after its copy ended)."""
+    start after the copy of its rows ended). A prefetched J is consumed in rhs_block
+    batches; with 20 they straddle the copy's batches (16, 20, 20, 14 rows)."""
     d, n, h = _fv((24, 24, 24))
     N = int(np.prod(n))
     m = 70
     rng = np.random.default_rng(43)
     Jhs = [torch.as_tensor(rng.standard_normal((m, N)) / np.sqrt(N)).pin_memory() for _ in range(3)]
     b = _t(rng.standard_normal(N))
-    ref = _gpu(d, n, h, 1e-2, m)
-    S = _gpu(d, n, h, 1e-2, m)
+    ref = _gpu(d, n, h, 1e-2, m, rhs_block=rhs_block)
+    S = _gpu(d, n, h, 1e-2, m, rhs_block=rhs_block)
     bufs = [torch.empty((m, N), dtype=torch.float64, device=DEV) for _ in range(2)]
     S.prefetch_J(Jhs[0], bufs[0])
     for k in range(3):
