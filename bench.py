@@ -894,7 +894,13 @@ def run_ours(args):
          "hbm", hbm, "8 bytes of J in, 14 bytes of digits out per entry of one K panel")
     rate("k_split_digits<df> (H digits)", kern["split_h"][0], kern["split_h"][1], 22.0 * m * kw_avg, "GB/s",
          "hbm", hbm, "8 bytes of H (double-float) in, 14 bytes of digits out per entry of one K panel")
-    if kern["d2df"][1]:
+    if kern["d2df"][1] and kern["split_j"][1] == 0 and args.arith == "mixed":
+        # J's digits split in line H together with its double-float copy (the full-K digit
+        # buffer): per row batch 8 bytes in, 8 + 14 bytes out per entry; line C splits only H
+        rate("k_split_digits<double> + double-float copy (J, line H)", kern["d2df"][0], kern["d2df"][1],
+             30.0 * m * N * args.steps / kern["d2df"][1], "GB/s", "hbm", hbm,
+             "8 bytes of J in, 8 bytes of double-float copy and 14 bytes of digits out per entry of the row batch")
+    elif kern["d2df"][1]:
         rate("k_d2df (J to double-floats, line H)", kern["d2df"][0], kern["d2df"][1],
              16.0 * m * N * args.steps / kern["d2df"][1], "GB/s", "hbm", hbm,
              "8 bytes in, 8 bytes out per entry of J's row batch")

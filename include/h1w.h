@@ -91,6 +91,11 @@ typedef struct {
                             Gershgorin bound; 1.5 .. 1000, or 0 (default) for the discretization's
                             ratio: 10 on FV cell grids, 6 on Q1 vertex grids. It also sets the interval
                             of h1w_forward's FP32 cycle (10 at 0) */
+  int32_t j_digits;      /* line C on the tensor cores: 1 (default) = while J is converted to double-floats
+                            in line H, also split it into the GEMM's digits for every K panel, kept in
+                            the workspace when they take at most 32 GB (14 bytes per entry of J, rows
+                            rounded up to 128), so that line C reads J no more; 0 = split J per K panel
+                            in line C (the workspace holds one panel's digits) */
 } h1w_options;
 
 typedef struct {

@@ -353,6 +353,7 @@ h1w_status validate(const h1w_grid* g, int32_t m_max, const h1w_options* o, std:
     if (o->mg_unfused != 0 && o->mg_unfused != 1) { why = "mg_unfused must be 0 or 1"; return H1W_EINVAL; }
     if (o->precond != 0 && o->precond != 1) { why = "precond must be 0 or 1"; return H1W_EINVAL; }
     if (o->pcg_mode != 0 && o->pcg_mode != 1) { why = "pcg_mode must be 0 or 1"; return H1W_EINVAL; }
+    if (o->j_digits != 0 && o->j_digits != 1) { why = "j_digits must be 0 or 1"; return H1W_EINVAL; }
     if (!(o->cheb_ratio == 0.0 || (o->cheb_ratio >= 1.5 && o->cheb_ratio <= 1000.0))) {
       why = "cheb_ratio neither 0 nor in [1.5, 1000]";
       return H1W_EINVAL;
@@ -427,7 +428,12 @@ size_t layout(h1w_ctx* c, const Plan& P, const h1w_grid& g, int m_max, const h1w
   const long long kp = ozaki_panel_width(N0);
   OzakiWork ow{};
   if (oz) {
-    ow.digitsA = B.take<uint16_t>((size_t)ozaki_digit_slices() * ((m_max + 127) / 128 * 128) * kp);
+    // the digits of J for every K panel when they fit the cap: line H then splits J as it
+    // converts it to double-floats, and line C reads J no more (one pass over J saved)
+    const size_t jfull = ozaki_j_digits_full_bytes(m_max, N0);
+    ow.j_full = o.j_digits == 1 && use_df && o.precond == 0 && jfull <= (size_t)kJDigitsFullMax;
+    ow.digitsA = ow.j_full ? static_cast<void*>(B.take<uint8_t>(jfull))
+                           : static_cast<void*>(B.take<uint16_t>((size_t)ozaki_digit_slices() * ((m_max + 127) / 128 * 128) * kp));
     ow.digitsB = B.take<uint16_t>((size_t)ozaki_digit_slices() * ((m_max + 63) / 64 * 64) * kp);
     ow.expo = B.take<int>(2 * (size_t)m_max * ozaki_chunks(N0));
     ow.tiles = B.take<int>(2 * (size_t)ozaki_num_tiles(m_max));
@@ -970,6 +976,7 @@ void h1w_default_options(h1w_options* opt) {
   opt->precond = 0;
   opt->pcg_mode = 0;
   opt->cheb_ratio = 0.0;
+  opt->j_digits = 1;
 }
 
 size_t h1w_workspace_size(const h1w_grid* grid, int32_t m_max, const h1w_options* opt) {
@@ -1348,9 +1355,12 @@ static h1w_status capacitance_core(h1w_ctx* c, int32_t m, const double* J, const
       cudaStreamWaitEvent(c->stream, hc->end[cov_last[bi]], 0);
       cudaEventRecord(c->cyc_beg[bi], c->stream);
     }
-    if (uses_df(c)) {  // J for the cycle and the Krylov passes
+    if (uses_df(c)) {  // J for the cycle and the Krylov passes (and, with j_full, J's digits for line C)
       timed_begin(c);
-      launch_d2df(nr * N, J + o, c->Jdf + o, c->stream);
+      if (c->oz.j_full && c->opt.cap_gemm == 0)
+        launch_split_j_rows(J, m, N, (int)r0, (int)(r0 + nr), c->oz, c->Jdf, c->stream);
+      else
+        launch_d2df(nr * N, J + o, c->Jdf + o, c->stream);
       timed_end(c, kCatD2df);
     }
     vc_ok = vcycle_many(c, (int)nr, J + o, uses_df(c) ? c->Jdf + o : nullptr, h_df_only ? nullptr : c->H + o,

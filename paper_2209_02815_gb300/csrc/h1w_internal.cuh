@@ -89,6 +89,8 @@ struct OzakiWork {
   long long klen;                // K panel width (multiple of 2048)
   unsigned long long wait_ns;    // limit of each bounded wait (0: one second)
   int stall;                     // failure-path test: withhold the operand copies (see h1w_inject_stall)
+  bool j_full = false;           // digitsA holds every K panel of J, split during line H
+                                 // (launch_split_j_rows); line C then splits only H
 };
 long long ozaki_panel_width(long long N);
 long long ozaki_chunks(long long N);
@@ -103,6 +105,14 @@ bool ozaki_supported();
 // hook (may be null) is called as hook(hook_arg, which, 1) before and hook(hook_arg, which, 0)
 // after each launch, which = kOzakiSplitJ, kOzakiSplitH (digit splits) or kOzakiGemm.
 enum { kOzakiGemm = 0, kOzakiSplitJ = 1, kOzakiSplitH = 2 };
+// J digits of every K panel kept between lines H and C while they take at most this much
+constexpr long long kJDigitsFullMax = 32LL << 30;
+size_t ozaki_j_digits_full_bytes(int m, long long N);
+// Line H's conversion of J rows [r0, r1) to double-floats (Jdf) fused with their digit split
+// for every K panel into the full-K buffer of w (w.j_full): one pass over those rows of J.
+// The launch that ends at row m also zeroes the digits of the last row block's padding rows.
+void launch_split_j_rows(const double* J, int m, long long N, int r0, int r1, const OzakiWork& w, df* Jdf,
+                         cudaStream_t s);
 bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, const df* Hdf, int m, long long N,
                               const OzakiWork& w, int splits, cudaStream_t s, void (*hook)(void*, int, int),
                               void* hook_arg);

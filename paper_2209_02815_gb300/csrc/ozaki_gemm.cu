@@ -478,20 +478,38 @@ __device__ __forceinline__ void store_digits(long long (&Y)[8], int row, long lo
 constexpr int kSplitRows = 1;
 constexpr int kSplitThreads = kChunkK / 8 * kSplitRows;  // 8 entries per thread
 
+//
+// row0 offsets the rows (a launch may cover a row range of the panel); XD (may be null, FP64
+// sources only) receives the double-float conversion of every entry read, the same values as
+// k_d2df, so that a pass that needs both reads X once.
 template <typename XS>
 __global__ void __launch_bounds__(kSplitThreads) k_split_digits(const XS* __restrict__ X, int m, long long N,
                                                                 long long k0, long long kw, long long klen, int R,
                                                                 long long chunk0, int* __restrict__ e,
-                                                                uint16_t* __restrict__ S) {
+                                                                uint16_t* __restrict__ S, int row0 = 0,
+                                                                df* __restrict__ XD = nullptr,
+                                                                long long pstride = 0) {
+  // pstride > 0: one launch over every K panel; blockIdx.y counts the chunks of all panels,
+  // and each block finds its panel (offset k0, width kw, digits at S + panel * pstride)
+  int by = static_cast<int>(blockIdx.y);
+  if (pstride > 0) {
+    const int cpp = static_cast<int>(klen / kChunkK);
+    const int p = by / cpp;
+    by -= p * cpp;
+    k0 = static_cast<long long>(p) * klen;
+    kw = (N - k0) < klen ? (N - k0) : klen;
+    chunk0 = k0 / kChunkK;
+    S += static_cast<long long>(p) * pstride;
+  }
   constexpr int kGroup = 4 * kSplitRows;   // lanes per stage
   constexpr int kStagesPerWarp = 32 / kGroup;
   constexpr int kWarps = kSplitThreads / 32;
   __shared__ int smax[kWarps][kSplitRows];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / kGroup, rg = (lane >> 2) % kSplitRows, ch = lane & 3;
-  const int row = blockIdx.x * kSplitRows + rg;
+  const int row = row0 + blockIdx.x * kSplitRows + rg;
   const long long kc =
-      static_cast<long long>(blockIdx.y) * kChunkK + (warp * kStagesPerWarp + sub) * kKt + ch * 8;
+      static_cast<long long>(by) * kChunkK + (warp * kStagesPerWarp + sub) * kKt + ch * 8;
   constexpr bool kDf = std::is_same<XS, df>::value;
   XS x[8];
   int best = 0;
@@ -520,6 +538,22 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_digits(const XS* __rest
       else x[t] = (k < kw && row < m) ? X[row * N + k0 + k] : 0.0;
     }
   }
+  if constexpr (!kDf) {
+    if (XD && row < m) {  // the double-float copy: 64 contiguous bytes, or entry by entry
+      df* dst = XD + row * N + k0 + kc;
+      if (whole && (reinterpret_cast<uintptr_t>(XD) & 15) == 0) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const df a = df_from_double_fast(x[2 * v]), b = df_from_double_fast(x[2 * v + 1]);
+          reinterpret_cast<float4*>(dst)[v] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (kc + t < kw) dst[t] = df_from_double_fast(x[t]);
+      }
+    }
+  }
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     int ex;
@@ -540,8 +574,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_digits(const XS* __rest
   int ech;
   if constexpr (kDf) ech = best ? best - 126 : -100000;
   else ech = best ? best - 1022 : -100000;
-  if (warp == 0 && sub == 0 && ch == 0 && row < m && static_cast<long long>(blockIdx.y) * kChunkK < kw)
-    e[(chunk0 + blockIdx.y) * m + row] = ech;
+  if (warp == 0 && sub == 0 && ch == 0 && row < m && static_cast<long long>(by) * kChunkK < kw)
+    e[(chunk0 + by) * m + row] = ech;
   long long Y[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
@@ -638,10 +672,14 @@ bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, c
     uint16_t* dA = static_cast<uint16_t*>(w.digitsA);
     uint16_t* dB = static_cast<uint16_t*>(w.digitsB);
     const dim3 ga(rowsA / kSplitRows, gx), gb(rowsB / kSplitRows, gx);
-    if (hook) hook(hook_arg, kOzakiSplitJ, 1);
-    if (Jdf) k_split_digits<df><<<ga, kSplitThreads, 0, s>>>(Jdf, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
-    else k_split_digits<double><<<ga, kSplitThreads, 0, s>>>(J, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
-    if (hook) hook(hook_arg, kOzakiSplitJ, 0);
+    if (w.j_full) {  // split during line H: this panel's digits in the full-K buffer
+      dA += (size_t)panel * kSlices * rowsA * kp;
+    } else {
+      if (hook) hook(hook_arg, kOzakiSplitJ, 1);
+      if (Jdf) k_split_digits<df><<<ga, kSplitThreads, 0, s>>>(Jdf, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
+      else k_split_digits<double><<<ga, kSplitThreads, 0, s>>>(J, m, N, k0, kw, kp, kTileM, chunk0, eA, dA);
+      if (hook) hook(hook_arg, kOzakiSplitJ, 0);
+    }
     if (hook) hook(hook_arg, kOzakiSplitH, 1);
     if (Hdf) k_split_digits<df><<<gb, kSplitThreads, 0, s>>>(Hdf, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
     else k_split_digits<double><<<gb, kSplitThreads, 0, s>>>(H, m, N, k0, kw, kp, kTileN, chunk0, eB, dB);
@@ -666,12 +704,33 @@ bool launch_ozaki_capacitance(const double* J, const double* H, const df* Jdf, c
     k_ozaki_gemm<<<dim3(tiles, splits), kGemmThreads, kSmemBytes, s>>>(a);
     if (cudaPeekAtLastError() != cudaSuccess) return false;  // a launch the GPU refused (resources)
     if (hook) hook(hook_arg, kOzakiGemm, 0);
-    note_launches(3);
+    note_launches(w.j_full ? 2 : 3);
   }
   return true;
 }
 
 long long ozaki_chunks(long long N) { return (N + kChunkK - 1) / kChunkK; }
+
+size_t ozaki_j_digits_full_bytes(int m, long long N) {
+  const long long kp = ozaki_panel_width(N);
+  const long long panels = (N + kp - 1) / kp;
+  const long long rowsA = (m + kTileM - 1) / kTileM * kTileM;
+  return sizeof(uint16_t) * (size_t)kSlices * rowsA * kp * panels;
+}
+
+void launch_split_j_rows(const double* J, int m, long long N, int r0, int r1, const OzakiWork& w, df* Jdf,
+                         cudaStream_t s) {
+  const long long kp = w.klen;
+  const int rowsA = (m + kTileM - 1) / kTileM * kTileM;
+  const int rend = r1 >= m ? rowsA : r1;
+  if (rend <= r0) return;
+  const long long panel_elems = (long long)kSlices * rowsA * kp;
+  const long long panels = (N + kp - 1) / kp;
+  const dim3 g((unsigned)((rend - r0) / kSplitRows), (unsigned)(panels * (kp / kChunkK)));
+  k_split_digits<double><<<g, kSplitThreads, 0, s>>>(J, m, N, 0, kp, kp, kTileM, 0, w.expo,
+                                                    static_cast<uint16_t*>(w.digitsA), r0, Jdf, panel_elems);
+  note_launches(1);
+}
 int ozaki_digit_slices() { return kSlices; }
 
 }  // namespace h1w

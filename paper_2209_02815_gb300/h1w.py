@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int32), ("rhs_block", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("cap_gemm", ctypes.c_int32),
                 ("mg_arith", ctypes.c_int32), ("mg_unfused", ctypes.c_int32), ("precond", ctypes.c_int32),
-                ("pcg_mode", ctypes.c_int32), ("cheb_ratio", ctypes.c_double)]
+                ("pcg_mode", ctypes.c_int32), ("cheb_ratio", ctypes.c_double), ("j_digits", ctypes.c_int32)]
 
 
 class Timings(ctypes.Structure):

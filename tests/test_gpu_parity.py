@@ -178,6 +178,31 @@ def test_capacitance_and_prec_parity(case, m, cap_gemm):
     assert _rel(z, P(r)) <= 1e-9
 
 
+@pytest.mark.parametrize("case", [_fv((24, 24, 24)), _fv((20, 12, 28)), _q1((130, 67))],
+                         ids=lambda c: f"{c[0]}{'x'.join(map(str, c[1]))}")
+@pytest.mark.parametrize("m", [13, 150])
+def test_j_digits_in_line_h_equal_per_panel_split(case, m):
+    """j_digits = 1 splits J into the GEMM's digits while line H converts it (digits of every
+    K panel kept), j_digits = 0 splits it per panel in line C: the same digits, so C, L and
+    the PCG solution (whose passes read the double-float copy of J written by either path)
+    agree bit for bit; with more than one 128-row block (m = 150) the padding rows of the
+    last block are zero in both."""
+    d, n, h = case
+    N = int(np.prod(n))
+    rng = np.random.default_rng(61 + m)
+    J = _t(rng.standard_normal((m, N)) / np.sqrt(N))
+    b = _t(rng.standard_normal(N))
+    out = []
+    for jd in (1, 0):
+        S = _gpu(d, n, h, 1e-2, m, j_digits=jd, rhs_block=64)
+        S.capacitance(J)
+        C, L = S.factors()
+        x, info = S.pcg(b, 1e-11, 300)
+        out.append((C.clone(), L.clone(), x.clone(), info.iters))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    assert torch.equal(out[0][2], out[1][2]) and out[0][3] == out[1][3]
+
+
 def test_m0_prec_is_scaled_vcycle():
     d, n, h = _fv((16, 8, 12))
     H = mg.build_hierarchy(d, n, h)
