@@ -38,7 +38,13 @@ def test_host_side_validation_without_gpu():
     neg = h1w.make_grid(h1w.H1W_Q1_VERTEX, (64, 64), (1 / 63,) * 2, -1.0)
     assert h1w.h1w_workspace_size(neg, 4) == 0
     o = h1w.h1w_default_options()
-    assert (o.cheb_degree, o.rhs_block, o.max_restarts) == (2, 128, 3)
+    assert (o.cheb_degree, o.rhs_block, o.max_restarts, o.j_digits) == (2, 128, 3, 1)
+    # J's digits for every K panel are kept when they fit: a larger workspace than with j_digits = 0
+    o0 = h1w.h1w_default_options()
+    o0.j_digits = 0
+    assert size > h1w.h1w_workspace_size(g, 496, o0) + 496 * N * 8
+    o0.j_digits = 2
+    assert h1w.h1w_workspace_size(g, 496, o0) == 0
 
 
 def test_rhs_block_buffers_capped_at_m_max():
