@@ -75,6 +75,7 @@ def test_new_entry_points_reject_null_context_without_gpu():
     assert lib.h1w_adjoint(None, ctypes.byref(sv.c), None, None, None, None, None, None, 0) == h1w.H1W_EINVAL
     assert lib.h1w_ert_jvp(None, ctypes.byref(sv.c), None, None, None, None, None, 0) == h1w.H1W_EINVAL
     assert lib.h1w_solve_direct(None, None, None, None, 0) == h1w.H1W_EINVAL
+    assert lib.h1w_pcg_host(None, None, None, 1e-8, 10, None) == h1w.H1W_EINVAL
     assert lib.h1w_gn_step(None, ctypes.byref(sv.c), None, None, None, None, None, None, None, None, 0, 1e-10, 1e-8,
                            10, 0, None) == h1w.H1W_EINVAL
     assert h1w.h1w_default_options().precond == 0
